@@ -1,0 +1,381 @@
+"""Benchmark of one DVGOv2 training iteration (forward + backward + TV + Adam)
+on GB300, in fwd+bwd ray-samples/s (samples after bbox and occupancy
+culling).
+
+Default workload: the 160^3 DVGO-sized scene (10 blobs, occupancy mask,
+colour MLP 39-128-128-3 in FP32, 8192 rays, TV, sparse Adam), seeded
+synthetic inputs.  Each timed step is bracketed by CUDA events on the
+launching stream after an L2 flush (a 256 MB memset outside the events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload dvgo_160|dvgo_160_bf16|small_64|unbounded_320]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ray-samples/s"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dvgo_160")
+    ap.add_argument("--tv-dense", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warmup+steps with no clock sampling or CPU baseline (for ncu)")
+    return ap.parse_args()
+
+
+def precision_of(workload):
+    return "bf16" if workload.endswith("bf16") else "f32"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- ours
+def kernel_flops_bytes(tr):
+    """Algorithmic work per step of the main kernels."""
+    import torch
+    from paper_2206_05085_gb300 import _lib as L
+    torch.cuda.synchronize()
+    S = int(tr.ray_off[-1].item())
+    S_live = int(tr.live_count.item())
+    nb_touch_d = int(tr.density.touched.sum().item())
+    nb_touch_f = int(tr.feature.touched.sum().item())
+    return S, S_live, nb_touch_d, nb_touch_f
+
+
+def per_kernel_times(tr, batches, reps=5):
+    """Average duration of each C-ABI call of one step, CUDA events on the
+    launching stream (the current stream)."""
+    import torch
+    from paper_2206_05085_gb300 import _lib as L
+    names = []
+    orig = L._call
+    stream = torch.cuda.current_stream()
+    events = []
+
+    def timed(name, *args):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        orig(name, *args)
+        e1.record(stream)
+        events.append((name, e0, e1))
+
+    L._call = timed
+    try:
+        for r in range(reps):
+            o, d, t = batches[r % len(batches)]
+            tr.step(o, d, t)
+    finally:
+        L._call = orig
+    torch.cuda.synchronize()
+    acc = {}
+    for name, e0, e1 in events:
+        acc.setdefault(name, []).append(e0.elapsed_time(e1))
+    out = {}
+    for name, ts in acc.items():
+        calls_per_step = len(ts) // reps
+        out[name] = {"ms_per_step": sum(ts) / reps, "calls_per_step": calls_per_step,
+                     "ms_per_call": sum(ts) / len(ts)}
+    return out
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2206_05085_gb300 import build as B
+    from paper_2206_05085_gb300 import synth, train
+    B.build()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    cfg = synth.CONFIGS[args.workload]
+    rp = synth.render_params(cfg)
+    prec = precision_of(args.workload)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
+    nb = args.warmup + args.steps
+    # distinct ray batches per step, resident in HBM (seed = 1000*rank + step)
+    batches, host_batches = [], []
+    for i in range(min(nb, 8)):
+        seed = 1000 * rank + i
+        o, d = synth.rays(cfg, seed=seed)
+        t = synth.target_rgb(cfg, seed=seed)
+        host_batches.append((o, d, t))
+        batches.append(tuple(torch.from_numpy(a).cuda() for a in (o, d, t)))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # samples per batch (deterministic: the mask is fixed)
+    S_of = []
+    for o, d, t in batches:
+        tr.forward(o, d, t)
+        torch.cuda.synchronize()
+        S_of.append(int(tr.ray_off[-1].item()))
+    # restore a clean optimizer state after the sample-count passes
+    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
+
+    for i in range(args.warmup):
+        o, d, t = batches[i % len(batches)]
+        tr.step(o, d, t, tv_dense=args.tv_dense)
+    torch.cuda.synchronize()
+    if args.profile_only:
+        for i in range(args.steps):
+            o, d, t = batches[i % len(batches)]
+            tr.step(o, d, t, tv_dense=args.tv_dense)
+        torch.cuda.synchronize()
+        return None
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = []
+    samples = 0
+    for i in range(args.steps):
+        flush.zero_()
+        b = (args.warmup + i) % len(batches)
+        o, d, t = batches[b]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr.step(o, d, t, tv_dense=args.tv_dense)
+        e1.record(stream)
+        ev.append((e0, e1))
+        samples += S_of[b]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+
+    # end-to-end through the public API with host buffers: pinned H2D of the
+    # step's rays and targets, D2H of the loss, inside the timed region
+    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in hb) for hb in host_batches]
+    dev_in = [torch.empty_like(x) for x in batches[0]]
+    loss_host = torch.empty(3, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    h2d_bytes = sum(x.numel() * x.element_size() for x in pinned[0])
+    for i in range(args.steps):
+        flush.zero_()
+        b = (args.warmup + i) % len(pinned)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for dst, src in zip(dev_in, pinned[b]):
+            dst.copy_(src, non_blocking=True)
+        loss = tr.step(dev_in[0], dev_in[1], dev_in[2], tv_dense=args.tv_dense)
+        loss_host.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    clock_info = clocks.stop() if clocks else None
+
+    kt = per_kernel_times(tr, batches[:1], reps=5)
+    S, S_live, nbd, nbf = kernel_flops_bytes(tr)
+    if world > 1:
+        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_total = float(t[0]), float(t[1])
+        s = torch.tensor([samples], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(s)
+        samples = float(s[0])
+    else:
+        e2e_total = sum(e2e_ms)
+    return dict(total_ms=total_ms, samples=samples, e2e_total_ms=e2e_total,
+                e2e_samples=samples, kt=kt, clocks=clock_info, S=S, S_live=S_live,
+                touched=(nbd, nbf), h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
+
+
+def roofline(res, peaks):
+    """Roofline record of the dominant kernel (largest share of the step)."""
+    kt = res["kt"]
+    name, rec = max(kt.items(), key=lambda kv: kv[1]["ms_per_step"])
+    S, S_live = res["S"], res["S_live"]
+    prec = res["prec"]
+    # per-unit algorithmic work ("Roofline arithmetic")
+    fwd_flop = 2 * (39 * 128 + 128 * 128 + 128 * 3)
+    bwd_flop = 2 * (39 * 128 + 128 * 128 + 128 * 3 + 3 * 128 * 2 + 128 * 128 * 2 + 128 * 40 + 128 * 12)
+    ms = rec["ms_per_call"]
+    sm_peak_alu = 152 * 128 * 2 * 2070e6 / 1e12   # FP32 FMA TFLOP/s at the max SM clock
+    if name in ("dvgo_rgbnet_bwd", "dvgo_rgbnet_fwd"):
+        flop = (bwd_flop if name.endswith("bwd") else fwd_flop) * S_live
+        achieved = flop / (ms * 1e-3) / 1e12
+        if prec == "bf16":
+            bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
+        else:
+            bound, peak, unit = "alu", sm_peak_alu, "TFLOP/s"
+        traffic = None
+    else:
+        # memory-bound kernels: algorithmic bytes per call
+        b = {"dvgo_sample_grid_bwd": S_live * (12 + 4 + 12 * 4) / 2,
+             "dvgo_sample_grid_fwd": S * (12 + 4 + 4) / 2,
+             "dvgo_adam_step": (res["touched"][0] * 512 + res["touched"][1] * 512 * 12) * 28 / 3,
+             }.get(name, 0)
+        achieved = b / (ms * 1e-3) / 1e9
+        bound, peak, unit = "hbm", peaks.get("hbm_gbs", 6701.5), "GB/s"
+        traffic = None
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+            "ms_per_call": round(ms, 4), "share": round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)}
+
+
+def cpu_baseline(workload, max_seconds=20.0):
+    """The FP64 oracle timed on the host on a bounded slice of the workload."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from oracle_step import forward_backward
+    from paper_2206_05085_gb300 import synth
+    oracle.build()
+    cfg = synth.CONFIGS[workload]
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    if precision_of(workload) == "bf16":
+        D, Fg, P = synth.bf16_round(D), synth.bf16_round(Fg), synth.bf16_round(P)
+    o, d = synth.rays(cfg, seed=0)
+    t = synth.target_rgb(cfg, seed=0)
+    n = 64
+    samples, t0 = 0, time.perf_counter()
+    start = 0
+    while True:
+        sl = slice(start, start + n)
+        fb = forward_backward(cfg, rp, D, Fg, P, o[sl], d[sl], t[sl])
+        samples += fb["smp"].S
+        start += n
+        el = time.perf_counter() - t0
+        if el > max_seconds or start >= cfg.n_rays:
+            break
+    return {"value": samples / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{start} of {cfg.n_rays} rays of {workload}, forward+backward, "
+                      f"single-threaded FP64 C oracle, {el:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(args.workload, max_seconds=max(5.0, 2.0 * (args.steps + args.warmup)))
+        line = {"impl": "reference", "metric": METRIC, "value": round(cb["value"], 1),
+                "unit": "ray-samples/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload},
+                "cpu_baseline": cb,
+                "e2e": {"value": round(cb["value"], 1), "unit": "ray-samples/s",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    res = run_ours(args, rank, world)
+    if res is None or rank != 0:
+        return
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    cfg, rp = res["cfg"], res["rp"]
+    value = res["samples"] / (res["total_ms"] * 1e-3)
+    e2e = res["e2e_samples"] / (res["e2e_total_ms"] * 1e-3)
+    launches_per_step = sum(v["calls_per_step"] for v in res["kt"].values()) + 2  # + scan/fill pairs
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "ray-samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["total_ms"] / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if res["prec"] == "f32" else "bf16", "data": "synthetic",
+        "config": {"workload": cfg.name, "grid": cfg.grid, "rays": cfg.n_rays,
+                   "samples_per_step": res["S"], "live_samples_per_step": res["S_live"],
+                   "mlp": "39-128-128-3", "tv_dense": bool(args.tv_dense), "l2": "flushed (256 MB memset) before each timed step",
+                   "parallelism": "replicas" if args.gpus > 1 else "single"},
+        "e2e": {"value": round(e2e, 1), "unit": "ray-samples/s", "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": 12},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline(res, peaks),
+        "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in res["kt"].items()},
+        "clocks": res["clocks"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

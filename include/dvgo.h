@@ -1,0 +1,259 @@
+/*
+ * dvgo.h — C ABI of the GB300 (sm_103a) DVGOv2 training-step library.
+ *
+ * Sun, Sun, Chen, "Improved Direct Voxel Grid Optimization for Radiance
+ * Fields Reconstruction" (arXiv 2206.05085).  The library computes one
+ * training iteration of the differentiable volume renderer: ray sampling
+ * inside the scene bbox with occupancy culling, trilinear grid queries,
+ * softplus-shifted raw->alpha, front-to-back compositing with early stop,
+ * the colour MLP, the O(N) distortion loss, the TV gradient and the sparse
+ * Adam grid step, each with its backward.
+ *
+ * Conventions (apply to every call unless stated):
+ *  - Return value: DVGO_OK (0) or a negative dvgo_status.  Arguments are
+ *    validated on the host before any launch; invalid arguments launch
+ *    nothing.  DVGO_ERR_CUDA reports a launch error (cudaGetLastError).
+ *  - No call allocates or frees memory and no call synchronises.  Every
+ *    buffer is caller-owned device memory unless marked "host".  Scratch is
+ *    passed as (ws, ws_bytes); the required size comes from the matching
+ *    *_workspace_size call.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Ragged sample lists are CSR: ray_off[R+1] int64, non-decreasing,
+ *    ray_off[0] = 0; the samples of ray r are [ray_off[r], ray_off[r+1]).
+ *    Where a call takes seg_len[R] (int32, may be NULL), ray r is limited to
+ *    its first seg_len[r] samples (the live samples before early stop).
+ *  - Sample counts: calls over samples take a capacity n_cap (host) and an
+ *    optional device count n_dev (int64, may be NULL).  With n_dev set only
+ *    the first *n_dev (<= n_cap) samples are processed, so a whole
+ *    iteration can run without reading counts back to the host.
+ *  - Grids are corner aligned: grid point i along axis a sits at
+ *    lo_a + i (hi_a - lo_a)/(G_a - 1).  Library-side grid storage is
+ *    "bricked": 8x8x8 bricks in raster order (x fastest), Morton (z-order)
+ *    order of the 512 voxels inside a brick, channels innermost.
+ *    dvgo_grid_pack/unpack convert from/to the dense layout
+ *    g[((z*Gy + y)*Gx + x)*C + c].
+ */
+#ifndef DVGO_H_
+#define DVGO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DVGO_OK = 0,
+  DVGO_ERR_INVALID_ARG = -1, /* null pointer, bad enum or parameter */
+  DVGO_ERR_SHAPE = -2,       /* inconsistent sizes / capacity too small */
+  DVGO_ERR_CUDA = -3,        /* a CUDA runtime error was reported */
+  DVGO_ERR_BOUNDS = -4,      /* device-side bounds check failed (checked builds) */
+  DVGO_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  DVGO_ERR_UNSUPPORTED = -6, /* valid but not implemented combination */
+  DVGO_ERR_WORKSPACE = -7    /* ws_bytes smaller than the required size */
+} dvgo_status;
+
+typedef enum { DVGO_F32 = 0, DVGO_BF16 = 1 } dvgo_dtype;
+
+/* Scene grid: box [lo, hi] and grid points per axis (corner aligned). */
+typedef struct {
+  float lo[3];
+  float hi[3];
+  int32_t G[3];
+} dvgo_grid_desc;
+
+/* Ray sampler (Sec. 3 "Re-implement rendering utils", Sec. 5.3).
+ * mode 0 (bbox): t_k = t_lo + (k + step_offset) step, k < n, where
+ *   [t_lo, t_hi] = [near, far], clipped to the ray/bbox slab when use_slab,
+ *   n = min(max_steps, ceil((t_hi - t_lo)/step - step_offset)); a sample
+ *   exists iff its point lies in the box and, with a mask, the mask is on at
+ *   its nearest grid point.  All these decisions are IEEE FP32 with the
+ *   operation order written in the sampler source, so they are reproducible
+ *   bit for bit.  s_mid/s_len (the distortion loss's normalised interval)
+ *   are (k + step_offset) step/(t_hi - t_lo) and step/(t_hi - t_lo).
+ * mode 1 (contracted, Eq. ub): march x_{k+1} = x_k + h_k d from
+ *   x_0 = o + near d with h_k = step_c / |J(x_k) d| (J the Jacobian of the
+ *   contraction with parameter b, p = inf when p_inf else 2); emits the
+ *   contracted points for k < max_steps while their contracted p-norm
+ *   radius stays below (1 + b) - step_c; s_mid = (k + 0.5)/max_steps,
+ *   s_len = 1/max_steps. */
+typedef struct {
+  int32_t mode;
+  float near;
+  float far;
+  float step;
+  float step_offset;
+  int32_t use_slab;
+  int32_t max_steps;
+  float contract_b;
+  int32_t p_inf;
+  float step_c;
+} dvgo_sampler_desc;
+
+int dvgo_version(void);
+const char* dvgo_status_string(int status);
+
+/* ------------------------------------------------------------------ grid */
+/* Number of elements (voxels x C, including brick padding) of a bricked
+ * grid with G points per axis and C channels. */
+int64_t dvgo_grid_bricked_elems(const int32_t G[3], int32_t C);
+int64_t dvgo_grid_num_bricks(const int32_t G[3]);
+
+/* dense -> bricked (pack) and bricked -> dense (unpack).  dtype applies to
+ * both buffers; padding voxels of the bricked grid are set to zero by pack. */
+int dvgo_grid_pack(const void* dense, void* bricked, const int32_t G[3], int32_t C, int dtype,
+                   void* stream);
+int dvgo_grid_unpack(const void* bricked, void* dense, const int32_t G[3], int32_t C, int dtype,
+                     void* stream);
+
+/* Occupancy mask (Sec. 1): mask[v] = alpha(density[v]) >= alpha_thres with
+ * alpha = 1 - exp(-interval softplus(raw + shift)).  density is bricked
+ * (dtype F32 or BF16); mask is dense uint8 [Gz][Gy][Gx]. */
+int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_desc* grid, float shift,
+                    float interval, float alpha_thres, uint8_t* mask, void* stream);
+
+/* Trilinear query (Sec. 1, "constant time" grid query) of a bricked grid
+ * with C channels at points xyz[n][3] (f32).  u_a = (x_a - lo_a) (G_a - 1) /
+ * (hi_a - lo_a) is clamped to [0, G_a - 1].  If idx (int32, may be NULL) is
+ * given, thread j queries sample idx[j] and writes row idx[j] of out;
+ * otherwise sample j.  out: f32 [.., C] rows at the sample index. */
+int dvgo_sample_grid_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd, int32_t C,
+                         const float* xyz, const int32_t* idx, int64_t n_cap,
+                         const int64_t* n_dev, float* out, void* stream);
+
+/* Adjoint of dvgo_sample_grid_fwd: g_grid (bricked f32, C channels) +=
+ * trilinear weights x g_out[row]; touched (uint8 per brick, may be NULL) is
+ * set to 1 for every brick that received a contribution.  Uses atomics
+ * (summation order is not deterministic). */
+int dvgo_sample_grid_bwd(const float* g_out, const dvgo_grid_desc* gd, int32_t C, const float* xyz,
+                         const int32_t* idx, int64_t n_cap, const int64_t* n_dev, float* g_grid,
+                         uint8_t* touched, void* stream);
+
+/* ---------------------------------------------------------------- sampler */
+size_t dvgo_sample_rays_workspace_size(int64_t R);
+
+/* Ray sampling (see dvgo_sampler_desc).  rays_o/rays_d: f32 [R][3].  mask:
+ * dense uint8 grid (may be NULL).  Outputs (capacity S_cap >= R*max_steps
+ * is required, so the list never overflows): ray_off [R+1] (ray_off[R] is
+ * the sample count S), xyz [S_cap][3], ray_id, step_k [S_cap] int32,
+ * s_mid, s_len [S_cap] f32.  ws: dvgo_sample_rays_workspace_size(R) bytes. */
+int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
+                     const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
+                     const uint8_t* mask, int64_t S_cap, int64_t* ray_off, float* xyz,
+                     int32_t* ray_id, int32_t* step_k, float* s_mid, float* s_len, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* Live-sample list after early stop: live_idx lists, ray by ray, the first
+ * seg_len[r] samples of every ray (the samples with nonzero weight), and
+ * *live_count their number.  live_idx: int32 [capacity ray_off total].
+ * ws: dvgo_live_samples_workspace_size(R) bytes. */
+size_t dvgo_live_samples_workspace_size(int64_t R);
+int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len, int64_t R,
+                      int32_t* live_idx, int64_t* live_count, void* ws, size_t ws_bytes,
+                      void* stream);
+
+/* -------------------------------------------------------------- rendering */
+/* raw -> alpha and transmittance (Sec. 3 "Re-implement rendering utils",
+ * fused): per ray, alpha_i = 1 - exp(-interval softplus(raw_i + shift)),
+ * T_i = prod_{j<i}(1 - alpha_j) carried as an FP32 log-sum with compensated
+ * carries, w_i = T_i alpha_i; the ray halts at the first i with T_i < T_stop
+ * (that sample is not composited).  Writes w[S], T[S] (T_end beyond the
+ * stop), n_live[R] (halting index) and T_end[R]. */
+int dvgo_alpha_weights_fwd(const float* raw, const int64_t* ray_off, int64_t R, float shift,
+                           float interval, float T_stop, float* w, float* T, int32_t* n_live,
+                           float* T_end, void* stream);
+
+/* Colour accumulation: color[r] = sum_{i < n_live[r]} w_i rgb_i + T_end[r] bg. */
+int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_off,
+                           const int32_t* n_live, const float* T_end, int64_t R, const float bg[3],
+                           float* color, void* stream);
+
+/* Backward of raw->alpha + compositing: with g_i = <rgb_i, g_color[r]> +
+ * g_w[i] (rgb and g_w may be NULL: that term is 0) and g_T = <bg,
+ * g_color[r]>, a reverse scan over the live samples gives
+ * R_k = g_{k+1} alpha_{k+1} + (1 - alpha_{k+1}) R_{k+1}, R_{n-1} = g_T, and
+ * g_raw[k] = interval sigmoid(raw_k + shift) T_{k+1} (g_k - R_k).  g_rgb
+ * (may be NULL) receives w_k g_color[r].  Samples past the halting index get
+ * zero gradients. */
+int dvgo_composite_bwd(const float* g_color, const float* g_w, const float* raw, const float* T,
+                       const float* rgb, const int64_t* ray_off, const int32_t* n_live, int64_t R,
+                       float shift, float interval, const float bg[3], float* g_raw, float* g_rgb,
+                       void* stream);
+
+/* Distortion loss (Sec. 2, Eq. dist_loss, O(N) prefix-sum form) per ray:
+ * L_r = 2 sum_i w_i (m_i W_{<i} - WM_{<i}) + 1/3 sum_i w_i^2 ds_i over the
+ * ray's first seg_len[r] samples (all samples if seg_len is NULL); the
+ * running sums of w and w m are Kahan-compensated FP32. */
+int dvgo_distortion_fwd(const float* w, const float* m, const float* ds, const int64_t* ray_off,
+                        const int32_t* seg_len, int64_t R, float* L_r, void* stream);
+
+/* Gradient (Sec. 2): g_w[k] = g_L[r] (2 (m_k W_{<k} - WM_{<k} + WM_{>k} -
+ * m_k W_{>k}) + 2/3 w_k ds_k); g_L is per ray, or (g_L == NULL) the scalar
+ * g_L_scalar for every ray.  Samples beyond seg_len get 0. */
+int dvgo_distortion_bwd(const float* g_L, float g_L_scalar, const float* w, const float* m,
+                        const float* ds, const int64_t* ray_off, const int32_t* seg_len, int64_t R,
+                        float* g_w, void* stream);
+
+/* Photometric loss and its gradient: loss_out[0] = mean over R x 3 of
+ * (color - target)^2, loss_out[1] = mean_r L_r (0 if L_r is NULL),
+ * loss_out[2] = loss_out[0] + lambda_dist loss_out[1]; g_color =
+ * 2 (color - target)/(3R).  Deterministic single-pass reduction. */
+int dvgo_rgb_loss(const float* color, const float* target, const float* L_r, int64_t R,
+                  float lambda_dist, float* loss_out, float* g_color, void* stream);
+
+/* -------------------------------------------------------------- colour MLP */
+/* rgbnet (Tab. 1 "hybrid" colour): input [k0 (12 features), view-direction
+ * encoding [d, sin(2^f d_a), cos(2^f d_a)], f < 4, axis major] = 39 ->
+ * ReLU 128 -> ReLU 128 -> sigmoid 3.  params: f32 flat W1[128][39], b1,
+ * W2[128][128], b2, W3[3][128], b3 (22019 values).  Processes samples
+ * idx[j] (j < *n_dev or n_cap); k0 rows and rgb rows are at the sample
+ * index; the direction is rays_d[ray_id[sample]].  precision: DVGO_F32
+ * (FP32-accurate: TF32 tensor cores with a 3-pass hi/lo split) or
+ * DVGO_BF16 (BF16 tensor cores, FP32 accumulation). */
+int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
+                    const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
+                    int precision, float* rgb, void* stream);
+
+/* Backward: the upstream colour gradient of sample s is g_rgb[s] (f32
+ * [.., 3] at the sample index) when g_rgb is given, else w[s] *
+ * g_color[ray_id[s]] (the colour part of the compositing gradient).
+ * Accumulates g_params (+=, f32) and writes g_k0 [.., 12] rows at the
+ * sample index. */
+int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
+                    const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
+                    const int64_t* n_dev, const float* params, int precision, float* g_params,
+                    float* g_k0, void* stream);
+
+/* ------------------------------------------------------------ regularisers */
+/* TV gradient (Sec. 2, "Efficient total variation (TV) loss"), added into
+ * g_grid without a forward pass: for each grid point v and channel c,
+ * g += weight * 2/(N C) sum_{u in 6-nbr(v)} clamp(g[v,c] - g[u,c], -delta,
+ * delta), N = number of grid points.  dense_mode != 0: every entry;
+ * otherwise only entries whose incoming gradient is nonzero, and only in
+ * bricks flagged in touched (uint8 per brick, may be NULL = all bricks).  In
+ * dense mode every flag of touched (if given) is set to 1.  grid and g_grid
+ * are bricked; grid dtype F32 or BF16, g_grid f32. */
+int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3], int32_t C, float weight,
+                     float delta, int dense_mode, uint8_t* touched, float* g_grid, void* stream);
+
+/* ------------------------------------------------------------------ Adam */
+/* Fused Adam (Sec. 3 "Re-implement Adam optimizer"): for each entry with a
+ * nonzero gradient, m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps); entries with g == 0 are
+ * left untouched.  With touched (uint8 per block of block_elems entries,
+ * may be NULL) only flagged blocks are visited.  zero_grad != 0 clears the
+ * visited gradients and the visited flags.  p_shadow (may be NULL) receives
+ * a BF16 copy of every updated p. */
+int dvgo_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v, int64_t n,
+                   uint8_t* touched, int64_t block_elems, float lr, float beta1, float beta2,
+                   float eps, int64_t step, int zero_grad, void* stream);
+
+/* Reads and clears the device status word that kernels with bounded waits
+ * set (DVGO_ERR_TIMEOUT) instead of hanging.  Synchronises the stream. */
+int dvgo_device_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVGO_H_ */

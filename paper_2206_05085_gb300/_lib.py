@@ -1,0 +1,252 @@
+"""ctypes binding of libdvgo.so (declared in include/dvgo.h).
+
+Argument marshalling only: every function here takes torch tensors (device
+memory), turns them into raw pointers plus the current CUDA stream, and
+calls the C entry point of the same name.  A nonzero status raises
+DvgoError.  The library is loaded on first use; if it has not been built
+(``paper_2206_05085_gb300.build``), loading fails loudly -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdvgo.so")
+
+F32, BF16 = 0, 1
+
+P = ctypes.c_void_p
+I64 = ctypes.c_int64
+I32 = ctypes.c_int32
+F = ctypes.c_float
+INT = ctypes.c_int
+SZ = ctypes.c_size_t
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("lo", F * 3), ("hi", F * 3), ("G", I32 * 3)]
+
+    @staticmethod
+    def make(lo, hi, G):
+        d = GridDesc()
+        lo = [float(v) for v in (lo if hasattr(lo, "__len__") else (lo,) * 3)]
+        hi = [float(v) for v in (hi if hasattr(hi, "__len__") else (hi,) * 3)]
+        G = [int(v) for v in (G if hasattr(G, "__len__") else (G,) * 3)]
+        for a in range(3):
+            d.lo[a], d.hi[a], d.G[a] = lo[a], hi[a], G[a]
+        return d
+
+
+class SamplerDesc(ctypes.Structure):
+    _fields_ = [("mode", I32), ("near", F), ("far", F), ("step", F), ("step_offset", F),
+                ("use_slab", I32), ("max_steps", I32), ("contract_b", F), ("p_inf", I32),
+                ("step_c", F)]
+
+
+class DvgoError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise DvgoError(f"{LIB_PATH} not built; run paper_2206_05085_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    sig = {
+        "dvgo_version": ([], INT),
+        "dvgo_status_string": ([INT], ctypes.c_char_p),
+        "dvgo_grid_bricked_elems": ([P, I32], I64),
+        "dvgo_grid_num_bricks": ([P], I64),
+        "dvgo_grid_pack": ([P, P, P, I32, INT, P], INT),
+        "dvgo_grid_unpack": ([P, P, P, I32, INT, P], INT),
+        "dvgo_build_mask": ([P, INT, P, F, F, F, P, P], INT),
+        "dvgo_sample_grid_fwd": ([P, INT, P, I32, P, P, I64, P, P, P], INT),
+        "dvgo_sample_grid_bwd": ([P, P, I32, P, P, I64, P, P, P, P], INT),
+        "dvgo_sample_rays_workspace_size": ([I64], SZ),
+        "dvgo_sample_rays": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P, SZ, P], INT),
+        "dvgo_live_samples_workspace_size": ([I64], SZ),
+        "dvgo_live_samples": ([P, P, I64, P, P, P, SZ, P], INT),
+        "dvgo_alpha_weights_fwd": ([P, P, I64, F, F, F, P, P, P, P, P], INT),
+        "dvgo_composite_rgb_fwd": ([P, P, P, P, P, I64, P, P, P], INT),
+        "dvgo_composite_bwd": ([P, P, P, P, P, P, P, I64, F, F, P, P, P, P], INT),
+        "dvgo_distortion_fwd": ([P, P, P, P, P, I64, P, P], INT),
+        "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
+        "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
+        "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P], INT),
+        "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P], INT),
+        "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
+        "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
+        "dvgo_device_status": ([P], INT),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def exported_names():
+    """Names this binding expects the library to export."""
+    return [
+        "dvgo_version", "dvgo_status_string", "dvgo_grid_bricked_elems", "dvgo_grid_num_bricks",
+        "dvgo_grid_pack", "dvgo_grid_unpack", "dvgo_build_mask", "dvgo_sample_grid_fwd",
+        "dvgo_sample_grid_bwd", "dvgo_sample_rays_workspace_size", "dvgo_sample_rays",
+        "dvgo_live_samples_workspace_size", "dvgo_live_samples", "dvgo_alpha_weights_fwd",
+        "dvgo_composite_rgb_fwd", "dvgo_composite_bwd", "dvgo_distortion_fwd",
+        "dvgo_distortion_bwd", "dvgo_rgb_loss", "dvgo_rgbnet_fwd", "dvgo_rgbnet_bwd",
+        "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status"]
+
+
+def ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    assert t.is_cuda or not torch.cuda.is_available(), "expected a device tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(name, rc):
+    if rc != 0:
+        msg = lib().dvgo_status_string(rc).decode()
+        raise DvgoError(f"{name} failed: {msg} ({rc})")
+
+
+def _call(name, *args):
+    _check(name, getattr(lib(), name)(*args))
+
+
+def _vec3(v, ctype):
+    return (ctype * 3)(*v)
+
+
+# ---------------------------------------------------------------- grid
+def grid_bricked_elems(G, C):
+    return int(lib().dvgo_grid_bricked_elems(_vec3(G, I32), C))
+
+
+def grid_num_bricks(G):
+    return int(lib().dvgo_grid_num_bricks(_vec3(G, I32)))
+
+
+def grid_pack(dense, bricked, G, C, dtype, stream=None):
+    _call("dvgo_grid_pack", ptr(dense), ptr(bricked), _vec3(G, I32), C, dtype, _stream(stream))
+
+
+def grid_unpack(bricked, dense, G, C, dtype, stream=None):
+    _call("dvgo_grid_unpack", ptr(bricked), ptr(dense), _vec3(G, I32), C, dtype, _stream(stream))
+
+
+def build_mask(density, dtype, gd, shift, interval, thres, mask, stream=None):
+    _call("dvgo_build_mask", ptr(density), dtype, ctypes.byref(gd), shift, interval, thres,
+          ptr(mask), _stream(stream))
+
+
+def sample_grid_fwd(grid, dtype, gd, C, xyz, idx, n_cap, n_dev, out, stream=None):
+    _call("dvgo_sample_grid_fwd", ptr(grid), dtype, ctypes.byref(gd), C, ptr(xyz), ptr(idx),
+          n_cap, ptr(n_dev), ptr(out), _stream(stream))
+
+
+def sample_grid_bwd(g_out, gd, C, xyz, idx, n_cap, n_dev, g_grid, touched, stream=None):
+    _call("dvgo_sample_grid_bwd", ptr(g_out), ctypes.byref(gd), C, ptr(xyz), ptr(idx), n_cap,
+          ptr(n_dev), ptr(g_grid), ptr(touched), _stream(stream))
+
+
+# -------------------------------------------------------------- sampler
+def sample_rays_workspace_size(R):
+    return int(lib().dvgo_sample_rays_workspace_size(R))
+
+
+def sample_rays(rays_o, rays_d, R, gd, sd, mask, S_cap, ray_off, xyz, ray_id, step_k, s_mid,
+                s_len, ws, stream=None):
+    _call("dvgo_sample_rays", ptr(rays_o), ptr(rays_d), R, ctypes.byref(gd), ctypes.byref(sd),
+          ptr(mask), S_cap, ptr(ray_off), ptr(xyz), ptr(ray_id), ptr(step_k), ptr(s_mid),
+          ptr(s_len), ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def live_samples_workspace_size(R):
+    return int(lib().dvgo_live_samples_workspace_size(R))
+
+
+def live_samples(ray_off, seg_len, R, live_idx, live_count, ws, stream=None):
+    _call("dvgo_live_samples", ptr(ray_off), ptr(seg_len), R, ptr(live_idx), ptr(live_count),
+          ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+# ------------------------------------------------------------ rendering
+def alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end, stream=None):
+    _call("dvgo_alpha_weights_fwd", ptr(raw), ptr(ray_off), R, shift, interval, T_stop, ptr(w),
+          ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
+
+
+def composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream=None):
+    _call("dvgo_composite_rgb_fwd", ptr(w), ptr(rgb), ptr(ray_off), ptr(n_live), ptr(T_end), R,
+          _vec3(bg, F), ptr(color), _stream(stream))
+
+
+def composite_bwd(g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, bg, g_raw,
+                  g_rgb=None, stream=None):
+    _call("dvgo_composite_bwd", ptr(g_color), ptr(g_w), ptr(raw), ptr(T), ptr(rgb), ptr(ray_off),
+          ptr(n_live), R, shift, interval, _vec3(bg, F), ptr(g_raw), ptr(g_rgb), _stream(stream))
+
+
+def distortion_fwd(w, m, ds, ray_off, seg_len, R, L_r, stream=None):
+    _call("dvgo_distortion_fwd", ptr(w), ptr(m), ptr(ds), ptr(ray_off), ptr(seg_len), R, ptr(L_r),
+          _stream(stream))
+
+
+def distortion_bwd(g_L, g_L_scalar, w, m, ds, ray_off, seg_len, R, g_w, stream=None):
+    _call("dvgo_distortion_bwd", ptr(g_L), g_L_scalar, ptr(w), ptr(m), ptr(ds), ptr(ray_off),
+          ptr(seg_len), R, ptr(g_w), _stream(stream))
+
+
+def rgb_loss(color, target, L_r, R, lambda_dist, loss_out, g_color, stream=None):
+    _call("dvgo_rgb_loss", ptr(color), ptr(target), ptr(L_r), R, lambda_dist, ptr(loss_out),
+          ptr(g_color), _stream(stream))
+
+
+# ------------------------------------------------------------ colour MLP
+def rgbnet_fwd(k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision, rgb, stream=None):
+    _call("dvgo_rgbnet_fwd", ptr(k0), ptr(rays_d), ptr(ray_id), ptr(idx), n_cap, ptr(n_dev),
+          ptr(params), precision, ptr(rgb), _stream(stream))
+
+
+def rgbnet_bwd(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision,
+               g_params, g_k0, stream=None):
+    _call("dvgo_rgbnet_bwd", ptr(g_rgb), ptr(g_color), ptr(w), ptr(k0), ptr(rays_d), ptr(ray_id),
+          ptr(idx), n_cap, ptr(n_dev), ptr(params), precision, ptr(g_params), ptr(g_k0),
+          _stream(stream))
+
+
+# ------------------------------------------------------- regularisation
+def tv_add_grad(grid, dtype, G, C, weight, delta, dense_mode, touched, g_grid, stream=None):
+    _call("dvgo_tv_add_grad", ptr(grid), dtype, _vec3(G, I32), C, weight, delta, int(dense_mode),
+          ptr(touched), ptr(g_grid), _stream(stream))
+
+
+def adam_step(p, p_shadow, g, m, v, n, touched, block_elems, lr, beta1, beta2, eps, step,
+              zero_grad, stream=None):
+    _call("dvgo_adam_step", ptr(p), ptr(p_shadow), ptr(g), ptr(m), ptr(v), n, ptr(touched),
+          block_elems, lr, beta1, beta2, eps, step, int(zero_grad), _stream(stream))
+
+
+def device_status(stream=None):
+    return int(lib().dvgo_device_status(_stream(stream)))

@@ -1,0 +1,550 @@
+// Dense voxel grids (Tab. 1: explicit density grid, feature grid of the
+// hybrid colour model): bricked storage, trilinear query and its adjoint,
+// occupancy mask (Sec. 1), TV gradient (Sec. 2) and the fused sparse Adam
+// step (Sec. 3 "Re-implement Adam optimizer").
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dvgo {
+
+struct TriArgs {
+  BrickGeom g;
+  float lo[3];
+  float scale[3];  // (G-1)/(hi-lo)
+};
+
+static bool make_tri(TriArgs& T, const dvgo_grid_desc* d) {
+  for (int a = 0; a < 3; ++a) {
+    if (d->G[a] < 2 || !(d->hi[a] > d->lo[a])) return false;
+    T.lo[a] = d->lo[a];
+    T.scale[a] = (float)(d->G[a] - 1) / (d->hi[a] - d->lo[a]);
+  }
+  T.g = make_geom(d->G);
+  return true;
+}
+
+struct Corners {
+  int64_t slot[8];   // voxel slots of the 8 corners
+  float w[8];
+  int ix, iy, iz;    // lower corner
+};
+
+__device__ __forceinline__ void corners(const TriArgs& T, const float* __restrict__ xyz, int64_t s,
+                                        Corners& c) {
+  int i0[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = (__ldg(xyz + 3 * s + a) - T.lo[a]) * T.scale[a];
+    u = fminf(fmaxf(u, 0.0f), (float)(T.g.G[a] - 1));
+    int i = (int)floorf(u);
+    i = min(i, T.g.G[a] - 2);
+    i0[a] = i;
+    f[a] = u - (float)i;
+  }
+  c.ix = i0[0];
+  c.iy = i0[1];
+  c.iz = i0[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    c.slot[k] = voxel_slot(T.g, i0[0] + dx, i0[1] + dy, i0[2] + dz);
+    c.w[k] = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
+  }
+}
+
+__device__ __forceinline__ int64_t live_n(int64_t n_cap, const int64_t* n_dev) {
+  if (!n_dev) return n_cap;
+  int64_t n = *n_dev;
+  return n < n_cap ? n : n_cap;
+}
+
+// ---------------------------------------------------------------- gather
+template <int C, bool kBF16>
+__global__ void __launch_bounds__(256) gather_fwd_kernel(const void* __restrict__ grid, TriArgs T,
+                                                         const float* __restrict__ xyz,
+                                                         const int32_t* __restrict__ idx,
+                                                         int64_t n_cap, const int64_t* n_dev,
+                                                         float* __restrict__ out) {
+  const int64_t n = live_n(n_cap, n_dev);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    Corners c;
+    corners(T, xyz, s, c);
+    float acc[C];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+    if constexpr (!kBF16) {
+      const float* g = reinterpret_cast<const float*>(grid);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float* p = g + c.slot[k] * C;
+        if constexpr (C % 4 == 0) {
+#pragma unroll
+          for (int q = 0; q < C / 4; ++q) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(p) + q);
+            acc[4 * q + 0] += c.w[k] * v.x;
+            acc[4 * q + 1] += c.w[k] * v.y;
+            acc[4 * q + 2] += c.w[k] * v.z;
+            acc[4 * q + 3] += c.w[k] * v.w;
+          }
+        } else {
+#pragma unroll
+          for (int ch = 0; ch < C; ++ch) acc[ch] += c.w[k] * __ldg(p + ch);
+        }
+      }
+    } else {
+      const uint16_t* g = reinterpret_cast<const uint16_t*>(grid);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint16_t* p = g + c.slot[k] * C;
+        if constexpr (C % 4 == 0) {
+#pragma unroll
+          for (int q = 0; q < C / 4; ++q) {
+            uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + q);
+            acc[4 * q + 0] += c.w[k] * __uint_as_float(v.x << 16);
+            acc[4 * q + 1] += c.w[k] * __uint_as_float(v.x & 0xffff0000u);
+            acc[4 * q + 2] += c.w[k] * __uint_as_float(v.y << 16);
+            acc[4 * q + 3] += c.w[k] * __uint_as_float(v.y & 0xffff0000u);
+          }
+        } else {
+#pragma unroll
+          for (int ch = 0; ch < C; ++ch) acc[ch] += c.w[k] * bf16_bits_to_f32(__ldg(p + ch));
+        }
+      }
+    }
+    float* o = out + s * C;
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q)
+        reinterpret_cast<float4*>(o)[q] =
+            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) o[ch] = acc[ch];
+    }
+  }
+}
+
+// Any channel count (scalar loads).
+template <bool kBF16>
+__global__ void gather_fwd_generic_kernel(const void* __restrict__ grid, TriArgs T, int C,
+                                          const float* __restrict__ xyz,
+                                          const int32_t* __restrict__ idx, int64_t n_cap,
+                                          const int64_t* n_dev, float* __restrict__ out) {
+  const int64_t n = live_n(n_cap, n_dev);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    Corners c;
+    corners(T, xyz, s, c);
+    for (int ch = 0; ch < C; ++ch) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float v = kBF16 ? bf16_bits_to_f32(__ldg(reinterpret_cast<const uint16_t*>(grid) + c.slot[k] * C + ch))
+                        : __ldg(reinterpret_cast<const float*>(grid) + c.slot[k] * C + ch);
+        acc += c.w[k] * v;
+      }
+      out[s * C + ch] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scatter
+__device__ __forceinline__ void mark_touched(uint8_t* touched, const TriArgs& T, const Corners& c) {
+  if (!touched) return;
+  // the cell spans at most two bricks per axis
+  const int x1 = c.ix + 1, y1 = c.iy + 1, z1 = c.iz + 1;
+  const bool sx = (c.ix >> 3) != (x1 >> 3), sy = (c.iy >> 3) != (y1 >> 3), sz = (c.iz >> 3) != (z1 >> 3);
+  touched[brick_of(T.g, c.ix, c.iy, c.iz)] = 1;
+  if (sx) touched[brick_of(T.g, x1, c.iy, c.iz)] = 1;
+  if (sy) touched[brick_of(T.g, c.ix, y1, c.iz)] = 1;
+  if (sz) touched[brick_of(T.g, c.ix, c.iy, z1)] = 1;
+  if (sx && sy) touched[brick_of(T.g, x1, y1, c.iz)] = 1;
+  if (sx && sz) touched[brick_of(T.g, x1, c.iy, z1)] = 1;
+  if (sy && sz) touched[brick_of(T.g, c.ix, y1, z1)] = 1;
+  if (sx && sy && sz) touched[brick_of(T.g, x1, y1, z1)] = 1;
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) scatter_bwd_kernel(const float* __restrict__ g_out, TriArgs T,
+                                                          const float* __restrict__ xyz,
+                                                          const int32_t* __restrict__ idx,
+                                                          int64_t n_cap, const int64_t* n_dev,
+                                                          float* __restrict__ g_grid,
+                                                          uint8_t* __restrict__ touched) {
+  const int64_t n = live_n(n_cap, n_dev);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    Corners c;
+    corners(T, xyz, s, c);
+    float go[C];
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(g_out + s * C) + q);
+        go[4 * q] = v.x;
+        go[4 * q + 1] = v.y;
+        go[4 * q + 2] = v.z;
+        go[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) go[ch] = __ldg(g_out + s * C + ch);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float* p = g_grid + c.slot[k] * C;
+      if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q)
+          atomicAdd(reinterpret_cast<float4*>(p) + q,
+                    make_float4(c.w[k] * go[4 * q], c.w[k] * go[4 * q + 1], c.w[k] * go[4 * q + 2],
+                                c.w[k] * go[4 * q + 3]));
+      } else {
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) atomicAdd(p + ch, c.w[k] * go[ch]);
+      }
+    }
+    mark_touched(touched, T, c);
+  }
+}
+
+__global__ void scatter_bwd_generic_kernel(const float* __restrict__ g_out, TriArgs T, int C,
+                                           const float* __restrict__ xyz,
+                                           const int32_t* __restrict__ idx, int64_t n_cap,
+                                           const int64_t* n_dev, float* __restrict__ g_grid,
+                                           uint8_t* __restrict__ touched) {
+  const int64_t n = live_n(n_cap, n_dev);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    Corners c;
+    corners(T, xyz, s, c);
+    for (int ch = 0; ch < C; ++ch) {
+      float go = __ldg(g_out + s * C + ch);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) atomicAdd(g_grid + c.slot[k] * C + ch, c.w[k] * go);
+    }
+    mark_touched(touched, T, c);
+  }
+}
+
+// ------------------------------------------------------------ pack/unpack
+template <typename Tv>
+__global__ void pack_kernel(const Tv* __restrict__ dense, Tv* __restrict__ bricked, BrickGeom g,
+                            int C, bool to_bricked) {
+  const int64_t nvox = (int64_t)g.G[0] * g.G[1] * g.G[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(v % g.G[0]);
+    int y = (int)((v / g.G[0]) % g.G[1]);
+    int z = (int)(v / ((int64_t)g.G[0] * g.G[1]));
+    int64_t slot = voxel_slot(g, x, y, z);
+    for (int c = 0; c < C; ++c) {
+      if (to_bricked) bricked[slot * C + c] = dense[v * C + c];
+      else bricked[v * C + c] = dense[slot * C + c];  // here "dense" is the bricked input
+    }
+  }
+}
+
+// ----------------------------------------------------------------- mask
+__global__ void mask_kernel(const void* __restrict__ density, bool bf16, BrickGeom g, float thr,
+                            uint8_t* __restrict__ mask) {
+  const int64_t nvox = (int64_t)g.G[0] * g.G[1] * g.G[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(v % g.G[0]);
+    int y = (int)((v / g.G[0]) % g.G[1]);
+    int z = (int)(v / ((int64_t)g.G[0] * g.G[1]));
+    int64_t slot = voxel_slot(g, x, y, z);
+    float raw = bf16 ? bf16_bits_to_f32(reinterpret_cast<const uint16_t*>(density)[slot])
+                     : reinterpret_cast<const float*>(density)[slot];
+    mask[v] = raw >= thr ? 1 : 0;
+  }
+}
+
+// ------------------------------------------------------------------- TV
+// One block per brick (512 threads, one voxel each, channels looped).
+template <bool kBF16>
+__global__ void __launch_bounds__(512) tv_kernel(const void* __restrict__ grid, BrickGeom g, int C,
+                                                 float scale, float delta, int dense_mode,
+                                                 uint8_t* __restrict__ touched,
+                                                 float* __restrict__ g_grid) {
+  const int64_t nb = g.num_bricks();
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (!dense_mode && touched && touched[b] == 0) continue;
+    const int bx = (int)(b % g.nb[0]);
+    const int by = (int)((b / g.nb[0]) % g.nb[1]);
+    const int bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    const int t = threadIdx.x;
+    const int x = bx * 8 + (t & 7), y = by * 8 + ((t >> 3) & 7), z = bz * 8 + (t >> 6);
+    if (dense_mode && touched && t == 0) touched[b] = 1;
+    if (x >= g.G[0] || y >= g.G[1] || z >= g.G[2]) continue;
+    const int64_t self = voxel_slot(g, x, y, z);
+    int64_t nbr[6];
+    int nn = 0;
+    if (x > 0) nbr[nn++] = voxel_slot(g, x - 1, y, z);
+    if (x + 1 < g.G[0]) nbr[nn++] = voxel_slot(g, x + 1, y, z);
+    if (y > 0) nbr[nn++] = voxel_slot(g, x, y - 1, z);
+    if (y + 1 < g.G[1]) nbr[nn++] = voxel_slot(g, x, y + 1, z);
+    if (z > 0) nbr[nn++] = voxel_slot(g, x, y, z - 1);
+    if (z + 1 < g.G[2]) nbr[nn++] = voxel_slot(g, x, y, z + 1);
+    for (int c = 0; c < C; ++c) {
+      float* gp = g_grid + self * C + c;
+      float gin = *gp;
+      if (!dense_mode && gin == 0.0f) continue;
+      auto val = [&](int64_t slot) -> float {
+        return kBF16 ? bf16_bits_to_f32(reinterpret_cast<const uint16_t*>(grid)[slot * C + c])
+                     : reinterpret_cast<const float*>(grid)[slot * C + c];
+      };
+      const float v = val(self);
+      float acc = 0.0f;
+      for (int q = 0; q < nn; ++q) acc += fminf(fmaxf(v - val(nbr[q]), -delta), delta);
+      *gp = gin + scale * acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Adam
+struct AdamArgs {
+  float lr, b1, b2, eps, inv_c1, inv_c2;
+};
+
+__device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, const AdamArgs& a,
+                                         bool& changed) {
+  if (g == 0.0f) return;
+  m = a.b1 * m + (1.0f - a.b1) * g;
+  v = a.b2 * v + (1.0f - a.b2) * g * g;
+  p = p - a.lr * (m * a.inv_c1) / (sqrtf(v * a.inv_c2) + a.eps);
+  changed = true;
+}
+
+// One block per flagged block of entries (bricks of grids), float4 body.
+__global__ void __launch_bounds__(256) adam_blocks_kernel(float* __restrict__ p,
+                                                          uint16_t* __restrict__ shadow,
+                                                          float* __restrict__ g,
+                                                          float* __restrict__ m,
+                                                          float* __restrict__ v, int64_t n,
+                                                          uint8_t* __restrict__ touched,
+                                                          int64_t block_elems, AdamArgs a,
+                                                          int zero_grad) {
+  const int64_t nblk = (n + block_elems - 1) / block_elems;
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    if (touched && touched[b] == 0) continue;
+    const int64_t base = b * block_elems;
+    const int64_t end = min(base + block_elems, n);
+    // block_elems and base are multiples of 4 (checked on the host)
+    for (int64_t i = base + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
+      if (i + 4 <= end) {
+        float4 gg = *reinterpret_cast<float4*>(g + i);
+        if (gg.x == 0.0f && gg.y == 0.0f && gg.z == 0.0f && gg.w == 0.0f) continue;
+        float4 pp = *reinterpret_cast<float4*>(p + i);
+        float4 mm = *reinterpret_cast<float4*>(m + i);
+        float4 vv = *reinterpret_cast<float4*>(v + i);
+        bool ch = false;
+        adam_one(pp.x, gg.x, mm.x, vv.x, a, ch);
+        adam_one(pp.y, gg.y, mm.y, vv.y, a, ch);
+        adam_one(pp.z, gg.z, mm.z, vv.z, a, ch);
+        adam_one(pp.w, gg.w, mm.w, vv.w, a, ch);
+        *reinterpret_cast<float4*>(p + i) = pp;
+        *reinterpret_cast<float4*>(m + i) = mm;
+        *reinterpret_cast<float4*>(v + i) = vv;
+        if (zero_grad) *reinterpret_cast<float4*>(g + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (shadow) {
+          uint2 sh;
+          sh.x = (uint32_t)f32_to_bf16_bits(pp.x) | ((uint32_t)f32_to_bf16_bits(pp.y) << 16);
+          sh.y = (uint32_t)f32_to_bf16_bits(pp.z) | ((uint32_t)f32_to_bf16_bits(pp.w) << 16);
+          *reinterpret_cast<uint2*>(shadow + i) = sh;
+        }
+      } else {
+        for (int64_t e = i; e < end; ++e) {
+          bool ch = false;
+          adam_one(p[e], g[e], m[e], v[e], a, ch);
+          if (zero_grad) g[e] = 0.0f;
+          if (shadow && ch) shadow[e] = f32_to_bf16_bits(p[e]);
+        }
+      }
+    }
+    if (touched && zero_grad) {
+      __syncthreads();
+      if (threadIdx.x == 0) touched[b] = 0;
+    }
+  }
+}
+
+// Flat parameter vectors of any length and alignment (scalar).
+__global__ void adam_flat_kernel(float* __restrict__ p, uint16_t* __restrict__ shadow,
+                                 float* __restrict__ g, float* __restrict__ m,
+                                 float* __restrict__ v, int64_t n, AdamArgs a, int zero_grad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bool ch = false;
+    adam_one(p[i], g[i], m[i], v[i], a, ch);
+    if (zero_grad) g[i] = 0.0f;
+    if (shadow && ch) shadow[i] = f32_to_bf16_bits(p[i]);
+  }
+}
+
+}  // namespace dvgo
+
+using namespace dvgo;
+
+extern "C" int64_t dvgo_grid_num_bricks(const int32_t G[3]) {
+  if (!G || G[0] < 1 || G[1] < 1 || G[2] < 1) return -1;
+  return make_geom(G).num_bricks();
+}
+
+extern "C" int64_t dvgo_grid_bricked_elems(const int32_t G[3], int32_t C) {
+  int64_t nb = dvgo_grid_num_bricks(G);
+  if (nb < 0 || C < 1) return -1;
+  return nb * kBrickVox * C;
+}
+
+static int pack_impl(const void* src, void* dst, const int32_t G[3], int32_t C, int dtype,
+                     void* stream, bool to_bricked) {
+  DVGO_CHECK_ARG(src && dst && G && C >= 1 && (dtype == DVGO_F32 || dtype == DVGO_BF16));
+  DVGO_CHECK_ARG(G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
+  BrickGeom g = make_geom(G);
+  cudaStream_t st = as_stream(stream);
+  size_t esz = dtype == DVGO_F32 ? 4 : 2;
+  if (to_bricked) cudaMemsetAsync(dst, 0, (size_t)g.num_bricks() * kBrickVox * C * esz, st);
+  int64_t nvox = (int64_t)G[0] * G[1] * G[2];
+  int grid = grid_for(nvox, 256, 16);
+  if (dtype == DVGO_F32) {
+    if (to_bricked)
+      pack_kernel<float><<<grid, 256, 0, st>>>((const float*)src, (float*)dst, g, C, true);
+    else
+      pack_kernel<float><<<grid, 256, 0, st>>>((const float*)src, (float*)dst, g, C, false);
+  } else {
+    pack_kernel<uint16_t><<<grid, 256, 0, st>>>((const uint16_t*)src, (uint16_t*)dst, g, C,
+                                                to_bricked);
+  }
+  return launch_status();
+}
+
+extern "C" int dvgo_grid_pack(const void* dense, void* bricked, const int32_t G[3], int32_t C,
+                              int dtype, void* stream) {
+  return pack_impl(dense, bricked, G, C, dtype, stream, true);
+}
+
+extern "C" int dvgo_grid_unpack(const void* bricked, void* dense, const int32_t G[3], int32_t C,
+                                int dtype, void* stream) {
+  return pack_impl(bricked, dense, G, C, dtype, stream, false);
+}
+
+extern "C" int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_desc* grid,
+                               float shift, float interval, float alpha_thres, uint8_t* mask,
+                               void* stream) {
+  DVGO_CHECK_ARG(density && grid && mask && (dtype == DVGO_F32 || dtype == DVGO_BF16));
+  DVGO_CHECK_ARG(interval > 0.0f && alpha_thres > 0.0f && alpha_thres < 1.0f);
+  DVGO_CHECK_ARG(grid->G[0] >= 1 && grid->G[1] >= 1 && grid->G[2] >= 1);
+  // alpha(raw) >= thr  <=>  raw >= log(expm1(-log1p(-thr)/interval)) - shift.
+  // The FP32 threshold is the smallest float not below the exact one, so the
+  // FP32 comparison decides exactly like the FP64 one.
+  double q = -log1p(-(double)alpha_thres) / (double)interval;
+  double thr64 = log(expm1(q)) - (double)shift;
+  float thr = (float)thr64;
+  if ((double)thr < thr64) thr = nextafterf(thr, INFINITY);
+  BrickGeom g = make_geom(grid->G);
+  int64_t nvox = (int64_t)grid->G[0] * grid->G[1] * grid->G[2];
+  cudaStream_t st = as_stream(stream);
+  mask_kernel<<<grid_for(nvox, 256, 16), 256, 0, st>>>(density, dtype == DVGO_BF16, g, thr, mask);
+  return launch_status();
+}
+
+extern "C" int dvgo_sample_grid_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd,
+                                    int32_t C, const float* xyz, const int32_t* idx, int64_t n_cap,
+                                    const int64_t* n_dev, float* out, void* stream) {
+  DVGO_CHECK_ARG(gd && C >= 1 && n_cap >= 0 && (dtype == DVGO_F32 || dtype == DVGO_BF16));
+  if (n_cap == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(grid && xyz && out);
+  TriArgs T;
+  DVGO_CHECK_ARG(make_tri(T, gd));
+  cudaStream_t st = as_stream(stream);
+  const int block = 256;
+  int g = grid_for(n_cap, block, 16);
+  if (dtype == DVGO_F32) {
+    if (C == 1) gather_fwd_kernel<1, false><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
+    else if (C == 12) gather_fwd_kernel<12, false><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
+    else gather_fwd_generic_kernel<false><<<g, block, 0, st>>>(grid, T, C, xyz, idx, n_cap, n_dev, out);
+  } else {
+    if (C == 1) gather_fwd_kernel<1, true><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
+    else if (C == 12) gather_fwd_kernel<12, true><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
+    else gather_fwd_generic_kernel<true><<<g, block, 0, st>>>(grid, T, C, xyz, idx, n_cap, n_dev, out);
+  }
+  return launch_status();
+}
+
+extern "C" int dvgo_sample_grid_bwd(const float* g_out, const dvgo_grid_desc* gd, int32_t C,
+                                    const float* xyz, const int32_t* idx, int64_t n_cap,
+                                    const int64_t* n_dev, float* g_grid, uint8_t* touched,
+                                    void* stream) {
+  DVGO_CHECK_ARG(gd && C >= 1 && n_cap >= 0);
+  if (n_cap == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(g_out && xyz && g_grid);
+  TriArgs T;
+  DVGO_CHECK_ARG(make_tri(T, gd));
+  cudaStream_t st = as_stream(stream);
+  const int block = 256;
+  int g = grid_for(n_cap, block, 16);
+  if (C == 1) scatter_bwd_kernel<1><<<g, block, 0, st>>>(g_out, T, xyz, idx, n_cap, n_dev, g_grid, touched);
+  else if (C == 12) scatter_bwd_kernel<12><<<g, block, 0, st>>>(g_out, T, xyz, idx, n_cap, n_dev, g_grid, touched);
+  else scatter_bwd_generic_kernel<<<g, block, 0, st>>>(g_out, T, C, xyz, idx, n_cap, n_dev, g_grid, touched);
+  return launch_status();
+}
+
+extern "C" int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3], int32_t C,
+                                float weight, float delta, int dense_mode, uint8_t* touched,
+                                float* g_grid, void* stream) {
+  DVGO_CHECK_ARG(grid && G && g_grid && C >= 1 && delta > 0.0f);
+  DVGO_CHECK_ARG(dtype == DVGO_F32 || dtype == DVGO_BF16);
+  DVGO_CHECK_ARG(G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
+  BrickGeom g = make_geom(G);
+  double N = (double)G[0] * G[1] * G[2];
+  float scale = (float)((double)weight * 2.0 / (N * C));
+  cudaStream_t st = as_stream(stream);
+  int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 4);
+  if (dtype == DVGO_F32)
+    tv_kernel<false><<<nb, 512, 0, st>>>(grid, g, C, scale, delta, dense_mode, touched, g_grid);
+  else
+    tv_kernel<true><<<nb, 512, 0, st>>>(grid, g, C, scale, delta, dense_mode, touched, g_grid);
+  return launch_status();
+}
+
+extern "C" int dvgo_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v, int64_t n,
+                              uint8_t* touched, int64_t block_elems, float lr, float beta1,
+                              float beta2, float eps, int64_t step, int zero_grad, void* stream) {
+  DVGO_CHECK_ARG(n >= 0 && step >= 1);
+  if (n == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(p && g && m && v);
+  AdamArgs a;
+  a.lr = lr;
+  a.b1 = beta1;
+  a.b2 = beta2;
+  a.eps = eps;
+  a.inv_c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
+  a.inv_c2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
+  cudaStream_t st = as_stream(stream);
+  bool aligned = ((uintptr_t)p % 16 == 0) && ((uintptr_t)g % 16 == 0) && ((uintptr_t)m % 16 == 0) &&
+                 ((uintptr_t)v % 16 == 0) && (!p_shadow || (uintptr_t)p_shadow % 8 == 0);
+  if (touched) {
+    DVGO_CHECK_ARG(block_elems > 0 && block_elems % 4 == 0 && aligned);
+    int64_t nblk = (n + block_elems - 1) / block_elems;
+    int grid = (int)std::min<int64_t>(nblk, (int64_t)kNumSMs * 8);
+    adam_blocks_kernel<<<grid, 256, 0, st>>>(p, p_shadow, g, m, v, n, touched, block_elems, a,
+                                             zero_grad);
+  } else if (aligned && n % 4 == 0) {
+    int64_t be = 4096;
+    int64_t nblk = (n + be - 1) / be;
+    int grid = (int)std::min<int64_t>(nblk, (int64_t)kNumSMs * 8);
+    adam_blocks_kernel<<<grid, 256, 0, st>>>(p, p_shadow, g, m, v, n, nullptr, be, a, zero_grad);
+  } else {
+    adam_flat_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(p, p_shadow, g, m, v, n, a, zero_grad);
+  }
+  return launch_status();
+}

@@ -1,0 +1,90 @@
+// Shared definitions of the colour MLP kernels (rgbnet, Tab. 1 "hybrid").
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dvgo {
+
+constexpr int kFeat = 12;        // feature-grid channels
+constexpr int kIn = 39;          // 12 + 3 + 2*3*4 view-direction encoding
+constexpr int kInP = 40;         // + constant 1 column carrying the layer-1 bias
+constexpr int kHid = 128;
+constexpr int kOut = 3;
+constexpr int kTile = 128;       // samples per tile
+constexpr int kNumFreq = 4;
+
+// flat FP32 parameter layout: W1[128][39], b1, W2[128][128], b2, W3[3][128], b3
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHid * kIn;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kOut * kHid;
+constexpr int kNumParams = kOffB3 + kOut;  // 22019
+
+__device__ __forceinline__ int64_t mlp_count(int64_t n_cap, const int64_t* n_dev) {
+  if (!n_dev) return n_cap;
+  int64_t n = *n_dev;
+  return n < n_cap ? n : n_cap;
+}
+
+// Input row of sample j of the list: [k0 (12), d (3), sin(2^f d_a) (a major,
+// f inner), cos(2^f d_a), 1].  Rows past the list end are zero (including
+// the bias column), so they contribute nothing to any gradient.
+__device__ __forceinline__ void encode_row(const float* __restrict__ k0,
+                                           const float* __restrict__ rays_d,
+                                           const int32_t* __restrict__ ray_id,
+                                           const int32_t* __restrict__ idx, int64_t j, int64_t n,
+                                           float row[kInP]) {
+  if (j >= n) {
+#pragma unroll
+    for (int k = 0; k < kInP; ++k) row[k] = 0.0f;
+    return;
+  }
+  const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+  const float4* kp = reinterpret_cast<const float4*>(k0 + s * kFeat);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float4 v = __ldg(kp + q);
+    row[4 * q] = v.x;
+    row[4 * q + 1] = v.y;
+    row[4 * q + 2] = v.z;
+    row[4 * q + 3] = v.w;
+  }
+  const int64_t r = __ldg(ray_id + s);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float d = __ldg(rays_d + 3 * r + a);
+    row[kFeat + a] = d;
+#pragma unroll
+    for (int f = 0; f < kNumFreq; ++f) {
+      float sn, cs;
+      sincosf(d * (float)(1 << f), &sn, &cs);
+      row[kFeat + 3 + a * kNumFreq + f] = sn;
+      row[kFeat + 3 + 3 * kNumFreq + a * kNumFreq + f] = cs;
+    }
+  }
+  row[kIn] = 1.0f;
+}
+
+// Upstream gradient of the colour of sample s: g_rgb[s] if given, else
+// w[s] * g_color[ray_id[s]].
+__device__ __forceinline__ void upstream_rgb_grad(const float* __restrict__ g_rgb,
+                                                  const float* __restrict__ g_color,
+                                                  const float* __restrict__ w,
+                                                  const int32_t* __restrict__ ray_id, int64_t s,
+                                                  float out[3]) {
+  if (g_rgb) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = __ldg(g_rgb + 3 * s + c);
+  } else {
+    const float ws = __ldg(w + s);
+    const int64_t r = __ldg(ray_id + s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = ws * __ldg(g_color + 3 * r + c);
+  }
+}
+
+}  // namespace dvgo

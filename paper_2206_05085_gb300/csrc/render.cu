@@ -1,0 +1,367 @@
+// Volume rendering over ragged per-ray sample lists: raw->alpha with
+// log-space transmittance and early stop (Sec. 3 "Re-implement rendering
+// utils"), colour accumulation and its adjoint, the O(N) distortion loss and
+// its gradient (Sec. 2), and the photometric loss.  One warp per ray; the
+// samples of a ray are processed in chunks of 32 with warp scans and a
+// carried running value between chunks.
+#include "common.cuh"
+
+namespace dvgo {
+
+__device__ __forceinline__ void ray_range(const int64_t* __restrict__ ray_off,
+                                          const int32_t* __restrict__ seg_len, int64_t r,
+                                          int64_t& b, int& n, int& N) {
+  b = ray_off[r];
+  N = (int)(ray_off[r + 1] - b);
+  n = N;
+  if (seg_len) n = min(n, (int)seg_len[r]);
+}
+
+#define DVGO_WARP_LOOP(R)                                                   \
+  const int lane = threadIdx.x & 31;                                        \
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; \
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;            \
+  for (int64_t r = warp0; r < (R); r += nwarps)
+
+// ------------------------------------------------------------- weights fwd
+__global__ void __launch_bounds__(256) alpha_weights_kernel(
+    const float* __restrict__ raw, const int64_t* __restrict__ ray_off, int64_t R, float shift,
+    float interval, float T_stop, float* __restrict__ w, float* __restrict__ T,
+    int32_t* __restrict__ n_live, float* __restrict__ T_end) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, nullptr, r, b, n, N);
+    Kahan carry;  // log T before the current chunk
+    int stop = N;
+    float t_end = 1.0f;
+    int c0 = 0;
+    for (; c0 < N; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < N;
+      const float la = valid ? -interval * softplus_f(__ldg(raw + b + i) + shift) : 0.0f;
+      const float incl = warp_incl_sum(la);
+      const float logT = __fadd_rn(carry.s, __fsub_rn(incl - la, carry.c));
+      const float Ti = expf(logT);
+      const unsigned below = __ballot_sync(0xffffffffu, valid && Ti < T_stop);
+      const int first = below ? __ffs(below) - 1 : 32;
+      if (below) {
+        stop = c0 + first;
+        t_end = __shfl_sync(0xffffffffu, Ti, first);
+      }
+      if (valid) {
+        if (lane < first) {
+          w[b + i] = Ti * -expm1f(la);
+          T[b + i] = Ti;
+        } else {
+          w[b + i] = 0.0f;
+          T[b + i] = t_end;
+        }
+      }
+      if (below) break;
+      carry.add(__shfl_sync(0xffffffffu, incl, 31));
+    }
+    if (stop == N) t_end = expf(__fsub_rn(carry.s, carry.c));
+    for (c0 += 32; c0 < N; c0 += 32) {
+      const int i = c0 + lane;
+      if (i < N) {
+        w[b + i] = 0.0f;
+        T[b + i] = t_end;
+      }
+    }
+    if (lane == 0) {
+      n_live[r] = stop;
+      T_end[r] = t_end;
+    }
+  }
+}
+
+// --------------------------------------------------------- colour forward
+__global__ void __launch_bounds__(256) composite_rgb_kernel(
+    const float* __restrict__ w, const float* __restrict__ rgb, const int64_t* __restrict__ ray_off,
+    const int32_t* __restrict__ n_live, const float* __restrict__ T_end, int64_t R, float bg0,
+    float bg1, float bg2, float* __restrict__ color) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, n_live, r, b, n, N);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float wi = __ldg(w + b + i);
+      a0 += wi * __ldg(rgb + 3 * (b + i));
+      a1 += wi * __ldg(rgb + 3 * (b + i) + 1);
+      a2 += wi * __ldg(rgb + 3 * (b + i) + 2);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+      const float te = T_end[r];
+      color[3 * r] = a0 + te * bg0;
+      color[3 * r + 1] = a1 + te * bg1;
+      color[3 * r + 2] = a2 + te * bg2;
+    }
+  }
+}
+
+// -------------------------------------------------------- composite bwd
+// Reverse scan of the affine maps F_k(x) = (1 - alpha_k) x + g_k alpha_k:
+// R_k = (F_{k+1} o ... o F_{n-1})(g_T).
+__global__ void __launch_bounds__(256) composite_bwd_kernel(
+    const float* __restrict__ g_color, const float* __restrict__ g_w, const float* __restrict__ raw,
+    const float* __restrict__ T, const float* __restrict__ rgb, const int64_t* __restrict__ ray_off,
+    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval, float bg0,
+    float bg1, float bg2, float* __restrict__ g_raw, float* __restrict__ g_rgb) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, n_live, r, b, n, N);
+    const float gc0 = __ldg(g_color + 3 * r), gc1 = __ldg(g_color + 3 * r + 1),
+                gc2 = __ldg(g_color + 3 * r + 2);
+    float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;  // R_{n-1} = g_T
+    const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
+    for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
+      const int k = c0 + lane;
+      const bool valid = k < n;
+      float A = 1.0f, B = 0.0f, gk = 0.0f, la = 0.0f, rk = 0.0f, Tk = 0.0f;
+      if (valid) {
+        const int64_t s = b + k;
+        rk = __ldg(raw + s);
+        la = -interval * softplus_f(rk + shift);
+        const float al = -expm1f(la);
+        if (rgb) gk = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
+        if (g_w) gk += __ldg(g_w + s);
+        Tk = __ldg(T + s);
+        A = 1.0f - al;
+        B = gk * al;
+      }
+      // inclusive suffix composition Suf_lane = F_k o F_{k+1} o ... o F_{c0+31}
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float A2 = __shfl_down_sync(0xffffffffu, A, o);
+        const float B2 = __shfl_down_sync(0xffffffffu, B, o);
+        if (lane + o < 32) {
+          B = A * B2 + B;
+          A = A * A2;
+        }
+      }
+      float An = __shfl_down_sync(0xffffffffu, A, 1);
+      float Bn = __shfl_down_sync(0xffffffffu, B, 1);
+      if (lane == 31) {
+        An = 1.0f;
+        Bn = 0.0f;
+      }
+      const float Rk = An * carry + Bn;
+      if (valid) {
+        const float Tk1 = Tk * expf(la);
+        g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
+        if (g_rgb) {
+          const float wk = Tk * -expm1f(la);
+          g_rgb[3 * (b + k)] = wk * gc0;
+          g_rgb[3 * (b + k) + 1] = wk * gc1;
+          g_rgb[3 * (b + k) + 2] = wk * gc2;
+        }
+      }
+      const float A0 = __shfl_sync(0xffffffffu, A, 0);
+      const float B0 = __shfl_sync(0xffffffffu, B, 0);
+      carry = A0 * carry + B0;
+    }
+    for (int k = n + lane; k < N; k += 32) {
+      g_raw[b + k] = 0.0f;
+      if (g_rgb) {
+        g_rgb[3 * (b + k)] = 0.0f;
+        g_rgb[3 * (b + k) + 1] = 0.0f;
+        g_rgb[3 * (b + k) + 2] = 0.0f;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ distortion
+// Midpoints are measured from the segment's first midpoint (the loss and its
+// gradient only depend on differences of m), which keeps the prefix-sum
+// difference m_i W_{<i} - WM_{<i} free of cancellation against large m.
+__global__ void __launch_bounds__(256) distortion_fwd_kernel(
+    const float* __restrict__ w, const float* __restrict__ m, const float* __restrict__ ds,
+    const int64_t* __restrict__ ray_off, const int32_t* __restrict__ seg_len, int64_t R,
+    float* __restrict__ L_r) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, seg_len, r, b, n, N);
+    const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+    Kahan cW, cWM;
+    float acc = 0.0f;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < n;
+      const float wi = valid ? __ldg(w + b + i) : 0.0f;
+      const float mi = valid ? __ldg(m + b + i) - m0 : 0.0f;
+      const float di = valid ? __ldg(ds + b + i) : 0.0f;
+      const float iw = warp_incl_sum(wi);
+      const float iwm = warp_incl_sum(wi * mi);
+      const float Wlt = __fadd_rn(cW.s, __fsub_rn(iw - wi, cW.c));
+      const float WMlt = __fadd_rn(cWM.s, __fsub_rn(iwm - wi * mi, cWM.c));
+      acc += 2.0f * wi * (mi * Wlt - WMlt) + wi * wi * di * (1.0f / 3.0f);
+      cW.add(__shfl_sync(0xffffffffu, iw, 31));
+      cWM.add(__shfl_sync(0xffffffffu, iwm, 31));
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) L_r[r] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) distortion_bwd_kernel(
+    const float* __restrict__ g_L, float g_L_scalar, const float* __restrict__ w,
+    const float* __restrict__ m, const float* __restrict__ ds, const int64_t* __restrict__ ray_off,
+    const int32_t* __restrict__ seg_len, int64_t R, float* __restrict__ g_w) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, seg_len, r, b, n, N);
+    const float gl = g_L ? __ldg(g_L + r) : g_L_scalar;
+    const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+    // totals
+    Kahan tW, tWM;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const float wi = i < n ? __ldg(w + b + i) : 0.0f;
+      const float mi = i < n ? __ldg(m + b + i) - m0 : 0.0f;
+      tW.add(warp_sum(wi));
+      tWM.add(warp_sum(wi * mi));
+    }
+    const float Wt = __fsub_rn(tW.s, tW.c), WMt = __fsub_rn(tWM.s, tWM.c);
+    Kahan cW, cWM;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < n;
+      const float wi = valid ? __ldg(w + b + i) : 0.0f;
+      const float mi = valid ? __ldg(m + b + i) - m0 : 0.0f;
+      const float di = valid ? __ldg(ds + b + i) : 0.0f;
+      const float iw = warp_incl_sum(wi);
+      const float iwm = warp_incl_sum(wi * mi);
+      const float Wlt = __fadd_rn(cW.s, __fsub_rn(iw - wi, cW.c));
+      const float WMlt = __fadd_rn(cWM.s, __fsub_rn(iwm - wi * mi, cWM.c));
+      const float Wgt = Wt - Wlt - wi;
+      const float WMgt = WMt - WMlt - wi * mi;
+      if (valid)
+        g_w[b + i] = gl * (2.0f * (mi * (Wlt - Wgt) - WMlt + WMgt) + (2.0f / 3.0f) * wi * di);
+      cW.add(__shfl_sync(0xffffffffu, iw, 31));
+      cWM.add(__shfl_sync(0xffffffffu, iwm, 31));
+    }
+    for (int k = n + lane; k < N; k += 32) g_w[b + k] = 0.0f;
+  }
+}
+
+// ------------------------------------------------------------------ loss
+__global__ void __launch_bounds__(1024) rgb_loss_kernel(const float* __restrict__ color,
+                                                        const float* __restrict__ target,
+                                                        const float* __restrict__ L_r, int64_t R,
+                                                        float lambda_dist,
+                                                        float* __restrict__ loss_out,
+                                                        float* __restrict__ g_color) {
+  __shared__ float s1[32], s2[32];
+  float a = 0.0f, d = 0.0f;
+  const float gscale = 2.0f / (3.0f * (float)R);
+  for (int64_t i = threadIdx.x; i < 3 * R; i += blockDim.x) {
+    const float e = color[i] - target[i];
+    a += e * e;
+    g_color[i] = gscale * e;
+  }
+  if (L_r)
+    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) d += L_r[i];
+  a = warp_sum(a);
+  d = warp_sum(d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s1[wid] = a;
+    s2[wid] = d;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? s1[lane] : 0.0f;
+    d = lane < nw ? s2[lane] : 0.0f;
+    a = warp_sum(a);
+    d = warp_sum(d);
+    if (lane == 0) {
+      const float lr = a / (3.0f * (float)R);
+      const float ld = d / (float)R;
+      loss_out[0] = lr;
+      loss_out[1] = ld;
+      loss_out[2] = lr + lambda_dist * ld;
+    }
+  }
+}
+
+}  // namespace dvgo
+
+using namespace dvgo;
+
+static int warp_grid(int64_t R) { return grid_for(R * 32, 256, 16); }
+
+extern "C" int dvgo_alpha_weights_fwd(const float* raw, const int64_t* ray_off, int64_t R,
+                                      float shift, float interval, float T_stop, float* w, float* T,
+                                      int32_t* n_live, float* T_end, void* stream) {
+  DVGO_CHECK_ARG(R >= 0 && interval > 0.0f && T_stop >= 0.0f);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(raw && ray_off && w && T && n_live && T_end);
+  alpha_weights_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(raw, ray_off, R, shift,
+                                                                    interval, T_stop, w, T, n_live,
+                                                                    T_end);
+  return launch_status();
+}
+
+extern "C" int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_off,
+                                      const int32_t* n_live, const float* T_end, int64_t R,
+                                      const float bg[3], float* color, void* stream) {
+  DVGO_CHECK_ARG(R >= 0);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(w && rgb && ray_off && T_end && bg && color);
+  composite_rgb_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(w, rgb, ray_off, n_live, T_end,
+                                                                    R, bg[0], bg[1], bg[2], color);
+  return launch_status();
+}
+
+extern "C" int dvgo_composite_bwd(const float* g_color, const float* g_w, const float* raw,
+                                  const float* T, const float* rgb, const int64_t* ray_off,
+                                  const int32_t* n_live, int64_t R, float shift, float interval,
+                                  const float bg[3], float* g_raw, float* g_rgb, void* stream) {
+  DVGO_CHECK_ARG(R >= 0 && interval > 0.0f);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(g_color && raw && T && ray_off && n_live && bg && g_raw);
+  composite_bwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, bg[0], bg[1], bg[2], g_raw,
+      g_rgb);
+  return launch_status();
+}
+
+extern "C" int dvgo_distortion_fwd(const float* w, const float* m, const float* ds,
+                                   const int64_t* ray_off, const int32_t* seg_len, int64_t R,
+                                   float* L_r, void* stream) {
+  DVGO_CHECK_ARG(R >= 0);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(w && m && ds && ray_off && L_r);
+  distortion_fwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(w, m, ds, ray_off, seg_len, R,
+                                                                     L_r);
+  return launch_status();
+}
+
+extern "C" int dvgo_distortion_bwd(const float* g_L, float g_L_scalar, const float* w,
+                                   const float* m, const float* ds, const int64_t* ray_off,
+                                   const int32_t* seg_len, int64_t R, float* g_w, void* stream) {
+  DVGO_CHECK_ARG(R >= 0);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(w && m && ds && ray_off && g_w);
+  distortion_bwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(g_L, g_L_scalar, w, m, ds,
+                                                                     ray_off, seg_len, R, g_w);
+  return launch_status();
+}
+
+extern "C" int dvgo_rgb_loss(const float* color, const float* target, const float* L_r, int64_t R,
+                             float lambda_dist, float* loss_out, float* g_color, void* stream) {
+  DVGO_CHECK_ARG(R > 0 && color && target && loss_out && g_color);
+  rgb_loss_kernel<<<1, 1024, 0, as_stream(stream)>>>(color, target, L_r, R, lambda_dist, loss_out,
+                                                     g_color);
+  return launch_status();
+}

@@ -1,0 +1,394 @@
+// Ray sampling (Sec. 3 "Re-implement rendering utils": sample only inside
+// the scene bbox; Sec. 1 occupancy mask; Sec. 5.3 contracted step for
+// unbounded scenes) and the live-sample list used after early stop.
+//
+// Every decision that creates or drops a sample is IEEE FP32 with explicit
+// round-to-nearest intrinsics (no FMA contraction), in the operation order
+// stated in dvgo.h / below, so the integer results are reproducible bit for
+// bit by any IEEE FP32 implementation of the same formulas.
+#include "common.cuh"
+
+namespace dvgo {
+
+struct SamplerArgs {
+  float lo[3], hi[3];
+  int G[3];
+  float scale[3];  // (G-1)/(hi-lo), FP32
+  dvgo_sampler_desc s;
+};
+
+__device__ __forceinline__ int nearest_idx(float x, float lo, float scale, int G) {
+  float u = __fmul_rn(__fsub_rn(x, lo), scale);
+  float f = floorf(__fadd_rn(u, 0.5f));
+  int n = (int)f;
+  if (!(f >= 0.0f)) n = 0;
+  if (f > (float)(G - 1)) n = G - 1;
+  return n;
+}
+
+__device__ __forceinline__ bool keep_point(const SamplerArgs& A, const uint8_t* __restrict__ mask,
+                                           const float x[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (!(x[a] >= A.lo[a] && x[a] <= A.hi[a])) return false;
+  if (!mask) return true;
+  int ix = nearest_idx(x[0], A.lo[0], A.scale[0], A.G[0]);
+  int iy = nearest_idx(x[1], A.lo[1], A.scale[1], A.G[1]);
+  int iz = nearest_idx(x[2], A.lo[2], A.scale[2], A.G[2]);
+  return __ldg(mask + ((int64_t)iz * A.G[1] + iy) * A.G[0] + ix) != 0;
+}
+
+struct RaySpan {
+  float tlo, thi;
+  int n;
+};
+
+// Ray/bbox slab and step count (mode 0).
+__device__ __forceinline__ RaySpan ray_span(const SamplerArgs& A, const float o[3], const float d[3]) {
+  float tlo = A.s.near, thi = A.s.far;
+  bool empty = false;
+  if (A.s.use_slab) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (d[a] == 0.0f) {
+        if (o[a] < A.lo[a] || o[a] > A.hi[a]) empty = true;
+      } else {
+        float ta = __fdiv_rn(__fsub_rn(A.lo[a], o[a]), d[a]);
+        float tb = __fdiv_rn(__fsub_rn(A.hi[a], o[a]), d[a]);
+        float tn = ta < tb ? ta : tb;
+        float tf = ta < tb ? tb : ta;
+        if (tn > tlo) tlo = tn;
+        if (tf < thi) thi = tf;
+      }
+    }
+  }
+  int n = 0;
+  if (!empty && thi > tlo) {
+    float u = __fdiv_rn(__fsub_rn(thi, tlo), A.s.step);
+    float nf = ceilf(__fsub_rn(u, A.s.step_offset));
+    if (nf > (float)A.s.max_steps) n = A.s.max_steps;
+    else if (nf > 0.0f) n = (int)nf;
+  }
+  return {tlo, thi, n};
+}
+
+__device__ __forceinline__ void point_at(const SamplerArgs& A, const float o[3], const float d[3],
+                                         float tlo, int k, float x[3]) {
+  float t = __fadd_rn(tlo, __fmul_rn(__fadd_rn((float)k, A.s.step_offset), A.s.step));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+}
+
+__device__ __forceinline__ void load_ray(const float* __restrict__ ro, const float* __restrict__ rd,
+                                         int64_t r, float o[3], float d[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o[a] = __ldg(ro + 3 * r + a);
+    d[a] = __ldg(rd + 3 * r + a);
+  }
+}
+
+// Mode 0, pass 1: one warp per ray counts the kept samples.
+__global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
+                                  const float* __restrict__ rd, int64_t R,
+                                  const uint8_t* __restrict__ mask, int32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < R; r += nwarps) {
+    float o[3], d[3];
+    load_ray(ro, rd, r, o, d);
+    RaySpan sp = ray_span(A, o, d);
+    int cnt = 0;
+    for (int k0 = 0; k0 < sp.n; k0 += 32) {
+      int k = k0 + lane;
+      bool keep = false;
+      if (k < sp.n) {
+        float x[3];
+        point_at(A, o, d, sp.tlo, k, x);
+        keep = keep_point(A, mask, x);
+      }
+      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    if (lane == 0) counts[r] = cnt;
+  }
+}
+
+// Mode 0, pass 2: one warp per ray writes the kept samples in step order.
+__global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
+                                 const float* __restrict__ rd, int64_t R,
+                                 const uint8_t* __restrict__ mask,
+                                 const int64_t* __restrict__ ray_off, float* __restrict__ xyz,
+                                 int32_t* __restrict__ ray_id, int32_t* __restrict__ step_k,
+                                 float* __restrict__ s_mid, float* __restrict__ s_len) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < R; r += nwarps) {
+    float o[3], d[3];
+    load_ray(ro, rd, r, o, d);
+    RaySpan sp = ray_span(A, o, d);
+    float span = __fsub_rn(sp.thi, sp.tlo);
+    float slen = __fdiv_rn(A.s.step, span);
+    int64_t pos = ray_off[r];
+    for (int k0 = 0; k0 < sp.n; k0 += 32) {
+      int k = k0 + lane;
+      bool keep = false;
+      float x[3];
+      if (k < sp.n) {
+        point_at(A, o, d, sp.tlo, k, x);
+        keep = keep_point(A, mask, x);
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        int64_t s = pos + __popc(bal & lt_mask);
+        xyz[3 * s + 0] = x[0];
+        xyz[3 * s + 1] = x[1];
+        xyz[3 * s + 2] = x[2];
+        ray_id[s] = (int32_t)r;
+        step_k[s] = k;
+        s_mid[s] = __fdiv_rn(__fmul_rn(__fadd_rn((float)k, A.s.step_offset), A.s.step), span);
+        s_len[s] = slen;
+      }
+      pos += __popc(bal);
+    }
+  }
+}
+
+// Mode 1: contracted-space march (Eq. ub), one thread per ray.  The march is
+// sequential; pass 1 counts, pass 2 repeats it and writes.
+template <bool kWrite>
+__global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
+                                  const float* __restrict__ rd, int64_t R,
+                                  const uint8_t* __restrict__ mask, int32_t* __restrict__ counts,
+                                  const int64_t* __restrict__ ray_off, float* __restrict__ xyz,
+                                  int32_t* __restrict__ ray_id, int32_t* __restrict__ step_k,
+                                  float* __restrict__ s_mid, float* __restrict__ s_len) {
+  const float b = A.s.contract_b;
+  const float opb = __fadd_rn(1.0f, b);
+  const float rmax = __fsub_rn(opb, A.s.step_c);
+  const float two_b = __fmul_rn(2.0f, b);
+  const bool p_inf = A.s.p_inf != 0;
+  const float inv_steps = __fdiv_rn(1.0f, (float)A.s.max_steps);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    float o[3], d[3];
+    load_ray(ro, rd, r, o, d);
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(A.s.near, d[a]));
+    int cnt = 0;
+    int64_t pos = kWrite ? ray_off[r] : 0;
+    for (int k = 0; k < A.s.max_steps; ++k) {
+      float rad;
+      int m = 0;
+      if (p_inf) {
+        float a0 = fabsf(x[0]), a1 = fabsf(x[1]), a2 = fabsf(x[2]);
+        rad = a0;
+        if (a1 > rad) { rad = a1; m = 1; }
+        if (a2 > rad) { rad = a2; m = 2; }
+      } else {
+        rad = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])),
+                                   __fmul_rn(x[2], x[2])));
+      }
+      float xc[3], j[3];
+      if (rad <= 1.0f) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { xc[a] = x[a]; j[a] = d[a]; }
+      } else {
+        float r2 = __fmul_rn(rad, rad);
+        float gr = __fsub_rn(__fdiv_rn(opb, rad), __fdiv_rn(b, r2));
+        float gp = __fsub_rn(__fdiv_rn(two_b, __fmul_rn(r2, rad)), __fdiv_rn(opb, r2));
+        float rdot;
+        if (p_inf) {
+          float xm = m == 0 ? x[0] : (m == 1 ? x[1] : x[2]);
+          float dm = m == 0 ? d[0] : (m == 1 ? d[1] : d[2]);
+          rdot = xm < 0.0f ? -dm : dm;
+        } else {
+          rdot = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], d[0]), __fmul_rn(x[1], d[1])),
+                                     __fmul_rn(x[2], d[2])), rad);
+        }
+        float gq = __fmul_rn(gp, rdot);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          xc[a] = __fmul_rn(gr, x[a]);
+          j[a] = __fadd_rn(__fmul_rn(gr, d[a]), __fmul_rn(gq, x[a]));
+        }
+      }
+      float cr;
+      if (p_inf) {
+        cr = fabsf(xc[0]);
+        if (fabsf(xc[1]) > cr) cr = fabsf(xc[1]);
+        if (fabsf(xc[2]) > cr) cr = fabsf(xc[2]);
+      } else {
+        cr = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(xc[0], xc[0]), __fmul_rn(xc[1], xc[1])),
+                                  __fmul_rn(xc[2], xc[2])));
+      }
+      if (!(cr < rmax)) break;
+      if (keep_point(A, mask, xc)) {
+        if (kWrite) {
+          int64_t s = pos + cnt;
+          xyz[3 * s + 0] = xc[0];
+          xyz[3 * s + 1] = xc[1];
+          xyz[3 * s + 2] = xc[2];
+          ray_id[s] = (int32_t)r;
+          step_k[s] = k;
+          s_mid[s] = __fmul_rn(__fadd_rn((float)k, 0.5f), inv_steps);
+          s_len[s] = inv_steps;
+        }
+        ++cnt;
+      }
+      float nj = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(j[0], j[0]), __fmul_rn(j[1], j[1])),
+                                      __fmul_rn(j[2], j[2])));
+      float h = __fdiv_rn(A.s.step_c, nj);
+      if (!(h > 0.0f) || isinf(h)) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(x[a], __fmul_rn(h, d[a]));
+    }
+    if (!kWrite) counts[r] = cnt;
+  }
+}
+
+// Exclusive scan of int32 counts into int64 offsets off[0..n] (one block).
+__global__ void scan_counts_kernel(const int32_t* __restrict__ counts, int64_t n,
+                                   int64_t* __restrict__ off, int64_t* __restrict__ total_out) {
+  __shared__ int64_t warp_tot[32];
+  const int t = threadIdx.x;
+  const int nt = blockDim.x;
+  int64_t chunk = (n + nt - 1) / nt;
+  int64_t b = (int64_t)t * chunk, e = b + chunk;
+  if (b > n) b = n;
+  if (e > n) e = n;
+  int64_t local = 0;
+  for (int64_t i = b; i < e; ++i) local += counts[i];
+  // block exclusive scan of local
+  int lane = t & 31, wid = t >> 5;
+  int64_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = nt >> 5;
+    int64_t v = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < nw) warp_tot[lane] = v;  // inclusive warp totals
+  }
+  __syncthreads();
+  int64_t run = (wid > 0 ? warp_tot[wid - 1] : 0) + incl - local;
+  for (int64_t i = b; i < e; ++i) {
+    off[i] = run;
+    run += counts[i];
+  }
+  if (t == nt - 1) {
+    off[n] = run;
+    if (total_out) *total_out = run;
+  }
+}
+
+// Live list: live_idx[live_off[r] + i] = ray_off[r] + i for i < seg_len[r].
+__global__ void live_fill_kernel(const int64_t* __restrict__ ray_off,
+                                 const int32_t* __restrict__ seg_len, int64_t R,
+                                 const int64_t* __restrict__ live_off, int32_t* __restrict__ live_idx) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < R; r += nwarps) {
+    int64_t b = ray_off[r];
+    int64_t dst = live_off[r];
+    int n = seg_len[r];
+    for (int i = lane; i < n; i += 32) live_idx[dst + i] = (int32_t)(b + i);
+  }
+}
+
+static bool fill_args(SamplerArgs& A, const dvgo_grid_desc* g, const dvgo_sampler_desc* s) {
+  for (int a = 0; a < 3; ++a) {
+    A.lo[a] = g->lo[a];
+    A.hi[a] = g->hi[a];
+    A.G[a] = g->G[a];
+    if (g->G[a] < 2 || !(g->hi[a] > g->lo[a])) return false;
+    // FP32: (float)(G-1) / (hi - lo)
+    volatile float num = (float)(g->G[a] - 1);
+    volatile float den = g->hi[a] - g->lo[a];
+    A.scale[a] = num / den;
+  }
+  A.s = *s;
+  return true;
+}
+
+}  // namespace dvgo
+
+using namespace dvgo;
+
+extern "C" size_t dvgo_sample_rays_workspace_size(int64_t R) {
+  return (size_t)((R + 1) * sizeof(int32_t) + 255) / 256 * 256;
+}
+
+extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
+                                const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
+                                const uint8_t* mask, int64_t S_cap, int64_t* ray_off, float* xyz,
+                                int32_t* ray_id, int32_t* step_k, float* s_mid, float* s_len,
+                                void* ws, size_t ws_bytes, void* stream) {
+  DVGO_CHECK_ARG(grid && smp && ray_off && R >= 0);
+  DVGO_CHECK_ARG(R == 0 || (rays_o && rays_d && xyz && ray_id && step_k && s_mid && s_len && ws));
+  DVGO_CHECK_ARG(smp->mode == 0 || smp->mode == 1);
+  DVGO_CHECK_ARG(smp->max_steps >= 0);
+  if (smp->mode == 0) DVGO_CHECK_ARG(smp->step > 0.0f);
+  if (smp->mode == 1) DVGO_CHECK_ARG(smp->step_c > 0.0f && smp->contract_b > 0.0f);
+  if (S_cap < R * (int64_t)smp->max_steps || S_cap > INT32_MAX) return DVGO_ERR_SHAPE;
+  if (ws_bytes < dvgo_sample_rays_workspace_size(R)) return DVGO_ERR_WORKSPACE;
+  SamplerArgs A;
+  DVGO_CHECK_ARG(fill_args(A, grid, smp));
+  cudaStream_t st = as_stream(stream);
+  if (R == 0) {
+    cudaMemsetAsync(ray_off, 0, sizeof(int64_t), st);
+    return launch_status();
+  }
+  int32_t* counts = reinterpret_cast<int32_t*>(ws);
+  if (smp->mode == 0) {
+    const int block = 256;
+    int g = grid_for(R * 32, block, 16);
+    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
+                                          step_k, s_mid, s_len);
+  } else {
+    const int block = 128;
+    int g = (int)ceil_div(R, block);
+    contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+    contracted_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+                                                 ray_id, step_k, s_mid, s_len);
+  }
+  return launch_status();
+}
+
+extern "C" size_t dvgo_live_samples_workspace_size(int64_t R) {
+  return (size_t)((R + 1) * sizeof(int64_t) + 255) / 256 * 256;
+}
+
+extern "C" int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len, int64_t R,
+                                 int32_t* live_idx, int64_t* live_count, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  DVGO_CHECK_ARG(ray_off && seg_len && live_idx && live_count && ws && R >= 0);
+  if (ws_bytes < dvgo_live_samples_workspace_size(R)) return DVGO_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  if (R == 0) {
+    cudaMemsetAsync(live_count, 0, sizeof(int64_t), st);
+    return launch_status();
+  }
+  int64_t* live_off = reinterpret_cast<int64_t*>(ws);
+  scan_counts_kernel<<<1, 1024, 0, st>>>(seg_len, R, live_off, live_count);
+  live_fill_kernel<<<grid_for(R * 32, 256, 16), 256, 0, st>>>(ray_off, seg_len, R, live_off,
+                                                              live_idx);
+  return launch_status();
+}

@@ -1,0 +1,195 @@
+"""One DVGOv2 training iteration on the GPU, driven through the C ABI.
+
+The order follows the paper's training loop (Sec. 2 listing: zero_grad ->
+loss -> backward -> TV add-grad -> optimizer step) with the rendering
+utilities of Sec. 3:
+
+  forward : sample rays (bbox + occupancy mask, or contracted march) ->
+            density query -> raw->alpha, transmittance, early stop ->
+            live-sample list -> feature query -> colour MLP -> colour
+            accumulation -> distortion loss -> photometric loss
+  backward: distortion grad -> compositing adjoint -> colour-MLP adjoint ->
+            grid scatters -> TV gradient -> sparse Adam (grids) + Adam (MLP)
+
+Only samples in front of the halting point (T >= 1e-3) reach the colour
+MLP: past it every weight and gradient is exactly zero.  Every buffer is
+allocated once here (torch is used for device memory and the stream); the
+step itself reads nothing back to the host.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .synth import RenderParams, SceneConfig
+
+FEAT = 12
+
+
+def alpha_shift(alpha_init: float) -> float:
+    """shift = log(1/(1 - alpha_init) - 1), rounded to FP32 (Sec. 5.3 alpha_init)."""
+    return float(np.float32(math.log(1.0 / (1.0 - alpha_init) - 1.0)))
+
+
+@dataclasses.dataclass
+class GridParam:
+    """A bricked grid parameter with its optimizer state."""
+    C: int
+    p: torch.Tensor            # FP32 master (bricked)
+    g: torch.Tensor            # FP32 gradient (bricked)
+    m: torch.Tensor
+    v: torch.Tensor
+    touched: torch.Tensor      # uint8 per brick
+    shadow: torch.Tensor | None  # BF16 copy read by the renderer (BF16 form)
+
+    @property
+    def render_view(self):
+        return (self.shadow, L.BF16) if self.shadow is not None else (self.p, L.F32)
+
+
+class Trainer:
+    def __init__(self, cfg: SceneConfig, rp: RenderParams, density: np.ndarray,
+                 feature: np.ndarray, mlp_params: np.ndarray, n_rays: int,
+                 precision: str = "f32", device: str = "cuda"):
+        self.cfg, self.rp, self.R = cfg, rp, int(n_rays)
+        self.dev = torch.device(device)
+        self.precision = L.BF16 if precision == "bf16" else L.F32
+        G = [cfg.grid] * 3
+        self.G = G
+        self.gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, G)
+        self.shift = alpha_shift(rp.alpha_init)
+        self.density = self._grid_param(density, 1)
+        self.feature = self._grid_param(feature, FEAT)
+        # colour MLP (flat FP32) and its Adam state
+        self.mlp = torch.tensor(mlp_params, dtype=torch.float32, device=self.dev)
+        self.mlp_g = torch.zeros_like(self.mlp)
+        self.mlp_m = torch.zeros_like(self.mlp)
+        self.mlp_v = torch.zeros_like(self.mlp)
+        # occupancy mask (Sec. 1), built from the initial density
+        self.mask = None
+        if rp.mask_thres is not None:
+            self.mask = torch.empty(G[2], G[1], G[0], dtype=torch.uint8, device=self.dev)
+            grid, dt = self.density.render_view
+            L.build_mask(grid, dt, self.gd, self.shift, rp.interval, rp.mask_thres, self.mask)
+        # sampler
+        sd = L.SamplerDesc()
+        if rp.contracted:
+            sd.mode, sd.near, sd.max_steps = 1, rp.near, rp.max_steps
+            sd.contract_b, sd.p_inf, sd.step_c = rp.contract_b, int(rp.contract_p_inf), rp.step_c
+        else:
+            sd.mode, sd.near, sd.far, sd.step = 0, rp.near, rp.far, rp.step
+            sd.step_offset, sd.use_slab, sd.max_steps = rp.step_offset, int(rp.use_slab), rp.max_steps
+        self.sd = sd
+        self.S_cap = self.R * rp.max_steps
+        self._alloc_step_buffers()
+        self.it = 0
+
+    # ------------------------------------------------------------------ setup
+    def _grid_param(self, dense: np.ndarray, C: int) -> GridParam:
+        G = self.G
+        n = L.grid_bricked_elems(G, C)
+        d = torch.tensor(np.ascontiguousarray(dense, dtype=np.float32), device=self.dev)
+        p = torch.empty(n, dtype=torch.float32, device=self.dev)
+        L.grid_pack(d, p, G, C, L.F32)
+        nb = L.grid_num_bricks(G)
+        shadow = None
+        if self.precision == L.BF16:
+            shadow = torch.empty(n, dtype=torch.bfloat16, device=self.dev)
+            L.grid_pack(d.to(torch.bfloat16), shadow, G, C, L.BF16)
+        return GridParam(C, p, torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p),
+                         torch.zeros(nb, dtype=torch.uint8, device=self.dev), shadow)
+
+    def _alloc_step_buffers(self):
+        S, R, dev = self.S_cap, self.R, self.dev
+        f32 = dict(dtype=torch.float32, device=dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.ray_off = torch.zeros(R + 1, dtype=torch.int64, device=dev)
+        self.xyz = torch.empty(S, 3, **f32)
+        self.ray_id = torch.empty(S, **i32)
+        self.step_k = torch.empty(S, **i32)
+        self.s_mid = torch.empty(S, **f32)
+        self.s_len = torch.empty(S, **f32)
+        self.raw = torch.empty(S, **f32)
+        self.w = torch.empty(S, **f32)
+        self.T = torch.empty(S, **f32)
+        self.n_live = torch.empty(R, **i32)
+        self.T_end = torch.empty(R, **f32)
+        self.live_idx = torch.empty(S, **i32)
+        self.live_count = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.k0 = torch.empty(S, FEAT, **f32)
+        self.rgb = torch.empty(S, 3, **f32)
+        self.color = torch.empty(R, 3, **f32)
+        self.L_r = torch.empty(R, **f32)
+        self.loss = torch.zeros(3, **f32)
+        self.g_color = torch.empty(R, 3, **f32)
+        self.g_w = torch.empty(S, **f32)
+        self.g_raw = torch.empty(S, **f32)
+        self.g_k0 = torch.empty(S, FEAT, **f32)
+        self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
+        self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
+
+    # --------------------------------------------------------------- forward
+    def forward(self, rays_o, rays_d, target):
+        rp, R, S = self.rp, self.R, self.S_cap
+        L.sample_rays(rays_o, rays_d, R, self.gd, self.sd, self.mask, S, self.ray_off, self.xyz,
+                      self.ray_id, self.step_k, self.s_mid, self.s_len, self.ws_sample)
+        S_dev = self.ray_off[R:]
+        dgrid, ddt = self.density.render_view
+        L.sample_grid_fwd(dgrid, ddt, self.gd, 1, self.xyz, None, S, S_dev, self.raw)
+        L.alpha_weights_fwd(self.raw, self.ray_off, R, self.shift, rp.interval, rp.T_stop, self.w,
+                            self.T, self.n_live, self.T_end)
+        L.live_samples(self.ray_off, self.n_live, R, self.live_idx, self.live_count, self.ws_live)
+        fgrid, fdt = self.feature.render_view
+        L.sample_grid_fwd(fgrid, fdt, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,
+                          self.k0)
+        L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
+                     self.precision, self.rgb)
+        L.composite_rgb_fwd(self.w, self.rgb, self.ray_off, self.n_live, self.T_end, R, rp.bg,
+                            self.color)
+        L.distortion_fwd(self.w, self.s_mid, self.s_len, self.ray_off, self.n_live, R, self.L_r)
+        L.rgb_loss(self.color, target, self.L_r, R, rp.lambda_dist, self.loss, self.g_color)
+
+    # -------------------------------------------------------------- backward
+    def backward(self, rays_d):
+        rp, R, S = self.rp, self.R, self.S_cap
+        L.distortion_bwd(None, rp.lambda_dist / R, self.w, self.s_mid, self.s_len, self.ray_off,
+                         self.n_live, R, self.g_w)
+        L.composite_bwd(self.g_color, self.g_w, self.raw, self.T, self.rgb, self.ray_off,
+                        self.n_live, R, self.shift, rp.interval, rp.bg, self.g_raw)
+        L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.live_idx, S,
+                     self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0)
+        L.sample_grid_bwd(self.g_raw, self.gd, 1, self.xyz, self.live_idx, S, self.live_count,
+                          self.density.g, self.density.touched)
+        L.sample_grid_bwd(self.g_k0, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,
+                          self.feature.g, self.feature.touched)
+
+    # ----------------------------------------------------------- optimizer
+    def regularize_and_step(self, tv_dense: bool):
+        rp = self.rp
+        self.it += 1
+        for gp, tvw in ((self.density, rp.tv_w_density), (self.feature, rp.tv_w_feature)):
+            if tvw > 0:
+                grid, dt = gp.render_view
+                L.tv_add_grad(grid, dt, self.G, gp.C, tvw, rp.tv_delta, tv_dense, gp.touched, gp.g)
+            L.adam_step(gp.p, gp.shadow, gp.g, gp.m, gp.v, gp.p.numel(), gp.touched,
+                        512 * gp.C, rp.lr_grid, rp.beta1, rp.beta2, rp.eps, self.it, True)
+        L.adam_step(self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
+                    rp.lr_mlp, rp.beta1, rp.beta2, rp.eps, self.it, True)
+
+    def step(self, rays_o, rays_d, target, tv_dense: bool = False):
+        """One full training iteration; returns the device loss tensor [3]."""
+        self.forward(rays_o, rays_d, target)
+        self.backward(rays_d)
+        self.regularize_and_step(tv_dense)
+        return self.loss
+
+    # ------------------------------------------------------------- helpers
+    def dense(self, gp: GridParam, which: str = "p") -> torch.Tensor:
+        src = getattr(gp, which)
+        out = torch.empty(self.G[2], self.G[1], self.G[0], gp.C, dtype=src.dtype, device=self.dev)
+        L.grid_unpack(src, out, self.G, gp.C, L.BF16 if src.dtype == torch.bfloat16 else L.F32)
+        return out

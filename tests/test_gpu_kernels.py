@@ -1,0 +1,426 @@
+"""GPU parity of each C-ABI kernel against the FP64 oracle on seeded inputs.
+
+Tolerances: integer/index outputs bit-exact; FP32 form 1e-5 relative
+(max|x - ref| / max|ref| per tensor); BF16 form 2e-3 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import rel_err
+from paper_2206_05085_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2206_05085_gb300 import build
+    build.build()
+    from paper_2206_05085_gb300 import _lib
+    _lib.lib()
+    return _lib
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def shift32():
+    return float(np.float32(oracle.alpha_shift(1e-4)))
+
+
+# ----------------------------------------------------------------- grids
+@pytest.mark.parametrize("G,C", [((16, 16, 16), 1), ((19, 9, 13), 12), ((8, 24, 17), 5)])
+def test_pack_unpack_roundtrip(L, G, C):
+    rng = np.random.default_rng(0)
+    dense = rng.normal(size=(G[2], G[1], G[0], C)).astype(np.float32)
+    for dt, tdt in ((L.F32, torch.float32), (L.BF16, torch.bfloat16)):
+        d = dev(dense).to(tdt)
+        b = torch.empty(L.grid_bricked_elems(G, C), dtype=tdt, device="cuda")
+        L.grid_pack(d, b, G, C, dt)
+        back = torch.empty_like(d)
+        L.grid_unpack(b, back, G, C, dt)
+        assert torch.equal(back, d)
+
+
+def _bricked(L, dense, G, C, dtype=torch.float32):
+    b = torch.empty(L.grid_bricked_elems(G, C), dtype=dtype, device="cuda")
+    L.grid_pack(dev(dense).to(dtype), b, G, C, L.BF16 if dtype == torch.bfloat16 else L.F32)
+    return b
+
+
+@pytest.mark.parametrize("C", [1, 12, 5])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_trilinear_fwd_bwd(L, C, bf16):
+    rng = np.random.default_rng(C)
+    G = (21, 18, 26)
+    lo, hi = np.array([-1.0, -0.5, -2.0]), np.array([1.0, 1.5, 2.0])
+    dense = rng.normal(size=(G[2], G[1], G[0], C)).astype(np.float32)
+    if bf16:
+        dense = synth.bf16_round(dense)
+    n = 10000
+    xyz = (lo + (hi - lo) * rng.uniform(-0.02, 1.02, (n, 3))).astype(np.float32)  # some clamp
+    gd = L.GridDesc.make(lo, hi, G)
+    grid = _bricked(L, dense, G, C, torch.bfloat16 if bf16 else torch.float32)
+    out = torch.full((n, C), -7.0, device="cuda")
+    # subset through idx, count on the device
+    idx = np.sort(rng.choice(n, 6000, replace=False)).astype(np.int32)
+    n_dev = torch.tensor([5000], dtype=torch.int64, device="cuda")
+    L.sample_grid_fwd(grid, L.BF16 if bf16 else L.F32, gd, C, dev(xyz), dev(idx), len(idx), n_dev, out)
+    got = host(out)
+    ref = oracle.trilinear(dense.reshape(G[2], G[1], G[0], C), lo, hi, xyz)
+    sel = idx[:5000]
+    assert rel_err(got[sel], ref[sel]) < TOL32
+    untouched = np.setdiff1d(np.arange(n), sel)
+    assert np.all(got[untouched] == -7.0)
+    # adjoint
+    g_out = rng.normal(size=(n, C)).astype(np.float32)
+    g_grid = torch.zeros(L.grid_bricked_elems(G, C), device="cuda")
+    touched = torch.zeros(L.grid_num_bricks(G), dtype=torch.uint8, device="cuda")
+    L.sample_grid_bwd(dev(g_out), gd, C, dev(xyz), dev(idx), len(idx), n_dev, g_grid, touched)
+    gg = torch.empty(G[2], G[1], G[0], C, device="cuda")
+    L.grid_unpack(g_grid, gg, G, C, L.F32)
+    ref_g = oracle.trilinear_adjoint(g_out[sel], (G[2], G[1], G[0], C), lo, hi, xyz[sel])
+    assert rel_err(host(gg), ref_g) < TOL32
+    # touched bricks = bricks holding a nonzero adjoint entry (or none)
+    nz = np.abs(ref_g).sum(-1) > 0
+    nb = [(g + 7) // 8 for g in G]
+    tb = np.zeros((nb[2], nb[1], nb[0]), bool)
+    zz, yy, xx = np.nonzero(nz)
+    tb[zz // 8, yy // 8, xx // 8] = True
+    got_t = host(touched).reshape(nb[2], nb[1], nb[0]).astype(bool)
+    assert np.all(got_t[tb])
+
+
+def test_build_mask_bit_exact(L):
+    cfg = synth.CFG2
+    D = synth.density_grid(cfg)
+    G = [cfg.grid] * 3
+    gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, G)
+    m = torch.empty(G[2], G[1], G[0], dtype=torch.uint8, device="cuda")
+    L.build_mask(_bricked(L, D, G, 1), L.F32, gd, shift32(), 0.5, 1e-4, m)
+    ref = oracle.build_mask(D, shift32(), 0.5, 1e-4)
+    assert np.array_equal(host(m), ref)
+
+
+# --------------------------------------------------------------- sampler
+def _gpu_sample(L, cfg, rp, o, d, mask=None):
+    R = o.shape[0]
+    S_cap = R * rp.max_steps
+    gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, [cfg.grid] * 3)
+    sd = L.SamplerDesc()
+    if rp.contracted:
+        sd.mode, sd.near, sd.max_steps = 1, rp.near, rp.max_steps
+        sd.contract_b, sd.p_inf, sd.step_c = rp.contract_b, int(rp.contract_p_inf), rp.step_c
+    else:
+        sd.mode, sd.near, sd.far, sd.step = 0, rp.near, rp.far, rp.step
+        sd.step_offset, sd.use_slab, sd.max_steps = rp.step_offset, int(rp.use_slab), rp.max_steps
+    out = dict(ray_off=torch.zeros(R + 1, dtype=torch.int64, device="cuda"),
+               xyz=torch.empty(S_cap, 3, device="cuda"),
+               ray_id=torch.empty(S_cap, dtype=torch.int32, device="cuda"),
+               step_k=torch.empty(S_cap, dtype=torch.int32, device="cuda"),
+               s_mid=torch.empty(S_cap, device="cuda"), s_len=torch.empty(S_cap, device="cuda"))
+    ws = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device="cuda")
+    L.sample_rays(dev(o), dev(d), R, gd, sd, mask, S_cap, out["ray_off"], out["xyz"],
+                  out["ray_id"], out["step_k"], out["s_mid"], out["s_len"], ws)
+    res = {k: host(v) for k, v in out.items()}
+    S = int(res["ray_off"][-1])
+    for k in ("xyz", "ray_id", "step_k", "s_mid", "s_len"):
+        res[k] = res[k][:S]
+    return res
+
+
+def _check_samples(got, ref):
+    assert np.array_equal(got["ray_off"], ref.ray_off)
+    assert np.array_equal(got["ray_id"], ref.ray_id)
+    assert np.array_equal(got["step_k"], ref.step_k)
+    assert np.array_equal(got["xyz"], ref.xyz)          # FP32 positions bit for bit
+    assert rel_err(got["s_mid"], ref.s_mid) < TOL32
+    assert rel_err(got["s_len"], ref.s_len) < TOL32
+
+
+@pytest.mark.parametrize("name", ["small_64", "dvgo_160", "unbounded_320"])
+def test_sampler_bit_exact(L, name):
+    cfg = synth.CONFIGS[name]
+    rp = synth.render_params(cfg)
+    o, d = synth.rays(cfg)            # full ray count of the workload
+    mask_np = mask_t = None
+    if rp.mask_thres is not None:
+        D = synth.density_grid(cfg)
+        mask_np = oracle.build_mask(D, shift32(), rp.interval, rp.mask_thres)
+        mask_t = dev(mask_np)
+    got = _gpu_sample(L, cfg, rp, o, d, mask_t)
+    from oracle_step import sample
+    ref = sample(cfg, rp, o, d, mask_np)
+    assert ref.S > 0
+    _check_samples(got, ref)
+
+
+def test_sampler_edge_cases(L):
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    # rays that miss the box, start inside it, run along an axis, zero components
+    o = np.array([[-4, 3, 0], [0.1, 0.2, 0.3], [-4, 0, 0], [0, -4, 0.5], [4, 4, 4]], np.float32)
+    d = np.array([[1, 0, 0], [0, 0, 1], [1, 0, 0], [0, 1, 0], [-1, -1, -1]], np.float32)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = _gpu_sample(L, cfg, rp, o, d)
+    from oracle_step import sample
+    ref = sample(cfg, rp, o, d, None)
+    _check_samples(got, ref)
+    assert got["ray_off"][1] == 0
+    # empty ray batch
+    got0 = _gpu_sample(L, cfg, rp, o[:0], d[:0])
+    assert got0["ray_off"].tolist() == [0]
+
+
+# ------------------------------------------------------------- rendering
+def _ragged_case(seed, counts, scale=3.0, bias=8.0):
+    rng = np.random.default_rng(seed)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(off[-1])
+    raw = (rng.normal(0, scale, S) + bias).astype(np.float32)
+    rgb = rng.uniform(0, 1, (S, 3)).astype(np.float32)
+    return off, raw, rgb
+
+
+COUNTS = [0, 1, 2, 31, 32, 33, 64, 100, 300, 559] + list(np.random.default_rng(9).integers(0, 260, 500))
+
+
+@pytest.mark.parametrize("T_stop", [1e-3, 0.0])
+def test_alpha_weights_and_composite(L, T_stop):
+    off, raw, rgb = _ragged_case(1, COUNTS)
+    R, S = len(off) - 1, int(off[-1])
+    bg = np.array([1.0, 0.5, 0.25], np.float32)
+    sh = shift32()
+    w, T = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+    n_live = torch.empty(R, dtype=torch.int32, device="cuda")
+    T_end = torch.empty(R, device="cuda")
+    L.alpha_weights_fwd(dev(raw), dev(off), R, sh, 0.5, T_stop, w, T, n_live, T_end)
+    color = torch.empty(R, 3, device="cuda")
+    L.composite_rgb_fwd(w, dev(rgb), dev(off), n_live, T_end, R, bg, color)
+    ref = oracle.composite(raw, rgb, off, sh, 0.5, T_stop, bg)
+    nl = host(n_live)
+    # halting index: exact except where T sits on the threshold within FP32 rounding
+    diff = np.nonzero(nl != ref["n_live"])[0]
+    for r in diff:
+        k = min(nl[r], ref["n_live"][r])
+        assert abs(ref["T"][off[r] + k] / T_stop - 1) < 1e-5, (r, nl[r], ref["n_live"][r])
+    ok = np.setdiff1d(np.arange(R), diff)
+    okS = np.concatenate([np.arange(off[r], off[r + 1]) for r in ok])
+    assert rel_err(host(w)[okS], ref["w"][okS]) < TOL32
+    assert rel_err(host(T)[okS], ref["T"][okS]) < TOL32
+    assert rel_err(host(T_end)[ok], ref["T_end"][ok]) < TOL32
+    assert rel_err(host(color)[ok], ref["color"][ok]) < TOL32
+    assert (nl < np.diff(off)).sum() > 10 or T_stop == 0.0
+
+
+def test_composite_backward(L):
+    off, raw, rgb = _ragged_case(2, COUNTS, scale=2.0, bias=7.0)
+    R, S = len(off) - 1, int(off[-1])
+    bg = np.array([0.2, 0.9, 0.4], np.float32)
+    sh = shift32()
+    rng = np.random.default_rng(3)
+    g_color = rng.normal(size=(R, 3)).astype(np.float32)
+    g_w = rng.normal(size=S).astype(np.float32)
+    for T_stop in (1e-3, 0.0):
+        w, T = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+        n_live = torch.empty(R, dtype=torch.int32, device="cuda")
+        T_end = torch.empty(R, device="cuda")
+        L.alpha_weights_fwd(dev(raw), dev(off), R, sh, 0.5, T_stop, w, T, n_live, T_end)
+        g_raw = torch.empty(S, device="cuda")
+        g_rgb = torch.empty(S, 3, device="cuda")
+        L.composite_bwd(dev(g_color), dev(g_w), dev(raw), T, dev(rgb), dev(off), n_live, R, sh,
+                        0.5, bg, g_raw, g_rgb)
+        ref = oracle.composite(raw, rgb, off, sh, 0.5, T_stop, bg)
+        assert np.array_equal(host(n_live), ref["n_live"])
+        gr, gc = oracle.composite_bwd(raw, rgb, off, sh, 0.5, T_stop, bg, g_color, g_w)
+        assert rel_err(host(g_raw), gr) < TOL32
+        assert rel_err(host(g_rgb), gc) < TOL32
+
+
+def test_distortion(L):
+    rng = np.random.default_rng(4)
+    counts = COUNTS
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    R, S = len(counts), int(off[-1])
+    w = rng.uniform(0, 0.05, S).astype(np.float32)
+    m = np.zeros(S, np.float32)
+    for r in range(R):
+        m[off[r]:off[r + 1]] = np.sort(rng.uniform(0, 1, counts[r]))
+    ds = rng.uniform(0.001, 0.01, S).astype(np.float32)
+    seg = np.array([min(c, int(rng.integers(0, c + 1))) if r % 3 == 0 else c
+                    for r, c in enumerate(counts)], np.int32)
+    for seg_len in (None, seg):
+        L_r = torch.empty(R, device="cuda")
+        sl = None if seg_len is None else dev(seg_len)
+        L.distortion_fwd(dev(w), dev(m), dev(ds), dev(off), sl, R, L_r)
+        ref = oracle.distortion(w, m, ds, off, seg_len)
+        assert rel_err(host(L_r), ref) < TOL32
+        gL = rng.normal(size=R).astype(np.float32)
+        g_w = torch.full((S,), 9.0, device="cuda")
+        L.distortion_bwd(dev(gL), 0.0, dev(w), dev(m), dev(ds), dev(off), sl, R, g_w)
+        assert rel_err(host(g_w), oracle.distortion_grad(gL, w, m, ds, off, seg_len)) < TOL32
+        L.distortion_bwd(None, 0.25, dev(w), dev(m), dev(ds), dev(off), sl, R, g_w)
+        assert rel_err(host(g_w), oracle.distortion_grad(0.25, w, m, ds, off, seg_len)) < TOL32
+
+
+def test_rgb_loss(L):
+    rng = np.random.default_rng(5)
+    R = 3000
+    color = rng.uniform(0, 1, (R, 3)).astype(np.float32)
+    target = rng.uniform(0, 1, (R, 3)).astype(np.float32)
+    L_r = rng.uniform(0, 0.1, R).astype(np.float32)
+    loss = torch.empty(3, device="cuda")
+    g = torch.empty(R, 3, device="cuda")
+    L.rgb_loss(dev(color), dev(target), dev(L_r), R, 0.01, loss, g)
+    c64, t64 = color.astype(np.float64), target.astype(np.float64)
+    ref = np.mean((c64 - t64) ** 2)
+    got = host(loss)
+    assert abs(got[0] - ref) / ref < TOL32
+    assert abs(got[1] - L_r.astype(np.float64).mean()) / L_r.mean() < TOL32
+    assert abs(got[2] - (ref + 0.01 * L_r.astype(np.float64).mean())) / ref < TOL32
+    assert rel_err(host(g), 2 * (c64 - t64) / (3 * R)) < TOL32
+
+
+# ------------------------------------------------------------ colour MLP
+def _mlp_case(n, seed=6):
+    rng = np.random.default_rng(seed)
+    k0 = rng.normal(0, 0.3, (n, 12)).astype(np.float32)
+    R = 97
+    d = rng.normal(size=(R, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    ray_id = rng.integers(0, R, n).astype(np.int32)
+    params = synth.mlp_params()
+    params = (params * 2.0).astype(np.float32)   # larger activations than init
+    g_rgb = rng.normal(size=(n, 3)).astype(np.float32)
+    return k0, d, ray_id, params, g_rgb
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 5000])
+def test_rgbnet_fwd_bwd(L, precision, n):
+    k0, d, ray_id, params, g_rgb = _mlp_case(n)
+    prec = L.BF16 if precision == "bf16" else L.F32
+    tol = TOL16 if precision == "bf16" else TOL32
+    p_ref = synth.bf16_round(params) if precision == "bf16" else params
+    # every other sample through idx, count on the device
+    idx = np.arange(0, n, 2 if n > 2 else 1).astype(np.int32)
+    m = len(idx)
+    rgb = torch.full((n, 3), -1.0, device="cuda")
+    n_dev = torch.tensor([m], dtype=torch.int64, device="cuda")
+    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb)
+    x = oracle.rgbnet_input(k0[idx], d[ray_id[idx]])
+    ref = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True)
+    got = host(rgb)
+    assert rel_err(got[idx], ref) < tol
+    rest = np.setdiff1d(np.arange(n), idx)
+    assert np.all(got[rest] == -1.0)
+    g_params = torch.zeros(len(params), device="cuda")
+    g_k0 = torch.zeros(n, 12, device="cuda")
+    L.rgbnet_bwd(dev(g_rgb), None, None, dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev,
+                 dev(params), prec, g_params, g_k0)
+    gp, gx = oracle.mlp_bwd(synth.RGBNET_DIMS, p_ref, x, g_rgb[idx], True)
+    gpg = host(g_params)
+    offs = np.cumsum([0, 128 * 39, 128, 128 * 128, 128, 3 * 128, 3])
+    for a, b in zip(offs[:-1], offs[1:]):     # each weight / bias tensor separately
+        assert rel_err(gpg[a:b], gp[a:b]) < tol, (a, b, rel_err(gpg[a:b], gp[a:b]))
+    assert rel_err(host(g_k0)[idx], gx[:, :12]) < tol
+
+
+def test_rgbnet_bwd_from_compositing_gradient(L):
+    # upstream colour gradient formed in-kernel as w[s] * g_color[ray_id[s]]
+    n = 3000
+    k0, d, ray_id, params, _ = _mlp_case(n, 8)
+    rng = np.random.default_rng(8)
+    w = rng.uniform(0, 1, n).astype(np.float32)
+    g_color = rng.normal(size=(d.shape[0], 3)).astype(np.float32)
+    g_params = torch.zeros(len(params), device="cuda")
+    g_k0 = torch.zeros(n, 12, device="cuda")
+    L.rgbnet_bwd(None, dev(g_color), dev(w), dev(k0), dev(d), dev(ray_id), None, n, None,
+                 dev(params), L.F32, g_params, g_k0)
+    x = oracle.rgbnet_input(k0, d[ray_id])
+    gp, gx = oracle.mlp_bwd(synth.RGBNET_DIMS, params, x, w[:, None] * g_color[ray_id], True)
+    assert rel_err(host(g_params), gp) < TOL32
+    assert rel_err(host(g_k0), gx[:, :12]) < TOL32
+
+
+# --------------------------------------------------------- TV and Adam
+@pytest.mark.parametrize("C", [1, 12])
+@pytest.mark.parametrize("dense_mode", [True, False])
+def test_tv_add_grad(L, C, dense_mode):
+    rng = np.random.default_rng(10 + C)
+    G = (20, 17, 11)
+    grid = rng.normal(0, 1.2, (G[2], G[1], G[0], C)).astype(np.float32)
+    g0 = np.where(rng.uniform(size=grid.shape) < 0.2, rng.normal(size=grid.shape), 0.0).astype(np.float32)
+    gb = _bricked(L, g0, G, C)
+    touched = torch.zeros(L.grid_num_bricks(G), dtype=torch.uint8, device="cuda")
+    if not dense_mode:
+        nb = [(g + 7) // 8 for g in G]
+        t = np.zeros((nb[2], nb[1], nb[0]), np.uint8)
+        zz, yy, xx = np.nonzero(np.abs(g0).sum(-1) > 0)
+        t[zz // 8, yy // 8, xx // 8] = 1
+        touched = dev(t.reshape(-1))
+    L.tv_add_grad(_bricked(L, grid, G, C), L.F32, G, C, 0.5, 1.0, dense_mode, touched, gb)
+    out = torch.empty(G[2], G[1], G[0], C, device="cuda")
+    L.grid_unpack(gb, out, G, C, L.F32)
+    ref = oracle.tv_add_grad(grid, g0, 0.5, 1.0, dense_mode)
+    assert rel_err(host(out), ref) < TOL32
+    if dense_mode:
+        assert np.all(host(touched) == 1)
+
+
+@pytest.mark.parametrize("sparse", [True, False])
+def test_adam_step(L, sparse):
+    rng = np.random.default_rng(11)
+    C, nb = 12, 40
+    n = nb * 512 * C
+    p = rng.normal(size=n).astype(np.float32)
+    m = rng.normal(0, 0.1, n).astype(np.float32)
+    v = rng.uniform(0, 0.1, n).astype(np.float32)
+    g = np.zeros(n, np.float32)
+    flags = (rng.uniform(size=nb) < 0.5).astype(np.uint8)
+    for b in np.nonzero(flags)[0]:
+        blk = slice(b * 512 * C, (b + 1) * 512 * C)
+        g[blk] = np.where(rng.uniform(size=512 * C) < 0.7, rng.normal(size=512 * C), 0.0)
+    tp, tg, tm, tv = dev(p), dev(g), dev(m), dev(v)
+    sh = torch.zeros(n, dtype=torch.bfloat16, device="cuda")
+    touched = dev(flags) if sparse else None
+    L.adam_step(tp, sh, tg, tm, tv, n, touched, 512 * C, 0.1, 0.9, 0.99, 1e-15, 7, True)
+    rp, rm, rv = oracle.adam(p, g, m, v, 0.1, 0.9, 0.99, 1e-15, 7)
+    assert rel_err(host(tp), rp) < TOL32
+    assert rel_err(host(tm), rm) < TOL32
+    assert rel_err(host(tv), rv) < TOL32
+    z = g == 0
+    assert np.array_equal(host(tp)[z], p[z])          # skipped entries bit-unchanged
+    assert np.all(host(tg) == 0)
+    upd = ~z
+    assert np.array_equal(host(sh.float())[upd], synth.bf16_round(host(tp))[upd])
+    if sparse:
+        assert np.all(host(touched) == 0)
+    # odd-length flat vector (MLP parameters)
+    q = rng.normal(size=22019).astype(np.float32)
+    gq = rng.normal(size=22019).astype(np.float32)
+    tq, tgq = dev(q), dev(gq)
+    tmq, tvq = torch.zeros_like(tq), torch.zeros_like(tq)
+    L.adam_step(tq, None, tgq, tmq, tvq, 22019, None, 0, 1e-3, 0.9, 0.99, 1e-15, 1, True)
+    rq, _, _ = oracle.adam(q, gq, np.zeros(22019), np.zeros(22019), 1e-3, 0.9, 0.99, 1e-15, 1)
+    assert rel_err(host(tq), rq) < TOL32
+
+
+def test_invalid_arguments_raise(L):
+    with pytest.raises(L.DvgoError):
+        L.distortion_fwd(None, None, None, None, None, 5, None)
+    with pytest.raises(L.DvgoError):
+        L.rgbnet_fwd(None, None, None, None, 10, None, None, 7, None)
+    assert L.device_status() == 0
