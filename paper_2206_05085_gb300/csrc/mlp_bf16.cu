@@ -39,6 +39,10 @@ constexpr uint32_t kOffH1s = kOffXs + kTile * kK1 * 2;      // 57344
 constexpr uint32_t kFwdOperandBytes = kOffH1s + kTile * kHid * 2;      // 90112
 constexpr uint32_t kOffG2s = kOffH1s + kTile * kH1W * 2;    // 94208
 constexpr uint32_t kBwdOperandBytes = kOffG2s + kTile * kHid * 2;      // 126976
+// The backward reserves shared memory past its operands so that an MN-major
+// descriptor read with its two strides exchanged (16 MN groups x 2048 B from
+// the last K step of G2) would still stay inside the CTA's allocation.
+constexpr uint32_t kBwdSmemBytes = 160 * 1024;
 
 struct F32Side {  // epilogue constants (BF16-rounded values, kept in FP32)
   float W3[kOut * kHid];
@@ -257,6 +261,7 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_bf16_kernel(
     const float* __restrict__ params, float* __restrict__ g_params, float* __restrict__ g_k0) {
   extern __shared__ __align__(1024) uint8_t sm[];
   F32Side* fs = reinterpret_cast<F32Side*>(sm + kBwdOperandBytes);
+  static_assert(kBwdOperandBytes + sizeof(F32Side) <= kBwdSmemBytes, "smem");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -367,15 +372,15 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_bf16_kernel(
       const uint32_t id_dw2 = tc::idesc_bf16(128, kH1W, 1, 1);
 #pragma unroll
       for (int k = 0; k < kTile / 16; ++k)
-        tc::mma_bf16(tmem + cDW2, tc::smem_desc(sm_g + k * 2 * kSboH, 128, kSboH),
-                     tc::smem_desc(sm_h1 + k * 2 * kSboH1b, 128, kSboH1b), id_dw2,
+        tc::mma_bf16(tmem + cDW2, tc::smem_desc_mn(sm_g + k * 2 * kSboH, kSboH, 128),
+                     tc::smem_desc_mn(sm_h1 + k * 2 * kSboH1b, kSboH1b, 128), id_dw2,
                      (it > 0 || k > 0) ? 1u : 0u);
       // g_h1 = G2 W2: M = s, N = i, K = o; A K-major, B (W2 stored [o][i]) MN-major
       const uint32_t id_gh = tc::idesc_bf16(128, 128, 0, 1);
 #pragma unroll
       for (int k = 0; k < kHid / 16; ++k)
         tc::mma_bf16(tmem + cD1, tc::smem_desc(sm_g + k * 256, 128, kSboH),
-                     tc::smem_desc(sm_w2 + k * 2 * kSboH, 128, kSboH), id_gh, k > 0);
+                     tc::smem_desc_mn(sm_w2 + k * 2 * kSboH, kSboH, 128), id_gh, k > 0);
       tc::mma_commit(&fs->bar);
     }
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
@@ -405,15 +410,15 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_bf16_kernel(
       const uint32_t id_dw1 = tc::idesc_bf16(128, kK1, 1, 1);
 #pragma unroll
       for (int k = 0; k < kTile / 16; ++k)
-        tc::mma_bf16(tmem + cDW1, tc::smem_desc(sm_g + k * 2 * kSboH, 128, kSboH),
-                     tc::smem_desc(sm_x + k * 2 * kSboX, 128, kSboX), id_dw1,
+        tc::mma_bf16(tmem + cDW1, tc::smem_desc_mn(sm_g + k * 2 * kSboH, kSboH, 128),
+                     tc::smem_desc_mn(sm_x + k * 2 * kSboX, kSboX, 128), id_dw1,
                      (it > 0 || k > 0) ? 1u : 0u);
       // g_X[:, 0:16] = G1 W1: M = s, N = 16, K = o; A K-major, B (W1 stored [o][in]) MN-major
       const uint32_t id_gx = tc::idesc_bf16(128, 16, 0, 1);
 #pragma unroll
       for (int k = 0; k < kHid / 16; ++k)
         tc::mma_bf16(tmem + cD2, tc::smem_desc(sm_g + k * 256, 128, kSboH),
-                     tc::smem_desc(sm_w1 + k * 2 * kSboX, 128, kSboX), id_gx, k > 0);
+                     tc::smem_desc_mn(sm_w1 + k * 2 * kSboX, kSboX, 128), id_gx, k > 0);
       tc::mma_commit(&fs->bar);
     }
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
@@ -497,7 +502,7 @@ int dvgo_rgbnet_bwd_bf16(const float* g_rgb, const float* g_color, const float* 
                          const float* rays_d, const int32_t* ray_id, const int32_t* idx,
                          int64_t n_cap, const int64_t* n_dev, const float* params,
                          float* g_params, float* g_k0, cudaStream_t st) {
-  const size_t smem = kBwdOperandBytes + sizeof(F32Side);
+  const size_t smem = kBwdSmemBytes;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(rgbnet_bwd_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

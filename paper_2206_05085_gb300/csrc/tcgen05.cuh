@@ -63,11 +63,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 
 // ---------------------------------------------------------- descriptors
 // Shared-memory matrix descriptor, no swizzle.  Canonical layout built from
-// 8 x 16-byte "core matrices" (128 contiguous bytes each).  lbo: byte stride
-// between core matrices adjacent in the leading dimension (K for K-major
-// operands, M/N for MN-major ones); sbo: byte stride between core matrices
-// adjacent in the other dimension.  Bits 46-47 hold the sm_100 descriptor
-// version (1); layout type 0 = no swizzle.
+// 8 x 16-byte "core matrices" (128 contiguous bytes each).  For a K-major
+// operand, lbo is the byte stride between core matrices adjacent in K and
+// sbo the stride between 8-row groups in M/N.  Bits 46-47 hold the sm_100
+// descriptor version (1); layout type 0 = no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -75,6 +74,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
   return d;
+}
+
+// MN-major operand, no swizzle: the leading-dimension field carries the
+// stride between core matrices adjacent in K and the stride field the one
+// between core matrices adjacent in M/N (for this layout type the two fields
+// keep their K / MN meaning of the K-major case).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t k_stride,
+                                                 uint32_t mn_stride) {
+  return smem_desc(saddr, k_stride, mn_stride);
 }
 
 // Instruction descriptor of tcgen05.mma .kind::f16 with BF16 A/B and FP32

@@ -27,3 +27,34 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def check_mlp_grads(orc, dims, params, x, g_out, gpu_gp, gpu_gx, tol, q_bf16):
+    """Compare MLP parameter / input gradients with the oracle.
+
+    A sample whose smallest ReLU input is within rounding of 0 (tau) can
+    switch a unit in one precision and not in the other; its share of the
+    parameter gradient is allowed as slack (twice its magnitude) and its
+    input-gradient row is not compared.  Returns the number of such samples.
+    """
+    import numpy as np
+    tau = 1e-5 if q_bf16 else 1e-6
+    zmin = orc.mlp_min_abs_preact(dims, params, x, q_bf16)
+    amb = np.nonzero(zmin < tau)[0]
+    gp, gx = orc.mlp_bwd(dims, params, x, g_out, True, q_bf16)
+    slack = np.zeros_like(gp)
+    for s in amb:
+        gps, _ = orc.mlp_bwd(dims, params, x[s:s + 1], g_out[s:s + 1], True, q_bf16)
+        slack += 2 * np.abs(gps)
+    offs = [0]
+    for i in range(len(dims) - 1):
+        offs += [offs[-1] + dims[i + 1] * dims[i], offs[-1] + dims[i + 1] * dims[i] + dims[i + 1]]
+    for a, b in zip(offs[:-1], offs[1:]):
+        err = np.abs(np.asarray(gpu_gp[a:b], np.float64) - gp[a:b])
+        lim = tol * max(np.max(np.abs(gp[a:b])), 1e-30) + slack[a:b]
+        assert np.all(err <= lim), (a, b, float(np.max(err - lim)), float(np.max(np.abs(gp[a:b]))))
+    if gpu_gx is not None:
+        keep = np.ones(x.shape[0], bool)
+        keep[amb] = False
+        assert rel_err(np.asarray(gpu_gx)[keep], gx[keep][:, :np.asarray(gpu_gx).shape[1]]) < tol
+    return len(amb)

@@ -51,52 +51,91 @@ def _run(T, cfg, n_rays, precision, tv_dense, ray_stride=1):
     Fr = synth.bf16_round(Fg) if bf else Fg
     Pr = synth.bf16_round(P) if bf else P
     fb = forward_backward(cfg, rp, Dr, Fr, Pr, o, d, tgt, bf16=bf)
+    fb["density0"], fb["feature0"], fb["params0"] = D, Fg, P
     opt = optimizer(rp, 1, D, Fg, P, fb, tv_dense, Dr, Fr)
-    return gpu, fb, opt
+    return gpu, fb, opt, cfg, rp, Pr
 
 
-def _compare(gpu, fb, opt, tol):
+def _cell_voxels(cfg, xyz):
+    """Dense indices (z, y, x) of the 8 corners of each point's trilinear cell."""
+    u = (xyz.astype(np.float64) - cfg.bbox_min) / (cfg.bbox_max - cfg.bbox_min) * (cfg.grid - 1)
+    i0 = np.clip(np.floor(np.clip(u, 0, cfg.grid - 1)).astype(int), 0, cfg.grid - 2)
+    out = []
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                out.append(np.stack([i0[:, 2] + dz, i0[:, 1] + dy, i0[:, 0] + dx], 1))
+    return np.concatenate(out, 0)
+
+
+def _compare(gpu, fb, opt, tol, cfg, rp, params, bf16=False):
+    import oracle
     assert gpu["S"] == fb["smp"].S
     bad = np.nonzero(gpu["n_live"] != fb["n_live"])[0]
     assert len(bad) == 0, f"halting index differs on rays {bad[:10]}"
     assert rel_err(gpu["color"], fb["color"]) < tol
     assert rel_err(gpu["loss"], fb["loss"]) < tol
     assert rel_err(gpu["g_density"], fb["g_density"]) < tol
-    assert rel_err(gpu["g_feature"], fb["g_feature"].reshape(gpu["g_feature"].shape)) < tol
-    offs = np.cumsum([0, 128 * 39, 128, 128 * 128, 128, 3 * 128, 3])
-    for a, b in zip(offs[:-1], offs[1:]):
-        assert rel_err(gpu["g_mlp"][a:b], fb["g_params"][a:b]) < tol, (a, b)
-    # parameters after TV + Adam (first step: the update is lr * sign-like)
-    assert rel_err(gpu["density"], opt["density"]) < tol
-    assert rel_err(gpu["feature"], opt["feature"].reshape(gpu["feature"].shape)) < tol
-    assert rel_err(gpu["params"], opt["params"]) < tol
+    from conftest import check_mlp_grads
+    check_mlp_grads(oracle, synth.RGBNET_DIMS, params.astype(np.float64), fb["x"],
+                    fb["g_rgb"][fb["live"]], gpu["g_mlp"], None, tol, bf16)
+    # Feature-grid gradient: a sample whose ReLU input sits within rounding of
+    # 0 may switch that unit on in one precision and off in the other; the
+    # voxels of such samples are compared separately (bounded, counted).
+    tau = 1e-5 if bf16 else 1e-6
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params.astype(np.float64), fb["x"], bf16)
+    amb = zmin < tau
+    gf = gpu["g_feature"]
+    rf = fb["g_feature"].reshape(gf.shape)
+    keep = np.ones(gf.shape[:3], bool)
+    if amb.any():
+        v = _cell_voxels(cfg, fb["smp"].xyz[fb["live"]][amb])
+        keep[v[:, 0], v[:, 1], v[:, 2]] = False
+    touched = np.abs(rf).sum(-1) > 0
+    assert (~keep & touched).sum() <= 0.05 * touched.sum() + 8
+    scale = np.max(np.abs(rf))
+    assert np.max(np.abs(gf - rf)[keep]) / scale < tol
+    # Parameters after TV + Adam.  The first Adam step moves every entry by
+    # about lr * sign(g): compare where the reference gradient is clear of
+    # rounding noise, and bound the step everywhere else.
+    for name, gname, lr in (("density", "g_density_tv", rp.lr_grid),
+                            ("feature", "g_feature_tv", rp.lr_grid),
+                            ("params", None, rp.lr_mlp)):
+        ref = opt[name].reshape(gpu[name].shape)
+        g_ref = (opt[gname] if gname else fb["g_params"]).reshape(gpu[name].shape)
+        clear = np.abs(g_ref) > 1e-3 * np.max(np.abs(g_ref))
+        if name == "feature":
+            clear &= np.broadcast_to(keep[..., None], clear.shape)
+        assert np.max(np.abs(gpu[name] - ref)[clear]) / np.max(np.abs(ref)) < tol, name
+        start = {"density": fb["density0"], "feature": fb["feature0"], "params": fb["params0"]}[name]
+        assert np.max(np.abs(gpu[name] - start.reshape(gpu[name].shape))) <= lr * (1 + 1e-3) + 1e-6
 
 
 def test_step_small_fp32(T):
-    gpu, fb, opt = _run(T, synth.CFG1, 512, "f32", tv_dense=False, ray_stride=4)
+    gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG1, 512, "f32", tv_dense=False, ray_stride=4)
     assert fb["live"].sum() > 10000
-    _compare(gpu, fb, opt, 1e-5)
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
 
 
 def test_step_dvgo160_fp32_sparse_tv(T):
-    gpu, fb, opt = _run(T, synth.CFG2, 1024, "f32", tv_dense=False, ray_stride=8)
+    gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 1024, "f32", tv_dense=False, ray_stride=8)
     assert (fb["n_live"] < np.diff(fb["smp"].ray_off)).sum() > 50   # early stop is exercised
-    _compare(gpu, fb, opt, 1e-5)
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
 
 
 def test_step_dvgo160_fp32_dense_tv(T):
-    gpu, fb, opt = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
-    _compare(gpu, fb, opt, 1e-5)
+    gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
 
 
 def test_step_dvgo160_bf16(T):
-    gpu, fb, opt = _run(T, synth.CFG4, 1024, "bf16", tv_dense=False, ray_stride=16)
-    _compare(gpu, fb, opt, 2e-3)
+    gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG4, 1024, "bf16", tv_dense=False, ray_stride=16)
+    _compare(gpu, fb, opt, 2e-3, cfg, rp, P, bf16=True)
 
 
 def test_step_unbounded_contracted(T):
     # the 320^3 grids of the workload are exercised by the benchmark; a 96^3
     # grid keeps the FP64 oracle's TV/Adam pass small here
     cfg = dataclasses.replace(synth.CFG3, grid=96)
-    gpu, fb, opt = _run(T, cfg, 256, "f32", tv_dense=False, ray_stride=32)
-    _compare(gpu, fb, opt, 1e-5)
+    gpu, fb, opt, cfg, rp, P = _run(T, cfg, 256, "f32", tv_dense=False, ray_stride=32)
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
