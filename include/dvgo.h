@@ -225,6 +225,43 @@ int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, co
                     const int64_t* n_dev, const float* params, int precision, float* g_params,
                     float* g_k0, void* stream);
 
+/* ------------------------------------------------------- learned proposal */
+/* Not in the paper: a small network that predicts where each ray's
+ * compositing weight lies, so that far fewer samples are rendered.  It is
+ * trained on the plain renderer's own weights and the plain dense render
+ * stays the fallback.  Network: position encoding [x, sin(2^f x_a),
+ * cos(2^f x_a)], f < 6 (39 values) -> ReLU 64 -> ReLU 64 -> 1 logit, BF16
+ * operands on the tensor cores with FP32 accumulation.  params: f32 flat
+ * W1[64][39], b1, W2[64][64], b2, W3[1][64], b3 (6785 values). */
+int dvgo_proposal_fwd(const float* xyz, const int32_t* idx, int64_t n_cap, const int64_t* n_dev,
+                      const float* params, float* logits, void* stream);
+/* Accumulates g_params (+=) from the per-sample logit gradients. */
+int dvgo_proposal_bwd(const float* g_logits, const float* xyz, const int32_t* idx, int64_t n_cap,
+                      const int64_t* n_dev, const float* params, float* g_params, void* stream);
+/* Per ray (CSR ray_off): q = softmax(logits); with w_target (the plain
+ * renderer's weights over the same samples, may be NULL) the target is
+ * p_j = (w_j / W + eps_u) / (1 + N eps_u), W = sum w (uniform if W = 0),
+ * loss_r = -sum p_j log q_j and g_logits = g_scale (q - p).  q, loss_r and
+ * g_logits may each be NULL. */
+int dvgo_proposal_xent(const float* logits, const float* w_target, const int64_t* ray_off, int64_t R,
+                       float eps_u, float g_scale, float* loss_r, float* g_logits, float* q,
+                       void* stream);
+/* Inverse-CDF selection per ray: for u_k = (k + 0.5)/n_draw, k < n_draw, the
+ * first candidate j whose running FP32 sum of q (in candidate order)
+ * exceeds u_k; repeated picks collapse.  sel [R][n_draw] holds candidate
+ * indices relative to the ray start (ascending, -1 past n_sel[r]). */
+int dvgo_proposal_select(const float* q, const int64_t* ray_off, int64_t R, int32_t n_draw,
+                         int32_t* sel, int32_t* n_sel, void* stream);
+/* Gathers the selected samples into a new ragged list (out_ray_off [R+1]
+ * from a scan of n_sel; per-sample arrays copied; out_src, may be NULL,
+ * receives each kept sample's index in the input list). */
+int dvgo_compact_samples(const int32_t* sel, const int32_t* n_sel, int32_t n_draw,
+                         const int64_t* ray_off, int64_t R, const float* xyz, const int32_t* ray_id,
+                         const int32_t* step_k, const float* s_mid, const float* s_len,
+                         int64_t* out_ray_off, float* out_xyz, int32_t* out_ray_id,
+                         int32_t* out_step_k, float* out_s_mid, float* out_s_len, int32_t* out_src,
+                         void* stream);
+
 /* ------------------------------------------------------------ regularisers */
 /* TV gradient (Sec. 2, "Efficient total variation (TV) loss"), added into
  * g_grid without a forward pass: for each grid point v and channel c,

@@ -29,8 +29,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
 * ``sample_rays_contracted`` / ``contract``: pinned (identity inside the unit
   ball, limit 1 + b, continuity, monotone along rays, finite-difference
   Jacobian step).
-* ``softmax_xent`` / ``inverse_cdf_select``: pinned (torch cross-entropy,
-  numpy searchsorted).
+* ``softmax_xent`` / ``inverse_cdf_select`` and their ragged forms: pinned
+  (torch cross-entropy, numpy searchsorted, ragged = per-ray dense call).
 """
 from __future__ import annotations
 
@@ -105,6 +105,8 @@ def _declare(L):
     L.or_adam.argtypes = [P, P, P, P, I64, D, D, D, D, I64, INT]
     L.or_softmax_xent.argtypes = [P, P, I64, INT, P, P, P]
     L.or_inverse_cdf_select.argtypes = [P, I64, INT, INT, P, P]
+    L.or_proposal_xent_ragged.argtypes = [P, P, P, I64, D, P, P, P]
+    L.or_inverse_cdf_select_ragged.argtypes = [P, P, I64, INT, P, P]
 
 
 def _p(a):
@@ -393,4 +395,24 @@ def inverse_cdf_select(q32, n_draw):
     sel = np.zeros((R, n_draw), np.int32)
     n_sel = np.zeros(R, np.int32)
     lib().or_inverse_cdf_select(_p(q32), R, K, n_draw, _p(sel), _p(n_sel))
+    return sel, n_sel
+
+
+def proposal_xent_ragged(logits, w, ray_off, eps_u):
+    """Per-ray softmax cross-entropy against p = normalised w + uniform floor."""
+    logits, w, ray_off = _f64(logits), _f64(w), _i64(ray_off)
+    R = ray_off.size - 1
+    loss = np.zeros(R)
+    g = np.zeros_like(logits)
+    q = np.zeros_like(logits)
+    lib().or_proposal_xent_ragged(_p(logits), _p(w), _p(ray_off), R, eps_u, _p(loss), _p(g), _p(q))
+    return loss, g, q
+
+
+def inverse_cdf_select_ragged(q32, ray_off, n_draw):
+    q32, ray_off = _f32(q32), _i64(ray_off)
+    R = ray_off.size - 1
+    sel = np.zeros((R, n_draw), np.int32)
+    n_sel = np.zeros(R, np.int32)
+    lib().or_inverse_cdf_select_ragged(_p(q32), _p(ray_off), R, n_draw, _p(sel), _p(n_sel))
     return sel, n_sel

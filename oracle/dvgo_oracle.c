@@ -798,3 +798,53 @@ OR_API void or_inverse_cdf_select(const float* q, int64_t R, int K, int n_draw, 
     for (int k = cnt; k < n_draw; ++k) sel[r * n_draw + k] = -1;
   }
 }
+
+/* Ragged forms of the two functions above, over a CSR list of candidates.  */
+/* Target: p_j = (w_j / W + eps_u) / (1 + N eps_u) with W = sum_j w_j (the   */
+/* plain renderer's weights, plus a uniform floor), uniform if W = 0.       */
+OR_API void or_proposal_xent_ragged(const double* logits, const double* w, const int64_t* ray_off,
+                                    int64_t R, double eps_u, double* loss, double* g_logits,
+                                    double* q_out) {
+  for (int64_t r = 0; r < R; ++r) {
+    int64_t b = ray_off[r], e = ray_off[r + 1];
+    int64_t N = e - b;
+    loss[r] = 0.0;
+    if (N == 0) continue;
+    double mx = logits[b], W = 0.0;
+    for (int64_t i = b; i < e; ++i) {
+      if (logits[i] > mx) mx = logits[i];
+      W += w[i];
+    }
+    double se = 0.0;
+    for (int64_t i = b; i < e; ++i) se += exp(logits[i] - mx);
+    double lse = mx + log(se);
+    for (int64_t i = b; i < e; ++i) {
+      double q = exp(logits[i] - lse);
+      double p = W > 0 ? (w[i] / W + eps_u) / (1.0 + (double)N * eps_u) : 1.0 / (double)N;
+      loss[r] -= p * (logits[i] - lse);
+      if (g_logits) g_logits[i] = q - p;
+      if (q_out) q_out[i] = q;
+    }
+  }
+}
+
+OR_API void or_inverse_cdf_select_ragged(const float* q, const int64_t* ray_off, int64_t R,
+                                         int n_draw, int32_t* sel, int32_t* n_sel) {
+  for (int64_t r = 0; r < R; ++r) {
+    int64_t b = ray_off[r];
+    int N = (int)(ray_off[r + 1] - b);
+    int32_t* out = sel + r * n_draw;
+    int cnt = 0;
+    if (N > 0) {
+      int j = 0;
+      float cdf = q[b];
+      for (int k = 0; k < n_draw; ++k) {
+        float u = ((float)k + 0.5f) / (float)n_draw;
+        while (j < N - 1 && !(u < cdf)) { ++j; cdf = cdf + q[b + j]; }
+        if (cnt == 0 || out[cnt - 1] != j) out[cnt++] = j;
+      }
+    }
+    n_sel[r] = cnt;
+    for (int k = cnt; k < n_draw; ++k) out[k] = -1;
+  }
+}

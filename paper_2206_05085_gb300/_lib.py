@@ -91,6 +91,11 @@ def _declare(L):
         "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
         "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
         "dvgo_device_status": ([P], INT),
+        "dvgo_proposal_fwd": ([P, P, I64, P, P, P, P], INT),
+        "dvgo_proposal_bwd": ([P, P, P, I64, P, P, P, P], INT),
+        "dvgo_proposal_xent": ([P, P, P, I64, F, F, P, P, P, P], INT),
+        "dvgo_proposal_select": ([P, P, I64, I32, P, P, P], INT),
+        "dvgo_compact_samples": ([P, P, I32, P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -107,7 +112,8 @@ def exported_names():
         "dvgo_live_samples_workspace_size", "dvgo_live_samples", "dvgo_alpha_weights_fwd",
         "dvgo_composite_rgb_fwd", "dvgo_composite_bwd", "dvgo_distortion_fwd",
         "dvgo_distortion_bwd", "dvgo_rgb_loss", "dvgo_rgbnet_fwd", "dvgo_rgbnet_bwd",
-        "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status"]
+        "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status", "dvgo_proposal_fwd",
+        "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples"]
 
 
 def ptr(t):
@@ -250,3 +256,32 @@ def adam_step(p, p_shadow, g, m, v, n, touched, block_elems, lr, beta1, beta2, e
 
 def device_status(stream=None):
     return int(lib().dvgo_device_status(_stream(stream)))
+
+
+# ------------------------------------------------------ learned proposal
+def proposal_fwd(xyz, idx, n_cap, n_dev, params, logits, stream=None):
+    _call("dvgo_proposal_fwd", ptr(xyz), ptr(idx), n_cap, ptr(n_dev), ptr(params), ptr(logits),
+          _stream(stream))
+
+
+def proposal_bwd(g_logits, xyz, idx, n_cap, n_dev, params, g_params, stream=None):
+    _call("dvgo_proposal_bwd", ptr(g_logits), ptr(xyz), ptr(idx), n_cap, ptr(n_dev), ptr(params),
+          ptr(g_params), _stream(stream))
+
+
+def proposal_xent(logits, w_target, ray_off, R, eps_u, g_scale, loss_r, g_logits, q, stream=None):
+    _call("dvgo_proposal_xent", ptr(logits), ptr(w_target), ptr(ray_off), R, eps_u, g_scale,
+          ptr(loss_r), ptr(g_logits), ptr(q), _stream(stream))
+
+
+def proposal_select(q, ray_off, R, n_draw, sel, n_sel, stream=None):
+    _call("dvgo_proposal_select", ptr(q), ptr(ray_off), R, n_draw, ptr(sel), ptr(n_sel),
+          _stream(stream))
+
+
+def compact_samples(sel, n_sel, n_draw, ray_off, R, xyz, ray_id, step_k, s_mid, s_len, out_ray_off,
+                    out_xyz, out_ray_id, out_step_k, out_s_mid, out_s_len, out_src=None, stream=None):
+    _call("dvgo_compact_samples", ptr(sel), ptr(n_sel), n_draw, ptr(ray_off), R, ptr(xyz),
+          ptr(ray_id), ptr(step_k), ptr(s_mid), ptr(s_len), ptr(out_ray_off), ptr(out_xyz),
+          ptr(out_ray_id), ptr(out_step_k), ptr(out_s_mid), ptr(out_s_len), ptr(out_src),
+          _stream(stream))

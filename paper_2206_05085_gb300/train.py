@@ -133,10 +133,17 @@ class Trainer:
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
 
     # --------------------------------------------------------------- forward
-    def forward(self, rays_o, rays_d, target):
+    def sample(self, rays_o, rays_d):
+        L.sample_rays(rays_o, rays_d, self.R, self.gd, self.sd, self.mask, self.S_cap, self.ray_off,
+                      self.xyz, self.ray_id, self.step_k, self.s_mid, self.s_len, self.ws_sample)
+
+    def forward(self, rays_o, rays_d, target, sample: bool = True):
+        """Forward pass.  sample=False renders the sample list already in the
+        buffers (ray_off, xyz, ray_id, step_k, s_mid, s_len), e.g. the samples
+        a proposal network selected."""
         rp, R, S = self.rp, self.R, self.S_cap
-        L.sample_rays(rays_o, rays_d, R, self.gd, self.sd, self.mask, S, self.ray_off, self.xyz,
-                      self.ray_id, self.step_k, self.s_mid, self.s_len, self.ws_sample)
+        if sample:
+            self.sample(rays_o, rays_d)
         S_dev = self.ray_off[R:]
         dgrid, ddt = self.density.render_view
         L.sample_grid_fwd(dgrid, ddt, self.gd, 1, self.xyz, None, S, S_dev, self.raw)
@@ -180,9 +187,9 @@ class Trainer:
         L.adam_step(self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
                     rp.lr_mlp, rp.beta1, rp.beta2, rp.eps, self.it, True)
 
-    def step(self, rays_o, rays_d, target, tv_dense: bool = False):
+    def step(self, rays_o, rays_d, target, tv_dense: bool = False, sample: bool = True):
         """One full training iteration; returns the device loss tensor [3]."""
-        self.forward(rays_o, rays_d, target)
+        self.forward(rays_o, rays_d, target, sample=sample)
         self.backward(rays_d)
         self.regularize_and_step(tv_dense)
         return self.loss

@@ -29,7 +29,7 @@ def orc():
     return oracle
 
 
-def check_mlp_grads(orc, dims, params, x, g_out, gpu_gp, gpu_gx, tol, q_bf16):
+def check_mlp_grads(orc, dims, params, x, g_out, gpu_gp, gpu_gx, tol, q_bf16, out_sigmoid=True):
     """Compare MLP parameter / input gradients with the oracle.
 
     A sample whose smallest ReLU input is within rounding of 0 (tau) can
@@ -41,10 +41,10 @@ def check_mlp_grads(orc, dims, params, x, g_out, gpu_gp, gpu_gx, tol, q_bf16):
     tau = 1e-5 if q_bf16 else 1e-6
     zmin = orc.mlp_min_abs_preact(dims, params, x, q_bf16)
     amb = np.nonzero(zmin < tau)[0]
-    gp, gx = orc.mlp_bwd(dims, params, x, g_out, True, q_bf16)
+    gp, gx = orc.mlp_bwd(dims, params, x, g_out, out_sigmoid, q_bf16)
     slack = np.zeros_like(gp)
     for s in amb:
-        gps, _ = orc.mlp_bwd(dims, params, x[s:s + 1], g_out[s:s + 1], True, q_bf16)
+        gps, _ = orc.mlp_bwd(dims, params, x[s:s + 1], g_out[s:s + 1], out_sigmoid, q_bf16)
         slack += 2 * np.abs(gps)
     offs = [0]
     for i in range(len(dims) - 1):

@@ -212,3 +212,28 @@ def test_mlp_bf16_operands_against_torch_rounding(orc):
     # that switch between the two)
     gp0, _ = orc.mlp_bwd(dims, params, x, g_out, True)
     assert 1e-4 < rel_err(gp, gp0) < 0.2
+
+
+def test_ragged_proposal_pieces_match_per_ray_dense(orc):
+    rng = np.random.default_rng(14)
+    counts = [0, 1, 7, 64, 300]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(off[-1])
+    z = rng.normal(0, 2, S)
+    w = np.where(rng.uniform(size=S) < 0.3, rng.uniform(0, 1, S), 0.0)
+    loss, g, q = orc.proposal_xent_ragged(z, w, off, 1e-3)
+    for r, n in enumerate(counts):
+        sl = slice(off[r], off[r + 1])
+        if n == 0:
+            assert loss[r] == 0
+            continue
+        W = w[sl].sum()
+        p = (w[sl] / W + 1e-3) / (1 + n * 1e-3) if W > 0 else np.full(n, 1.0 / n)
+        assert abs(p.sum() - 1) < 1e-12
+        l1, g1, q1 = orc.softmax_xent(z[sl][None], p[None])
+        assert loss[r] == pytest.approx(l1[0], rel=1e-12)
+        assert np.allclose(g[sl], g1[0], atol=1e-14) and np.allclose(q[sl], q1[0], atol=1e-15)
+        qq = q[sl].astype(np.float32)
+        s1, n1 = orc.inverse_cdf_select(qq[None], 64)
+        s_all, n_all = orc.inverse_cdf_select_ragged(q.astype(np.float32), off, 64)
+        assert n_all[r] == n1[0] and np.array_equal(s_all[r], s1[0])
