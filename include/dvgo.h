@@ -144,6 +144,26 @@ int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
                      int32_t* ray_id, int32_t* step_k, float* s_mid, float* s_len, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* dvgo_sample_rays for callers that cannot allocate device memory (for
+ * instance a host application that owns the whole memory budget and does not
+ * let libraries allocate, so no workspace can be passed).  The paper has no
+ * counterpart; this is a deployment variant.  Same arguments and results as
+ * dvgo_sample_rays without ws/ws_bytes.  Its scratch is a fixed array inside
+ * the library, present on every GPU that loads the library until the
+ * process exits, limited to R <= dvgo_sample_rays_noalloc_max_rays()
+ * (1,048,576 rays; larger R returns DVGO_ERR_SHAPE).  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) and
+ * caches it, so make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  No allocation of any
+ * kind is made. */
+int64_t dvgo_sample_rays_noalloc_max_rays(void);
+int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d, int64_t R,
+                             const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
+                             const uint8_t* mask, int64_t S_cap, int64_t* ray_off, float* xyz,
+                             int32_t* ray_id, int32_t* step_k, float* s_mid, float* s_len,
+                             void* stream);
+
 /* Live-sample list after early stop: live_idx lists, ray by ray, the first
  * seg_len[r] samples of every ray (the samples with nonzero weight), and
  * *live_count their number.  live_idx: int32 [capacity ray_off total].

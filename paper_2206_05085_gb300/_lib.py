@@ -96,6 +96,8 @@ def _declare(L):
         "dvgo_proposal_xent": ([P, P, P, I64, F, F, P, P, P, P], INT),
         "dvgo_proposal_select": ([P, P, I64, I32, P, P, P], INT),
         "dvgo_compact_samples": ([P, P, I32, P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P], INT),
+        "dvgo_sample_rays_noalloc_max_rays": ([], I64),
+        "dvgo_sample_rays_noalloc": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -113,7 +115,8 @@ def exported_names():
         "dvgo_composite_rgb_fwd", "dvgo_composite_bwd", "dvgo_distortion_fwd",
         "dvgo_distortion_bwd", "dvgo_rgb_loss", "dvgo_rgbnet_fwd", "dvgo_rgbnet_bwd",
         "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status", "dvgo_proposal_fwd",
-        "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples"]
+        "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
+        "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc"]
 
 
 def ptr(t):
@@ -186,6 +189,18 @@ def sample_rays(rays_o, rays_d, R, gd, sd, mask, S_cap, ray_off, xyz, ray_id, st
     _call("dvgo_sample_rays", ptr(rays_o), ptr(rays_d), R, ctypes.byref(gd), ctypes.byref(sd),
           ptr(mask), S_cap, ptr(ray_off), ptr(xyz), ptr(ray_id), ptr(step_k), ptr(s_mid),
           ptr(s_len), ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def sample_rays_noalloc_max_rays():
+    return int(lib().dvgo_sample_rays_noalloc_max_rays())
+
+
+def sample_rays_noalloc(rays_o, rays_d, R, gd, sd, mask, S_cap, ray_off, xyz, ray_id, step_k,
+                        s_mid, s_len, stream=None):
+    """dvgo_sample_rays without a workspace, for callers that cannot allocate."""
+    _call("dvgo_sample_rays_noalloc", ptr(rays_o), ptr(rays_d), R, ctypes.byref(gd),
+          ctypes.byref(sd), ptr(mask), S_cap, ptr(ray_off), ptr(xyz), ptr(ray_id), ptr(step_k),
+          ptr(s_mid), ptr(s_len), _stream(stream))
 
 
 def live_samples_workspace_size(R):

@@ -6,6 +6,8 @@
 // round-to-nearest intrinsics (no FMA contraction), in the operation order
 // stated in dvgo.h / below, so the integer results are reproducible bit for
 // bit by any IEEE FP32 implementation of the same formulas.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace dvgo {
@@ -390,5 +392,87 @@ extern "C" int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len,
   scan_counts_kernel<<<1, 1024, 0, st>>>(seg_len, R, live_off, live_count);
   live_fill_kernel<<<grid_for(R * 32, 256, 16), 256, 0, st>>>(ray_off, seg_len, R, live_off,
                                                               live_idx);
+  return launch_status();
+}
+
+// ------------------------------------------------------------------------
+// Ray sampling that allocates nothing.  Some callers cannot call cudaMalloc
+// at all -- for example a host application that owns the device's whole
+// memory budget and does not let libraries allocate, or code running where
+// allocation is not permitted -- so they cannot provide the workspace that
+// dvgo_sample_rays needs.  For them the per-ray count scratch lives in a
+// fixed-size array in this library's own device memory: every GPU that
+// loads the library holds it (4 MiB) until the process exits.
+namespace dvgo {
+
+constexpr int64_t kNoAllocMaxRays = 1 << 20;
+static __device__ __align__(256) int32_t g_noalloc_counts[kNoAllocMaxRays + 1];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::atomic<int32_t*> g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of g_noalloc_counts on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked
+// up once per device, with that device current, and cached.
+static int noalloc_counts(int32_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DVGO_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return DVGO_ERR_UNSUPPORTED;
+  int32_t* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_counts) != cudaSuccess || !addr) return DVGO_ERR_CUDA;
+    p = static_cast<int32_t*>(addr);
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return DVGO_OK;
+}
+
+}  // namespace dvgo
+
+extern "C" int64_t dvgo_sample_rays_noalloc_max_rays(void) { return dvgo::kNoAllocMaxRays; }
+
+extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d, int64_t R,
+                                        const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
+                                        const uint8_t* mask, int64_t S_cap, int64_t* ray_off,
+                                        float* xyz, int32_t* ray_id, int32_t* step_k,
+                                        float* s_mid, float* s_len, void* stream) {
+  DVGO_CHECK_ARG(grid && smp && ray_off && R >= 0);
+  DVGO_CHECK_ARG(R == 0 || (rays_o && rays_d && xyz && ray_id && step_k && s_mid && s_len));
+  DVGO_CHECK_ARG(smp->mode == 0 || smp->mode == 1);
+  DVGO_CHECK_ARG(smp->max_steps >= 0);
+  if (smp->mode == 0) DVGO_CHECK_ARG(smp->step > 0.0f);
+  if (smp->mode == 1) DVGO_CHECK_ARG(smp->step_c > 0.0f && smp->contract_b > 0.0f);
+  if (R > kNoAllocMaxRays) return DVGO_ERR_SHAPE;
+  if (S_cap < R * (int64_t)smp->max_steps || S_cap > INT32_MAX) return DVGO_ERR_SHAPE;
+  SamplerArgs A;
+  DVGO_CHECK_ARG(fill_args(A, grid, smp));
+  int32_t* counts = nullptr;
+  int rc = noalloc_counts(&counts);
+  if (rc != DVGO_OK) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (R == 0) {
+    cudaMemsetAsync(ray_off, 0, sizeof(int64_t), st);
+    return launch_status();
+  }
+  // the count kernel writes counts[0, R) before the scan reads them, so the
+  // shared array needs no clearing between calls
+  if (smp->mode == 0) {
+    const int block = 256;
+    int g = grid_for(R * 32, block, 16);
+    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
+                                          step_k, s_mid, s_len);
+  } else {
+    const int block = 128;
+    int g = (int)ceil_div(R, block);
+    contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+    contracted_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+                                                 ray_id, step_k, s_mid, s_len);
+  }
   return launch_status();
 }
