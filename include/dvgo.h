@@ -229,21 +229,26 @@ int dvgo_rgb_loss(const float* color, const float* target, const float* L_r, int
  * W2[128][128], b2, W3[3][128], b3 (22019 values).  Processes samples
  * idx[j] (j < *n_dev or n_cap); k0 rows and rgb rows are at the sample
  * index; the direction is rays_d[ray_id[sample]].  precision: DVGO_F32
- * (FP32-accurate: TF32 tensor cores with a 3-pass hi/lo split) or
- * DVGO_BF16 (BF16 tensor cores, FP32 accumulation). */
+ * (exact FP32 on the CUDA cores) or DVGO_BF16 (BF16 operands on the tensor
+ * cores, FP32 accumulation).  act (FP32 form, may be NULL): see
+ * dvgo_rgbnet_bwd. */
 int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
                     const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
-                    int precision, float* rgb, void* stream);
+                    int precision, float* rgb, float* act, void* stream);
 
 /* Backward: the upstream colour gradient of sample s is g_rgb[s] (f32
  * [.., 3] at the sample index) when g_rgb is given, else w[s] *
  * g_color[ray_id[s]] (the colour part of the compositing gradient).
  * Accumulates g_params (+=, f32) and writes g_k0 [.., 12] rows at the
- * sample index. */
+ * sample index.  act (FP32 form, may be NULL): f32 [n_cap][256] written by
+ * dvgo_rgbnet_fwd for the same list, row j = [h1 (128) | h2 (128)] of list
+ * position j; with it (and rgb, the forward's output, may be NULL) the
+ * backward reads the hidden activations instead of recomputing them.  The
+ * BF16 form ignores act and rgb (it recomputes on the tensor cores). */
 int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                     const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
-                    const int64_t* n_dev, const float* params, int precision, float* g_params,
-                    float* g_k0, void* stream);
+                    const int64_t* n_dev, const float* params, int precision, const float* act,
+                    const float* rgb, float* g_params, float* g_k0, void* stream);
 
 /* ------------------------------------------------------- learned proposal */
 /* Not in the paper: a small network that predicts where each ray's

@@ -86,8 +86,8 @@ def _declare(L):
         "dvgo_distortion_fwd": ([P, P, P, P, P, I64, P, P], INT),
         "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
         "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
-        "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P], INT),
-        "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P], INT),
+        "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
+        "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
         "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
         "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
         "dvgo_device_status": ([P], INT),
@@ -245,16 +245,17 @@ def rgb_loss(color, target, L_r, R, lambda_dist, loss_out, g_color, stream=None)
 
 
 # ------------------------------------------------------------ colour MLP
-def rgbnet_fwd(k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision, rgb, stream=None):
+def rgbnet_fwd(k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision, rgb, act=None,
+               stream=None):
     _call("dvgo_rgbnet_fwd", ptr(k0), ptr(rays_d), ptr(ray_id), ptr(idx), n_cap, ptr(n_dev),
-          ptr(params), precision, ptr(rgb), _stream(stream))
+          ptr(params), precision, ptr(rgb), ptr(act), _stream(stream))
 
 
 def rgbnet_bwd(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision,
-               g_params, g_k0, stream=None):
+               g_params, g_k0, act=None, rgb=None, stream=None):
     _call("dvgo_rgbnet_bwd", ptr(g_rgb), ptr(g_color), ptr(w), ptr(k0), ptr(rays_d), ptr(ray_id),
-          ptr(idx), n_cap, ptr(n_dev), ptr(params), precision, ptr(g_params), ptr(g_k0),
-          _stream(stream))
+          ptr(idx), n_cap, ptr(n_dev), ptr(params), precision, ptr(act), ptr(rgb), ptr(g_params),
+          ptr(g_k0), _stream(stream))
 
 
 # ------------------------------------------------------- regularisation

@@ -3,10 +3,10 @@
 #include "mlp_common.cuh"
 
 int dvgo_rgbnet_fwd_f32(const float*, const float*, const int32_t*, const int32_t*, int64_t,
-                        const int64_t*, const float*, float*, cudaStream_t);
-int dvgo_rgbnet_bwd_f32(const float*, const float*, const float*, const float*, const float*, const int32_t*,
-                        const int32_t*, int64_t, const int64_t*, const float*, float*, float*,
-                        cudaStream_t);
+                        const int64_t*, const float*, float*, float*, cudaStream_t);
+int dvgo_rgbnet_bwd_f32(const float*, const float*, const float*, const float*, const float*,
+                        const int32_t*, const int32_t*, int64_t, const int64_t*, const float*,
+                        const float*, const float*, float*, float*, cudaStream_t);
 int dvgo_rgbnet_fwd_bf16(const float*, const float*, const int32_t*, const int32_t*, int64_t,
                          const int64_t*, const float*, float*, cudaStream_t);
 int dvgo_rgbnet_bwd_bf16(const float*, const float*, const float*, const float*, const float*, const int32_t*,
@@ -34,14 +34,15 @@ extern "C" const char* dvgo_status_string(int status) {
 
 extern "C" int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
                                const int32_t* idx, int64_t n_cap, const int64_t* n_dev,
-                               const float* params, int precision, float* rgb, void* stream) {
+                               const float* params, int precision, float* rgb, float* act,
+                               void* stream) {
   DVGO_CHECK_ARG(n_cap >= 0);
   if (n_cap == 0) return DVGO_OK;
   DVGO_CHECK_ARG(k0 && rays_d && ray_id && params && rgb);
-  DVGO_CHECK_ARG(((uintptr_t)k0 % 16) == 0);
+  DVGO_CHECK_ARG(((uintptr_t)k0 % 16) == 0 && ((uintptr_t)act % 16) == 0);
   cudaStream_t st = as_stream(stream);
   if (precision == DVGO_F32)
-    return dvgo_rgbnet_fwd_f32(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, st);
+    return dvgo_rgbnet_fwd_f32(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
   if (precision == DVGO_BF16)
     return dvgo_rgbnet_fwd_bf16(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, st);
   return DVGO_ERR_INVALID_ARG;
@@ -50,15 +51,17 @@ extern "C" int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32
 extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                                const float* rays_d, const int32_t* ray_id, const int32_t* idx,
                                int64_t n_cap, const int64_t* n_dev, const float* params,
-                               int precision, float* g_params, float* g_k0, void* stream) {
+                               int precision, const float* act, const float* rgb, float* g_params,
+                               float* g_k0, void* stream) {
   DVGO_CHECK_ARG(n_cap >= 0);
   if (n_cap == 0) return DVGO_OK;
   DVGO_CHECK_ARG((g_rgb || (g_color && w)) && k0 && rays_d && ray_id && params && g_params && g_k0);
-  DVGO_CHECK_ARG(((uintptr_t)k0 % 16) == 0 && ((uintptr_t)g_k0 % 16) == 0);
+  DVGO_CHECK_ARG(((uintptr_t)k0 % 16) == 0 && ((uintptr_t)g_k0 % 16) == 0 &&
+                 ((uintptr_t)act % 16) == 0);
   cudaStream_t st = as_stream(stream);
   if (precision == DVGO_F32)
-    return dvgo_rgbnet_bwd_f32(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, g_params,
-                               g_k0, st);
+    return dvgo_rgbnet_bwd_f32(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, act,
+                               rgb, g_params, g_k0, st);
   if (precision == DVGO_BF16)
     return dvgo_rgbnet_bwd_bf16(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
                                 g_params, g_k0, st);

@@ -129,6 +129,8 @@ class Trainer:
         self.g_w = torch.empty(S, **f32)
         self.g_raw = torch.empty(S, **f32)
         self.g_k0 = torch.empty(S, FEAT, **f32)
+        # FP32 form: hidden activations saved by the colour-MLP forward for its backward
+        self.act = torch.empty(S, 256, **f32) if self.precision == L.F32 else None
         self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
 
@@ -154,7 +156,7 @@ class Trainer:
         L.sample_grid_fwd(fgrid, fdt, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,
                           self.k0)
         L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
-                     self.precision, self.rgb)
+                     self.precision, self.rgb, self.act)
         L.composite_rgb_fwd(self.w, self.rgb, self.ray_off, self.n_live, self.T_end, R, rp.bg,
                             self.color)
         L.distortion_fwd(self.w, self.s_mid, self.s_len, self.ray_off, self.n_live, R, self.L_r)
@@ -168,7 +170,8 @@ class Trainer:
         L.composite_bwd(self.g_color, self.g_w, self.raw, self.T, self.rgb, self.ray_off,
                         self.n_live, R, self.shift, rp.interval, rp.bg, self.g_raw)
         L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.live_idx, S,
-                     self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0)
+                     self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
+                     self.act, self.rgb)
         L.sample_grid_bwd(self.g_raw, self.gd, 1, self.xyz, self.live_idx, S, self.live_count,
                           self.density.g, self.density.touched)
         L.sample_grid_bwd(self.g_k0, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,

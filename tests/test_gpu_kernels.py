@@ -328,12 +328,19 @@ def test_rgbnet_fwd_bwd(L, precision, n):
     assert rel_err(got[idx], ref) < tol
     rest = np.setdiff1d(np.arange(n), idx)
     assert np.all(got[rest] == -1.0)
-    g_params = torch.zeros(len(params), device="cuda")
-    g_k0 = torch.zeros(n, 12, device="cuda")
-    L.rgbnet_bwd(dev(g_rgb), None, None, dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev,
-                 dev(params), prec, g_params, g_k0)
-    check_mlp_grads(oracle, synth.RGBNET_DIMS, p_ref, x, g_rgb[idx], host(g_params),
-                    host(g_k0)[idx], tol, bf)
+    # backward recomputing the forward, and (FP32 form) from stored activations
+    for use_act in ((False, True) if not bf else (False,)):
+        act = None
+        if use_act:
+            act = torch.empty(n, 256, device="cuda")
+            L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb,
+                         act)
+        g_params = torch.zeros(len(params), device="cuda")
+        g_k0 = torch.zeros(n, 12, device="cuda")
+        L.rgbnet_bwd(dev(g_rgb), None, None, dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev,
+                     dev(params), prec, g_params, g_k0, act, rgb if use_act else None)
+        check_mlp_grads(oracle, synth.RGBNET_DIMS, p_ref, x, g_rgb[idx], host(g_params),
+                        host(g_k0)[idx], tol, bf)
     if bf:
         # error of the BF16 form against the unrounded FP64 MLP (reported)
         ref64 = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True)
@@ -351,6 +358,16 @@ def test_rgbnet_bwd_from_compositing_gradient(L):
     g_k0 = torch.zeros(n, 12, device="cuda")
     L.rgbnet_bwd(None, dev(g_color), dev(w), dev(k0), dev(d), dev(ray_id), None, n, None,
                  dev(params), L.F32, g_params, g_k0)
+    # the stored activations of the forward give the same gradients
+    rgb = torch.empty(n, 3, device="cuda")
+    act = torch.empty(n, 256, device="cuda")
+    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), None, n, None, dev(params), L.F32, rgb, act)
+    g2 = torch.zeros(len(params), device="cuda")
+    gk2 = torch.zeros(n, 12, device="cuda")
+    L.rgbnet_bwd(None, dev(g_color), dev(w), dev(k0), dev(d), dev(ray_id), None, n, None,
+                 dev(params), L.F32, g2, gk2, act, rgb)
+    assert rel_err(host(g2), host(g_params)) < 1e-6
+    assert rel_err(host(gk2), host(g_k0)) < 1e-6
     x = oracle.rgbnet_input(k0, d[ray_id])
     from conftest import check_mlp_grads
     check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, w[:, None] * g_color[ray_id],
