@@ -33,12 +33,14 @@ FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dvgo_160")
     ap.add_argument("--tv-dense", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BF16 / learned-proposal comparison")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup+steps with no clock sampling or CPU baseline (for ncu)")
     return ap.parse_args()
@@ -259,37 +261,142 @@ def run_ours(args, rank, world):
                 touched=(nbd, nbf), h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
 
 
+# Algorithmic work per unit ("Kernels and their rooflines").
+# Colour MLP, per live sample: forward 2*(39*128 + 128*128 + 128*3) FLOP; backward
+# (activations stored by the forward, nothing recomputed) g_z2 + dW3 (2*3*128 each),
+# dW2 and g_h1 (128*128 each), dW1 (128*40), g_k0 (128*12), all x2.
+MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)
+MLP_BWD_FLOP = 2 * (2 * 3 * 128 + 2 * 128 * 128 + 128 * 40 + 128 * 12)
+# The BF16 backward recomputes the forward on the tensor cores.
+MLP_BWD_FLOP_RECOMPUTE = MLP_BWD_FLOP + 2 * (39 * 128 + 128 * 128)
+KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2}
+
+
 def roofline(res, peaks):
     """Roofline record of the dominant kernel (largest share of the step)."""
     kt = res["kt"]
     name, rec = max(kt.items(), key=lambda kv: kv[1]["ms_per_step"])
-    S, S_live = res["S"], res["S_live"]
-    prec = res["prec"]
-    # per-unit algorithmic work (DESIGN.md, "Roofline arithmetic")
-    fwd_flop = 2 * (39 * 128 + 128 * 128 + 128 * 3)
-    bwd_flop = 2 * (39 * 128 + 128 * 128 + 128 * 3 + 3 * 128 * 2 + 128 * 128 * 2 + 128 * 40 + 128 * 12)
+    S_live, prec = res["S_live"], res["prec"]
     ms = rec["ms_per_call"]
-    sm_peak_alu = 152 * 128 * 2 * 2070e6 / 1e12   # FP32 FMA TFLOP/s at the max SM clock
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12   # FP32 FMA TFLOP/s at the maximum SM clock
+    out = {"kernel": name}
     if name in ("dvgo_rgbnet_bwd", "dvgo_rgbnet_fwd"):
-        flop = (bwd_flop if name.endswith("bwd") else fwd_flop) * S_live
+        if name.endswith("fwd"):
+            per = MLP_FWD_FLOP
+        else:
+            per = MLP_BWD_FLOP_RECOMPUTE if prec == "bf16" else MLP_BWD_FLOP
+        flop = per * S_live
         achieved = flop / (ms * 1e-3) / 1e12
         if prec == "bf16":
             bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
+            peak_src = "bf16_tflops_sustained of measured"
         else:
-            bound, peak, unit = "alu", sm_peak_alu, "TFLOP/s"
-        traffic = None
+            bound, peak, unit = "alu", round(fp32_peak, 2), "TFLOP/s"
+            peak_src = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"
+        out.update(bound=bound, achieved=round(achieved, 2), peak=peak, unit=unit,
+                   frac=round(achieved / peak, 4), flop_per_unit=per, units=S_live,
+                   peak_source=peak_src)
     else:
-        # memory-bound kernels: algorithmic bytes per call
-        b = {"dvgo_sample_grid_bwd": S_live * (12 + 4 + 12 * 4) / 2,
-             "dvgo_sample_grid_fwd": S * (12 + 4 + 4) / 2,
-             "dvgo_adam_step": (res["touched"][0] * 512 + res["touched"][1] * 512 * 12) * 28 / 3,
-             }.get(name, 0)
-        achieved = b / (ms * 1e-3) / 1e9
-        bound, peak, unit = "hbm", peaks.get("hbm_gbs", 6701.5), "GB/s"
-        traffic = None
-    return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
-            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
-            "ms_per_call": round(ms, 4), "share": round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)}
+        out.update(bound="hbm", achieved=None, peak=peaks.get("hbm_gbs", 6701.5), unit="GB/s",
+                   frac=None)
+    out["traffic"] = traffic_for(name, prec, S_live)
+    out["ms_per_call"] = round(ms, 4)
+    out["share"] = round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)
+    return out
+
+
+def traffic_for(name, prec, units):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    scaled by units processed; None if the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(f"{name}:{prec}")
+        if not rec:
+            return None
+        src = os.path.join(ROOT, rec["source"])
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["sha1"]:
+            return None
+        return int(rec["dram_bytes"] * units / rec["units"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def forms_report(args):
+    """The BF16 and learned-proposal forms against the plain FP32 form on the
+    same rays: PSNR of each render against the target and against the plain
+    render, and the iteration time of each (CUDA events, mean of 10 steps)."""
+    import torch
+    from paper_2206_05085_gb300 import proposal, synth, train
+    out = {}
+    # BF16 vs FP32 on the dvgo_160 scene
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg, seed=11)
+    t = synth.target_rgb(cfg, seed=11)
+    to, td, tt = (torch.from_numpy(a).cuda() for a in (o, d, t))
+    colors = {}
+    for prec in ("f32", "bf16"):
+        tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
+        tr.forward(to, td, tt)
+        colors[prec] = tr.color.clone()
+    out["bf16"] = {"psnr_vs_fp32_render_db": round(proposal.psnr(colors["bf16"], colors["f32"]), 2),
+                   "psnr_gap_vs_target_db": round(abs(proposal.psnr(colors["bf16"], tt) -
+                                                      proposal.psnr(colors["f32"], tt)), 4)}
+    # learned proposal vs dense candidates (<= 512 / ray), 16384 rays
+    cfg5 = synth.CFG5
+    R = cfg5.n_rays
+    dense, prop_tr, prop = proposal.make_forms(cfg5, rp, D, Fg, P, synth.proposal_params(), R)
+    batches = [tuple(torch.from_numpy(a).cuda() for a in synth.rays(cfg5, seed=500 + i, n_rays=R))
+               for i in range(8)]
+    t0 = time.perf_counter()
+    for it in range(400):
+        ro, rd = batches[it % len(batches)]
+        prop.train_step(ro, rd)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    o5, d5 = synth.rays(cfg5, seed=9)
+    t5 = synth.target_rgb(cfg5, seed=9)
+    to5, td5, tt5 = (torch.from_numpy(a).cuda() for a in (o5, d5, t5))
+    st = torch.cuda.current_stream()
+
+    def timed(fn, n=10):
+        for _ in range(3):
+            fn()
+        ev = []
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in ev) / n
+
+    dense.forward(to5, td5, tt5)
+    c_dense = dense.color.clone()
+    s_dense = int(dense.ray_off[-1].item())
+    prop.select_into(prop_tr, to5, td5)
+    prop_tr.forward(to5, td5, tt5, sample=False)
+    c_prop = prop_tr.color.clone()
+    s_prop = int(prop_tr.ray_off[-1].item())
+    ms_dense = timed(lambda: dense.step(to5, td5, tt5))
+
+    def prop_step():
+        prop.select_into(prop_tr, to5, td5)
+        prop_tr.step(to5, td5, tt5, sample=False)
+    ms_prop = timed(prop_step)
+    out["proposal"] = {
+        "rays": R, "samples_dense": s_dense, "samples_proposal": s_prop,
+        "psnr_vs_dense_render_db": round(proposal.psnr(c_prop, c_dense), 2),
+        "psnr_gap_vs_target_db": round(abs(proposal.psnr(c_prop, tt5) - proposal.psnr(c_dense, tt5)), 4),
+        "ms_per_step_dense": round(ms_dense, 3), "ms_per_step_proposal": round(ms_prop, 3),
+        "proposal_training": f"400 steps x {R} rays on the plain renderer's weights, {train_s:.1f} s"}
+    return out
 
 
 def cpu_baseline(workload, max_seconds=20.0):
@@ -355,7 +462,8 @@ def main():
     cfg, rp = res["cfg"], res["rp"]
     value = res["samples"] / (res["total_ms"] * 1e-3)
     e2e = res["e2e_samples"] / (res["e2e_total_ms"] * 1e-3)
-    launches_per_step = sum(v["calls_per_step"] for v in res["kt"].values()) + 2  # + scan/fill pairs
+    launches_per_step = sum(v["calls_per_step"] * KERNELS_PER_CALL.get(k, 1)
+                            for k, v in res["kt"].items())
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "ray-samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["total_ms"] / args.steps, 4),
@@ -372,6 +480,8 @@ def main():
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in res["kt"].items()},
         "clocks": res["clocks"],
     }
+    if not args.no_forms and world == 1:
+        line["forms"] = forms_report(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line))

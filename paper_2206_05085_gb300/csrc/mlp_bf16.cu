@@ -100,10 +100,6 @@ constexpr uint32_t kSboX = (kK1 / 8) * 128;   // 768: 8-row group stride of 48-w
 constexpr int kGW = 128;                      // gradient-tile width (hidden width, zero padded)
 constexpr uint32_t kSboG = (kGW / 8) * 128;   // 2048
 constexpr uint32_t kSpin = 1u << 24;
-// The backward reserves shared memory past its operands so that an MN-major
-// descriptor read with its two strides exchanged would still stay inside the
-// CTA's allocation.
-constexpr uint32_t kBwdSmemBytes = 160 * 1024;
 
 template <class Net>
 struct Layout {
@@ -336,206 +332,335 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_bf16_kernel(MlpIO io) {
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// Backward, warp specialised.  Two groups of four warps (WG0, WG1) take
+// alternate tiles; each owns its shared-memory operand buffers (X, [H1 | 1],
+// G) and a 128-column TMEM region that successively holds D1, D2, g_h1 and
+// g_X of its tile.  A ninth warp issues every MMA: it waits until a group
+// signals that the operands of the group's next stage are in shared memory,
+// issues that stage and commits it to the group's "done" barrier, so the
+// tensor core runs one group's products while the other group's epilogue
+// runs on the CUDA cores.  The weight-gradient accumulators (dW2|db2,
+// dW1|db1) sit in TMEM for the whole kernel and are only ever updated by
+// the issuing thread.  Every wait is bounded.
+namespace bf {
+
+__device__ __forceinline__ void named_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
+}
+
 template <class Net>
-__global__ void __launch_bounds__(128, 1) mlp_bwd_bf16_kernel(MlpIO io) {
-  using Lo = Layout<Net>;
+struct WsLayout {
+  static constexpr int H = Net::H;
+  static constexpr int H1W = H + 16;
+  static constexpr uint32_t kSboW2 = (H / 8) * 128;
+  static constexpr uint32_t kSboH1 = (H1W / 8) * 128;
+  static constexpr uint32_t oW1 = 0;
+  static constexpr uint32_t oW2 = oW1 + H * kK1 * 2;
+  static constexpr uint32_t oGroup = oW2 + H * H * 2;          // first group's buffers
+  static constexpr uint32_t gX = 0;                             // offsets inside a group
+  static constexpr uint32_t gH1 = gX + kTile * kK1 * 2;
+  static constexpr uint32_t gG = gH1 + kTile * H1W * 2;
+  static constexpr uint32_t kGroupBytes = gG + kTile * kGW * 2;
+  static constexpr uint32_t kOperands = oGroup + 2 * kGroupBytes;
+};
+
+template <class Net>
+struct WsSide {
+  float W3[Net::OUT * Net::H];
+  float b2[Net::H];
+  float b3[4];
+  uint64_t ready[2];
+  uint64_t done[2];
+  uint32_t tmem_slot;
+  int error;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+}  // namespace bf
+
+template <class Net>
+__global__ void __launch_bounds__(288, 1) mlp_bwd_bf16_kernel(MlpIO io) {
+  using Lo = WsLayout<Net>;
   constexpr int H = Net::H, OUT = Net::OUT, NCH = H / 32;
+  constexpr uint32_t cDW2 = 256, cDW1 = 400;
   extern __shared__ __align__(1024) uint8_t sm[];
-  F32Side<Net>* fs = reinterpret_cast<F32Side<Net>*>(sm + Lo::kBwdOperands);
-  static_assert(Lo::kBwdOperands + sizeof(F32Side<Net>) <= kBwdSmemBytes, "smem");
+  WsSide<Net>* fs = reinterpret_cast<WsSide<Net>*>(sm + Lo::kOperands);
+  static_assert(Lo::kOperands + sizeof(WsSide<Net>) <= 227 * 1024, "smem");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t n = mlp_count(io.n_cap, io.n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
-  if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
-  if (tid == 0) tc::mbar_init(&fs->bar, 1);
-  load_weights<Net>(io.params, sm, fs);
-  {  // constant columns of [H1 | 1 | 0...] and the zero columns of G past H
+  if (warp == 8) tc::tmem_alloc(&fs->tmem_slot, 512);
+  if (tid == 0) {
+    tc::mbar_init(&fs->ready[0], 1);
+    tc::mbar_init(&fs->ready[1], 1);
+    tc::mbar_init(&fs->done[0], 1);
+    tc::mbar_init(&fs->done[1], 1);
+    fs->error = 0;
+  }
+  // weights (all 288 threads)
+  for (int e = tid; e < H * kK1; e += blockDim.x) {
+    const int o = e / kK1, k = e % kK1;
+    float v = k < kIn ? io.params[Net::oW1 + o * kIn + k] : (k == kIn ? io.params[Net::oB1 + o] : 0.0f);
+    st_bf16(sm + Lo::oW1, tc::cm_off(o, k, kSboX), v);
+  }
+  for (int e = tid; e < H * H; e += blockDim.x) {
+    const int o = e / H, i = e % H;
+    st_bf16(sm + Lo::oW2, tc::cm_off(o, i, Lo::kSboW2), io.params[Net::oW2 + e]);
+  }
+  for (int e = tid; e < OUT * H; e += blockDim.x) fs->W3[e] = bfr(io.params[Net::oW3 + e]);
+  for (int e = tid; e < H; e += blockDim.x) fs->b2[e] = bfr(io.params[Net::oB2 + e]);
+  if (tid < 4) fs->b3[tid] = tid < OUT ? bfr(io.params[Net::oB3 + tid]) : 0.0f;
+  if (tid < 256) {  // constant columns of [H1 | 1 | 0..] and zero columns of G past H
+    uint8_t* grp = sm + Lo::oGroup + (tid >> 7) * Lo::kGroupBytes;
+    const int row = tid & 127;
     float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    st_row8(sm + Lo::oH1, tid, H, Lo::kSboH1, one);
-    st_row8(sm + Lo::oH1, tid, H + 8, Lo::kSboH1, z);
-    for (int k = H; k < kGW; k += 8) st_row8(sm + Lo::oG, tid, k, kSboG, z);
+    st_row8(grp + Lo::gH1, row, H, Lo::kSboH1, one);
+    st_row8(grp + Lo::gH1, row, H + 8, Lo::kSboH1, z);
+    for (int k = H; k < kGW; k += 8) st_row8(grp + Lo::gG, row, k, kSboG, z);
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  // TMEM columns: [0,H) D1 / g_h1, [128,128+H) D2 / g_X, [256,256+H+16) dW2|db2, [400,448) dW1|db1
-  constexpr uint32_t cD1 = 0, cD2 = 128, cDW2 = 256, cDW1 = 400;
-  const uint32_t sm_x = tc::smem_u32(sm + Lo::oX), sm_w1 = tc::smem_u32(sm + Lo::oW1);
-  const uint32_t sm_w2 = tc::smem_u32(sm + Lo::oW2), sm_h1 = tc::smem_u32(sm + Lo::oH1);
-  const uint32_t sm_g = tc::smem_u32(sm + Lo::oG);
-  float dW3acc[OUT * NCH];
+  const uint32_t sm_w1 = tc::smem_u32(sm + Lo::oW1), sm_w2 = tc::smem_u32(sm + Lo::oW2);
+
+  if (warp == 8) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int64_t left[2];
+      for (int w = 0; w < 2; ++w) {
+        const int64_t first = blockIdx.x + (int64_t)w * gridDim.x;
+        const int64_t tiles = first < ntiles ? (ntiles - 1 - first) / (2 * (int64_t)gridDim.x) + 1 : 0;
+        left[w] = 4 * tiles;  // four MMA stages per tile
+      }
+      int stage[2] = {0, 0};
+      uint32_t ph[2] = {0, 0};
+      bool dw2_started = false, dw1_started = false;  // first accumulation initialises
+      uint32_t spins = 0;
+      while ((left[0] > 0 || left[1] > 0) && !*(volatile int*)&fs->error) {
+        bool served = false;
+        for (int w = 0; w < 2; ++w) {
+          if (left[w] == 0 || !tc::mbar_try_wait(&fs->ready[w], ph[w])) continue;
+          ph[w] ^= 1;
+          served = true;
+          tc::fence_after_sync();
+          uint8_t* grp = sm + Lo::oGroup + w * Lo::kGroupBytes;
+          const uint32_t sx = tc::smem_u32(grp + Lo::gX), sh1 = tc::smem_u32(grp + Lo::gH1);
+          const uint32_t sg = tc::smem_u32(grp + Lo::gG);
+          const uint32_t dcol = tmem + 128 * w;
+          if (stage[w] == 0) {          // D = X W1^T
+            const uint32_t id = tc::idesc_bf16(128, H, 0, 0);
 #pragma unroll
-  for (int i = 0; i < OUT * NCH; ++i) dW3acc[i] = 0.0f;
-  float db3acc[OUT];
+            for (int j = 0; j < kK1 / 16; ++j)
+              tc::mma_bf16(dcol, tc::smem_desc(sx + 256 * j, 128, kSboX),
+                           tc::smem_desc(sm_w1 + 256 * j, 128, kSboX), id, j > 0);
+          } else if (stage[w] == 1) {   // D = H1 W2^T
+            const uint32_t id = tc::idesc_bf16(128, H, 0, 0);
 #pragma unroll
-  for (int c = 0; c < OUT; ++c) db3acc[c] = 0.0f;
-  uint32_t phase = 0;
-  bool ok = true;
-  int it = 0;
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-    const int64_t j = t * kTile + tid;
-    const bool valid = j < n;
-    int64_t s = 0;
-    float gup[OUT];
+            for (int j = 0; j < H / 16; ++j)
+              tc::mma_bf16(dcol, tc::smem_desc(sh1 + 256 * j, 128, Lo::kSboH1),
+                           tc::smem_desc(sm_w2 + 256 * j, 128, Lo::kSboW2), id, j > 0);
+          } else if (stage[w] == 2) {   // dW2|db2 += G^T [H1 | 1];  D = G W2
+            const uint32_t id_dw2 = tc::idesc_bf16(128, Lo::H1W, 1, 1);
 #pragma unroll
-    for (int c = 0; c < OUT; ++c) gup[c] = 0.0f;
-    if (valid) {
-      s = io.idx ? (int64_t)__ldg(io.idx + j) : j;
-      Net::upstream(io, s, gup);
+            for (int k = 0; k < kTile / 16; ++k)
+              tc::mma_bf16(tmem + cDW2, tc::smem_desc_mn(sg + k * 2 * kSboG, kSboG, 128),
+                           tc::smem_desc_mn(sh1 + k * 2 * Lo::kSboH1, Lo::kSboH1, 128), id_dw2,
+                           (dw2_started || k > 0) ? 1u : 0u);
+            dw2_started = true;
+            const uint32_t id_gh = tc::idesc_bf16(128, H, 0, 1);
+#pragma unroll
+            for (int k = 0; k < H / 16; ++k)
+              tc::mma_bf16(dcol, tc::smem_desc(sg + k * 256, 128, kSboG),
+                           tc::smem_desc_mn(sm_w2 + k * 2 * Lo::kSboW2, Lo::kSboW2, 128), id_gh, k > 0);
+          } else {                      // dW1|db1 += G^T X;  D[:, 0:16] = G W1[:, 0:16]
+            const uint32_t id_dw1 = tc::idesc_bf16(128, kK1, 1, 1);
+#pragma unroll
+            for (int k = 0; k < kTile / 16; ++k)
+              tc::mma_bf16(tmem + cDW1, tc::smem_desc_mn(sg + k * 2 * kSboG, kSboG, 128),
+                           tc::smem_desc_mn(sx + k * 2 * kSboX, kSboX, 128), id_dw1,
+                           (dw1_started || k > 0) ? 1u : 0u);
+            dw1_started = true;
+            if (Net::kInputGrad) {
+              const uint32_t id_gx = tc::idesc_bf16(128, 16, 0, 1);
+#pragma unroll
+              for (int k = 0; k < H / 16; ++k)
+                tc::mma_bf16(dcol, tc::smem_desc(sg + k * 256, 128, kSboG),
+                             tc::smem_desc_mn(sm_w1 + k * 2 * kSboX, kSboX, 128), id_gx, k > 0);
+            }
+          }
+          tc::mma_commit(&fs->done[w]);
+          stage[w] = (stage[w] + 1) & 3;
+          --left[w];
+        }
+        if (served) spins = 0;
+        else if (++spins > kSpin) atomicExch(&fs->error, 1);
+      }
     }
-    {
-      float x[kInP];
-      Net::encode(io, j, n, x);
-      write_x_row<Net>(sm, tid, x);
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();
+  } else {
+    // --------------------------------------------------- epilogue groups
+    const int w = warp >> 2;                 // group
+    const int row = tid & 127;               // tile row = TMEM lane
+    uint8_t* grp = sm + Lo::oGroup + w * Lo::kGroupBytes;
+    const uint32_t lane_base = tmem + 128 * w + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t ph = 0;
+    float dW3acc[OUT * NCH];
+#pragma unroll
+    for (int i = 0; i < OUT * NCH; ++i) dW3acc[i] = 0.0f;
+    float db3acc[OUT];
+#pragma unroll
+    for (int c = 0; c < OUT; ++c) db3acc[c] = 0.0f;
+    auto signal = [&]() {
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      named_bar(1 + w);
+      if (row == 0) mbar_arrive(&fs->ready[w]);
+    };
+    auto await = [&]() -> bool {
+      bool ok = tc::mbar_wait(&fs->done[w], ph, kSpin);
+      ph ^= 1;
+      if (!ok) atomicExch(&fs->error, 1);
       tc::fence_after_sync();
-      issue_layer1<Net>(sm, tmem + cD1);
-      tc::mma_commit(&fs->bar);
-    }
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
-    tc::fence_after_sync();
-    epilogue_h1<Net>(sm, lane_base + cD1, tid);
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      issue_layer2<Net>(sm, tmem + cD2);
-      tc::mma_commit(&fs->bar);
-    }
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
-    tc::fence_after_sync();
-    // ---- epilogue 2: output-layer gradient, g_z2, dW3
-    float z3[OUT];
-    layer3_z<Net>(fs, lane_base + cD2, z3);
-    float gz3[OUT];
+      return ok && !*(volatile int*)&fs->error;
+    };
+    for (int64_t t = blockIdx.x + (int64_t)w * gridDim.x; t < ntiles; t += 2 * (int64_t)gridDim.x) {
+      const int64_t j = t * kTile + row;
+      const bool valid = j < n;
+      int64_t s = 0;
+      float gup[OUT];
 #pragma unroll
-    for (int c = 0; c < OUT; ++c) {
-      if (Net::kSigmoid) {
-        const float y = sigmoid_f(z3[c]);
-        gz3[c] = gup[c] * y * (1.0f - y);
-      } else {
-        gz3[c] = gup[c];
-      }
-      db3acc[c] += gz3[c];
-    }
-#pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
-      float v[32], g[32];
-      tc::tmem_ld32(lane_base + cD2 + ch * 32, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int o = ch * 32 + i;
-        const float z2 = v[i] + fs->b2[o];
-        float gs = 0.0f;
-#pragma unroll
-        for (int c = 0; c < OUT; ++c) gs = fmaf(gz3[c], fs->W3[c * H + o], gs);
-        g[i] = z2 > 0.0f ? gs : 0.0f;
-        v[i] = fmaxf(z2, 0.0f);  // h2
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) st_row8(sm + Lo::oG, tid, ch * 32 + q * 8, kSboG, g + 8 * q);
-#pragma unroll 1
-      for (int c = 0; c < OUT; ++c) {
-        float p[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
-        dW3acc[c * NCH + ch] += reduce_scatter32(p, lane);
-      }
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      // dW2|db2 (+)= G^T [H1 | 1]: M = o (128, rows past H stay 0), N = H + 16, K = s
-      const uint32_t id_dw2 = tc::idesc_bf16(128, Lo::H1W, 1, 1);
-#pragma unroll
-      for (int k = 0; k < kTile / 16; ++k)
-        tc::mma_bf16(tmem + cDW2, tc::smem_desc_mn(sm_g + k * 2 * kSboG, kSboG, 128),
-                     tc::smem_desc_mn(sm_h1 + k * 2 * Lo::kSboH1, Lo::kSboH1, 128), id_dw2,
-                     (it > 0 || k > 0) ? 1u : 0u);
-      // g_h1 = G W2: M = s, N = i, K = o; A K-major, B (W2 stored [o][i]) MN-major
-      const uint32_t id_gh = tc::idesc_bf16(128, H, 0, 1);
-#pragma unroll
-      for (int k = 0; k < H / 16; ++k)
-        tc::mma_bf16(tmem + cD1, tc::smem_desc(sm_g + k * 256, 128, kSboG),
-                     tc::smem_desc_mn(sm_w2 + k * 2 * Lo::kSboW2, Lo::kSboW2, 128), id_gh, k > 0);
-      tc::mma_commit(&fs->bar);
-    }
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
-    tc::fence_after_sync();
-    // ---- epilogue 3: g_z1 = g_h1 * (H1 > 0), written over G
-#pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
-      float v[32];
-      tc::tmem_ld32(lane_base + cD1 + ch * 32, v);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float h[8];
-        ld_row8(sm + Lo::oH1, tid, ch * 32 + q * 8, Lo::kSboH1, h);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[8 * q + i] = h[i] > 0.0f ? v[8 * q + i] : 0.0f;
-        st_row8(sm + Lo::oG, tid, ch * 32 + q * 8, kSboG, v + 8 * q);
-      }
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      // dW1|db1 (+)= G1^T X: M = o (128), N = 48, K = s; both MN-major
-      const uint32_t id_dw1 = tc::idesc_bf16(128, kK1, 1, 1);
-#pragma unroll
-      for (int k = 0; k < kTile / 16; ++k)
-        tc::mma_bf16(tmem + cDW1, tc::smem_desc_mn(sm_g + k * 2 * kSboG, kSboG, 128),
-                     tc::smem_desc_mn(sm_x + k * 2 * kSboX, kSboX, 128), id_dw1,
-                     (it > 0 || k > 0) ? 1u : 0u);
-      if (Net::kInputGrad) {
-        // g_X[:, 0:16] = G1 W1: M = s, N = 16, K = o; A K-major, B (W1 stored [o][in]) MN-major
-        const uint32_t id_gx = tc::idesc_bf16(128, 16, 0, 1);
-#pragma unroll
-        for (int k = 0; k < H / 16; ++k)
-          tc::mma_bf16(tmem + cD2, tc::smem_desc(sm_g + k * 256, 128, kSboG),
-                       tc::smem_desc_mn(sm_w1 + k * 2 * kSboX, kSboX, 128), id_gx, k > 0);
-      }
-      tc::mma_commit(&fs->bar);
-    }
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
-    tc::fence_after_sync();
-    if (Net::kInputGrad) {
-      float gx[16];
-      tc::tmem_ld16(lane_base + cD2, gx);
+      for (int c = 0; c < OUT; ++c) gup[c] = 0.0f;
       if (valid) {
-        float4* dst = reinterpret_cast<float4*>(io.g_in + s * kFeat);
-        dst[0] = make_float4(gx[0], gx[1], gx[2], gx[3]);
-        dst[1] = make_float4(gx[4], gx[5], gx[6], gx[7]);
-        dst[2] = make_float4(gx[8], gx[9], gx[10], gx[11]);
+        s = io.idx ? (int64_t)__ldg(io.idx + j) : j;
+        Net::upstream(io, s, gup);
       }
+      {
+        float x[kInP];
+        Net::encode(io, j, n, x);
+        float v[8];
+#pragma unroll
+        for (int kb = 0; kb < kK1 / 8; ++kb) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = kb * 8 + i < kInP ? x[kb * 8 + i] : 0.0f;
+          st_row8(grp + Lo::gX, row, kb * 8, kSboX, v);
+        }
+      }
+      signal();                                   // stage 0: D = X W1^T
+      if (!await()) break;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {          // epilogue 1: H1 = relu(D)
+        float v[32];
+        tc::tmem_ld32(lane_base + ch * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.0f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st_row8(grp + Lo::gH1, row, ch * 32 + q * 8, Lo::kSboH1, v + 8 * q);
+      }
+      signal();                                   // stage 1: D = H1 W2^T
+      if (!await()) break;
+      float z3[OUT];                              // epilogue 2
+#pragma unroll
+      for (int c = 0; c < OUT; ++c) z3[c] = fs->b3[c];
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {
+        float v[32];
+        tc::tmem_ld32(lane_base + ch * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int o = ch * 32 + i;
+          const float h = fmaxf(v[i] + fs->b2[o], 0.0f);
+#pragma unroll
+          for (int c = 0; c < OUT; ++c) z3[c] = fmaf(fs->W3[c * H + o], h, z3[c]);
+        }
+      }
+      float gz3[OUT];
+#pragma unroll
+      for (int c = 0; c < OUT; ++c) {
+        if (Net::kSigmoid) {
+          const float y = sigmoid_f(z3[c]);
+          gz3[c] = gup[c] * y * (1.0f - y);
+        } else {
+          gz3[c] = gup[c];
+        }
+        db3acc[c] += gz3[c];
+      }
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {
+        float v[32], g[32];
+        tc::tmem_ld32(lane_base + ch * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int o = ch * 32 + i;
+          const float z2 = v[i] + fs->b2[o];
+          float gs = 0.0f;
+#pragma unroll
+          for (int c = 0; c < OUT; ++c) gs = fmaf(gz3[c], fs->W3[c * H + o], gs);
+          g[i] = z2 > 0.0f ? gs : 0.0f;
+          v[i] = fmaxf(z2, 0.0f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st_row8(grp + Lo::gG, row, ch * 32 + q * 8, kSboG, g + 8 * q);
+#pragma unroll 1
+        for (int c = 0; c < OUT; ++c) {
+          float p[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
+          dW3acc[c * NCH + ch] += reduce_scatter32(p, lane);
+        }
+      }
+      signal();                                   // stage 2: dW2 += G^T [H1|1]; D = G W2
+      if (!await()) break;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {          // epilogue 3: g_z1 over G
+        float v[32];
+        tc::tmem_ld32(lane_base + ch * 32, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float h[8];
+          ld_row8(grp + Lo::gH1, row, ch * 32 + q * 8, Lo::kSboH1, h);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[8 * q + i] = h[i] > 0.0f ? v[8 * q + i] : 0.0f;
+          st_row8(grp + Lo::gG, row, ch * 32 + q * 8, kSboG, v + 8 * q);
+        }
+      }
+      signal();                                   // stage 3: dW1 += G^T X; D = G W1
+      if (!await()) break;
+      if (Net::kInputGrad) {                      // epilogue 4
+        float gx[16];
+        tc::tmem_ld16(lane_base, gx);
+        if (valid) {
+          float4* dst = reinterpret_cast<float4*>(io.g_in + s * kFeat);
+          dst[0] = make_float4(gx[0], gx[1], gx[2], gx[3]);
+          dst[1] = make_float4(gx[4], gx[5], gx[6], gx[7]);
+          dst[2] = make_float4(gx[8], gx[9], gx[10], gx[11]);
+        }
+      }
+      tc::fence_before_sync();
+      named_bar(1 + w);                           // TMEM region and X free for the next tile
     }
-    tc::fence_before_sync();
+    // output-layer partials of this thread
+#pragma unroll
+    for (int c = 0; c < OUT; ++c)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch)
+        atomicAdd(io.g_params + Net::oW3 + c * H + ch * 32 + lane, dW3acc[c * NCH + ch]);
+#pragma unroll
+    for (int c = 0; c < OUT; ++c) atomicAdd(io.g_params + Net::oB3 + c, db3acc[c]);
   }
+  tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (ok && it > 0) {
+  const bool ok = fs->error == 0;
+  if (ok && warp < 4 && ntiles > blockIdx.x) {
     // TMEM lane = output neuron o (rows o >= H are padding)
     const int o = tid;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int ch = 0; ch < NCH; ++ch) {
       float v[32];
@@ -561,19 +686,12 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_bf16_kernel(MlpIO io) {
         atomicAdd(io.g_params + Net::oB1 + o, u[kIn - 32]);
       }
     }
-#pragma unroll
-    for (int c = 0; c < OUT; ++c)
-#pragma unroll
-      for (int ch = 0; ch < NCH; ++ch)
-        atomicAdd(io.g_params + Net::oW3 + c * H + ch * 32 + lane, dW3acc[c * NCH + ch]);
-#pragma unroll
-    for (int c = 0; c < OUT; ++c) atomicAdd(io.g_params + Net::oB3 + c, db3acc[c]);
   }
   if (!ok && tid == 0) atomicExch(&g_mlp_status, (int)DVGO_ERR_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  if (warp == 8) tc::tmem_dealloc(tmem, 512);
 }
 
 template <class Net>
@@ -592,7 +710,7 @@ static int launch_fwd(const MlpIO& io, cudaStream_t st) {
 
 template <class Net>
 static int launch_bwd(const MlpIO& io, cudaStream_t st) {
-  const size_t smem = kBwdSmemBytes;
+  const size_t smem = WsLayout<Net>::kOperands + sizeof(WsSide<Net>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(mlp_bwd_bf16_kernel<Net>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -600,7 +718,7 @@ static int launch_bwd(const MlpIO& io, cudaStream_t st) {
   }
   int grid = (int)std::min<int64_t>((io.n_cap + kTile - 1) / kTile, kNumSMs);
   if (grid < 1) return DVGO_OK;
-  mlp_bwd_bf16_kernel<Net><<<grid, 128, smem, st>>>(io);
+  mlp_bwd_bf16_kernel<Net><<<grid, 288, smem, st>>>(io);
   return launch_status();
 }
 
