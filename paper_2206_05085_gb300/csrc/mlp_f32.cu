@@ -64,10 +64,13 @@ __device__ __forceinline__ void gemm_nt(const float* A, int lda, const float* B,
     for (int a = 0; a < 8; ++a) av[a] = ld4(A + (ty + 16 * a) * lda + k);
 #pragma unroll
     for (int b = 0; b < 8; ++b) bv[b] = ld4(B + (tx + 16 * b) * ldb + k);
+    // outer-product order: 64 independent FMAs per k
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = dot4(av[a], bv[b], acc[a][b]);
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(comp(av[a], q), comp(bv[b], q), acc[a][b]);
   }
 }
 
