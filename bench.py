@@ -106,26 +106,45 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- ours
 def kernel_flops_bytes(tr):
-    """Algorithmic work per step of the main kernels."""
+    """Counts of one step that the algorithmic-work formulas use: samples, live
+    samples, and the distinct grid voxels and bricks the trilinear corners of
+    all samples / of the live samples touch (the lower corner follows the
+    sampler's border clamp; measurement only, outside every timed region)."""
     import torch
-    from paper_2206_05085_gb300 import _lib as L
     torch.cuda.synchronize()
     S = int(tr.ray_off[-1].item())
     S_live = int(tr.live_count.item())
-    nb_touch_d = int(tr.density.touched.sum().item())
-    nb_touch_f = int(tr.feature.touched.sum().item())
-    return S, S_live, nb_touch_d, nb_touch_f
+    G = tr.G[0]
+    cfg = tr.cfg
+    scale = (G - 1) / (cfg.bbox_max - cfg.bbox_min)
+    offs = torch.tensor([(k >> 2) * G * G + ((k >> 1) & 1) * G + (k & 1) for k in range(8)],
+                        dtype=torch.int64, device=tr.xyz.device)
+
+    def distinct(xyz):
+        u = ((xyz - cfg.bbox_min) * scale).clamp(0, G - 1).floor().to(torch.int64).clamp(max=G - 2)
+        base = (u[:, 2] * G + u[:, 1]) * G + u[:, 0]
+        vox = torch.unique((base[:, None] + offs).reshape(-1))
+        x, y, z = vox % G, (vox // G) % G, vox // (G * G)
+        nbx = (G + 7) // 8
+        bricks = torch.unique(((z // 8) * nbx + y // 8) * nbx + x // 8)
+        return int(vox.numel()), int(bricks.numel())
+
+    V_all, _ = distinct(tr.xyz[:S])
+    V_live, B_live = distinct(tr.xyz[tr.live_idx[:S_live].long()])
+    return dict(S=S, S_live=S_live, R=tr.R, V_all=V_all, V_live=V_live, B_live=B_live)
 
 
-def per_kernel_times(tr, batches, reps=5):
-    """Average duration of each C-ABI call of one step, CUDA events on the
-    launching stream (the current stream)."""
+def per_kernel_times(tr, batches, flush, reps=5):
+    """Duration of each C-ABI call of one step, CUDA events on the launching
+    stream (the current stream), L2 flushed before each step as in the timed
+    run.  Calls are keyed "name#k", k the call's position among the step's
+    calls of that name (e.g. density then feature for the grid calls)."""
     import torch
     from paper_2206_05085_gb300 import _lib as L
-    names = []
     orig = L._call
     stream = torch.cuda.current_stream()
     events = []
+    seen = {}
 
     def timed(name, *args):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -133,24 +152,36 @@ def per_kernel_times(tr, batches, reps=5):
         e0.record(stream)
         orig(name, *args)
         e1.record(stream)
-        events.append((name, e0, e1))
+        k = seen.get(name, 0)
+        seen[name] = k + 1
+        events.append((f"{name}#{k}", e0, e1))
 
     L._call = timed
     try:
         for r in range(reps):
+            flush.zero_()
+            seen.clear()
             o, d, t = batches[r % len(batches)]
             tr.step(o, d, t)
     finally:
         L._call = orig
     torch.cuda.synchronize()
     acc = {}
-    for name, e0, e1 in events:
-        acc.setdefault(name, []).append(e0.elapsed_time(e1))
+    for key, e0, e1 in events:
+        acc.setdefault(key, []).append(e0.elapsed_time(e1))
+    return {key: sum(ts) / len(ts) for key, ts in acc.items()}
+
+
+def by_entry_point(calls):
+    """Per C-ABI entry point: ms per step, calls per step, ms per call."""
     out = {}
-    for name, ts in acc.items():
-        calls_per_step = len(ts) // reps
-        out[name] = {"ms_per_step": sum(ts) / reps, "calls_per_step": calls_per_step,
-                     "ms_per_call": sum(ts) / len(ts)}
+    for key, ms in calls.items():
+        name = key.split("#")[0]
+        r = out.setdefault(name, {"ms_per_step": 0.0, "calls_per_step": 0})
+        r["ms_per_step"] += ms
+        r["calls_per_step"] += 1
+    for r in out.values():
+        r["ms_per_call"] = r["ms_per_step"] / r["calls_per_step"]
     return out
 
 
@@ -245,8 +276,10 @@ def run_ours(args, rank, world):
         e2e_ms.append(e0.elapsed_time(e1))
     clock_info = clocks.stop() if clocks else None
 
-    kt = per_kernel_times(tr, batches[:1], reps=5)
-    S, S_live, nbd, nbf = kernel_flops_bytes(tr)
+    calls = per_kernel_times(tr, batches[:1], flush, reps=5)
+    kt = by_entry_point(calls)
+    counts = kernel_flops_bytes(tr)
+    S, S_live = counts["S"], counts["S_live"]
     if world > 1:
         t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -257,8 +290,8 @@ def run_ours(args, rank, world):
     else:
         e2e_total = sum(e2e_ms)
     return dict(total_ms=total_ms, samples=samples, e2e_total_ms=e2e_total,
-                e2e_samples=samples, kt=kt, clocks=clock_info, S=S, S_live=S_live,
-                touched=(nbd, nbf), h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
+                e2e_samples=samples, kt=kt, calls=calls, counts=counts, clocks=clock_info, S=S,
+                S_live=S_live, h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
 
 
 # Algorithmic work per unit ("Kernels and their rooflines").
@@ -303,6 +336,60 @@ def roofline(res, peaks):
     out["ms_per_call"] = round(ms, 4)
     out["share"] = round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)
     return out
+
+
+def memory_kernels(res, peaks):
+    """Achieved bandwidth of the memory-bound kernels of one step: algorithmic
+    bytes per launch (what the method must move; formulas below, per sample /
+    per live sample / per distinct voxel / per ray) / CUDA-event duration,
+    against the measured HBM copy peak."""
+    c, calls, prec = res["counts"], res["calls"], res["prec"]
+    S, SL, R, Va, Vl, Bl = c["S"], c["S_live"], c["R"], c["V_all"], c["V_live"], c["B_live"]
+    F = 12
+    e = 2 if prec == "bf16" else 4          # bytes per grid element the renderer reads
+    sh = 2 if prec == "bf16" else 0         # BF16 shadow written by Adam
+    ent_d, ent_f = Bl * 512, Bl * 512 * F   # grid entries in the touched bricks
+    algo = {
+        # xyz + value out per sample, each distinct corner voxel once
+        "dvgo_sample_grid_fwd#0": S * (12 + 4) + Va * e,
+        "dvgo_sample_grid_fwd#1": SL * (4 + 12 + 4 * F) + Vl * e * F,
+        # raw in, w and T out per sample; ray_off, n_live, T_end per ray
+        "dvgo_alpha_weights_fwd#0": S * 12 + R * 16,
+        "dvgo_composite_rgb_fwd#0": SL * 16 + R * 28,
+        "dvgo_distortion_fwd#0": SL * 12 + R * 16,
+        "dvgo_distortion_bwd#0": SL * 16 + R * 12,
+        # g_w, raw, T, rgb in and g_raw out per live sample, g_raw zeroed past the halt
+        "dvgo_composite_bwd#0": SL * 28 + (S - SL) * 4 + R * 24,
+        # g, xyz, index per live sample; FP32 gradient read-modify-write per distinct voxel
+        "dvgo_sample_grid_bwd#0": SL * (4 + 12 + 4) + Vl * 8,
+        "dvgo_sample_grid_bwd#1": SL * (4 * F + 12 + 4) + Vl * 8 * F,
+        # sparse TV: the gradient of every entry of a touched brick is read; entries
+        # with a non-zero gradient (the distinct voxels the scatter reached) also
+        # read their value and write the gradient back
+        "dvgo_tv_add_grad#0": ent_d * 4 + Vl * (e + 4),
+        "dvgo_tv_add_grad#1": ent_f * 4 + Vl * F * (e + 4),
+        # Adam: g of every entry of a touched brick; where g != 0, p, m, v in and
+        # p, m, v, g (and the BF16 shadow) out
+        "dvgo_adam_step#0": ent_d * 4 + Vl * (28 + sh),
+        "dvgo_adam_step#1": ent_f * 4 + Vl * F * (28 + sh),
+    }
+    peak = peaks.get("hbm_gbs", 6701.5)
+    out = {}
+    for key, b in algo.items():
+        if key not in calls:
+            continue
+        ms = calls[key]
+        gbs = b / (ms * 1e-3) / 1e9
+        out[key] = {"bytes": int(b), "ms": round(ms, 4), "achieved_gbs": round(gbs, 1),
+                    "frac": round(gbs / peak, 3)}
+    tot_b = sum(v["bytes"] for v in out.values())
+    tot_ms = sum(v["ms"] for v in out.values())
+    return {"peak_gbs": peak, "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks
+            else "6701.5 GB/s (earlier measurement on this pool)",
+            "counts": c, "kernels": out,
+            "all": {"bytes": tot_b, "ms": round(tot_ms, 4),
+                    "achieved_gbs": round(tot_b / (tot_ms * 1e-3) / 1e9, 1),
+                    "frac": round(tot_b / (tot_ms * 1e-3) / 1e9 / peak, 3)}}
 
 
 def traffic_for(name, prec, units):
@@ -477,6 +564,7 @@ def main():
                 "d2h_bytes_per_step": 12},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline(res, peaks),
+        "memory_kernels": memory_kernels(res, peaks),
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in res["kt"].items()},
         "clocks": res["clocks"],
     }

@@ -269,43 +269,105 @@ __global__ void mask_kernel(const void* __restrict__ density, bool bf16, BrickGe
 }
 
 // ------------------------------------------------------------------- TV
-// One block per brick (512 threads, one voxel each, channels looped).
+// One block per brick, 512 threads, thread t on the brick's Morton slot t, so a
+// warp covers 32 consecutive voxels (contiguous memory) and the +-x/y/z
+// neighbours of most voxels sit in the same or an adjacent warp's lines.
+// Each thread handles all channels of its voxel with 128-bit loads when C % 4
+// == 0.  Neighbours are summed in the order -x, +x, -y, +y, -z, +z.
+__device__ __forceinline__ int compact3(uint32_t v) {
+  return (int)((v & 1u) | ((v >> 2) & 2u) | ((v >> 4) & 4u));
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void load_vox4(const void* grid, int64_t slot, int C, int q, float v[4]) {
+  if constexpr (kBF16) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(grid) + slot * C) + q);
+    v[0] = __uint_as_float(u.x << 16);
+    v[1] = __uint_as_float(u.x & 0xffff0000u);
+    v[2] = __uint_as_float(u.y << 16);
+    v[3] = __uint_as_float(u.y & 0xffff0000u);
+  } else {
+    float4 f = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(grid) + slot * C) + q);
+    v[0] = f.x;
+    v[1] = f.y;
+    v[2] = f.z;
+    v[3] = f.w;
+  }
+}
+
+template <bool kBF16>
+__device__ __forceinline__ float load_val(const void* grid, int64_t e) {
+  return kBF16 ? bf16_bits_to_f32(__ldg(reinterpret_cast<const uint16_t*>(grid) + e))
+               : __ldg(reinterpret_cast<const float*>(grid) + e);
+}
+
 template <bool kBF16>
 __global__ void __launch_bounds__(512) tv_kernel(const void* __restrict__ grid, BrickGeom g, int C,
                                                  float scale, float delta, int dense_mode,
                                                  uint8_t* __restrict__ touched,
                                                  float* __restrict__ g_grid) {
   const int64_t nb = g.num_bricks();
+  const int t = threadIdx.x;
+  const int lx = compact3(t), ly = compact3(t >> 1), lz = compact3(t >> 2);
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
     if (!dense_mode && touched && touched[b] == 0) continue;
+    if (dense_mode && touched && t == 0) touched[b] = 1;
     const int bx = (int)(b % g.nb[0]);
     const int by = (int)((b / g.nb[0]) % g.nb[1]);
     const int bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
-    const int t = threadIdx.x;
-    const int x = bx * 8 + (t & 7), y = by * 8 + ((t >> 3) & 7), z = bz * 8 + (t >> 6);
-    if (dense_mode && touched && t == 0) touched[b] = 1;
+    const int x = bx * 8 + lx, y = by * 8 + ly, z = bz * 8 + lz;
     if (x >= g.G[0] || y >= g.G[1] || z >= g.G[2]) continue;
-    const int64_t self = voxel_slot(g, x, y, z);
+    const int64_t self = b * kBrickVox + t;
     int64_t nbr[6];
-    int nn = 0;
-    if (x > 0) nbr[nn++] = voxel_slot(g, x - 1, y, z);
-    if (x + 1 < g.G[0]) nbr[nn++] = voxel_slot(g, x + 1, y, z);
-    if (y > 0) nbr[nn++] = voxel_slot(g, x, y - 1, z);
-    if (y + 1 < g.G[1]) nbr[nn++] = voxel_slot(g, x, y + 1, z);
-    if (z > 0) nbr[nn++] = voxel_slot(g, x, y, z - 1);
-    if (z + 1 < g.G[2]) nbr[nn++] = voxel_slot(g, x, y, z + 1);
-    for (int c = 0; c < C; ++c) {
-      float* gp = g_grid + self * C + c;
-      float gin = *gp;
-      if (!dense_mode && gin == 0.0f) continue;
-      auto val = [&](int64_t slot) -> float {
-        return kBF16 ? bf16_bits_to_f32(reinterpret_cast<const uint16_t*>(grid)[slot * C + c])
-                     : reinterpret_cast<const float*>(grid)[slot * C + c];
-      };
-      const float v = val(self);
-      float acc = 0.0f;
-      for (int q = 0; q < nn; ++q) acc += fminf(fmaxf(v - val(nbr[q]), -delta), delta);
-      *gp = gin + scale * acc;
+    bool has[6];
+    has[0] = x > 0;
+    has[1] = x + 1 < g.G[0];
+    has[2] = y > 0;
+    has[3] = y + 1 < g.G[1];
+    has[4] = z > 0;
+    has[5] = z + 1 < g.G[2];
+    nbr[0] = has[0] ? voxel_slot(g, x - 1, y, z) : self;
+    nbr[1] = has[1] ? voxel_slot(g, x + 1, y, z) : self;
+    nbr[2] = has[2] ? voxel_slot(g, x, y - 1, z) : self;
+    nbr[3] = has[3] ? voxel_slot(g, x, y + 1, z) : self;
+    nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
+    nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
+    if (C % 4 == 0) {
+      for (int q = 0; q < C / 4; ++q) {
+        float4* gp = reinterpret_cast<float4*>(g_grid + self * C) + q;
+        const float4 gin = *gp;
+        const bool any = gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
+        if (!dense_mode && !any) continue;
+        float v[4], acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        load_vox4<kBF16>(grid, self, C, q, v);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          if (!has[d]) continue;
+          float u[4];
+          load_vox4<kBF16>(grid, nbr[d], C, q, u);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i] += fminf(fmaxf(v[i] - u[i], -delta), delta);
+        }
+        float4 out = gin;
+        // sparse mode adds the TV gradient only where the data gradient is non-zero
+        if (dense_mode || gin.x != 0.0f) out.x = gin.x + scale * acc[0];
+        if (dense_mode || gin.y != 0.0f) out.y = gin.y + scale * acc[1];
+        if (dense_mode || gin.z != 0.0f) out.z = gin.z + scale * acc[2];
+        if (dense_mode || gin.w != 0.0f) out.w = gin.w + scale * acc[3];
+        *gp = out;
+      }
+    } else {
+      for (int c = 0; c < C; ++c) {
+        float* gp = g_grid + self * C + c;
+        const float gin = *gp;
+        if (!dense_mode && gin == 0.0f) continue;
+        const float v = load_val<kBF16>(grid, self * C + c);
+        float acc = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+          if (has[d]) acc += fminf(fmaxf(v - load_val<kBF16>(grid, nbr[d] * C + c), -delta), delta);
+        *gp = gin + scale * acc;
+      }
     }
   }
 }
@@ -508,7 +570,7 @@ extern "C" int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3],
   double N = (double)G[0] * G[1] * G[2];
   float scale = (float)((double)weight * 2.0 / (N * C));
   cudaStream_t st = as_stream(stream);
-  int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 4);
+  int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 16);
   if (dtype == DVGO_F32)
     tv_kernel<false><<<nb, 512, 0, st>>>(grid, g, C, scale, delta, dense_mode, touched, g_grid);
   else

@@ -103,6 +103,46 @@ def test_trilinear_fwd_bwd(L, C, bf16):
     assert np.all(got_t[tb])
 
 
+@pytest.mark.parametrize("C", [1, 12])
+def test_trilinear_adjoint_along_rays(L, C):
+    """Ray-ordered samples (the layout the renderer produces): consecutive list
+    positions share corner voxels, so the scatter's per-warp aggregation table
+    sums most contributions before the global reductions; rays of 1-3 samples
+    mixed with long ones also fill the table past its capacity."""
+    rng = np.random.default_rng(40 + C)
+    G = (40, 33, 37)
+    lo, hi = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0])
+    vs = 2.0 / 32
+    pts = []
+    for r in range(300):
+        o = rng.uniform(-0.9, 0.9, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        k = int(rng.choice([1, 2, 3, 40, 90]))
+        step = vs * rng.choice([0.25, 0.5, 1.0])
+        pts.append(np.clip(o + d * step * np.arange(k)[:, None], -1.05, 1.05))
+    xyz = np.concatenate(pts).astype(np.float32)
+    n = len(xyz)
+    live = np.sort(rng.choice(n, int(0.8 * n), replace=False)).astype(np.int32)
+    g_out = rng.normal(size=(n, C)).astype(np.float32)
+    gd = L.GridDesc.make(lo, hi, G)
+    g_grid = torch.zeros(L.grid_bricked_elems(G, C), device="cuda")
+    touched = torch.zeros(L.grid_num_bricks(G), dtype=torch.uint8, device="cuda")
+    n_dev = torch.tensor([len(live)], dtype=torch.int64, device="cuda")
+    L.sample_grid_bwd(dev(g_out), gd, C, dev(xyz), dev(live), n, n_dev, g_grid, touched)
+    gg = torch.empty(G[2], G[1], G[0], C, device="cuda")
+    L.grid_unpack(g_grid, gg, G, C, L.F32)
+    ref_g = oracle.trilinear_adjoint(g_out[live], (G[2], G[1], G[0], C), lo, hi, xyz[live])
+    assert rel_err(host(gg), ref_g) < TOL32
+    nz = np.abs(ref_g).sum(-1) > 0
+    nb = [(g + 7) // 8 for g in G]
+    tb = np.zeros((nb[2], nb[1], nb[0]), bool)
+    zz, yy, xx = np.nonzero(nz)
+    tb[zz // 8, yy // 8, xx // 8] = True
+    got_t = host(touched).reshape(nb[2], nb[1], nb[0]).astype(bool)
+    assert np.all(got_t[tb])
+
+
 def test_build_mask_bit_exact(L):
     cfg = synth.CFG2
     D = synth.density_grid(cfg)
@@ -375,12 +415,15 @@ def test_rgbnet_bwd_from_compositing_gradient(L):
 
 
 # --------------------------------------------------------- TV and Adam
-@pytest.mark.parametrize("C", [1, 12])
+@pytest.mark.parametrize("C", [1, 12, 3])
 @pytest.mark.parametrize("dense_mode", [True, False])
-def test_tv_add_grad(L, C, dense_mode):
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tv_add_grad(L, C, dense_mode, bf16):
     rng = np.random.default_rng(10 + C)
     G = (20, 17, 11)
     grid = rng.normal(0, 1.2, (G[2], G[1], G[0], C)).astype(np.float32)
+    if bf16:
+        grid = synth.bf16_round(grid)
     g0 = np.where(rng.uniform(size=grid.shape) < 0.2, rng.normal(size=grid.shape), 0.0).astype(np.float32)
     gb = _bricked(L, g0, G, C)
     touched = torch.zeros(L.grid_num_bricks(G), dtype=torch.uint8, device="cuda")
@@ -390,7 +433,11 @@ def test_tv_add_grad(L, C, dense_mode):
         zz, yy, xx = np.nonzero(np.abs(g0).sum(-1) > 0)
         t[zz // 8, yy // 8, xx // 8] = 1
         touched = dev(t.reshape(-1))
-    L.tv_add_grad(_bricked(L, grid, G, C), L.F32, G, C, 0.5, 1.0, dense_mode, touched, gb)
+    if bf16:
+        L.tv_add_grad(_bricked(L, grid, G, C, torch.bfloat16), L.BF16, G, C, 0.5, 1.0, dense_mode,
+                      touched, gb)
+    else:
+        L.tv_add_grad(_bricked(L, grid, G, C), L.F32, G, C, 0.5, 1.0, dense_mode, touched, gb)
     out = torch.empty(G[2], G[1], G[0], C, device="cuda")
     L.grid_unpack(gb, out, G, C, L.F32)
     ref = oracle.tv_add_grad(grid, g0, 0.5, 1.0, dense_mode)
