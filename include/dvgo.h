@@ -51,10 +51,13 @@ typedef enum {
   DVGO_ERR_BOUNDS = -4,      /* device-side bounds check failed (checked builds) */
   DVGO_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
   DVGO_ERR_UNSUPPORTED = -6, /* valid but not implemented combination */
-  DVGO_ERR_WORKSPACE = -7    /* ws_bytes smaller than the required size */
+  DVGO_ERR_WORKSPACE = -7,   /* ws_bytes smaller than the required size */
+  DVGO_ERR_RANGE = -8        /* a value left the range a split-FP16 operand holds */
 } dvgo_status;
 
-typedef enum { DVGO_F32 = 0, DVGO_BF16 = 1 } dvgo_dtype;
+/* Arithmetic forms.  DVGO_F32_TC is a colour-MLP precision only: FP32
+ * accuracy on the tensor cores (see dvgo_rgbnet_fwd). */
+typedef enum { DVGO_F32 = 0, DVGO_BF16 = 1, DVGO_F32_TC = 2 } dvgo_dtype;
 
 /* Scene grid: box [lo, hi] and grid points per axis (corner aligned). */
 typedef struct {
@@ -228,10 +231,20 @@ int dvgo_rgb_loss(const float* color, const float* target, const float* L_r, int
  * ReLU 128 -> ReLU 128 -> sigmoid 3.  params: f32 flat W1[128][39], b1,
  * W2[128][128], b2, W3[3][128], b3 (22019 values).  Processes samples
  * idx[j] (j < *n_dev or n_cap); k0 rows and rgb rows are at the sample
- * index; the direction is rays_d[ray_id[sample]].  precision: DVGO_F32
- * (exact FP32 on the CUDA cores) or DVGO_BF16 (BF16 operands on the tensor
- * cores, FP32 accumulation).  act (FP32 form, may be NULL): see
- * dvgo_rgbnet_bwd. */
+ * index; the direction is rays_d[ray_id[sample]].  precision:
+ *   DVGO_F32     exact FP32 on the CUDA cores;
+ *   DVGO_F32_TC  FP32 accuracy on the tensor cores: every operand, after an
+ *                exact power-of-two scale, is split into two FP16 terms
+ *                hi + lo and each product is taken as hi*hi + hi*lo + lo*hi
+ *                with FP32 accumulation (relative error about 2^-22 per
+ *                product, like FP32 arithmetic).  Inputs must stay below
+ *                512 in magnitude and hidden activations below 2048, else
+ *                dvgo_device_status reports DVGO_ERR_RANGE;
+ *   DVGO_BF16    BF16 operands on the tensor cores, FP32 accumulation.
+ * act: DVGO_F32 may be NULL, else see dvgo_rgbnet_bwd; DVGO_F32_TC
+ * required, dvgo_rgbnet_act_bytes(n_cap, DVGO_F32_TC) bytes, 16-byte
+ * aligned (the forward stores each 128-sample tile's split layer inputs
+ * for the backward); DVGO_BF16 ignored. */
 int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
                     const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
                     int precision, float* rgb, float* act, void* stream);
@@ -243,12 +256,21 @@ int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
  * sample index.  act (FP32 form, may be NULL): f32 [n_cap][256] written by
  * dvgo_rgbnet_fwd for the same list, row j = [h1 (128) | h2 (128)] of list
  * position j; with it (and rgb, the forward's output, may be NULL) the
- * backward reads the hidden activations instead of recomputing them.  The
- * BF16 form ignores act and rgb (it recomputes on the tensor cores). */
+ * backward reads the hidden activations instead of recomputing them.
+ * DVGO_F32_TC: act is the buffer its forward filled for the same list and
+ * count (required; rgb ignored); the backward also uses its first 256
+ * bytes as scratch.  The BF16 form ignores act and rgb (it recomputes on
+ * the tensor cores). */
 int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                     const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
                     const int64_t* n_dev, const float* params, int precision, const float* act,
                     const float* rgb, float* g_params, float* g_k0, void* stream);
+
+/* Bytes of the act buffer dvgo_rgbnet_fwd / _bwd need for n_cap list
+ * positions: n_cap * 1024 for DVGO_F32 (optional there), 256 + 90112 per
+ * 128-position tile for DVGO_F32_TC, 0 for DVGO_BF16; -1 for a bad
+ * precision or n_cap < 0. */
+int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision);
 
 /* ------------------------------------------------------- learned proposal */
 /* Not in the paper: a small network that predicts where each ray's

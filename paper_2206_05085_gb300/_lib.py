@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdvgo.so")
 
-F32, BF16 = 0, 1
+F32, BF16, F32_TC = 0, 1, 2
 
 P = ctypes.c_void_p
 I64 = ctypes.c_int64
@@ -88,6 +88,7 @@ def _declare(L):
         "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
         "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
+        "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
         "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
         "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
         "dvgo_device_status": ([P], INT),
@@ -116,7 +117,7 @@ def exported_names():
         "dvgo_distortion_bwd", "dvgo_rgb_loss", "dvgo_rgbnet_fwd", "dvgo_rgbnet_bwd",
         "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status", "dvgo_proposal_fwd",
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
-        "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc"]
+        "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes"]
 
 
 def ptr(t):
@@ -249,6 +250,10 @@ def rgbnet_fwd(k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision, rgb, ac
                stream=None):
     _call("dvgo_rgbnet_fwd", ptr(k0), ptr(rays_d), ptr(ray_id), ptr(idx), n_cap, ptr(n_dev),
           ptr(params), precision, ptr(rgb), ptr(act), _stream(stream))
+
+
+def rgbnet_act_bytes(n_cap, precision):
+    return int(lib().dvgo_rgbnet_act_bytes(n_cap, precision))
 
 
 def rgbnet_bwd(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, precision,

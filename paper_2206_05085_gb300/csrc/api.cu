@@ -13,6 +13,12 @@ int dvgo_rgbnet_bwd_bf16(const float*, const float*, const float*, const float*,
                          const int32_t*, int64_t, const int64_t*, const float*, float*, float*,
                          cudaStream_t);
 int dvgo_mlp_status_read_and_clear(cudaStream_t);
+int dvgo_rgbnet_fwd_f32tc(const float*, const float*, const int32_t*, const int32_t*, int64_t,
+                          const int64_t*, const float*, float*, float*, cudaStream_t);
+int dvgo_rgbnet_bwd_f32tc(const float*, const float*, const float*, const int32_t*, const int32_t*,
+                          int64_t, const int64_t*, const float*, float*, float*, float*, cudaStream_t);
+int64_t rgbnet_act_bytes_tc(int64_t);
+int dvgo_mlp_tc_status_read_and_clear(cudaStream_t);
 
 using namespace dvgo;
 
@@ -28,6 +34,7 @@ extern "C" const char* dvgo_status_string(int status) {
     case DVGO_ERR_TIMEOUT: return "bounded device-side wait gave up";
     case DVGO_ERR_UNSUPPORTED: return "unsupported combination";
     case DVGO_ERR_WORKSPACE: return "workspace too small";
+    case DVGO_ERR_RANGE: return "value outside the range of a split-FP16 operand";
     default: return "unknown status";
   }
 }
@@ -45,6 +52,10 @@ extern "C" int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32
     return dvgo_rgbnet_fwd_f32(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
   if (precision == DVGO_BF16)
     return dvgo_rgbnet_fwd_bf16(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, st);
+  if (precision == DVGO_F32_TC) {
+    DVGO_CHECK_ARG(act != nullptr);
+    return dvgo_rgbnet_fwd_f32tc(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
+  }
   return DVGO_ERR_INVALID_ARG;
 }
 
@@ -65,9 +76,25 @@ extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const f
   if (precision == DVGO_BF16)
     return dvgo_rgbnet_bwd_bf16(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
                                 g_params, g_k0, st);
+  if (precision == DVGO_F32_TC) {
+    DVGO_CHECK_ARG(act != nullptr);
+    // the backward writes its gradient bound into the first bytes of act
+    return dvgo_rgbnet_bwd_f32tc(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
+                                 const_cast<float*>(act), g_params, g_k0, st);
+  }
   return DVGO_ERR_INVALID_ARG;
 }
 
+extern "C" int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision) {
+  if (n_cap < 0) return -1;
+  if (precision == DVGO_F32) return n_cap * 1024;
+  if (precision == DVGO_F32_TC) return rgbnet_act_bytes_tc(n_cap);
+  if (precision == DVGO_BF16) return 0;
+  return -1;
+}
+
 extern "C" int dvgo_device_status(void* stream) {
-  return dvgo_mlp_status_read_and_clear(as_stream(stream));
+  const int a = dvgo_mlp_status_read_and_clear(as_stream(stream));
+  const int b = dvgo_mlp_tc_status_read_and_clear(as_stream(stream));
+  return a != DVGO_OK ? a : b;
 }

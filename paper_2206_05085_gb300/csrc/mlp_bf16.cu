@@ -246,21 +246,6 @@ __device__ __forceinline__ void layer3_z(const F32Side<Net>* fs, uint32_t taddr_
   }
 }
 
-// Butterfly reduce-scatter: lane l returns sum over the warp of v[l].
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool up = (lane & h) != 0;
-#pragma unroll
-    for (int j = 0; j < h; ++j) {
-      const float send = up ? v[j] : v[j + h];
-      const float keep = up ? v[j + h] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-    }
-  }
-  return v[0];
-}
-
 }  // namespace bf
 
 using namespace bf;

@@ -1,0 +1,667 @@
+// Colour MLP (rgbnet, 39 -> ReLU 128 -> ReLU 128 -> sigmoid 3; the shallow
+// decoder of the hybrid representation, Tab. 1) with FP32 accuracy on the
+// 5th-generation tensor cores.
+//
+// Split operands.  A value v, first multiplied by an exact power of two s,
+// is stored as two FP16 terms hi = fp16(s v) and lo = fp16(s v - hi); hi
+// carries 11 significant bits and lo the next 11.  A product of two split
+// matrices is accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi
+// (three tcgen05.mma of kind::f16); the dropped lo*lo term is 2^-22 of the
+// product, so each dot product carries an FP32-like relative error.  The
+// scales keep the terms inside FP16's normal range: weights per matrix
+// (largest |w| s in [2^13, 2^14)), layer inputs by 2^6, hidden activations
+// by 2^4, and the backward's gradient rows G2 = g_z2 and G1 = g_z1 per sample
+// from a bound on that sample's output-layer gradient, so that every sample's
+// input gradient keeps FP32 relative accuracy however small it is.  In the
+// weight-gradient products (sums over samples) the per-sample factor is undone
+// on the other operand: row s of H1 (X) is multiplied by S / s_s, with S the
+// smallest per-sample scale of the whole list (from a first kernel's bound on
+// the upstream gradient), so the accumulator carries the single factor S.
+// Every scale is an exact power of two, undone exactly in the epilogues.  A
+// value whose scaled magnitude reaches 2^15 sets DVGO_ERR_RANGE.
+//
+// Forward, per 128-sample tile (thread = tile row = TMEM lane):
+//   X (39 inputs, a 1 carrying b1, zero pad to 48) -> D1 = X W1^T -> H1 =
+//   relu(D1) -> D2 = H1 W2^T -> z2 = D2 + b2 -> output layer and sigmoid on
+//   the CUDA cores in FP32.  The split X and H1 of the tile (90112 bytes, the
+//   shared-memory image) go to the act buffer with one bulk copy.
+// Backward, per tile: bulk-load the tile's image; D2 = H1 W2^T again; on the
+//   CUDA cores z3, g_z3, dW3, db3, g_h2 and G2 = g_z2 (and db2 = sum of G2);
+//   then dW2 += G2^T H1 and g_h1 = G2 W2; G1 = g_h1 * (H1 > 0);
+//   dW1 (+db1 through X's ones column) += G1^T X and g_X = G1 W1[:, 0:16]
+//   (-> g_k0).  dW2 and dW1 stay in tensor memory for the whole kernel.
+// Every wait on an mbarrier is bounded (DVGO_ERR_TIMEOUT).
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "mlp_common.cuh"
+#include "tcgen05.cuh"
+
+namespace dvgo {
+
+__device__ int g_mlp_tc_status;  // first error a kernel of this file met
+
+namespace x3 {
+
+constexpr int kK1 = 48;                           // padded input width
+constexpr int kNCH = kHid / 32;                   // 32-column TMEM chunks of a hidden layer
+constexpr uint32_t kSboX = (kK1 / 8) * 128;       // 768: 8-row group stride, 48-wide rows
+constexpr uint32_t kSboH = (kHid / 8) * 128;      // 2048: 128-wide rows
+constexpr uint32_t kSboW1s = (16 / 8) * 128;      // 256: 16-wide rows (W1[:, 0:16])
+constexpr uint32_t kXBytes = kTile * kK1 * 2;     // one term of X
+constexpr uint32_t kHBytes = kTile * kHid * 2;    // one term of H1 or G
+constexpr uint32_t kW1Bytes = kHid * kK1 * 2;
+constexpr uint32_t kW1sBytes = kHid * 16 * 2;
+constexpr uint32_t kW2Bytes = kHid * kHid * 2;
+constexpr uint32_t kImage = 2 * kXBytes + 2 * kHBytes;  // [Xh | Xl | H1h | H1l]
+constexpr uint32_t iXh = 0, iXl = kXBytes, iHh = 2 * kXBytes, iHl = 2 * kXBytes + kHBytes;
+constexpr uint32_t kActHeader = 256;
+constexpr float kSX = 64.0f;     // input scale
+constexpr float kSH = 16.0f;     // hidden-activation scale
+constexpr float kRange = 32768.0f;
+constexpr uint32_t kSpin = 1u << 24;
+
+// forward shared memory
+constexpr uint32_t fW1h = 0, fW1l = fW1h + kW1Bytes, fW2h = fW1l + kW1Bytes,
+                   fW2l = fW2h + kW2Bytes, fImg = fW2l + kW2Bytes, fEnd = fImg + kImage;
+// backward shared memory
+constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
+                   bW1l = bW1h + kW1sBytes, bImg = bW1l + kW1sBytes, bGh = bImg + kImage,
+                   bGl = bGh + kHBytes, bEnd = bGl + kHBytes;
+// tensor-memory columns of the backward
+constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256;
+
+struct Side {
+  float W3[kOut * kHid];
+  float b2[kHid];
+  float b3[4];
+  float red[16];
+  uint64_t bar_h;     // H1 terms of a tile image landed
+  uint64_t bar_x;     // X terms landed
+  uint64_t bar_mma;
+  uint32_t tmem_slot;
+};
+static_assert(fEnd + sizeof(Side) <= 227 * 1024, "forward shared memory");
+static_assert(bEnd + sizeof(Side) <= 227 * 1024, "backward shared memory");
+
+// Largest value of v over the block (all threads call it).
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
+// 2^(13 - floor(log2 m)): maps the largest magnitude m into [2^13, 2^14).
+__device__ __forceinline__ float pow2_scale(float m) {
+  if (!(m > 0.0f) || !(m <= 3.0e38f)) return 1.0f;
+  int e = ilogbf(m);
+  e = max(-100, min(100, e));
+  return ldexpf(1.0f, 13 - e);
+}
+
+__device__ __forceinline__ uint32_t pack_h(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Split 8 (already scaled) values into the hi / lo core-matrix rows at (row, k8).
+__device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int k8, uint32_t sbo,
+                                          const float* v, bool& bad) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float a = v[2 * i], b = v[2 * i + 1];
+    bad |= fabsf(a) >= kRange || fabsf(b) >= kRange;
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    const __half la = __float2half_rn(a - __half2float(ha));
+    const __half lb = __float2half_rn(b - __half2float(hb));
+    h[i] = pack_h(ha, hb);
+    l[i] = pack_h(la, lb);
+  }
+  const uint32_t off = tc::cm_off(row, k8, sbo);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Multiply row `row` (K values, split) by the power of two r <= 1, re-splitting.
+template <int K>
+__device__ __forceinline__ void rescale_row(uint8_t* hi, uint8_t* lo, int row, uint32_t sbo, float r,
+                                            bool& bad) {
+#pragma unroll 2
+  for (int k8 = 0; k8 < K; k8 += 8) {
+    const uint32_t off = tc::cm_off(row, k8, sbo);
+    const uint4 qh = *reinterpret_cast<const uint4*>(hi + off);
+    const uint4 ql = *reinterpret_cast<const uint4*>(lo + off);
+    const uint32_t wh[4] = {qh.x, qh.y, qh.z, qh.w}, wl[4] = {ql.x, ql.y, ql.z, ql.w};
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __half2 h2 = *reinterpret_cast<const __half2*>(&wh[i]);
+      const __half2 l2 = *reinterpret_cast<const __half2*>(&wl[i]);
+      v[2 * i] = r * (__low2float(h2) + __low2float(l2));
+      v[2 * i + 1] = r * (__high2float(h2) + __high2float(l2));
+    }
+    st_split8(hi, lo, row, k8, sbo, v, bad);
+  }
+}
+
+// One scaled, split element (setup only).
+__device__ __forceinline__ void st_split1(uint8_t* hi, uint8_t* lo, uint32_t off, float v) {
+  const __half h = __float2half_rn(v);
+  *reinterpret_cast<__half*>(hi + off) = h;
+  *reinterpret_cast<__half*>(lo + off) = __float2half_rn(v - __half2float(h));
+}
+
+// D (+)= A B^T over K = 16 * ksteps, split operands: three MMAs per K step.
+// a_step / b_step: byte advance of the descriptors' start address per step.
+__device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint32_t a_step, uint32_t a_lbo,
+                                     uint32_t a_sbo, uint32_t bh, uint32_t bl, uint32_t b_step,
+                                     uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
+                                     bool accumulate) {
+#pragma unroll 1
+  for (int k = 0; k < ksteps; ++k) {
+    const uint64_t dah = tc::smem_desc(ah + k * a_step, a_lbo, a_sbo);
+    const uint64_t dal = tc::smem_desc(al + k * a_step, a_lbo, a_sbo);
+    const uint64_t dbh = tc::smem_desc(bh + k * b_step, b_lbo, b_sbo);
+    const uint64_t dbl = tc::smem_desc(bl + k * b_step, b_lbo, b_sbo);
+    tc::mma_bf16(d, dah, dbh, idesc, (accumulate || k > 0) ? 1u : 0u);
+    tc::mma_bf16(d, dah, dbl, idesc, 1u);
+    tc::mma_bf16(d, dal, dbh, idesc, 1u);
+  }
+}
+
+// Output-layer constants (exact FP32).
+__device__ __forceinline__ void load_out_layer(const float* __restrict__ params, Side* fs) {
+  for (int e = threadIdx.x; e < kOut * kHid; e += blockDim.x) fs->W3[e] = params[kOffW3 + e];
+  for (int e = threadIdx.x; e < kHid; e += blockDim.x) fs->b2[e] = params[kOffB2 + e];
+  if (threadIdx.x < 4) fs->b3[threadIdx.x] = threadIdx.x < kOut ? params[kOffB3 + threadIdx.x] : 0.0f;
+}
+
+// W2 (scaled by s) as split K-major core matrices [o][i].
+__device__ __forceinline__ void load_w2(const float* __restrict__ params, uint8_t* hi, uint8_t* lo, float s) {
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+    const int o = e / kHid, i = e % kHid;
+    st_split1(hi, lo, tc::cm_off(o, i, kSboH), s * params[kOffW2 + e]);
+  }
+}
+
+__device__ __forceinline__ void set_status(int code) { atomicCAS(&g_mlp_tc_status, 0, code); }
+
+}  // namespace x3
+
+using namespace x3;
+
+// ------------------------------------------------------------------ forward
+__global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
+    const float* __restrict__ k0, const float* __restrict__ rays_d, const int32_t* __restrict__ ray_id,
+    const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* __restrict__ n_dev,
+    const float* __restrict__ params, float* __restrict__ rgb, uint8_t* __restrict__ act) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  Side* fs = reinterpret_cast<Side*>(sm + fEnd);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t n = mlp_count(n_cap, n_dev);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 256);
+  if (tid == 0) tc::mbar_init(&fs->bar_mma, 1);
+  // weights: W1 | b1 (column 39) and W2, split, each with its own scale
+  float m1 = 0.0f, m2 = 0.0f;
+  for (int e = tid; e < kHid * kIn + kHid; e += blockDim.x) m1 = fmaxf(m1, fabsf(params[kOffW1 + e]));
+  for (int e = tid; e < kHid * kHid; e += blockDim.x) m2 = fmaxf(m2, fabsf(params[kOffW2 + e]));
+  const float sW1 = pow2_scale(block_max(m1, fs->red));
+  const float sW2 = pow2_scale(block_max(m2, fs->red));
+  for (int e = tid; e < kHid * kK1; e += blockDim.x) {
+    const int o = e / kK1, k = e % kK1;
+    const float v = k < kIn ? params[kOffW1 + o * kIn + k] : (k == kIn ? params[kOffB1 + o] : 0.0f);
+    st_split1(sm + fW1h, sm + fW1l, tc::cm_off(o, k, kSboX), sW1 * v);
+  }
+  load_w2(params, sm + fW2h, sm + fW2l, sW2);
+  load_out_layer(params, fs);
+  const float inv1 = 1.0f / (kSX * sW1), inv2 = 1.0f / (kSH * sW2);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = fs->tmem_slot;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t sW1h = tc::smem_u32(sm + fW1h), sW1l = tc::smem_u32(sm + fW1l);
+  const uint32_t sW2h = tc::smem_u32(sm + fW2h), sW2l = tc::smem_u32(sm + fW2l);
+  uint8_t* img = sm + fImg;
+  const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
+  const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
+  const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
+  uint32_t phase = 0;
+  bool ok = true, bad = false;
+  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const int64_t j = t * kTile + tid;
+    {
+      float x[kInP];
+      encode_row(k0, rays_d, ray_id, idx, j, n, x);
+      float v[8];
+#pragma unroll
+      for (int kb = 0; kb < kK1 / 8; ++kb) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = kb * 8 + i < kInP ? kSX * x[kb * 8 + i] : 0.0f;
+        st_split8(img + iXh, img + iXl, tid, kb * 8, kSboX, v, bad);
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      mma3(tmem, sXh, sXl, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
+      tc::mma_commit(&fs->bar_mma);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
+    phase ^= 1;
+    if (!ok) break;
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int ch = 0; ch < kNCH; ++ch) {   // H1 = relu(D1), scaled and split
+      float v[32];
+      tc::tmem_ld32(lane_base + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = kSH * fmaxf(v[i] * inv1, 0.0f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, tid, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      mma3(tmem + 128, sHh, sHl, 256, 128, kSboH, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
+      tc::mma_commit(&fs->bar_mma);
+      tc::bulk_s2g(act + kActHeader + (size_t)t * kImage, img, kImage);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
+    phase ^= 1;
+    if (!ok) break;
+    tc::fence_after_sync();
+    float z3[kOut];
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) z3[c] = fs->b3[c];
+#pragma unroll 1
+    for (int ch = 0; ch < kNCH; ++ch) {
+      float v[32];
+      tc::tmem_ld32(lane_base + 128 + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int o = ch * 32 + i;
+        const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) z3[c] = fmaf(fs->W3[c * kHid + o], h, z3[c]);
+      }
+    }
+    if (j < n) {
+      const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) rgb[3 * s + c] = sigmoid_f(z3[c]);
+    }
+    if (tid == 0) tc::bulk_wait_read();   // the image may be overwritten again
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (tid == 0) tc::bulk_wait_all();
+  if (!ok && tid == 0) set_status(DVGO_ERR_TIMEOUT);
+  if (bad) set_status(DVGO_ERR_RANGE);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------- upstream gradient bound
+// act header word 0 (zeroed by the host) <- max over the list of |g_rgb|.
+__global__ void __launch_bounds__(256) grad_bound_kernel(const float* __restrict__ g_rgb,
+                                                         const float* __restrict__ g_color,
+                                                         const float* __restrict__ w,
+                                                         const int32_t* __restrict__ ray_id,
+                                                         const int32_t* __restrict__ idx, int64_t n_cap,
+                                                         const int64_t* __restrict__ n_dev,
+                                                         unsigned int* __restrict__ out) {
+  __shared__ float red[8];
+  const int64_t n = mlp_count(n_cap, n_dev);
+  float m = 0.0f;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    float g[3];
+    upstream_rgb_grad(g_rgb, g_color, w, ray_id, s, g);
+    m = fmaxf(m, fmaxf(fabsf(g[0]), fmaxf(fabsf(g[1]), fabsf(g[2]))));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// ----------------------------------------------------------------- backward
+__global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
+    const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
+    const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx, int64_t n_cap,
+    const int64_t* __restrict__ n_dev, const float* __restrict__ params, const uint8_t* __restrict__ act,
+    float* __restrict__ g_params, float* __restrict__ g_k0) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  Side* fs = reinterpret_cast<Side*>(sm + bEnd);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n = mlp_count(n_cap, n_dev);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
+  if (tid == 0) {
+    tc::mbar_init(&fs->bar_h, 1);
+    tc::mbar_init(&fs->bar_x, 1);
+    tc::mbar_init(&fs->bar_mma, 1);
+  }
+  // scales: W2 and W1[:, 0:16] per matrix; G2 from the upstream bound, G1 from G2's
+  float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+  for (int e = tid; e < kHid * 16; e += blockDim.x) m1 = fmaxf(m1, fabsf(params[kOffW1 + (e >> 4) * kIn + (e & 15)]));
+  for (int e = tid; e < kHid * kHid; e += blockDim.x) m2 = fmaxf(m2, fabsf(params[kOffW2 + e]));
+  for (int o = tid; o < kHid; o += blockDim.x) {
+    float a = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) a += fabsf(params[kOffW3 + c * kHid + o]);
+    m3 = fmaxf(m3, a);
+  }
+  const float mw1 = block_max(m1, fs->red);
+  const float mw2 = block_max(m2, fs->red);
+  const float mw3 = block_max(m3, fs->red);
+  const float sW1 = pow2_scale(mw1), sW2 = pow2_scale(mw2);
+  const float gmax = __uint_as_float(*reinterpret_cast<const unsigned int*>(act));
+  // |g_z2[s]| <= max_o sum_c |W3[c][o]| * max_c |g_z3[s][c]| and g_z3 <= g_rgb / 4;
+  // |g_h1[s]| <= 128 max|W2| max|g_z2[s]|.  S2 / S1: the scales of the largest bounds.
+  const float w21 = mw2 * (float)kHid;
+  const float S2 = pow2_scale(0.25f * gmax * mw3);
+  const float S1 = pow2_scale(0.25f * gmax * mw3 * w21);
+  // W1[:, 0:16] as split [o][k] rows for g_X = G1 W1[:, 0:16]
+  for (int e = tid; e < kHid * 16; e += blockDim.x) {
+    const int o = e >> 4, k = e & 15;
+    st_split1(sm + bW1h, sm + bW1l, tc::cm_off(o, k, kSboW1s), sW1 * params[kOffW1 + o * kIn + k]);
+  }
+  load_w2(params, sm + bW2h, sm + bW2l, sW2);
+  load_out_layer(params, fs);
+  const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
+  const uint8_t* img_g = act + kActHeader;
+  uint8_t* img = sm + bImg;
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = fs->tmem_slot;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t sW1h = tc::smem_u32(sm + bW1h), sW1l = tc::smem_u32(sm + bW1l);
+  const uint32_t sW2h = tc::smem_u32(sm + bW2h), sW2l = tc::smem_u32(sm + bW2l);
+  const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
+  const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
+  const uint32_t sGh = tc::smem_u32(sm + bGh), sGl = tc::smem_u32(sm + bGl);
+  float dW3acc[kOut * kNCH], db2acc[kNCH], db3acc[kOut];
+#pragma unroll
+  for (int i = 0; i < kOut * kNCH; ++i) dW3acc[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kNCH; ++i) db2acc[i] = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kOut; ++c) db3acc[c] = 0.0f;
+  uint32_t ph_in = 0, ph_mma = 0;
+  bool ok = true, bad = false, dw_started = false;
+  bool inflight_h = false, inflight_x = false;   // thread 0: copies not yet waited for
+  auto load_h = [&](int64_t tile) {
+    tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
+    tc::bulk_g2s(img + iHh, img_g + (size_t)tile * kImage + iHh, 2 * kHBytes, &fs->bar_h);
+    inflight_h = true;
+  };
+  auto load_x = [&](int64_t tile) {
+    tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
+    tc::bulk_g2s(img + iXh, img_g + (size_t)tile * kImage + iXh, 2 * kXBytes, &fs->bar_x);
+    inflight_x = true;
+  };
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
+    load_h(blockIdx.x);
+    load_x(blockIdx.x);
+  }
+  auto mma_wait = [&]() -> bool {
+    const bool r = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, ph_mma, kSpin));
+    ph_mma ^= 1;
+    tc::fence_after_sync();
+    return r;
+  };
+  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const int64_t j = t * kTile + tid;
+    const bool valid = j < n;
+    const int64_t tn = t + gridDim.x;   // this CTA's next tile
+    int64_t s = 0;
+    float gup[kOut] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+      s = idx ? (int64_t)__ldg(idx + j) : j;
+      upstream_rgb_grad(g_rgb, g_color, w, ray_id, s, gup);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_in, kSpin) &&
+                           tc::mbar_wait(&fs->bar_x, ph_in, kSpin));
+    if (!ok) break;
+    ph_in ^= 1;
+    inflight_h = inflight_x = false;
+    // relu mask of layer 1 from the stored activations (H1 > 0 <=> hi > 0)
+    uint32_t m1b[kNCH] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k8 = 0; k8 < kHid; k8 += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(tid, k8, kSboH));
+      const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = k8 + 2 * i;
+        if ((int16_t)(wd[i] & 0xffffu) > 0) m1b[k >> 5] |= 1u << (k & 31);
+        if ((int16_t)(wd[i] >> 16) > 0) m1b[(k + 1) >> 5] |= 1u << ((k + 1) & 31);
+      }
+    }
+    if (tid == 0) {   // D2 = H1 W2^T
+      tc::fence_after_sync();
+      mma3(tmem + cTmp, sHh, sHl, 256, 128, kSboH, sW2h, sW2l, 256, 128, kSboH, kHid / 16,
+           tc::idesc_f16(128, kHid, 0, 0), false);
+      tc::mma_commit(&fs->bar_mma);
+    }
+    if (!(ok = mma_wait())) break;
+    // output layer: z3, g_z3, db3
+    float z3[kOut];
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) z3[c] = fs->b3[c];
+#pragma unroll 1
+    for (int ch = 0; ch < kNCH; ++ch) {
+      float v[32];
+      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int o = ch * 32 + i;
+        const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) z3[c] = fmaf(fs->W3[c * kHid + o], h, z3[c]);
+      }
+    }
+    float gz3[kOut];
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) {
+      const float y = sigmoid_f(z3[c]);
+      gz3[c] = gup[c] * y * (1.0f - y);
+      db3acc[c] += gz3[c];
+    }
+    // this sample's gradient scales; its H1 and X rows carry the compensation
+    const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
+    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;   // S2 / sG2 <= 1
+    const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
+    const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
+    const float invX = 1.0f / (sG1 * sW1);           // g_X
+    if (S2 != sG2) rescale_row<kHid>(img + iHh, img + iHl, tid, kSboH, S2 / sG2, bad);
+    if (S1 != sG1) rescale_row<kK1>(img + iXh, img + iXl, tid, kSboX, S1 / sG1, bad);
+    // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
+#pragma unroll
+    for (int ch = 0; ch < kNCH; ++ch) {
+      float v[32], g[32];
+      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int o = ch * 32 + i;
+        const float z2 = fmaf(v[i], inv2, fs->b2[o]);
+        float gs = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) gs = fmaf(gz3[c], fs->W3[c * kHid + o], gs);
+        g[i] = z2 > 0.0f ? gs : 0.0f;
+        v[i] = fmaxf(z2, 0.0f);
+      }
+      float sg[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) sg[i] = sG2 * g[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, tid, ch * 32 + q * 8, kSboH, sg + 8 * q, bad);
+      db2acc[ch] += reduce_scatter32(g, lane);
+#pragma unroll 1
+      for (int c = 0; c < kOut; ++c) {
+        float p[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
+        dW3acc[c * kNCH + ch] += reduce_scatter32(p, lane);
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {   // dW2 += G2^T H1;  g_h1 = G2 W2
+      tc::fence_after_sync();
+      mma3(tmem + cDW2, sGh, sGl, 2 * kSboH, kSboH, 128, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
+           tc::idesc_f16(128, kHid, 1, 1), dw_started);
+      mma3(tmem + cTmp, sGh, sGl, 256, 128, kSboH, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
+           tc::idesc_f16(128, kHid, 0, 1), false);
+      tc::mma_commit(&fs->bar_mma);
+    }
+    if (!(ok = mma_wait())) break;
+    if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
+    // G1 = g_h1 * (H1 > 0), rescaled to sG1
+#pragma unroll
+    for (int ch = 0; ch < kNCH; ++ch) {
+      float v[32];
+      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = ((m1b[ch] >> i) & 1u) ? v[i] * fG1 : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, tid, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16]
+      tc::fence_after_sync();
+      mma3(tmem + cDW1, sGh, sGl, 2 * kSboH, kSboH, 128, sXh, sXl, 2 * kSboX, kSboX, 128, kTile / 16,
+           tc::idesc_f16(128, kK1, 1, 1), dw_started);
+      mma3(tmem + cTmp, sGh, sGl, 256, 128, kSboH, sW1h, sW1l, 2 * kSboW1s, kSboW1s, 128, kHid / 16,
+           tc::idesc_f16(128, 16, 0, 1), false);
+      tc::mma_commit(&fs->bar_mma);
+      dw_started = true;
+    }
+    if (!(ok = mma_wait())) break;
+    if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
+    {
+      float gx[16];
+      tc::tmem_ld16(lane_base + cTmp, gx);
+      if (valid) {
+        float4* dst = reinterpret_cast<float4*>(g_k0 + s * kFeat);
+        dst[0] = make_float4(gx[0] * invX, gx[1] * invX, gx[2] * invX, gx[3] * invX);
+        dst[1] = make_float4(gx[4] * invX, gx[5] * invX, gx[6] * invX, gx[7] * invX);
+        dst[2] = make_float4(gx[8] * invX, gx[9] * invX, gx[10] * invX, gx[11] * invX);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  // a load still in flight (only after a failed wait) must land before exit
+  if (!ok && tid == 0) {
+    if (inflight_h) tc::mbar_wait(&fs->bar_h, ph_in, kSpin);
+    if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_in, kSpin);
+    set_status(DVGO_ERR_TIMEOUT);
+  }
+  if (bad) set_status(DVGO_ERR_RANGE);
+  // output-layer and b2 partials of this warp
+#pragma unroll
+  for (int c = 0; c < kOut; ++c)
+#pragma unroll
+    for (int ch = 0; ch < kNCH; ++ch)
+      atomicAdd(g_params + kOffW3 + c * kHid + ch * 32 + lane, dW3acc[c * kNCH + ch]);
+#pragma unroll
+  for (int ch = 0; ch < kNCH; ++ch) atomicAdd(g_params + kOffB2 + ch * 32 + lane, db2acc[ch]);
+#pragma unroll
+  for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffB3 + c, db3acc[c]);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (ok && (int64_t)blockIdx.x < ntiles) {   // this CTA accumulated dW2 / dW1
+    // TMEM lane = output neuron o
+    const int o = tid;
+    const float u2 = 1.0f / (S2 * kSH), u1 = 1.0f / (S1 * kSX);
+#pragma unroll 1
+    for (int ch = 0; ch < kNCH; ++ch) {
+      float v[32];
+      tc::tmem_ld32(lane_base + cDW2 + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) atomicAdd(g_params + kOffW2 + o * kHid + ch * 32 + i, v[i] * u2);
+    }
+    float v[32], u[16];
+    tc::tmem_ld32(lane_base + cDW1, v);
+    tc::tmem_ld16(lane_base + cDW1 + 32, u);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) atomicAdd(g_params + kOffW1 + o * kIn + k, v[k] * u1);
+#pragma unroll
+    for (int k = 32; k < kIn; ++k) atomicAdd(g_params + kOffW1 + o * kIn + k, u[k - 32] * u1);
+    atomicAdd(g_params + kOffB1 + o, u[kIn - 32] * u1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace dvgo
+
+using namespace dvgo;
+
+int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
+  return (int64_t)kActHeader + (n_cap + kTile - 1) / kTile * (int64_t)kImage;
+}
+
+int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
+                          const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
+                          float* rgb, float* act, cudaStream_t st) {
+  const size_t smem = fEnd + sizeof(Side);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(rgbnet_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
+  rgbnet_fwd_tc_kernel<<<grid, 128, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
+                                                reinterpret_cast<uint8_t*>(act));
+  return launch_status();
+}
+
+int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float* w,
+                          const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
+                          const int64_t* n_dev, const float* params, float* act, float* g_params,
+                          float* g_k0, cudaStream_t st) {
+  const size_t smem = bEnd + sizeof(Side);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(rgbnet_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  cudaMemsetAsync(act, 0, sizeof(unsigned int), st);
+  grad_bound_kernel<<<grid_for(n_cap, 256, 4), 256, 0, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev,
+                                                             reinterpret_cast<unsigned int*>(act));
+  const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
+  rgbnet_bwd_tc_kernel<<<grid, 128, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
+                                                reinterpret_cast<const uint8_t*>(act), g_params, g_k0);
+  return launch_status();
+}
+
+int dvgo_mlp_tc_status_read_and_clear(cudaStream_t st) {
+  int v = 0, zero = 0;
+  cudaMemcpyFromSymbolAsync(&v, g_mlp_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyToSymbolAsync(g_mlp_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  return v;
+}

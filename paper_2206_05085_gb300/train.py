@@ -57,7 +57,9 @@ class Trainer:
                  precision: str = "f32", device: str = "cuda"):
         self.cfg, self.rp, self.R = cfg, rp, int(n_rays)
         self.dev = torch.device(device)
-        self.precision = L.BF16 if precision == "bf16" else L.F32
+        # "f32": colour MLP in FP32 on the CUDA cores; "f32tc": FP32-accurate on
+        # the tensor cores (split-FP16 operands); "bf16": BF16 grids and MLP
+        self.precision = {"f32": L.F32, "f32tc": L.F32_TC, "bf16": L.BF16}[precision]
         G = [cfg.grid] * 3
         self.G = G
         self.gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, G)
@@ -129,8 +131,13 @@ class Trainer:
         self.g_w = torch.empty(S, **f32)
         self.g_raw = torch.empty(S, **f32)
         self.g_k0 = torch.empty(S, FEAT, **f32)
-        # FP32 form: hidden activations saved by the colour-MLP forward for its backward
-        self.act = torch.empty(S, 256, **f32) if self.precision == L.F32 else None
+        # FP32 forms: what the colour-MLP forward saves for its backward (hidden
+        # activations, or the split layer inputs of each 128-sample tile)
+        self.act = None
+        if self.precision == L.F32:
+            self.act = torch.empty(S, 256, **f32)
+        elif self.precision == L.F32_TC:
+            self.act = torch.empty(L.rgbnet_act_bytes(S, L.F32_TC), dtype=torch.uint8, device=dev)
         self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
 

@@ -65,3 +65,14 @@ def test_host_validation_without_gpu(lib):
                                                              ctypes.c_void_p, ctypes.c_int,
                                                              ctypes.c_void_p, ctypes.c_void_p]
     assert lib.dvgo_rgbnet_fwd(p, p, p, None, 10, None, p, 9, p, None) == -1
+    # the tensor-core FP32 form needs its act buffer
+    assert lib.dvgo_rgbnet_fwd(p, p, p, None, 10, None, p, 2, p, None) == -1
+    lib.dvgo_rgbnet_act_bytes.restype = ctypes.c_int64
+    lib.dvgo_rgbnet_act_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]
+    assert lib.dvgo_rgbnet_act_bytes(10, 0) == 10 * 1024
+    assert lib.dvgo_rgbnet_act_bytes(300, 2) == 256 + 3 * 90112
+    assert lib.dvgo_rgbnet_act_bytes(0, 2) == 256
+    assert lib.dvgo_rgbnet_act_bytes(10, 1) == 0
+    assert lib.dvgo_rgbnet_act_bytes(-1, 0) == -1
+    assert lib.dvgo_rgbnet_act_bytes(5, 7) == -1
+    assert lib.dvgo_status_string(-8) == b"value outside the range of a split-FP16 operand"

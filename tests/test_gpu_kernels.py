@@ -347,21 +347,24 @@ def _mlp_case(n, seed=6):
     return k0, d, ray_id, params, g_rgb
 
 
-@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("precision", ["f32", "f32tc", "bf16"])
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 5000])
 def test_rgbnet_fwd_bwd(L, precision, n):
     from conftest import check_mlp_grads
     k0, d, ray_id, params, g_rgb = _mlp_case(n)
     bf = precision == "bf16"
-    prec = L.BF16 if bf else L.F32
+    prec = {"f32": L.F32, "f32tc": L.F32_TC, "bf16": L.BF16}[precision]
     tol = TOL16 if bf else TOL32
+    act_tc = None
+    if precision == "f32tc":
+        act_tc = torch.empty(L.rgbnet_act_bytes(n, prec), dtype=torch.uint8, device="cuda")
     p_ref = synth.bf16_round(params) if bf else params
     # every other sample through idx, count on the device
     idx = np.arange(0, n, 2 if n > 2 else 1).astype(np.int32)
     m = len(idx)
     rgb = torch.full((n, 3), -1.0, device="cuda")
     n_dev = torch.tensor([m], dtype=torch.int64, device="cuda")
-    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb)
+    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb, act_tc)
     x = oracle.rgbnet_input(k0[idx], d[ray_id[idx]])
     ref = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True, q_bf16=bf)
     got = host(rgb)
@@ -369,9 +372,9 @@ def test_rgbnet_fwd_bwd(L, precision, n):
     rest = np.setdiff1d(np.arange(n), idx)
     assert np.all(got[rest] == -1.0)
     # backward recomputing the forward, and (FP32 form) from stored activations
-    for use_act in ((False, True) if not bf else (False,)):
-        act = None
-        if use_act:
+    for use_act in ((False, True) if precision == "f32" else (precision == "f32tc",)):
+        act = act_tc
+        if use_act and precision == "f32":
             act = torch.empty(n, 256, device="cuda")
             L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb,
                          act)
@@ -381,6 +384,7 @@ def test_rgbnet_fwd_bwd(L, precision, n):
                      dev(params), prec, g_params, g_k0, act, rgb if use_act else None)
         check_mlp_grads(oracle, synth.RGBNET_DIMS, p_ref, x, g_rgb[idx], host(g_params),
                         host(g_k0)[idx], tol, bf)
+    assert L.device_status() == 0
     if bf:
         # error of the BF16 form against the unrounded FP64 MLP (reported)
         ref64 = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True)
@@ -412,6 +416,53 @@ def test_rgbnet_bwd_from_compositing_gradient(L):
     from conftest import check_mlp_grads
     check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, w[:, None] * g_color[ray_id],
                     host(g_params), host(g_k0), TOL32, False)
+
+
+def test_rgbnet_tc_compositing_gradient_wide_range(L):
+    """Tensor-core FP32 form with the in-kernel upstream w[s] * g_color[ray]:
+    weights spanning 1e-9..1 exercise the per-sample power-of-two gradient
+    scales: every sample's input gradient keeps FP32 relative accuracy."""
+    n = 4000
+    k0, d, ray_id, params, _ = _mlp_case(n, 9)
+    rng = np.random.default_rng(9)
+    w = (10.0 ** rng.uniform(-9, 0, n)).astype(np.float32)
+    g_color = (rng.normal(size=(d.shape[0], 3)) * 1e-4).astype(np.float32)
+    act = torch.empty(L.rgbnet_act_bytes(n, L.F32_TC), dtype=torch.uint8, device="cuda")
+    rgb = torch.empty(n, 3, device="cuda")
+    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), None, n, None, dev(params), L.F32_TC, rgb, act)
+    g_params = torch.zeros(len(params), device="cuda")
+    g_k0 = torch.zeros(n, 12, device="cuda")
+    L.rgbnet_bwd(None, dev(g_color), dev(w), dev(k0), dev(d), dev(ray_id), None, n, None,
+                 dev(params), L.F32_TC, g_params, g_k0, act)
+    assert L.device_status() == 0
+    x = oracle.rgbnet_input(k0, d[ray_id])
+    assert rel_err(host(rgb), oracle.mlp_fwd(synth.RGBNET_DIMS, params, x, True)) < TOL32
+    from conftest import check_mlp_grads
+    g_up = w[:, None] * g_color[ray_id]
+    check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, g_up, host(g_params), host(g_k0), TOL32,
+                    False)
+    _, gx = oracle.mlp_bwd(synth.RGBNET_DIMS, params, x, g_up, True, False)
+    gx = gx[:, :12]
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params, x, False)
+    got = host(g_k0)
+    keep = np.nonzero(zmin > 1e-6)[0]
+    assert len(keep) > 0.9 * n
+    err = np.linalg.norm(got[keep] - gx[keep], axis=1) / np.linalg.norm(gx[keep], axis=1)
+    worst = int(np.argmax(err))
+    assert err[worst] < TOL32, (int(keep[worst]), float(w[keep[worst]]), float(err[worst]))
+
+
+def test_rgbnet_tc_range_status(L):
+    """Inputs the split-FP16 operands cannot hold are reported (no fault)."""
+    n = 300
+    k0, d, ray_id, params, _ = _mlp_case(n, 10)
+    k0[17, 3] = 1.0e4
+    act = torch.empty(L.rgbnet_act_bytes(n, L.F32_TC), dtype=torch.uint8, device="cuda")
+    rgb = torch.empty(n, 3, device="cuda")
+    L.device_status()
+    L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), None, n, None, dev(params), L.F32_TC, rgb, act)
+    assert L.device_status() == -8
+    assert L.device_status() == 0
 
 
 # --------------------------------------------------------- TV and Adam

@@ -123,6 +123,14 @@ def test_step_dvgo160_fp32_sparse_tv(T):
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
 
 
+@pytest.mark.parametrize("cfg_name", ["small_64", "dvgo_160"])
+def test_step_fp32_tensor_core_mlp(T, cfg_name):
+    # the colour MLP on the tensor cores with split-FP16 operands: same FP32 bar
+    cfg = synth.CONFIGS[cfg_name]
+    gpu, fb, opt, cfg, rp, P = _run(T, cfg, 1024, "f32tc", tv_dense=False, ray_stride=8)
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
+
+
 def test_step_dvgo160_fp32_dense_tv(T):
     gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
