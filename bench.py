@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dvgo_160")
     ap.add_argument("--tv-dense", action="store_true")
+    ap.add_argument("--mlp", default="f32tc", choices=["f32tc", "f32"],
+                    help="colour MLP of the FP32 workloads: tensor cores with split-FP16 "
+                         "operands (FP32 accuracy) or the CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BF16 / learned-proposal comparison")
@@ -46,8 +49,10 @@ def parse():
     return ap.parse_args()
 
 
-def precision_of(workload):
-    return "bf16" if workload.endswith("bf16") else "f32"
+def precision_of(workload, mlp="f32"):
+    """Trainer precision of a workload: the BF16 form, else the FP32 form with
+    its colour MLP on the tensor cores ("f32tc") or on the CUDA cores ("f32")."""
+    return "bf16" if workload.endswith("bf16") else mlp
 
 
 # ----------------------------------------------------------------- clocks
@@ -193,7 +198,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
     cfg = synth.CONFIGS[args.workload]
     rp = synth.render_params(cfg)
-    prec = precision_of(args.workload)
+    prec = precision_of(args.workload, args.mlp)
     D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
     tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
     nb = args.warmup + args.steps
@@ -300,8 +305,10 @@ def run_ours(args, rank, world):
 # dW2 and g_h1 (128*128 each), dW1 (128*40), g_k0 (128*12), all x2.
 MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)
 MLP_BWD_FLOP = 2 * (2 * 3 * 128 + 2 * 128 * 128 + 128 * 40 + 128 * 12)
-# The BF16 backward recomputes the forward on the tensor cores.
+# The BF16 backward recomputes the forward on the tensor cores; the split-FP16
+# (FP32-accurate) backward recomputes the second layer only.
 MLP_BWD_FLOP_RECOMPUTE = MLP_BWD_FLOP + 2 * (39 * 128 + 128 * 128)
+MLP_BWD_FLOP_TC = MLP_BWD_FLOP + 2 * 128 * 128
 KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2}
 
 
@@ -317,12 +324,16 @@ def roofline(res, peaks):
         if name.endswith("fwd"):
             per = MLP_FWD_FLOP
         else:
-            per = MLP_BWD_FLOP_RECOMPUTE if prec == "bf16" else MLP_BWD_FLOP
+            per = {"bf16": MLP_BWD_FLOP_RECOMPUTE, "f32tc": MLP_BWD_FLOP_TC}.get(prec, MLP_BWD_FLOP)
         flop = per * S_live
         achieved = flop / (ms * 1e-3) / 1e12
         if prec == "bf16":
             bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
             peak_src = "bf16_tflops_sustained of measured"
+        elif prec == "f32tc":
+            bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
+            peak_src = ("bf16_tflops_sustained of measured (FP16 runs at the BF16 rate); each "
+                        "algorithmic product takes three FP16 MMAs, so 1/3 of it is the ceiling")
         else:
             bound, peak, unit = "alu", round(fp32_peak, 2), "TFLOP/s"
             peak_src = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"
@@ -425,29 +436,6 @@ def forms_report(args):
     o, d = synth.rays(cfg, seed=11)
     t = synth.target_rgb(cfg, seed=11)
     to, td, tt = (torch.from_numpy(a).cuda() for a in (o, d, t))
-    colors = {}
-    for prec in ("f32", "bf16"):
-        tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
-        tr.forward(to, td, tt)
-        colors[prec] = tr.color.clone()
-    out["bf16"] = {"psnr_vs_fp32_render_db": round(proposal.psnr(colors["bf16"], colors["f32"]), 2),
-                   "psnr_gap_vs_target_db": round(abs(proposal.psnr(colors["bf16"], tt) -
-                                                      proposal.psnr(colors["f32"], tt)), 4)}
-    # learned proposal vs dense candidates (<= 512 / ray), 16384 rays
-    cfg5 = synth.CFG5
-    R = cfg5.n_rays
-    dense, prop_tr, prop = proposal.make_forms(cfg5, rp, D, Fg, P, synth.proposal_params(), R)
-    batches = [tuple(torch.from_numpy(a).cuda() for a in synth.rays(cfg5, seed=500 + i, n_rays=R))
-               for i in range(8)]
-    t0 = time.perf_counter()
-    for it in range(400):
-        ro, rd = batches[it % len(batches)]
-        prop.train_step(ro, rd)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    o5, d5 = synth.rays(cfg5, seed=9)
-    t5 = synth.target_rgb(cfg5, seed=9)
-    to5, td5, tt5 = (torch.from_numpy(a).cuda() for a in (o5, d5, t5))
     st = torch.cuda.current_stream()
 
     def timed(fn, n=10):
@@ -464,6 +452,36 @@ def forms_report(args):
         torch.cuda.synchronize()
         return sum(x.elapsed_time(y) for x, y in ev) / n
 
+    colors, ms = {}, {}
+    for prec in ("f32", "f32tc", "bf16"):
+        tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
+        tr.forward(to, td, tt)
+        colors[prec] = tr.color.clone()
+        ms[prec] = timed(lambda: tr.step(to, td, tt))
+        del tr
+    out["fp32_mlp_on_cuda_cores"] = {
+        "psnr_vs_tensor_core_fp32_render_db": round(proposal.psnr(colors["f32"], colors["f32tc"]), 2),
+        "ms_per_step_cuda_cores": round(ms["f32"], 3), "ms_per_step_tensor_cores": round(ms["f32tc"], 3)}
+    out["bf16"] = {"psnr_vs_fp32_render_db": round(proposal.psnr(colors["bf16"], colors["f32"]), 2),
+                   "psnr_gap_vs_target_db": round(abs(proposal.psnr(colors["bf16"], tt) -
+                                                      proposal.psnr(colors["f32"], tt)), 4),
+                   "ms_per_step_8192_rays": round(ms["bf16"], 3)}
+    # learned proposal vs dense candidates (<= 512 / ray), 16384 rays
+    cfg5 = synth.CFG5
+    R = cfg5.n_rays
+    dense, prop_tr, prop = proposal.make_forms(cfg5, rp, D, Fg, P, synth.proposal_params(), R,
+                                               precision=args.mlp)
+    batches = [tuple(torch.from_numpy(a).cuda() for a in synth.rays(cfg5, seed=500 + i, n_rays=R))
+               for i in range(8)]
+    t0 = time.perf_counter()
+    for it in range(400):
+        ro, rd = batches[it % len(batches)]
+        prop.train_step(ro, rd)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    o5, d5 = synth.rays(cfg5, seed=9)
+    t5 = synth.target_rgb(cfg5, seed=9)
+    to5, td5, tt5 = (torch.from_numpy(a).cuda() for a in (o5, d5, t5))
     dense.forward(to5, td5, tt5)
     c_dense = dense.color.clone()
     s_dense = int(dense.ray_off[-1].item())
@@ -555,10 +573,14 @@ def main():
         "metric": METRIC, "value": round(value, 1), "unit": "ray-samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["total_ms"] / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if res["prec"] == "f32" else "bf16", "data": "synthetic",
+        "dtype": "bf16" if res["prec"] == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "grid": cfg.grid, "rays": cfg.n_rays,
                    "samples_per_step": res["S"], "live_samples_per_step": res["S_live"],
-                   "mlp": "39-128-128-3", "tv_dense": bool(args.tv_dense), "l2": "flushed (256 MB memset) before each timed step",
+                   "mlp": "39-128-128-3",
+                   "mlp_precision": {"f32tc": "FP32 accuracy on tcgen05 (split-FP16 operands)",
+                                     "f32": "FP32 on the CUDA cores",
+                                     "bf16": "BF16 on tcgen05"}[res["prec"]],
+                   "tv_dense": bool(args.tv_dense), "l2": "flushed (256 MB memset) before each timed step",
                    "parallelism": "replicas" if args.gpus > 1 else "single"},
         "e2e": {"value": round(e2e, 1), "unit": "ray-samples/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": 12},
