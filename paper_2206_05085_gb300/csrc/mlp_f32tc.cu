@@ -44,7 +44,6 @@ __device__ int g_mlp_tc_status;  // first error a kernel of this file met
 namespace x3 {
 
 constexpr int kK1 = 48;                           // padded input width
-constexpr int kNCH = kHid / 32;                   // 32-column TMEM chunks of a hidden layer
 constexpr uint32_t kSboX = (kK1 / 8) * 128;       // 768: 8-row group stride, 48-wide rows
 constexpr uint32_t kSboH = (kHid / 8) * 128;      // 2048: 128-wide rows
 constexpr uint32_t kSboW1s = (16 / 8) * 128;      // 256: 16-wide rows (W1[:, 0:16])
@@ -196,13 +195,76 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_mlp_tc_statu
 using namespace x3;
 
 // ------------------------------------------------------------------ forward
-__global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
+// 256 threads: warps w and w + 4 share TMEM lane quarter w & 3 (tile rows
+// 32 (w & 3) .. + 31); warp half h = w / 4 takes hidden columns 64 h .. + 63
+// and input k-blocks 3 h .. 3 h + 2.  The next tile's inputs are loaded in
+// three dependent steps spread over the current tile (list index; feature
+// row and ray id; direction), so their latency hides behind the MMAs.
+struct RowIn {
+  int64_t s;       // sample index (-1 past the list end)
+  int32_t r;       // ray id
+  float k0[kFeat];
+  float d[3];
+};
+
+__device__ __forceinline__ void row_in_l1(RowIn& in, const int32_t* __restrict__ idx, int64_t j, int64_t n) {
+  in.s = j < n ? (idx ? (int64_t)__ldg(idx + j) : j) : -1;
+}
+__device__ __forceinline__ void row_in_l2(RowIn& in, const float* __restrict__ k0,
+                                          const int32_t* __restrict__ ray_id, bool want_k0) {
+  if (in.s < 0) return;
+  if (want_k0) {
+    const float4* kp = reinterpret_cast<const float4*>(k0 + in.s * kFeat);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = __ldg(kp + q);
+      in.k0[4 * q] = v.x;
+      in.k0[4 * q + 1] = v.y;
+      in.k0[4 * q + 2] = v.z;
+      in.k0[4 * q + 3] = v.w;
+    }
+  }
+  in.r = __ldg(ray_id + in.s);
+}
+__device__ __forceinline__ void row_in_l3(RowIn& in, const float* __restrict__ rays_d) {
+  if (in.s < 0) return;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) in.d[a] = __ldg(rays_d + 3 * (int64_t)in.r + a);
+}
+
+// The input row of encode_row from loaded values (same arithmetic).
+__device__ __forceinline__ void row_from(const RowIn& in, float row[kInP]) {
+  if (in.s < 0) {
+#pragma unroll
+    for (int k = 0; k < kInP; ++k) row[k] = 0.0f;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < kFeat; ++k) row[k] = in.k0[k];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float d = in.d[a];
+    row[kFeat + a] = d;
+#pragma unroll
+    for (int f = 0; f < kNumFreq; ++f) {
+      float sn, cs;
+      sincosf(d * (float)(1 << f), &sn, &cs);
+      row[kFeat + 3 + a * kNumFreq + f] = sn;
+      row[kFeat + 3 + 3 * kNumFreq + a * kNumFreq + f] = cs;
+    }
+  }
+  row[kIn] = 1.0f;
+}
+
+__global__ void __launch_bounds__(256, 1) rgbnet_fwd_tc_kernel(
     const float* __restrict__ k0, const float* __restrict__ rays_d, const int32_t* __restrict__ ray_id,
     const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* __restrict__ n_dev,
     const float* __restrict__ params, float* __restrict__ rgb, uint8_t* __restrict__ act) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + fEnd);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  float* zx = reinterpret_cast<float*>(sm + fEnd + sizeof(Side));   // [128][3] output-layer partials
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = warp >> 2, row = (warp & 3) * 32 + lane;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 256);
@@ -226,7 +288,7 @@ __global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sW1h = tc::smem_u32(sm + fW1h), sW1l = tc::smem_u32(sm + fW1l);
   const uint32_t sW2h = tc::smem_u32(sm + fW2h), sW2l = tc::smem_u32(sm + fW2l);
   uint8_t* img = sm + fImg;
@@ -235,19 +297,28 @@ __global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
   const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
   uint32_t phase = 0;
   bool ok = true, bad = false;
+  RowIn cur, nxt;
+  {
+    const int64_t j = (int64_t)blockIdx.x * kTile + row;
+    row_in_l1(cur, idx, j, n);
+    row_in_l2(cur, k0, ray_id, half == 0);
+    row_in_l3(cur, rays_d);
+  }
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int64_t j = t * kTile + tid;
+    const int64_t jn = (t + gridDim.x) * kTile + row;   // same row of this CTA's next tile
     {
       float x[kInP];
-      encode_row(k0, rays_d, ray_id, idx, j, n, x);
+      row_from(cur, x);
       float v[8];
 #pragma unroll
-      for (int kb = 0; kb < kK1 / 8; ++kb) {
+      for (int kb = 0; kb < 3; ++kb) {
+        const int k8 = (3 * half + kb) * 8;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = kb * 8 + i < kInP ? kSX * x[kb * 8 + i] : 0.0f;
-        st_split8(img + iXh, img + iXl, tid, kb * 8, kSboX, v, bad);
+        for (int i = 0; i < 8; ++i) v[i] = k8 + i < kInP ? kSX * x[k8 + i] : 0.0f;
+        st_split8(img + iXh, img + iXl, row, k8, kSboX, v, bad);
       }
     }
+    const int64_t s_cur = cur.s;
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -256,18 +327,21 @@ __global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
       mma3(tmem, sXh, sXl, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
       tc::mma_commit(&fs->bar_mma);
     }
+    row_in_l1(nxt, idx, jn, n);
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
     phase ^= 1;
     if (!ok) break;
     tc::fence_after_sync();
-#pragma unroll 1
-    for (int ch = 0; ch < kNCH; ++ch) {   // H1 = relu(D1), scaled and split
+    row_in_l2(nxt, k0, ray_id, half == 0);
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {   // H1 = relu(D1), scaled and split
+      const int ch = 2 * half + c2;
       float v[32];
       tc::tmem_ld32(lane_base + ch * 32, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = kSH * fmaxf(v[i] * inv1, 0.0f);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, tid, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, row, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -278,15 +352,15 @@ __global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
       tc::mma_commit(&fs->bar_mma);
       tc::bulk_s2g(act + kActHeader + (size_t)t * kImage, img, kImage);
     }
+    row_in_l3(nxt, rays_d);
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
     phase ^= 1;
     if (!ok) break;
     tc::fence_after_sync();
-    float z3[kOut];
+    float z3[kOut] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int c = 0; c < kOut; ++c) z3[c] = fs->b3[c];
-#pragma unroll 1
-    for (int ch = 0; ch < kNCH; ++ch) {
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int ch = 2 * half + c2;
       float v[32];
       tc::tmem_ld32(lane_base + 128 + ch * 32, v);
 #pragma unroll
@@ -297,18 +371,23 @@ __global__ void __launch_bounds__(128, 1) rgbnet_fwd_tc_kernel(
         for (int c = 0; c < kOut; ++c) z3[c] = fmaf(fs->W3[c * kHid + o], h, z3[c]);
       }
     }
-    if (j < n) {
-      const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    if (half == 1) {
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) rgb[3 * s + c] = sigmoid_f(z3[c]);
+      for (int c = 0; c < kOut; ++c) zx[row * kOut + c] = z3[c];
     }
     if (tid == 0) tc::bulk_wait_read();   // the image may be overwritten again
     tc::fence_before_sync();
     __syncthreads();
+    if (half == 0 && s_cur >= 0) {
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) rgb[3 * s_cur + c] = sigmoid_f(fs->b3[c] + (z3[c] + zx[row * kOut + c]));
+    }
+    cur = nxt;
   }
   if (tid == 0) tc::bulk_wait_all();
   if (!ok && tid == 0) set_status(DVGO_ERR_TIMEOUT);
   if (bad) set_status(DVGO_ERR_RANGE);
+  tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -338,7 +417,40 @@ __global__ void __launch_bounds__(256) grad_bound_kernel(const float* __restrict
 }
 
 // ----------------------------------------------------------------- backward
-__global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
+// Same thread layout as the forward (256 threads, two warp halves per TMEM
+// lane quarter, half h on hidden columns 64 h .. + 63).  The upstream colour
+// gradient of the next tile is loaded in three dependent steps over the
+// current tile, and the next tile's image is copied in as soon as the MMAs
+// that read each part have completed.
+struct UpIn {
+  int64_t s;       // sample index (-1 past the list end)
+  int32_t r;
+  float ws;
+  float g[kOut];
+};
+
+__device__ __forceinline__ void up_l1(UpIn& u, const int32_t* __restrict__ idx, int64_t j, int64_t n) {
+  u.s = j < n ? (idx ? (int64_t)__ldg(idx + j) : j) : -1;
+}
+__device__ __forceinline__ void up_l2(UpIn& u, const float* __restrict__ g_rgb, const float* __restrict__ w,
+                                      const int32_t* __restrict__ ray_id) {
+  if (u.s < 0) return;
+  if (g_rgb) {
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) u.g[c] = __ldg(g_rgb + 3 * u.s + c);
+  } else {
+    u.ws = __ldg(w + u.s);
+    u.r = __ldg(ray_id + u.s);
+  }
+}
+__device__ __forceinline__ void up_l3(UpIn& u, const float* __restrict__ g_rgb,
+                                      const float* __restrict__ g_color) {
+  if (u.s < 0 || g_rgb) return;
+#pragma unroll
+  for (int c = 0; c < kOut; ++c) u.g[c] = u.ws * __ldg(g_color + 3 * (int64_t)u.r + c);
+}
+
+__global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
     const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx, int64_t n_cap,
     const int64_t* __restrict__ n_dev, const float* __restrict__ params, const uint8_t* __restrict__ act,
@@ -346,6 +458,7 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + bEnd);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = warp >> 2, row = (warp & 3) * 32 + lane;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
@@ -384,22 +497,22 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
   const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
   const uint8_t* img_g = act + kActHeader;
   uint8_t* img = sm + bImg;
+  float* zx = reinterpret_cast<float*>(sm + bGh);  // [2][128][3] output-layer partials (G is free then)
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sW1h = tc::smem_u32(sm + bW1h), sW1l = tc::smem_u32(sm + bW1l);
   const uint32_t sW2h = tc::smem_u32(sm + bW2h), sW2l = tc::smem_u32(sm + bW2l);
   const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
   const uint32_t sGh = tc::smem_u32(sm + bGh), sGl = tc::smem_u32(sm + bGl);
-  float dW3acc[kOut * kNCH], db2acc[kNCH], db3acc[kOut];
+  float dW3acc[kOut * 2], db2acc[2], db3acc[kOut];
 #pragma unroll
-  for (int i = 0; i < kOut * kNCH; ++i) dW3acc[i] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < kNCH; ++i) db2acc[i] = 0.0f;
+  for (int i = 0; i < kOut * 2; ++i) dW3acc[i] = 0.0f;
+  db2acc[0] = db2acc[1] = 0.0f;
 #pragma unroll
   for (int c = 0; c < kOut; ++c) db3acc[c] = 0.0f;
   uint32_t ph_in = 0, ph_mma = 0;
@@ -425,26 +538,30 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
     tc::fence_after_sync();
     return r;
   };
+  UpIn cur, nxt;
+  up_l1(cur, idx, (int64_t)blockIdx.x * kTile + row, n);
+  up_l2(cur, g_rgb, w, ray_id);
+  up_l3(cur, g_rgb, g_color);
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int64_t j = t * kTile + tid;
-    const bool valid = j < n;
     const int64_t tn = t + gridDim.x;   // this CTA's next tile
-    int64_t s = 0;
+    const bool valid = cur.s >= 0;
     float gup[kOut] = {0.0f, 0.0f, 0.0f};
     if (valid) {
-      s = idx ? (int64_t)__ldg(idx + j) : j;
-      upstream_rgb_grad(g_rgb, g_color, w, ray_id, s, gup);
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) gup[c] = cur.g[c];
     }
+    const int64_t s = cur.s;
+    up_l1(nxt, idx, tn * kTile + row, n);
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_in, kSpin) &&
                            tc::mbar_wait(&fs->bar_x, ph_in, kSpin));
     if (!ok) break;
     ph_in ^= 1;
     inflight_h = inflight_x = false;
-    // relu mask of layer 1 from the stored activations (H1 > 0 <=> hi > 0)
-    uint32_t m1b[kNCH] = {0u, 0u, 0u, 0u};
+    // relu mask of layer 1 on this half's columns (H1 > 0 <=> hi > 0)
+    uint32_t m1b[2] = {0u, 0u};
 #pragma unroll
-    for (int k8 = 0; k8 < kHid; k8 += 8) {
-      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(tid, k8, kSboH));
+    for (int k8 = 0; k8 < 64; k8 += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(row, 64 * half + k8, kSboH));
       const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -459,41 +576,52 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
            tc::idesc_f16(128, kHid, 0, 0), false);
       tc::mma_commit(&fs->bar_mma);
     }
+    up_l2(nxt, g_rgb, w, ray_id);
     if (!(ok = mma_wait())) break;
-    // output layer: z3, g_z3, db3
-    float z3[kOut];
+    // output layer: z3 from both halves, g_z3, db3
+    {
+      float zp[kOut] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int c = 0; c < kOut; ++c) z3[c] = fs->b3[c];
-#pragma unroll 1
-    for (int ch = 0; ch < kNCH; ++ch) {
-      float v[32];
-      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const int ch = 2 * half + c2;
+        float v[32];
+        tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int o = ch * 32 + i;
-        const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
+        for (int i = 0; i < 32; ++i) {
+          const int o = ch * 32 + i;
+          const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
 #pragma unroll
-        for (int c = 0; c < kOut; ++c) z3[c] = fmaf(fs->W3[c * kHid + o], h, z3[c]);
+          for (int c = 0; c < kOut; ++c) zp[c] = fmaf(fs->W3[c * kHid + o], h, zp[c]);
+        }
       }
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) zx[(half * kTile + row) * kOut + c] = zp[c];
     }
+    __syncthreads();
     float gz3[kOut];
 #pragma unroll
     for (int c = 0; c < kOut; ++c) {
-      const float y = sigmoid_f(z3[c]);
+      const float z3 = fs->b3[c] + (zx[row * kOut + c] + zx[(kTile + row) * kOut + c]);
+      const float y = sigmoid_f(z3);
       gz3[c] = gup[c] * y * (1.0f - y);
-      db3acc[c] += gz3[c];
     }
+    if (half == 0) {
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
+    }
+    __syncthreads();   // zx (inside the G buffer) is read; G may be written
     // this sample's gradient scales; its H1 and X rows carry the compensation
     const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
     const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;   // S2 / sG2 <= 1
     const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
     const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
     const float invX = 1.0f / (sG1 * sW1);           // g_X
-    if (S2 != sG2) rescale_row<kHid>(img + iHh, img + iHl, tid, kSboH, S2 / sG2, bad);
-    if (S1 != sG1) rescale_row<kK1>(img + iXh, img + iXl, tid, kSboX, S1 / sG1, bad);
+    if (S2 != sG2) rescale_row<64>(img + iHh + half * 128 * 8, img + iHl + half * 128 * 8, row, kSboH, S2 / sG2, bad);
+    if (S1 != sG1) rescale_row<24>(img + iXh + half * 128 * 3, img + iXl + half * 128 * 3, row, kSboX, S1 / sG1, bad);
     // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
 #pragma unroll
-    for (int ch = 0; ch < kNCH; ++ch) {
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int ch = 2 * half + c2;
       float v[32], g[32];
       tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
 #pragma unroll
@@ -510,14 +638,14 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
 #pragma unroll
       for (int i = 0; i < 32; ++i) sg[i] = sG2 * g[i];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, tid, ch * 32 + q * 8, kSboH, sg + 8 * q, bad);
-      db2acc[ch] += reduce_scatter32(g, lane);
-#pragma unroll 1
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, ch * 32 + q * 8, kSboH, sg + 8 * q, bad);
+      db2acc[c2] += reduce_scatter32(g, lane);
+#pragma unroll
       for (int c = 0; c < kOut; ++c) {
         float p[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
-        dW3acc[c * kNCH + ch] += reduce_scatter32(p, lane);
+        dW3acc[c * 2 + c2] += reduce_scatter32(p, lane);
       }
     }
     tc::fence_proxy_async_smem();
@@ -531,17 +659,19 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
            tc::idesc_f16(128, kHid, 0, 1), false);
       tc::mma_commit(&fs->bar_mma);
     }
+    up_l3(nxt, g_rgb, g_color);
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
     // G1 = g_h1 * (H1 > 0), rescaled to sG1
 #pragma unroll
-    for (int ch = 0; ch < kNCH; ++ch) {
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int ch = 2 * half + c2;
       float v[32];
       tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = ((m1b[ch] >> i) & 1u) ? v[i] * fG1 : 0.0f;
+      for (int i = 0; i < 32; ++i) v[i] = ((m1b[c2] >> i) & 1u) ? v[i] * fG1 : 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, tid, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -557,7 +687,7 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
     }
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
-    {
+    if (half == 0) {
       float gx[16];
       tc::tmem_ld16(lane_base + cTmp, gx);
       if (valid) {
@@ -567,6 +697,7 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
         dst[2] = make_float4(gx[8] * invX, gx[9] * invX, gx[10] * invX, gx[11] * invX);
       }
     }
+    cur = nxt;
     tc::fence_before_sync();
     __syncthreads();
   }
@@ -577,38 +708,52 @@ __global__ void __launch_bounds__(128, 1) rgbnet_bwd_tc_kernel(
     set_status(DVGO_ERR_TIMEOUT);
   }
   if (bad) set_status(DVGO_ERR_RANGE);
-  // output-layer and b2 partials of this warp
+  // output-layer and b2 partials of this warp (lane l holds column 64 half + 32 c2 + l)
 #pragma unroll
   for (int c = 0; c < kOut; ++c)
 #pragma unroll
-    for (int ch = 0; ch < kNCH; ++ch)
-      atomicAdd(g_params + kOffW3 + c * kHid + ch * 32 + lane, dW3acc[c * kNCH + ch]);
+    for (int c2 = 0; c2 < 2; ++c2)
+      atomicAdd(g_params + kOffW3 + c * kHid + 64 * half + 32 * c2 + lane, dW3acc[c * 2 + c2]);
 #pragma unroll
-  for (int ch = 0; ch < kNCH; ++ch) atomicAdd(g_params + kOffB2 + ch * 32 + lane, db2acc[ch]);
+  for (int c2 = 0; c2 < 2; ++c2) atomicAdd(g_params + kOffB2 + 64 * half + 32 * c2 + lane, db2acc[c2]);
+  if (half == 0)
 #pragma unroll
-  for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffB3 + c, db3acc[c]);
+    for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffB3 + c, db3acc[c]);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (ok && (int64_t)blockIdx.x < ntiles) {   // this CTA accumulated dW2 / dW1
-    // TMEM lane = output neuron o
-    const int o = tid;
+  if (ok && (int64_t)blockIdx.x < ntiles) {
+    // dW2 / dW1 rows (TMEM lane = output neuron) through a per-warp 32 x 33
+    // shared-memory transpose, so that each reduction instruction covers 32
+    // consecutive parameters of one row
+    float* tp = reinterpret_cast<float*>(sm + bGh) + warp * 32 * 33;
     const float u2 = 1.0f / (S2 * kSH), u1 = 1.0f / (S1 * kSX);
-#pragma unroll 1
-    for (int ch = 0; ch < kNCH; ++ch) {
+    const int o0 = (warp & 3) * 32;
+    auto flush32 = [&](uint32_t col, float scale, int base, int stride, int ncol) {
       float v[32];
-      tc::tmem_ld32(lane_base + cDW2 + ch * 32, v);
+      tc::tmem_ld32(lane_base + col, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) atomicAdd(g_params + kOffW2 + o * kHid + ch * 32 + i, v[i] * u2);
+      for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i] * scale;
+      __syncwarp();
+      if (lane < ncol)
+        for (int r = 0; r < 32; ++r) atomicAdd(g_params + base + (o0 + r) * stride + lane, tp[r * 33 + lane]);
+      __syncwarp();
+    };
+#pragma unroll 1
+    for (int c2 = 0; c2 < 2; ++c2) flush32(cDW2 + 64 * half + 32 * c2, u2, kOffW2 + 64 * half + 32 * c2, kHid, 32);
+    if (half == 0) {
+      flush32(cDW1, u1, kOffW1, kIn, 32);                       // W1[:, 0:32]
+    } else {
+      float v[16];
+      tc::tmem_ld16(lane_base + cDW1 + 32, v);                  // W1[:, 32:39] and b1 (column 39)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) tp[lane * 33 + i] = v[i] * u1;
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        if (lane < kIn - 32) atomicAdd(g_params + kOffW1 + (o0 + r) * kIn + 32 + lane, tp[r * 33 + lane]);
+        else if (lane == kIn - 32) atomicAdd(g_params + kOffB1 + o0 + r, tp[r * 33 + lane]);
+      }
     }
-    float v[32], u[16];
-    tc::tmem_ld32(lane_base + cDW1, v);
-    tc::tmem_ld16(lane_base + cDW1 + 32, u);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) atomicAdd(g_params + kOffW1 + o * kIn + k, v[k] * u1);
-#pragma unroll
-    for (int k = 32; k < kIn; ++k) atomicAdd(g_params + kOffW1 + o * kIn + k, u[k - 32] * u1);
-    atomicAdd(g_params + kOffB1 + o, u[kIn - 32] * u1);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -627,14 +772,14 @@ int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
 int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
                           const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
                           float* rgb, float* act, cudaStream_t st) {
-  const size_t smem = fEnd + sizeof(Side);
+  const size_t smem = fEnd + sizeof(Side) + kTile * kOut * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(rgbnet_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_fwd_tc_kernel<<<grid, 128, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
+  rgbnet_fwd_tc_kernel<<<grid, 256, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
                                                 reinterpret_cast<uint8_t*>(act));
   return launch_status();
 }
@@ -653,7 +798,7 @@ int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float*
   grad_bound_kernel<<<grid_for(n_cap, 256, 4), 256, 0, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev,
                                                              reinterpret_cast<unsigned int*>(act));
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_bwd_tc_kernel<<<grid, 128, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
+  rgbnet_bwd_tc_kernel<<<grid, 256, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
                                                 reinterpret_cast<const uint8_t*>(act), g_params, g_k0);
   return launch_status();
 }
