@@ -71,8 +71,7 @@ constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
 constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256;
 
 struct Side {
-  float W3[kOut * kHid];
-  float b2[kHid];
+  float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
   float b3[4];
   float red[16];
   uint64_t bar_h;     // H1 terms of a tile image landed
@@ -103,23 +102,20 @@ __device__ __forceinline__ float pow2_scale(float m) {
   return ldexpf(1.0f, 13 - e);
 }
 
-__device__ __forceinline__ uint32_t pack_h(__half a, __half b) {
-  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
-
-// Split 8 (already scaled) values into the hi / lo core-matrix rows at (row, k8).
+// Split 8 (already scaled) values into the hi / lo core-matrix rows at (row,
+// k8); vmax tracks the largest magnitude split (range check).
 __device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int k8, uint32_t sbo,
-                                          const float* v, bool& bad) {
+                                          const float* v, float& vmax) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float a = v[2 * i], b = v[2 * i + 1];
-    bad |= fabsf(a) >= kRange || fabsf(b) >= kRange;
-    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-    const __half la = __float2half_rn(a - __half2float(ha));
-    const __half lb = __float2half_rn(b - __half2float(hb));
-    h[i] = pack_h(ha, hb);
-    l[i] = pack_h(la, lb);
+    vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
+    const __half2 h2 = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h2);
+    const __half2 l2 = __floats2half2_rn(a - hf.x, b - hf.y);
+    h[i] = *reinterpret_cast<const uint32_t*>(&h2);
+    l[i] = *reinterpret_cast<const uint32_t*>(&l2);
   }
   const uint32_t off = tc::cm_off(row, k8, sbo);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -129,7 +125,7 @@ __device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int
 // Multiply row `row` (K values, split) by the power of two r <= 1, re-splitting.
 template <int K>
 __device__ __forceinline__ void rescale_row(uint8_t* hi, uint8_t* lo, int row, uint32_t sbo, float r,
-                                            bool& bad) {
+                                            float& vmax) {
 #pragma unroll 2
   for (int k8 = 0; k8 < K; k8 += 8) {
     const uint32_t off = tc::cm_off(row, k8, sbo);
@@ -144,7 +140,7 @@ __device__ __forceinline__ void rescale_row(uint8_t* hi, uint8_t* lo, int row, u
       v[2 * i] = r * (__low2float(h2) + __low2float(l2));
       v[2 * i + 1] = r * (__high2float(h2) + __high2float(l2));
     }
-    st_split8(hi, lo, row, k8, sbo, v, bad);
+    st_split8(hi, lo, row, k8, sbo, v, vmax);
   }
 }
 
@@ -156,27 +152,32 @@ __device__ __forceinline__ void st_split1(uint8_t* hi, uint8_t* lo, uint32_t off
 }
 
 // D (+)= A B^T over K = 16 * ksteps, split operands: three MMAs per K step.
-// a_step / b_step: byte advance of the descriptors' start address per step.
+// a_step / b_step: byte advance of the descriptors' start address per step
+// (the start-address field holds address / 16, so a step adds step / 16).
 __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint32_t a_step, uint32_t a_lbo,
                                      uint32_t a_sbo, uint32_t bh, uint32_t bl, uint32_t b_step,
                                      uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
                                      bool accumulate) {
+  uint64_t dah = tc::smem_desc(ah, a_lbo, a_sbo), dal = tc::smem_desc(al, a_lbo, a_sbo);
+  uint64_t dbh = tc::smem_desc(bh, b_lbo, b_sbo), dbl = tc::smem_desc(bl, b_lbo, b_sbo);
+  const uint64_t ia = a_step >> 4, ib = b_step >> 4;
 #pragma unroll 1
   for (int k = 0; k < ksteps; ++k) {
-    const uint64_t dah = tc::smem_desc(ah + k * a_step, a_lbo, a_sbo);
-    const uint64_t dal = tc::smem_desc(al + k * a_step, a_lbo, a_sbo);
-    const uint64_t dbh = tc::smem_desc(bh + k * b_step, b_lbo, b_sbo);
-    const uint64_t dbl = tc::smem_desc(bl + k * b_step, b_lbo, b_sbo);
     tc::mma_bf16(d, dah, dbh, idesc, (accumulate || k > 0) ? 1u : 0u);
     tc::mma_bf16(d, dah, dbl, idesc, 1u);
     tc::mma_bf16(d, dal, dbh, idesc, 1u);
+    dah += ia;
+    dal += ia;
+    dbh += ib;
+    dbl += ib;
   }
 }
 
 // Output-layer constants (exact FP32).
 __device__ __forceinline__ void load_out_layer(const float* __restrict__ params, Side* fs) {
-  for (int e = threadIdx.x; e < kOut * kHid; e += blockDim.x) fs->W3[e] = params[kOffW3 + e];
-  for (int e = threadIdx.x; e < kHid; e += blockDim.x) fs->b2[e] = params[kOffB2 + e];
+  for (int o = threadIdx.x; o < kHid; o += blockDim.x)
+    fs->ob[o] = make_float4(params[kOffB2 + o], params[kOffW3 + o], params[kOffW3 + kHid + o],
+                            params[kOffW3 + 2 * kHid + o]);
   if (threadIdx.x < 4) fs->b3[threadIdx.x] = threadIdx.x < kOut ? params[kOffB3 + threadIdx.x] : 0.0f;
 }
 
@@ -195,11 +196,12 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_mlp_tc_statu
 using namespace x3;
 
 // ------------------------------------------------------------------ forward
-// 256 threads: warps w and w + 4 share TMEM lane quarter w & 3 (tile rows
-// 32 (w & 3) .. + 31); warp half h = w / 4 takes hidden columns 64 h .. + 63
-// and input k-blocks 3 h .. 3 h + 2.  The next tile's inputs are loaded in
-// three dependent steps spread over the current tile (list index; feature
-// row and ray id; direction), so their latency hides behind the MMAs.
+// 512 threads: the four warps w, w + 4, w + 8, w + 12 share TMEM lane quarter
+// w & 3 (tile rows 32 (w & 3) .. + 31); warp quarter q = w / 4 takes hidden
+// columns 32 q .. 32 q + 31 and a quarter of the input columns.  The next
+// tile's inputs are loaded in three dependent steps spread over the current
+// tile (list index; feature row and ray id; direction), so their latency
+// hides behind the MMAs.
 struct RowIn {
   int64_t s;       // sample index (-1 past the list end)
   int32_t r;       // ray id
@@ -232,43 +234,56 @@ __device__ __forceinline__ void row_in_l3(RowIn& in, const float* __restrict__ r
   for (int a = 0; a < 3; ++a) in.d[a] = __ldg(rays_d + 3 * (int64_t)in.r + a);
 }
 
-// The input row of encode_row from loaded values (same arithmetic).
-__device__ __forceinline__ void row_from(const RowIn& in, float row[kInP]) {
-  if (in.s < 0) {
+// Input k-blocks (8 columns each) of warp quarter q: q0 blocks 0-1, q1 block
+// 2, q2 block 3, q3 blocks 4-5 (the transcendental work is spread evenly).
+__device__ __forceinline__ int x_first_block(int q) { return q == 0 ? 0 : (q == 3 ? 4 : q + 1); }
+__device__ __forceinline__ int x_num_blocks(int q) { return (q == 0 || q == 3) ? 2 : 1; }
+
+// Those columns of the input row [k0 (12), d (3), sin(2^f d_a) (a major, f
+// inner; p = 4 a + f), cos(2^f d_a), 1, 0 ...] from loaded values; rows past
+// the list end are zero.
+__device__ __forceinline__ void quarter_x(const RowIn& in, int q, float v[16]) {
 #pragma unroll
-    for (int k = 0; k < kInP; ++k) row[k] = 0.0f;
-    return;
+  for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+  if (in.s < 0) return;
+  auto arg = [&](int p) { return in.d[p >> 2] * (float)(1 << (p & 3)); };
+  if (q == 0) {
+#pragma unroll
+    for (int k = 0; k < kFeat; ++k) v[k] = in.k0[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[kFeat + a] = in.d[a];
+    v[15] = sinf(arg(0));
+  } else if (q == 1) {
+#pragma unroll
+    for (int p = 1; p <= 8; ++p) v[p - 1] = sinf(arg(p));
+  } else if (q == 2) {
+#pragma unroll
+    for (int p = 9; p <= 11; ++p) v[p - 9] = sinf(arg(p));
+#pragma unroll
+    for (int p = 0; p <= 4; ++p) v[3 + p] = cosf(arg(p));
+  } else {
+#pragma unroll
+    for (int p = 5; p <= 11; ++p) v[p - 5] = cosf(arg(p));
+    v[7] = 1.0f;
   }
-#pragma unroll
-  for (int k = 0; k < kFeat; ++k) row[k] = in.k0[k];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float d = in.d[a];
-    row[kFeat + a] = d;
-#pragma unroll
-    for (int f = 0; f < kNumFreq; ++f) {
-      float sn, cs;
-      sincosf(d * (float)(1 << f), &sn, &cs);
-      row[kFeat + 3 + a * kNumFreq + f] = sn;
-      row[kFeat + 3 + 3 * kNumFreq + a * kNumFreq + f] = cs;
-    }
-  }
-  row[kIn] = 1.0f;
 }
 
-__global__ void __launch_bounds__(256, 1) rgbnet_fwd_tc_kernel(
+__global__ void __launch_bounds__(512, 1) rgbnet_fwd_tc_kernel(
     const float* __restrict__ k0, const float* __restrict__ rays_d, const int32_t* __restrict__ ray_id,
     const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* __restrict__ n_dev,
     const float* __restrict__ params, float* __restrict__ rgb, uint8_t* __restrict__ act) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + fEnd);
-  float* zx = reinterpret_cast<float*>(sm + fEnd + sizeof(Side));   // [128][3] output-layer partials
+  float* zx = reinterpret_cast<float*>(sm + fEnd + sizeof(Side));   // [4][128][3] output-layer partials
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = warp >> 2, row = (warp & 3) * 32 + lane;
+  const int qw = warp >> 2, row = (warp & 3) * 32 + lane;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 256);
-  if (tid == 0) tc::mbar_init(&fs->bar_mma, 1);
+  if (tid == 0) {
+    tc::mbar_init(&fs->bar_h, 1);     // layer-1 MMAs done
+    tc::mbar_init(&fs->bar_mma, 1);   // layer-2 MMAs done
+  }
   // weights: W1 | b1 (column 39) and W2, split, each with its own scale
   float m1 = 0.0f, m2 = 0.0f;
   for (int e = tid; e < kHid * kIn + kHid; e += blockDim.x) m1 = fmaxf(m1, fabsf(params[kOffW1 + e]));
@@ -295,53 +310,54 @@ __global__ void __launch_bounds__(256, 1) rgbnet_fwd_tc_kernel(
   const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
   const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
-  uint32_t phase = 0;
-  bool ok = true, bad = false;
-  RowIn cur, nxt;
-  {
-    const int64_t j = (int64_t)blockIdx.x * kTile + row;
-    row_in_l1(cur, idx, j, n);
-    row_in_l2(cur, k0, ray_id, half == 0);
-    row_in_l3(cur, rays_d);
-  }
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int64_t jn = (t + gridDim.x) * kTile + row;   // same row of this CTA's next tile
-    {
-      float x[kInP];
-      row_from(cur, x);
-      float v[8];
+  uint8_t* act_img = act + kActHeader;
+  uint32_t ph1 = 0, ph2 = 0;
+  bool ok = true;
+  float vmax = 0.0f;
+  const int64_t step = gridDim.x;
+
+  // Software pipeline over this CTA's tiles t0, t1 = t0 + step, ...  While
+  // the layer-2 MMAs of tile t run, the threads write X of tile t + step and
+  // issue its layer-1 MMAs; while those run, they finish tile t's output layer.
+  // The X and H1 parts of each tile image are stored by separate bulk copies,
+  // so X of the next tile may be written as soon as the X copy has read it.
+  RowIn in, nxt;   // inputs of the tile whose X is written next / the one after
+  auto load_rows = [&](RowIn& r, int64_t tile) {
+    row_in_l1(r, idx, tile * kTile + row, n);
+    row_in_l2(r, k0, ray_id, qw == 0);
+    row_in_l3(r, rays_d);
+  };
+  auto write_x = [&](const RowIn& r) {
+    float x[16];
+    quarter_x(r, qw, x);
 #pragma unroll
-      for (int kb = 0; kb < 3; ++kb) {
-        const int k8 = (3 * half + kb) * 8;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = k8 + i < kInP ? kSX * x[k8 + i] : 0.0f;
-        st_split8(img + iXh, img + iXl, row, k8, kSboX, v, bad);
-      }
-    }
-    const int64_t s_cur = cur.s;
+    for (int i = 0; i < 16; ++i) x[i] *= kSX;
+    const int fb = x_first_block(qw);
+    st_split8(img + iXh, img + iXl, row, fb * 8, kSboX, x, vmax);
+    if (x_num_blocks(qw) == 2) st_split8(img + iXh, img + iXl, row, fb * 8 + 8, kSboX, x + 8, vmax);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      mma3(tmem, sXh, sXl, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
-      tc::mma_commit(&fs->bar_mma);
-    }
-    row_in_l1(nxt, idx, jn, n);
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
+  };
+  auto issue_l1 = [&](int64_t tile) {   // thread 0
     tc::fence_after_sync();
-    row_in_l2(nxt, k0, ray_id, half == 0);
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {   // H1 = relu(D1), scaled and split
-      const int ch = 2 * half + c2;
+    mma3(tmem, sXh, sXl, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
+    tc::mma_commit(&fs->bar_h);
+    tc::bulk_s2g(act_img + (size_t)tile * kImage + iXh, img + iXh, 2 * kXBytes);
+  };
+  // H1 = relu(D1) of a tile, split; then its layer-2 MMAs and the H1 copy
+  auto layer1_out = [&](int64_t tile) -> bool {
+    bool r = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph1, kSpin));
+    ph1 ^= 1;
+    if (!r) return false;
+    tc::fence_after_sync();
+    {
       float v[32];
-      tc::tmem_ld32(lane_base + ch * 32, v);
+      tc::tmem_ld32(lane_base + 32 * qw, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = kSH * fmaxf(v[i] * inv1, 0.0f);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, row, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, row, 32 * qw + q * 8, kSboH, v + 8 * q, vmax);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -350,43 +366,76 @@ __global__ void __launch_bounds__(256, 1) rgbnet_fwd_tc_kernel(
       tc::fence_after_sync();
       mma3(tmem + 128, sHh, sHl, 256, 128, kSboH, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
       tc::mma_commit(&fs->bar_mma);
-      tc::bulk_s2g(act + kActHeader + (size_t)t * kImage, img, kImage);
+      tc::bulk_s2g(act_img + (size_t)tile * kImage + iHh, img + iHh, 2 * kHBytes);
     }
-    row_in_l3(nxt, rays_d);
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, phase, kSpin));
-    phase ^= 1;
-    if (!ok) break;
-    tc::fence_after_sync();
-    float z3[kOut] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const int ch = 2 * half + c2;
-      float v[32];
-      tc::tmem_ld32(lane_base + 128 + ch * 32, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int o = ch * 32 + i;
-        const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) z3[c] = fmaf(fs->W3[c * kHid + o], h, z3[c]);
+    return true;
+  };
+
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    load_rows(in, t);
+    write_x(in);
+    int64_t s_t = in.s;
+    if (tid == 0) issue_l1(t);
+    load_rows(in, t + step);
+    ok = layer1_out(t);
+    while (ok) {
+      const int64_t tn = t + step;
+      const bool more = tn < ntiles;
+      // X (and layer 1) of the next tile, once its X region has been read out
+      if (more) {
+        if (tid == 0) tc::bulk_wait_read_allow1();   // the older group: X copy of tile t
+        __syncthreads();
+        write_x(in);
+        if (tid == 0) issue_l1(tn);
       }
-    }
-    if (half == 1) {
+      const int64_t s_n = in.s;
+      if (more) row_in_l1(nxt, idx, (tn + step) * kTile + row, n);
+      // output layer of tile t
+      ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, ph2, kSpin));
+      ph2 ^= 1;
+      if (!ok) break;
+      tc::fence_after_sync();
+      if (more) row_in_l2(nxt, k0, ray_id, qw == 0);
+      float z3[kOut] = {0.0f, 0.0f, 0.0f};
+      {
+        float v[32];
+        tc::tmem_ld32(lane_base + 128 + 32 * qw, v);
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) zx[row * kOut + c] = z3[c];
-    }
-    if (tid == 0) tc::bulk_wait_read();   // the image may be overwritten again
-    tc::fence_before_sync();
-    __syncthreads();
-    if (half == 0 && s_cur >= 0) {
+        for (int i = 0; i < 32; ++i) {
+          const int o = 32 * qw + i;
+          const float4 q = fs->ob[o];
+          const float h = fmaxf(fmaf(v[i], inv2, q.x), 0.0f);
+          z3[0] = fmaf(q.y, h, z3[0]);
+          z3[1] = fmaf(q.z, h, z3[1]);
+          z3[2] = fmaf(q.w, h, z3[2]);
+        }
+      }
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) rgb[3 * s_cur + c] = sigmoid_f(fs->b3[c] + (z3[c] + zx[row * kOut + c]));
+      for (int c = 0; c < kOut; ++c) zx[(qw * kTile + row) * kOut + c] = z3[c];
+      // the H1 region is free once tile t's H1 copy has read it
+      if (tid == 0) tc::bulk_wait_read_allow1();    // pending: the X copy of tile tn at most
+      tc::fence_before_sync();
+      __syncthreads();
+      if (qw == 0 && s_t >= 0) {
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) {
+          const float* zc = zx + row * kOut + c;
+          const float z = ((zc[0] + zc[kTile * kOut]) + zc[2 * kTile * kOut]) + zc[3 * kTile * kOut];
+          rgb[3 * s_t + c] = sigmoid_f(fs->b3[c] + z);
+        }
+      }
+      if (!more) break;
+      if (more) row_in_l3(nxt, rays_d);
+      ok = layer1_out(tn);
+      in = nxt;
+      s_t = s_n;
+      t = tn;
     }
-    cur = nxt;
   }
   if (tid == 0) tc::bulk_wait_all();
   if (!ok && tid == 0) set_status(DVGO_ERR_TIMEOUT);
-  if (bad) set_status(DVGO_ERR_RANGE);
+  if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -417,8 +466,8 @@ __global__ void __launch_bounds__(256) grad_bound_kernel(const float* __restrict
 }
 
 // ----------------------------------------------------------------- backward
-// Same thread layout as the forward (256 threads, two warp halves per TMEM
-// lane quarter, half h on hidden columns 64 h .. + 63).  The upstream colour
+// Same thread layout as the forward (512 threads, four warp quarters per TMEM
+// lane quarter, quarter q on hidden columns 32 q .. 32 q + 31).  The upstream colour
 // gradient of the next tile is loaded in three dependent steps over the
 // current tile, and the next tile's image is copied in as soon as the MMAs
 // that read each part have completed.
@@ -450,7 +499,7 @@ __device__ __forceinline__ void up_l3(UpIn& u, const float* __restrict__ g_rgb,
   for (int c = 0; c < kOut; ++c) u.g[c] = u.ws * __ldg(g_color + 3 * (int64_t)u.r + c);
 }
 
-__global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
+__global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
     const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx, int64_t n_cap,
     const int64_t* __restrict__ n_dev, const float* __restrict__ params, const uint8_t* __restrict__ act,
@@ -458,7 +507,7 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + bEnd);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = warp >> 2, row = (warp & 3) * 32 + lane;
+  const int qw = warp >> 2, row = (warp & 3) * 32 + lane;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
@@ -497,7 +546,7 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
   const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
   const uint8_t* img_g = act + kActHeader;
   uint8_t* img = sm + bImg;
-  float* zx = reinterpret_cast<float*>(sm + bGh);  // [2][128][3] output-layer partials (G is free then)
+  float* zx = reinterpret_cast<float*>(sm + bGh);  // [4][128][3] output-layer partials (G is free then)
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -509,14 +558,14 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
   const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
   const uint32_t sGh = tc::smem_u32(sm + bGh), sGl = tc::smem_u32(sm + bGl);
-  float dW3acc[kOut * 2], db2acc[2], db3acc[kOut];
+  float dW3acc[kOut], db2acc = 0.0f, db3acc[kOut];
 #pragma unroll
-  for (int i = 0; i < kOut * 2; ++i) dW3acc[i] = 0.0f;
-  db2acc[0] = db2acc[1] = 0.0f;
+  for (int i = 0; i < kOut; ++i) dW3acc[i] = 0.0f;
 #pragma unroll
   for (int c = 0; c < kOut; ++c) db3acc[c] = 0.0f;
   uint32_t ph_in = 0, ph_mma = 0;
-  bool ok = true, bad = false, dw_started = false;
+  bool ok = true, dw_started = false;
+  float vmax = 0.0f;   // largest magnitude split (range check)
   bool inflight_h = false, inflight_x = false;   // thread 0: copies not yet waited for
   auto load_h = [&](int64_t tile) {
     tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
@@ -557,17 +606,17 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     if (!ok) break;
     ph_in ^= 1;
     inflight_h = inflight_x = false;
-    // relu mask of layer 1 on this half's columns (H1 > 0 <=> hi > 0)
-    uint32_t m1b[2] = {0u, 0u};
+    // relu mask of layer 1 on this quarter's columns (H1 > 0 <=> hi > 0)
+    uint32_t m1b = 0u;
 #pragma unroll
-    for (int k8 = 0; k8 < 64; k8 += 8) {
-      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(row, 64 * half + k8, kSboH));
+    for (int k8 = 0; k8 < 32; k8 += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(row, 32 * qw + k8, kSboH));
       const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = k8 + 2 * i;
-        if ((int16_t)(wd[i] & 0xffffu) > 0) m1b[k >> 5] |= 1u << (k & 31);
-        if ((int16_t)(wd[i] >> 16) > 0) m1b[(k + 1) >> 5] |= 1u << ((k + 1) & 31);
+        if ((int16_t)(wd[i] & 0xffffu) > 0) m1b |= 1u << k;
+        if ((int16_t)(wd[i] >> 16) > 0) m1b |= 1u << (k + 1);
       }
     }
     if (tid == 0) {   // D2 = H1 W2^T
@@ -581,31 +630,32 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     // output layer: z3 from both halves, g_z3, db3
     {
       float zp[kOut] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
-        const int ch = 2 * half + c2;
+      {
         float v[32];
-        tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+        tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int o = ch * 32 + i;
-          const float h = fmaxf(fmaf(v[i], inv2, fs->b2[o]), 0.0f);
-#pragma unroll
-          for (int c = 0; c < kOut; ++c) zp[c] = fmaf(fs->W3[c * kHid + o], h, zp[c]);
+          const int o = 32 * qw + i;
+          const float4 q = fs->ob[o];
+          const float h = fmaxf(fmaf(v[i], inv2, q.x), 0.0f);
+          zp[0] = fmaf(q.y, h, zp[0]);
+          zp[1] = fmaf(q.z, h, zp[1]);
+          zp[2] = fmaf(q.w, h, zp[2]);
         }
       }
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) zx[(half * kTile + row) * kOut + c] = zp[c];
+      for (int c = 0; c < kOut; ++c) zx[(qw * kTile + row) * kOut + c] = zp[c];
     }
     __syncthreads();
     float gz3[kOut];
 #pragma unroll
     for (int c = 0; c < kOut; ++c) {
-      const float z3 = fs->b3[c] + (zx[row * kOut + c] + zx[(kTile + row) * kOut + c]);
+      const float* zc = zx + row * kOut + c;
+      const float z3 = fs->b3[c] + (((zc[0] + zc[kTile * kOut]) + zc[2 * kTile * kOut]) + zc[3 * kTile * kOut]);
       const float y = sigmoid_f(z3);
       gz3[c] = gup[c] * y * (1.0f - y);
     }
-    if (half == 0) {
+    if (qw == 0) {
 #pragma unroll
       for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
     }
@@ -616,21 +666,24 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
     const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
     const float invX = 1.0f / (sG1 * sW1);           // g_X
-    if (S2 != sG2) rescale_row<64>(img + iHh + half * 128 * 8, img + iHl + half * 128 * 8, row, kSboH, S2 / sG2, bad);
-    if (S1 != sG1) rescale_row<24>(img + iXh + half * 128 * 3, img + iXl + half * 128 * 3, row, kSboX, S1 / sG1, bad);
+    if (S2 != sG2) rescale_row<32>(img + iHh + qw * 128 * 4, img + iHl + qw * 128 * 4, row, kSboH, S2 / sG2, vmax);
+    if (S1 != sG1) {
+      const int fb = x_first_block(qw);
+      if (x_num_blocks(qw) == 2)
+        rescale_row<16>(img + iXh + fb * 128, img + iXl + fb * 128, row, kSboX, S1 / sG1, vmax);
+      else
+        rescale_row<8>(img + iXh + fb * 128, img + iXl + fb * 128, row, kSboX, S1 / sG1, vmax);
+    }
     // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const int ch = 2 * half + c2;
+    {
       float v[32], g[32];
-      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+      tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const int o = ch * 32 + i;
-        const float z2 = fmaf(v[i], inv2, fs->b2[o]);
-        float gs = 0.0f;
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) gs = fmaf(gz3[c], fs->W3[c * kHid + o], gs);
+        const int o = 32 * qw + i;
+        const float4 q = fs->ob[o];
+        const float z2 = fmaf(v[i], inv2, q.x);
+        const float gs = fmaf(gz3[2], q.w, fmaf(gz3[1], q.z, gz3[0] * q.y));
         g[i] = z2 > 0.0f ? gs : 0.0f;
         v[i] = fmaxf(z2, 0.0f);
       }
@@ -638,14 +691,14 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
 #pragma unroll
       for (int i = 0; i < 32; ++i) sg[i] = sG2 * g[i];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, ch * 32 + q * 8, kSboH, sg + 8 * q, bad);
-      db2acc[c2] += reduce_scatter32(g, lane);
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, sg + 8 * q, vmax);
+      db2acc += reduce_scatter32(g, lane);
 #pragma unroll
       for (int c = 0; c < kOut; ++c) {
         float p[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
-        dW3acc[c * 2 + c2] += reduce_scatter32(p, lane);
+        dW3acc[c] += reduce_scatter32(p, lane);
       }
     }
     tc::fence_proxy_async_smem();
@@ -663,15 +716,13 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
     // G1 = g_h1 * (H1 > 0), rescaled to sG1
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const int ch = 2 * half + c2;
+    {
       float v[32];
-      tc::tmem_ld32(lane_base + cTmp + ch * 32, v);
+      tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = ((m1b[c2] >> i) & 1u) ? v[i] * fG1 : 0.0f;
+      for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] * fG1 : 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, ch * 32 + q * 8, kSboH, v + 8 * q, bad);
+      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, v + 8 * q, vmax);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -687,7 +738,7 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     }
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
-    if (half == 0) {
+    if (qw == 0) {
       float gx[16];
       tc::tmem_ld16(lane_base + cTmp, gx);
       if (valid) {
@@ -707,16 +758,12 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_in, kSpin);
     set_status(DVGO_ERR_TIMEOUT);
   }
-  if (bad) set_status(DVGO_ERR_RANGE);
-  // output-layer and b2 partials of this warp (lane l holds column 64 half + 32 c2 + l)
+  if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
+  // output-layer and b2 partials of this warp (lane l holds column 32 q + l)
 #pragma unroll
-  for (int c = 0; c < kOut; ++c)
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2)
-      atomicAdd(g_params + kOffW3 + c * kHid + 64 * half + 32 * c2 + lane, dW3acc[c * 2 + c2]);
-#pragma unroll
-  for (int c2 = 0; c2 < 2; ++c2) atomicAdd(g_params + kOffB2 + 64 * half + 32 * c2 + lane, db2acc[c2]);
-  if (half == 0)
+  for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffW3 + c * kHid + 32 * qw + lane, dW3acc[c]);
+  atomicAdd(g_params + kOffB2 + 32 * qw + lane, db2acc);
+  if (qw == 0)
 #pragma unroll
     for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffB3 + c, db3acc[c]);
   tc::fence_before_sync();
@@ -726,7 +773,7 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
     // dW2 / dW1 rows (TMEM lane = output neuron) through a per-warp 32 x 33
     // shared-memory transpose, so that each reduction instruction covers 32
     // consecutive parameters of one row
-    float* tp = reinterpret_cast<float*>(sm + bGh) + warp * 32 * 33;
+    float* tp = reinterpret_cast<float*>(sm + bImg) + warp * 32 * 33;   // image and G are free
     const float u2 = 1.0f / (S2 * kSH), u1 = 1.0f / (S1 * kSX);
     const int o0 = (warp & 3) * 32;
     auto flush32 = [&](uint32_t col, float scale, int base, int stride, int ncol) {
@@ -739,11 +786,10 @@ __global__ void __launch_bounds__(256, 1) rgbnet_bwd_tc_kernel(
         for (int r = 0; r < 32; ++r) atomicAdd(g_params + base + (o0 + r) * stride + lane, tp[r * 33 + lane]);
       __syncwarp();
     };
-#pragma unroll 1
-    for (int c2 = 0; c2 < 2; ++c2) flush32(cDW2 + 64 * half + 32 * c2, u2, kOffW2 + 64 * half + 32 * c2, kHid, 32);
-    if (half == 0) {
+    flush32(cDW2 + 32 * qw, u2, kOffW2 + 32 * qw, kHid, 32);
+    if (qw == 0) {
       flush32(cDW1, u1, kOffW1, kIn, 32);                       // W1[:, 0:32]
-    } else {
+    } else if (qw == 1) {
       float v[16];
       tc::tmem_ld16(lane_base + cDW1 + 32, v);                  // W1[:, 32:39] and b1 (column 39)
 #pragma unroll
@@ -772,14 +818,14 @@ int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
 int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
                           const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
                           float* rgb, float* act, cudaStream_t st) {
-  const size_t smem = fEnd + sizeof(Side) + kTile * kOut * sizeof(float);
+  const size_t smem = fEnd + sizeof(Side) + 4 * kTile * kOut * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(rgbnet_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_fwd_tc_kernel<<<grid, 256, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
+  rgbnet_fwd_tc_kernel<<<grid, 512, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
                                                 reinterpret_cast<uint8_t*>(act));
   return launch_status();
 }
@@ -798,7 +844,7 @@ int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float*
   grad_bound_kernel<<<grid_for(n_cap, 256, 4), 256, 0, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev,
                                                              reinterpret_cast<unsigned int*>(act));
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_bwd_tc_kernel<<<grid, 256, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
+  rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
                                                 reinterpret_cast<const uint8_t*>(act), g_params, g_k0);
   return launch_status();
 }
