@@ -258,8 +258,9 @@ int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
  * position j; with it (and rgb, the forward's output, may be NULL) the
  * backward reads the hidden activations instead of recomputing them.
  * DVGO_F32_TC: act is the buffer its forward filled for the same list and
- * count (required; rgb ignored); the backward also uses its first 256
- * bytes as scratch.  The BF16 form ignores act and rgb (it recomputes on
+ * count (required; rgb ignored); the backward also writes its header (first
+ * 256 bytes) and the per-CTA partial gradients stored after the tile
+ * images, and sums those partials in a fixed order (deterministic).  The BF16 form ignores act and rgb (it recomputes on
  * the tensor cores). */
 int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                     const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
@@ -267,9 +268,10 @@ int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, co
                     const float* rgb, float* g_params, float* g_k0, void* stream);
 
 /* Bytes of the act buffer dvgo_rgbnet_fwd / _bwd need for n_cap list
- * positions: n_cap * 1024 for DVGO_F32 (optional there), 256 + 90112 per
- * 128-position tile for DVGO_F32_TC, 0 for DVGO_BF16; -1 for a bad
- * precision or n_cap < 0. */
+ * positions: n_cap * 1024 for DVGO_F32 (optional there); for DVGO_F32_TC
+ * 256 + 90112 per 128-position tile + 152 * 22019 * 4 (one partial
+ * parameter gradient per SM); 0 for DVGO_BF16; -1 for a bad precision or
+ * n_cap < 0. */
 int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision);
 
 /* ------------------------------------------------------- learned proposal */

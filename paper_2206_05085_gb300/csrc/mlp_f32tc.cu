@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
     const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx, int64_t n_cap,
     const int64_t* __restrict__ n_dev, const float* __restrict__ params, const uint8_t* __restrict__ act,
-    float* __restrict__ g_params, float* __restrict__ g_k0) {
+    float* __restrict__ part, float* __restrict__ g_k0) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + bEnd);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -759,36 +759,57 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     set_status(DVGO_ERR_TIMEOUT);
   }
   if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
-  // output-layer and b2 partials of this warp (lane l holds column 32 q + l)
+  // This CTA's gradient goes to its own row of the partials array (every
+  // parameter written, no atomics); a second kernel sums the rows in a fixed
+  // order.  Output-layer and b2 sums of the four lane quarters meet in shared
+  // memory first (the G and image buffers are free now).
+  float* pr = reinterpret_cast<float*>(sm + bGh);            // [16 warps][4][32]
+  float* pr3 = pr + 16 * 4 * 32;                             // [4 lane quarters][3]
 #pragma unroll
-  for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffW3 + c * kHid + 32 * qw + lane, dW3acc[c]);
-  atomicAdd(g_params + kOffB2 + 32 * qw + lane, db2acc);
-  if (qw == 0)
+  for (int c = 0; c < kOut; ++c) pr[(warp * 4 + c) * 32 + lane] = dW3acc[c];
+  pr[(warp * 4 + 3) * 32 + lane] = db2acc;
+  if (qw == 0) {
 #pragma unroll
-    for (int c = 0; c < kOut; ++c) atomicAdd(g_params + kOffB3 + c, db3acc[c]);
+    for (int c = 0; c < kOut; ++c) {
+      float v = db3acc[c];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) pr3[(warp & 3) * kOut + c] = v;
+    }
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (ok && (int64_t)blockIdx.x < ntiles) {
+  float* P = part + (size_t)blockIdx.x * kNumParams;
+  const bool has_tiles = (int64_t)blockIdx.x < ntiles;
+  if (has_tiles && (warp & 3) == 0) {   // warp 4 q: W3[:, 32 q + lane] and b2[32 q + lane]
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float v = ((pr[((warp + 0) * 4 + c) * 32 + lane] + pr[((warp + 1) * 4 + c) * 32 + lane]) +
+                       pr[((warp + 2) * 4 + c) * 32 + lane]) + pr[((warp + 3) * 4 + c) * 32 + lane];
+      P[(c < kOut ? kOffW3 + c * kHid : kOffB2) + 32 * qw + lane] = v;
+    }
+  }
+  if (has_tiles && tid < kOut) P[kOffB3 + tid] = ((pr3[tid] + pr3[kOut + tid]) + pr3[2 * kOut + tid]) + pr3[3 * kOut + tid];
+  if (has_tiles) {
     // dW2 / dW1 rows (TMEM lane = output neuron) through a per-warp 32 x 33
-    // shared-memory transpose, so that each reduction instruction covers 32
-    // consecutive parameters of one row
-    float* tp = reinterpret_cast<float*>(sm + bImg) + warp * 32 * 33;   // image and G are free
-    const float u2 = 1.0f / (S2 * kSH), u1 = 1.0f / (S1 * kSX);
+    // shared-memory transpose, so that each store covers 32 consecutive
+    // parameters of one row
+    float* tp = reinterpret_cast<float*>(sm + bImg) + warp * 32 * 33;
+    const float u2 = ok ? 1.0f / (S2 * kSH) : 0.0f, u1 = ok ? 1.0f / (S1 * kSX) : 0.0f;
     const int o0 = (warp & 3) * 32;
-    auto flush32 = [&](uint32_t col, float scale, int base, int stride, int ncol) {
+    auto flush32 = [&](uint32_t col, float scale, int base, int stride) {
       float v[32];
       tc::tmem_ld32(lane_base + col, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i] * scale;
       __syncwarp();
-      if (lane < ncol)
-        for (int r = 0; r < 32; ++r) atomicAdd(g_params + base + (o0 + r) * stride + lane, tp[r * 33 + lane]);
+      for (int r = 0; r < 32; ++r) P[base + (o0 + r) * stride + lane] = tp[r * 33 + lane];
       __syncwarp();
     };
-    flush32(cDW2 + 32 * qw, u2, kOffW2 + 32 * qw, kHid, 32);
+    flush32(cDW2 + 32 * qw, u2, kOffW2 + 32 * qw, kHid);
     if (qw == 0) {
-      flush32(cDW1, u1, kOffW1, kIn, 32);                       // W1[:, 0:32]
+      flush32(cDW1, u1, kOffW1, kIn);                           // W1[:, 0:32]
     } else if (qw == 1) {
       float v[16];
       tc::tmem_ld16(lane_base + cDW1 + 32, v);                  // W1[:, 32:39] and b1 (column 39)
@@ -796,8 +817,8 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       for (int i = 0; i < 8; ++i) tp[lane * 33 + i] = v[i] * u1;
       __syncwarp();
       for (int r = 0; r < 32; ++r) {
-        if (lane < kIn - 32) atomicAdd(g_params + kOffW1 + (o0 + r) * kIn + 32 + lane, tp[r * 33 + lane]);
-        else if (lane == kIn - 32) atomicAdd(g_params + kOffB1 + o0 + r, tp[r * 33 + lane]);
+        if (lane < kIn - 32) P[kOffW1 + (o0 + r) * kIn + 32 + lane] = tp[r * 33 + lane];
+        else if (lane == kIn - 32) P[kOffB1 + o0 + r] = tp[r * 33 + lane];
       }
     }
   }
@@ -807,12 +828,31 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// g_params += sum over the CTAs that had tiles of their partial rows, in CTA order.
+__global__ void __launch_bounds__(256) partials_reduce_kernel(const float* __restrict__ part, int nrows,
+                                                              int64_t n_cap, const int64_t* __restrict__ n_dev,
+                                                              float* __restrict__ g_params) {
+  const int64_t n = mlp_count(n_cap, n_dev);
+  const int rows = (int)std::min<int64_t>(nrows, (n + kTile - 1) / kTile);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kNumParams; p += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int b = 0; b < rows; ++b) acc += part[(size_t)b * kNumParams + p];
+    g_params[p] += acc;
+  }
+}
+
 }  // namespace dvgo
 
 using namespace dvgo;
 
-int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
+// act layout: [256-byte header | one 90112-byte image per 128-position tile |
+// kNumSMs partial gradient rows of kNumParams floats]
+static int64_t act_images_end(int64_t n_cap) {
   return (int64_t)kActHeader + (n_cap + kTile - 1) / kTile * (int64_t)kImage;
+}
+
+int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
+  return act_images_end(n_cap) + (int64_t)kNumSMs * kNumParams * (int64_t)sizeof(float);
 }
 
 int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
@@ -844,8 +884,10 @@ int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float*
   grad_bound_kernel<<<grid_for(n_cap, 256, 4), 256, 0, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev,
                                                              reinterpret_cast<unsigned int*>(act));
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
+  float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(act) + act_images_end(n_cap));
   rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
-                                                reinterpret_cast<const uint8_t*>(act), g_params, g_k0);
+                                                reinterpret_cast<const uint8_t*>(act), part, g_k0);
+  partials_reduce_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
   return launch_status();
 }
 
