@@ -369,11 +369,16 @@ def memory_kernels(res, peaks):
         "dvgo_composite_rgb_fwd#0": SL * 16 + R * 28,
         "dvgo_distortion_fwd#0": SL * 12 + R * 16,
         "dvgo_distortion_bwd#0": SL * 16 + R * 12,
+        # w, rgb, m, ds in per live sample; colour and L_r out per ray
+        "dvgo_composite_distortion_fwd#0": SL * 24 + R * 32,
         # g_w, raw, T, rgb in and g_raw out per live sample, g_raw zeroed past the halt
         "dvgo_composite_bwd#0": SL * 28 + (S - SL) * 4 + R * 24,
+        # w, m (twice), ds, raw, T, rgb in and g_raw out per live sample
+        "dvgo_composite_distortion_bwd#0": SL * 40 + (S - SL) * 4 + R * 24,
         # g, xyz, index per live sample; FP32 gradient read-modify-write per distinct voxel
         "dvgo_sample_grid_bwd#0": SL * (4 + 12 + 4) + Vl * 8,
         "dvgo_sample_grid_bwd#1": SL * (4 * F + 12 + 4) + Vl * 8 * F,
+        "dvgo_sample_grid_bwd2#0": SL * (4 + 4 * F + 12 + 4) + Vl * 8 * (1 + F),
         # sparse TV: the gradient of every entry of a touched brick is read; entries
         # with a non-zero gradient (the distinct voxels the scatter reached) also
         # read their value and write the gradient back

@@ -133,6 +133,16 @@ int dvgo_sample_grid_bwd(const float* g_out, const dvgo_grid_desc* gd, int32_t C
                          const int32_t* idx, int64_t n_cap, const int64_t* n_dev, float* g_grid,
                          uint8_t* touched, void* stream);
 
+/* Both adjoints at once for two grids of the same geometry queried at the
+ * same samples (the density grid, C_a channels, and the feature grid, C_b
+ * channels): each sample's corners are located once.  Same result as the
+ * two dvgo_sample_grid_bwd calls (g_out_a / g_grid_a / touched_a, then
+ * g_out_b / g_grid_b / touched_b). */
+int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g_grid_a, uint8_t* touched_a,
+                          const float* g_out_b, int32_t C_b, float* g_grid_b, uint8_t* touched_b,
+                          const dvgo_grid_desc* gd, const float* xyz, const int32_t* idx,
+                          int64_t n_cap, const int64_t* n_dev, void* stream);
+
 /* ---------------------------------------------------------------- sampler */
 size_t dvgo_sample_rays_workspace_size(int64_t R);
 
@@ -217,6 +227,23 @@ int dvgo_distortion_fwd(const float* w, const float* m, const float* ds, const i
 int dvgo_distortion_bwd(const float* g_L, float g_L_scalar, const float* w, const float* m,
                         const float* ds, const int64_t* ray_off, const int32_t* seg_len, int64_t R,
                         float* g_w, void* stream);
+
+/* The two per-ray forward tails in one pass over each ray's live samples:
+ * dvgo_composite_rgb_fwd (color) and dvgo_distortion_fwd with seg_len =
+ * n_live (L_r), m = sample midpoints, ds = interval lengths. */
+int dvgo_composite_distortion_fwd(const float* w, const float* rgb, const float* m, const float* ds,
+                                  const int64_t* ray_off, const int32_t* n_live, const float* T_end,
+                                  int64_t R, const float bg[3], float* color, float* L_r,
+                                  void* stream);
+
+/* dvgo_composite_bwd (g_rgb not written) with g_w = the distortion gradient
+ * of dvgo_distortion_bwd for the scalar upstream g_L and seg_len = n_live,
+ * formed inside the compositing adjoint's reverse scan (never stored). */
+int dvgo_composite_distortion_bwd(const float* g_color, float g_L, const float* w, const float* raw,
+                                  const float* T, const float* rgb, const float* m, const float* ds,
+                                  const int64_t* ray_off, const int32_t* n_live, int64_t R,
+                                  float shift, float interval, const float bg[3], float* g_raw,
+                                  void* stream);
 
 /* Photometric loss and its gradient: loss_out[0] = mean over R x 3 of
  * (color - target)^2, loss_out[1] = mean_r L_r (0 if L_r is NULL),

@@ -76,6 +76,7 @@ def _declare(L):
         "dvgo_build_mask": ([P, INT, P, F, F, F, P, P], INT),
         "dvgo_sample_grid_fwd": ([P, INT, P, I32, P, P, I64, P, P, P], INT),
         "dvgo_sample_grid_bwd": ([P, P, I32, P, P, I64, P, P, P, P], INT),
+        "dvgo_sample_grid_bwd2": ([P, I32, P, P, P, I32, P, P, P, P, P, I64, P, P], INT),
         "dvgo_sample_rays_workspace_size": ([I64], SZ),
         "dvgo_sample_rays": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P, SZ, P], INT),
         "dvgo_live_samples_workspace_size": ([I64], SZ),
@@ -86,6 +87,8 @@ def _declare(L):
         "dvgo_distortion_fwd": ([P, P, P, P, P, I64, P, P], INT),
         "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
         "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
+        "dvgo_composite_distortion_fwd": ([P, P, P, P, P, P, P, I64, P, P, P, P], INT),
+        "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
         "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
         "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
@@ -117,7 +120,8 @@ def exported_names():
         "dvgo_distortion_bwd", "dvgo_rgb_loss", "dvgo_rgbnet_fwd", "dvgo_rgbnet_bwd",
         "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status", "dvgo_proposal_fwd",
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
-        "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes"]
+        "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
+        "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd"]
 
 
 def ptr(t):
@@ -180,6 +184,13 @@ def sample_grid_bwd(g_out, gd, C, xyz, idx, n_cap, n_dev, g_grid, touched, strea
           ptr(n_dev), ptr(g_grid), ptr(touched), _stream(stream))
 
 
+def sample_grid_bwd2(g_out_a, C_a, g_grid_a, touched_a, g_out_b, C_b, g_grid_b, touched_b, gd, xyz,
+                     idx, n_cap, n_dev, stream=None):
+    _call("dvgo_sample_grid_bwd2", ptr(g_out_a), C_a, ptr(g_grid_a), ptr(touched_a), ptr(g_out_b),
+          C_b, ptr(g_grid_b), ptr(touched_b), ctypes.byref(gd), ptr(xyz), ptr(idx), n_cap,
+          ptr(n_dev), _stream(stream))
+
+
 # -------------------------------------------------------------- sampler
 def sample_rays_workspace_size(R):
     return int(lib().dvgo_sample_rays_workspace_size(R))
@@ -228,6 +239,18 @@ def composite_bwd(g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval
                   g_rgb=None, stream=None):
     _call("dvgo_composite_bwd", ptr(g_color), ptr(g_w), ptr(raw), ptr(T), ptr(rgb), ptr(ray_off),
           ptr(n_live), R, shift, interval, _vec3(bg, F), ptr(g_raw), ptr(g_rgb), _stream(stream))
+
+
+def composite_distortion_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, color, L_r, stream=None):
+    _call("dvgo_composite_distortion_fwd", ptr(w), ptr(rgb), ptr(m), ptr(ds), ptr(ray_off),
+          ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(color), ptr(L_r), _stream(stream))
+
+
+def composite_distortion_bwd(g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift,
+                             interval, bg, g_raw, stream=None):
+    _call("dvgo_composite_distortion_bwd", ptr(g_color), g_L, ptr(w), ptr(raw), ptr(T), ptr(rgb),
+          ptr(m), ptr(ds), ptr(ray_off), ptr(n_live), R, shift, interval, _vec3(bg, F), ptr(g_raw),
+          _stream(stream))
 
 
 def distortion_fwd(w, m, ds, ray_off, seg_len, R, L_r, stream=None):

@@ -214,6 +214,41 @@ __global__ void __launch_bounds__(256) scatter_bwd_kernel(const float* __restric
   }
 }
 
+// Density (1 channel) and feature (12 channels) adjoints in one pass.
+__global__ void __launch_bounds__(256) scatter_bwd_1_12_kernel(
+    const float* __restrict__ g_a, float* __restrict__ grid_a, uint8_t* __restrict__ touched_a,
+    const float* __restrict__ g_b, float* __restrict__ grid_b, uint8_t* __restrict__ touched_b, TriArgs T,
+    const float* __restrict__ xyz, const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* n_dev) {
+  const int64_t n = live_n(n_cap, n_dev);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+    Corners c;
+    corners(T, xyz, s, c);
+    const float ga = __ldg(g_a + s);
+    float gb[12];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(g_b + s * 12) + q);
+      gb[4 * q] = v.x;
+      gb[4 * q + 1] = v.y;
+      gb[4 * q + 2] = v.z;
+      gb[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      atomicAdd(grid_a + c.slot[k], c.w[k] * ga);
+      float4* p = reinterpret_cast<float4*>(grid_b + c.slot[k] * 12);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        atomicAdd(p + q, make_float4(c.w[k] * gb[4 * q], c.w[k] * gb[4 * q + 1], c.w[k] * gb[4 * q + 2],
+                                     c.w[k] * gb[4 * q + 3]));
+    }
+    mark_touched(touched_a, T, c);
+    mark_touched(touched_b, T, c);
+  }
+}
+
 __global__ void scatter_bwd_generic_kernel(const float* __restrict__ g_out, TriArgs T, int C,
                                            const float* __restrict__ xyz,
                                            const int32_t* __restrict__ idx, int64_t n_cap,
@@ -609,4 +644,25 @@ extern "C" int dvgo_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, 
     adam_flat_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(p, p_shadow, g, m, v, n, a, zero_grad);
   }
   return launch_status();
+}
+
+extern "C" int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g_grid_a,
+                                     uint8_t* touched_a, const float* g_out_b, int32_t C_b,
+                                     float* g_grid_b, uint8_t* touched_b, const dvgo_grid_desc* gd,
+                                     const float* xyz, const int32_t* idx, int64_t n_cap,
+                                     const int64_t* n_dev, void* stream) {
+  DVGO_CHECK_ARG(gd && C_a >= 1 && C_b >= 1 && n_cap >= 0);
+  if (n_cap == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(g_out_a && g_grid_a && g_out_b && g_grid_b && xyz);
+  if (C_a == 1 && C_b == 12 && (uintptr_t)g_out_b % 16 == 0 && (uintptr_t)g_grid_b % 16 == 0) {
+    TriArgs T;
+    DVGO_CHECK_ARG(make_tri(T, gd));
+    cudaStream_t st = as_stream(stream);
+    scatter_bwd_1_12_kernel<<<grid_for(n_cap, 256, 16), 256, 0, st>>>(
+        g_out_a, g_grid_a, touched_a, g_out_b, g_grid_b, touched_b, T, xyz, idx, n_cap, n_dev);
+    return launch_status();
+  }
+  int r = dvgo_sample_grid_bwd(g_out_a, gd, C_a, xyz, idx, n_cap, n_dev, g_grid_a, touched_a, stream);
+  if (r != DVGO_OK) return r;
+  return dvgo_sample_grid_bwd(g_out_b, gd, C_b, xyz, idx, n_cap, n_dev, g_grid_b, touched_b, stream);
 }

@@ -253,6 +253,154 @@ __global__ void __launch_bounds__(256) distortion_bwd_kernel(
   }
 }
 
+// ------------------------------------------------ fused per-ray tails
+// Colour accumulation and the distortion loss of the live samples in one pass
+// over each ray (both read w; same arithmetic as the two kernels above).
+__global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
+    const float* __restrict__ w, const float* __restrict__ rgb, const float* __restrict__ m,
+    const float* __restrict__ ds, const int64_t* __restrict__ ray_off, const int32_t* __restrict__ n_live,
+    const float* __restrict__ T_end, int64_t R, float bg0, float bg1, float bg2,
+    float* __restrict__ color, float* __restrict__ L_r) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, n_live, r, b, n, N);
+    const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, acc = 0.0f;
+    Kahan cW, cWM;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < n;
+      float wi = 0.0f, mi = 0.0f, di = 0.0f;
+      if (valid) {
+        const int64_t s = b + i;
+        wi = __ldg(w + s);
+        mi = __ldg(m + s) - m0;
+        di = __ldg(ds + s);
+        a0 += wi * __ldg(rgb + 3 * s);
+        a1 += wi * __ldg(rgb + 3 * s + 1);
+        a2 += wi * __ldg(rgb + 3 * s + 2);
+      }
+      const float iw = warp_incl_sum(wi);
+      const float iwm = warp_incl_sum(wi * mi);
+      const float Wlt = __fadd_rn(cW.s, __fsub_rn(iw - wi, cW.c));
+      const float WMlt = __fadd_rn(cWM.s, __fsub_rn(iwm - wi * mi, cWM.c));
+      acc += 2.0f * wi * (mi * Wlt - WMlt) + wi * wi * di * (1.0f / 3.0f);
+      cW.add(__shfl_sync(0xffffffffu, iw, 31));
+      cWM.add(__shfl_sync(0xffffffffu, iwm, 31));
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const float te = T_end[r];
+      color[3 * r] = a0 + te * bg0;
+      color[3 * r + 1] = a1 + te * bg1;
+      color[3 * r + 2] = a2 + te * bg2;
+      L_r[r] = acc;
+    }
+  }
+}
+
+// Compositing adjoint with the distortion gradient formed in place: one
+// forward pass for the ray's totals W and WM, then chunks from the last to the
+// first: Kahan-compensated suffix sums W_{>i}, WM_{>i} give g_w_i (W_{<i} =
+// W - W_{>i} - w_i), which enters the reverse affine scan of the colour
+// adjoint directly (g_w is never stored).
+__global__ void __launch_bounds__(256) composite_distortion_bwd_kernel(
+    const float* __restrict__ g_color, float g_L, const float* __restrict__ w,
+    const float* __restrict__ raw, const float* __restrict__ T, const float* __restrict__ rgb,
+    const float* __restrict__ m, const float* __restrict__ ds, const int64_t* __restrict__ ray_off,
+    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval, float bg0, float bg1,
+    float bg2, float* __restrict__ g_raw) {
+  DVGO_WARP_LOOP(R) {
+    int64_t b;
+    int n, N;
+    ray_range(ray_off, n_live, r, b, n, N);
+    const float gc0 = __ldg(g_color + 3 * r), gc1 = __ldg(g_color + 3 * r + 1),
+                gc2 = __ldg(g_color + 3 * r + 2);
+    const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+    Kahan tW, tWM;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const float wi = i < n ? __ldg(w + b + i) : 0.0f;
+      const float mi = i < n ? __ldg(m + b + i) - m0 : 0.0f;
+      tW.add(warp_sum(wi));
+      tWM.add(warp_sum(wi * mi));
+    }
+    const float Wt = __fsub_rn(tW.s, tW.c), WMt = __fsub_rn(tWM.s, tWM.c);
+    Kahan sW, sWM;                                     // sums over the chunks after the current one
+    float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;   // R_{n-1} = g_T
+    const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
+    for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
+      const int k = c0 + lane;
+      const bool valid = k < n;
+      float wi = 0.0f, mi = 0.0f, di = 0.0f, rk = 0.0f, Tk = 0.0f, la = 0.0f;
+      float c_rgb = 0.0f;
+      if (valid) {
+        const int64_t s = b + k;
+        wi = __ldg(w + s);
+        mi = __ldg(m + s) - m0;
+        di = __ldg(ds + s);
+        rk = __ldg(raw + s);
+        Tk = __ldg(T + s);
+        c_rgb = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
+      }
+      // inclusive suffix sums within the chunk (lane .. 31)
+      float sw = wi, swm = wi * mi;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float a = __shfl_down_sync(0xffffffffu, sw, o);
+        const float c = __shfl_down_sync(0xffffffffu, swm, o);
+        if (lane + o < 32) {
+          sw += a;
+          swm += c;
+        }
+      }
+      const float Wgt = __fadd_rn(sW.s, __fsub_rn(sw - wi, sW.c));
+      const float WMgt = __fadd_rn(sWM.s, __fsub_rn(swm - wi * mi, sWM.c));
+      const float Wlt = Wt - Wgt - wi;
+      const float WMlt = WMt - WMgt - wi * mi;
+      const float gw = g_L * (2.0f * (mi * (Wlt - Wgt) - WMlt + WMgt) + (2.0f / 3.0f) * wi * di);
+      float A = 1.0f, B = 0.0f, gk = 0.0f;
+      if (valid) {
+        la = -interval * softplus_f(rk + shift);
+        const float al = -expm1f(la);
+        gk = c_rgb + gw;
+        A = 1.0f - al;
+        B = gk * al;
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float A2 = __shfl_down_sync(0xffffffffu, A, o);
+        const float B2 = __shfl_down_sync(0xffffffffu, B, o);
+        if (lane + o < 32) {
+          B = A * B2 + B;
+          A = A * A2;
+        }
+      }
+      float An = __shfl_down_sync(0xffffffffu, A, 1);
+      float Bn = __shfl_down_sync(0xffffffffu, B, 1);
+      if (lane == 31) {
+        An = 1.0f;
+        Bn = 0.0f;
+      }
+      const float Rk = An * carry + Bn;
+      if (valid) {
+        const float Tk1 = Tk * expf(la);
+        g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
+      }
+      const float A0 = __shfl_sync(0xffffffffu, A, 0);
+      const float B0 = __shfl_sync(0xffffffffu, B, 0);
+      carry = A0 * carry + B0;
+      sW.add(__shfl_sync(0xffffffffu, sw, 0));
+      sWM.add(__shfl_sync(0xffffffffu, swm, 0));
+    }
+    for (int k = n + lane; k < N; k += 32) g_raw[b + k] = 0.0f;
+  }
+}
+
 // ------------------------------------------------------------------ loss
 __global__ void __launch_bounds__(1024) rgb_loss_kernel(const float* __restrict__ color,
                                                         const float* __restrict__ target,
@@ -263,13 +411,35 @@ __global__ void __launch_bounds__(1024) rgb_loss_kernel(const float* __restrict_
   __shared__ float s1[32], s2[32];
   float a = 0.0f, d = 0.0f;
   const float gscale = 2.0f / (3.0f * (float)R);
-  for (int64_t i = threadIdx.x; i < 3 * R; i += blockDim.x) {
-    const float e = color[i] - target[i];
-    a += e * e;
-    g_color[i] = gscale * e;
+  // eight independent loads in flight per thread and step
+  constexpr int U = 8;
+  for (int64_t i0 = threadIdx.x; i0 < 3 * R; i0 += U * (int64_t)blockDim.x) {
+    float c[U], t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * (int64_t)blockDim.x;
+      c[u] = i < 3 * R ? __ldg(color + i) : 0.0f;
+      t[u] = i < 3 * R ? __ldg(target + i) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * (int64_t)blockDim.x;
+      const float e = c[u] - t[u];
+      a += e * e;
+      if (i < 3 * R) g_color[i] = gscale * e;
+    }
   }
   if (L_r)
-    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) d += L_r[i];
+    for (int64_t i0 = threadIdx.x; i0 < R; i0 += U * (int64_t)blockDim.x) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * (int64_t)blockDim.x;
+        v[u] = i < R ? __ldg(L_r + i) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) d += v[u];
+    }
   a = warp_sum(a);
   d = warp_sum(d);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -363,5 +533,33 @@ extern "C" int dvgo_rgb_loss(const float* color, const float* target, const floa
   DVGO_CHECK_ARG(R > 0 && color && target && loss_out && g_color);
   rgb_loss_kernel<<<1, 1024, 0, as_stream(stream)>>>(color, target, L_r, R, lambda_dist, loss_out,
                                                      g_color);
+  return launch_status();
+}
+
+extern "C" int dvgo_composite_distortion_fwd(const float* w, const float* rgb, const float* m,
+                                             const float* ds, const int64_t* ray_off,
+                                             const int32_t* n_live, const float* T_end, int64_t R,
+                                             const float bg[3], float* color, float* L_r,
+                                             void* stream) {
+  DVGO_CHECK_ARG(R >= 0);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(w && rgb && m && ds && ray_off && T_end && bg && color && L_r);
+  composite_distortion_fwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r);
+  return launch_status();
+}
+
+extern "C" int dvgo_composite_distortion_bwd(const float* g_color, float g_L, const float* w,
+                                             const float* raw, const float* T, const float* rgb,
+                                             const float* m, const float* ds,
+                                             const int64_t* ray_off, const int32_t* n_live,
+                                             int64_t R, float shift, float interval,
+                                             const float bg[3], float* g_raw, void* stream) {
+  DVGO_CHECK_ARG(R >= 0 && interval > 0.0f);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(g_color && w && raw && T && rgb && m && ds && ray_off && n_live && bg && g_raw);
+  composite_distortion_bwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift, interval, bg[0], bg[1], bg[2],
+      g_raw);
   return launch_status();
 }

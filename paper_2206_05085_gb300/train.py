@@ -128,7 +128,6 @@ class Trainer:
         self.L_r = torch.empty(R, **f32)
         self.loss = torch.zeros(3, **f32)
         self.g_color = torch.empty(R, 3, **f32)
-        self.g_w = torch.empty(S, **f32)
         self.g_raw = torch.empty(S, **f32)
         self.g_k0 = torch.empty(S, FEAT, **f32)
         # FP32 forms: what the colour-MLP forward saves for its backward (hidden
@@ -164,25 +163,25 @@ class Trainer:
                           self.k0)
         L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
                      self.precision, self.rgb, self.act)
-        L.composite_rgb_fwd(self.w, self.rgb, self.ray_off, self.n_live, self.T_end, R, rp.bg,
-                            self.color)
-        L.distortion_fwd(self.w, self.s_mid, self.s_len, self.ray_off, self.n_live, R, self.L_r)
+        # colour accumulation and distortion loss in one pass over each ray
+        L.composite_distortion_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
+                                   self.n_live, self.T_end, R, rp.bg, self.color, self.L_r)
         L.rgb_loss(self.color, target, self.L_r, R, rp.lambda_dist, self.loss, self.g_color)
 
     # -------------------------------------------------------------- backward
     def backward(self, rays_d):
         rp, R, S = self.rp, self.R, self.S_cap
-        L.distortion_bwd(None, rp.lambda_dist / R, self.w, self.s_mid, self.s_len, self.ray_off,
-                         self.n_live, R, self.g_w)
-        L.composite_bwd(self.g_color, self.g_w, self.raw, self.T, self.rgb, self.ray_off,
-                        self.n_live, R, self.shift, rp.interval, rp.bg, self.g_raw)
+        # compositing adjoint with the distortion gradient formed inside its reverse scan
+        L.composite_distortion_bwd(self.g_color, rp.lambda_dist / R, self.w, self.raw, self.T,
+                                   self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live, R,
+                                   self.shift, rp.interval, rp.bg, self.g_raw)
         L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.live_idx, S,
                      self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
                      self.act, self.rgb)
-        L.sample_grid_bwd(self.g_raw, self.gd, 1, self.xyz, self.live_idx, S, self.live_count,
-                          self.density.g, self.density.touched)
-        L.sample_grid_bwd(self.g_k0, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,
-                          self.feature.g, self.feature.touched)
+        # both grid adjoints in one pass over the live samples
+        L.sample_grid_bwd2(self.g_raw, 1, self.density.g, self.density.touched, self.g_k0, FEAT,
+                           self.feature.g, self.feature.touched, self.gd, self.xyz, self.live_idx, S,
+                           self.live_count)
 
     # ----------------------------------------------------------- optimizer
     def regularize_and_step(self, tv_dense: bool):

@@ -143,6 +143,36 @@ def test_trilinear_adjoint_along_rays(L, C):
     assert np.all(got_t[tb])
 
 
+def test_trilinear_adjoint_pair(L):
+    """The paired density / feature adjoint equals the two single ones."""
+    rng = np.random.default_rng(44)
+    G = (30, 27, 33)
+    lo, hi = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0])
+    n = 20000
+    xyz = rng.uniform(-1.02, 1.02, (n, 3)).astype(np.float32)
+    live = np.sort(rng.choice(n, 15000, replace=False)).astype(np.int32)
+    ga = rng.normal(size=(n, 1)).astype(np.float32)
+    gb = rng.normal(size=(n, 12)).astype(np.float32)
+    gd = L.GridDesc.make(lo, hi, G)
+    nb = L.grid_num_bricks(G)
+    outs = []
+    for C in (1, 12):
+        outs.append((torch.zeros(L.grid_bricked_elems(G, C), device="cuda"),
+                     torch.zeros(nb, dtype=torch.uint8, device="cuda")))
+    n_dev = torch.tensor([len(live)], dtype=torch.int64, device="cuda")
+    L.sample_grid_bwd2(dev(ga), 1, outs[0][0], outs[0][1], dev(gb), 12, outs[1][0], outs[1][1], gd,
+                       dev(xyz), dev(live), n, n_dev)
+    for (g_grid, touched), C, g in zip(outs, (1, 12), (ga, gb)):
+        gg = torch.empty(G[2], G[1], G[0], C, device="cuda")
+        L.grid_unpack(g_grid, gg, G, C, L.F32)
+        ref = oracle.trilinear_adjoint(g[live], (G[2], G[1], G[0], C), lo, hi, xyz[live])
+        assert rel_err(host(gg), ref) < TOL32
+        one = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        g1 = torch.zeros(L.grid_bricked_elems(G, C), device="cuda")
+        L.sample_grid_bwd(dev(g), gd, C, dev(xyz), dev(live), n, n_dev, g1, one)
+        assert np.array_equal(host(touched), host(one))
+
+
 def test_build_mask_bit_exact(L):
     cfg = synth.CFG2
     D = synth.density_grid(cfg)
@@ -287,6 +317,42 @@ def test_composite_backward(L):
         gr, gc = oracle.composite_bwd(raw, rgb, off, sh, 0.5, T_stop, bg, g_color, g_w)
         assert rel_err(host(g_raw), gr) < TOL32
         assert rel_err(host(g_rgb), gc) < TOL32
+
+
+def test_composite_distortion_fused(L):
+    """The fused per-ray tails equal compositing + distortion (forward) and the
+    compositing adjoint fed with the distortion gradient (backward)."""
+    off, raw, rgb = _ragged_case(2, COUNTS, scale=2.0, bias=7.0)
+    R, S = len(off) - 1, int(off[-1])
+    bg = np.array([0.2, 0.9, 0.4], np.float32)
+    sh = shift32()
+    rng = np.random.default_rng(31)
+    m = np.zeros(S, np.float32)
+    for r in range(R):
+        m[off[r]:off[r + 1]] = np.sort(rng.uniform(2, 6, off[r + 1] - off[r]))
+    ds = rng.uniform(0.001, 0.01, S).astype(np.float32)
+    g_color = rng.normal(size=(R, 3)).astype(np.float32)
+    gL = 0.37
+    for T_stop in (1e-3, 0.0):
+        w, T = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+        n_live = torch.empty(R, dtype=torch.int32, device="cuda")
+        T_end = torch.empty(R, device="cuda")
+        L.alpha_weights_fwd(dev(raw), dev(off), R, sh, 0.5, T_stop, w, T, n_live, T_end)
+        ref = oracle.composite(raw, rgb, off, sh, 0.5, T_stop, bg)
+        assert np.array_equal(host(n_live), ref["n_live"])
+        color = torch.empty(R, 3, device="cuda")
+        L_r = torch.empty(R, device="cuda")
+        L.composite_distortion_fwd(w, dev(rgb), dev(m), dev(ds), dev(off), n_live, T_end, R, bg,
+                                   color, L_r)
+        assert rel_err(host(color), ref["color"]) < TOL32
+        L_ref = oracle.distortion(ref["w"], m, ds, off, ref["n_live"])
+        assert rel_err(host(L_r), L_ref) < TOL32
+        g_raw = torch.full((S,), 5.0, device="cuda")
+        L.composite_distortion_bwd(dev(g_color), gL, w, dev(raw), T, dev(rgb), dev(m), dev(ds),
+                                   dev(off), n_live, R, sh, 0.5, bg, g_raw)
+        g_w = oracle.distortion_grad(gL, ref["w"], m, ds, off, ref["n_live"])
+        gr, _ = oracle.composite_bwd(raw, rgb, off, sh, 0.5, T_stop, bg, g_color, g_w)
+        assert rel_err(host(g_raw), gr) < TOL32
 
 
 def test_distortion(L):
