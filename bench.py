@@ -388,6 +388,9 @@ def memory_kernels(res, peaks):
         # p, m, v, g (and the BF16 shadow) out
         "dvgo_adam_step#0": ent_d * 4 + Vl * (28 + sh),
         "dvgo_adam_step#1": ent_f * 4 + Vl * F * (28 + sh),
+        # both grids in one launch (the colour MLP's 22019 entries ride along: 32 B each)
+        "dvgo_tv_add_grad_multi#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (e + 4),
+        "dvgo_adam_step_multi#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (28 + sh) + 22019 * 32,
     }
     peak = peaks.get("hbm_gbs", 6701.5)
     out = {}

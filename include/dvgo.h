@@ -341,14 +341,30 @@ int dvgo_compact_samples(const int32_t* sel, const int32_t* n_sel, int32_t n_dra
 /* ------------------------------------------------------------ regularisers */
 /* TV gradient (Sec. 2, "Efficient total variation (TV) loss"), added into
  * g_grid without a forward pass: for each grid point v and channel c,
- * g += weight * 2/(N C) sum_{u in 6-nbr(v)} clamp(g[v,c] - g[u,c], -delta,
- * delta), N = number of grid points.  dense_mode != 0: every entry;
+ * g += weight * 2/(N C) sum_{u in 6-nbr(v)} clamp(grid[v,c] - grid[u,c],
+ * -delta, delta), N = number of grid points.  dense_mode != 0: every entry;
  * otherwise only entries whose incoming gradient is nonzero, and only in
  * bricks flagged in touched (uint8 per brick, may be NULL = all bricks).  In
  * dense mode every flag of touched (if given) is set to 1.  grid and g_grid
  * are bricked; grid dtype F32 or BF16, g_grid f32. */
 int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3], int32_t C, float weight,
                      float delta, int dense_mode, uint8_t* touched, float* g_grid, void* stream);
+
+/* Several grids of the same shape G in one launch (the density and the
+ * feature grid of a step): grid i behaves as dvgo_tv_add_grad(grids[i].grid,
+ * grids[i].dtype, G, grids[i].C, grids[i].weight, delta, dense_mode,
+ * grids[i].touched, grids[i].g_grid).  count <= 4; grids is a host array. */
+typedef struct {
+  const void* grid;
+  int32_t dtype;
+  int32_t C;
+  float weight;
+  uint8_t* touched;
+  float* g_grid;
+} dvgo_tv_grid;
+
+int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, const int32_t G[3], float delta,
+                           int dense_mode, void* stream);
 
 /* ------------------------------------------------------------------ Adam */
 /* Fused Adam (Sec. 3 "Re-implement Adam optimizer"): for each entry with a
@@ -361,6 +377,26 @@ int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3], int32_t C,
 int dvgo_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v, int64_t n,
                    uint8_t* touched, int64_t block_elems, float lr, float beta1, float beta2,
                    float eps, int64_t step, int zero_grad, void* stream);
+
+/* Several parameter arrays in one launch (density grid, feature grid, colour
+ * MLP): params[i] behaves as dvgo_adam_step(params[i].p, .p_shadow, .g, .m,
+ * .v, .n, .touched, .block_elems, .lr, beta1, beta2, eps, step, zero_grad).
+ * count <= 4; params is a host array; p, g, m, v 16-byte aligned (p_shadow
+ * 8-byte aligned) and, with touched, block_elems a multiple of 4. */
+typedef struct {
+  float* p;
+  uint16_t* p_shadow;
+  float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  uint8_t* touched;
+  int64_t block_elems;
+  float lr;
+} dvgo_adam_param;
+
+int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,
+                         float eps, int64_t step, int zero_grad, void* stream);
 
 /* Reads and clears the device status word that kernels with bounded waits
  * set (DVGO_ERR_TIMEOUT) instead of hanging.  Synchronises the stream. */

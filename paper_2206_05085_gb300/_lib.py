@@ -47,6 +47,16 @@ class SamplerDesc(ctypes.Structure):
                 ("step_c", F)]
 
 
+class TvGrid(ctypes.Structure):
+    _fields_ = [("grid", P), ("dtype", I32), ("C", I32), ("weight", F), ("touched", P),
+                ("g_grid", P)]
+
+
+class AdamParam(ctypes.Structure):
+    _fields_ = [("p", P), ("p_shadow", P), ("g", P), ("m", P), ("v", P), ("n", I64),
+                ("touched", P), ("block_elems", I64), ("lr", F)]
+
+
 class DvgoError(RuntimeError):
     pass
 
@@ -94,6 +104,8 @@ def _declare(L):
         "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
         "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
         "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
+        "dvgo_tv_add_grad_multi": ([P, I32, P, F, INT, P], INT),
+        "dvgo_adam_step_multi": ([P, I32, F, F, F, I64, INT, P], INT),
         "dvgo_device_status": ([P], INT),
         "dvgo_proposal_fwd": ([P, P, I64, P, P, P, P], INT),
         "dvgo_proposal_bwd": ([P, P, P, I64, P, P, P, P], INT),
@@ -121,7 +133,8 @@ def exported_names():
         "dvgo_tv_add_grad", "dvgo_adam_step", "dvgo_device_status", "dvgo_proposal_fwd",
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
-        "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd"]
+        "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
+        "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi"]
 
 
 def ptr(t):
@@ -290,6 +303,23 @@ def rgbnet_bwd(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
 def tv_add_grad(grid, dtype, G, C, weight, delta, dense_mode, touched, g_grid, stream=None):
     _call("dvgo_tv_add_grad", ptr(grid), dtype, _vec3(G, I32), C, weight, delta, int(dense_mode),
           ptr(touched), ptr(g_grid), _stream(stream))
+
+
+def tv_add_grad_multi(grids, G, delta, dense_mode, stream=None):
+    """grids: list of (grid, dtype, C, weight, touched, g_grid)."""
+    arr = (TvGrid * len(grids))(*[TvGrid(ptr(g), dt, C, w, ptr(t), ptr(gg))
+                                  for g, dt, C, w, t, gg in grids])
+    _call("dvgo_tv_add_grad_multi", arr, len(grids), _vec3(G, I32), delta, int(dense_mode),
+          _stream(stream))
+
+
+def adam_step_multi(params, beta1, beta2, eps, step, zero_grad, stream=None):
+    """params: list of (p, p_shadow, g, m, v, n, touched, block_elems, lr)."""
+    arr = (AdamParam * len(params))(*[AdamParam(ptr(p), ptr(sh), ptr(g), ptr(m), ptr(v), n, ptr(t),
+                                                be, lr)
+                                      for p, sh, g, m, v, n, t, be, lr in params])
+    _call("dvgo_adam_step_multi", arr, len(params), beta1, beta2, eps, step, int(zero_grad),
+          _stream(stream))
 
 
 def adam_step(p, p_shadow, g, m, v, n, touched, block_elems, lr, beta1, beta2, eps, step,

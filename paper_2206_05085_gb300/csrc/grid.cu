@@ -336,73 +336,101 @@ __device__ __forceinline__ float load_val(const void* grid, int64_t e) {
                : __ldg(reinterpret_cast<const float*>(grid) + e);
 }
 
+// TV gradient of one voxel (thread t of brick b) of one grid.
 template <bool kBF16>
-__global__ void __launch_bounds__(512) tv_kernel(const void* __restrict__ grid, BrickGeom g, int C,
-                                                 float scale, float delta, int dense_mode,
-                                                 uint8_t* __restrict__ touched,
-                                                 float* __restrict__ g_grid) {
+__device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const BrickGeom& g, int C,
+                                         float scale, float delta, int dense_mode,
+                                         float* __restrict__ g_grid, int64_t b, int t, int x, int y,
+                                         int z) {
+  const int64_t self = b * kBrickVox + t;
+  int64_t nbr[6];
+  bool has[6];
+  has[0] = x > 0;
+  has[1] = x + 1 < g.G[0];
+  has[2] = y > 0;
+  has[3] = y + 1 < g.G[1];
+  has[4] = z > 0;
+  has[5] = z + 1 < g.G[2];
+  nbr[0] = has[0] ? voxel_slot(g, x - 1, y, z) : self;
+  nbr[1] = has[1] ? voxel_slot(g, x + 1, y, z) : self;
+  nbr[2] = has[2] ? voxel_slot(g, x, y - 1, z) : self;
+  nbr[3] = has[3] ? voxel_slot(g, x, y + 1, z) : self;
+  nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
+  nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
+  if (C % 4 == 0) {
+    for (int q = 0; q < C / 4; ++q) {
+      float4* gp = reinterpret_cast<float4*>(g_grid + self * C) + q;
+      const float4 gin = *gp;
+      const bool any = gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
+      if (!dense_mode && !any) continue;
+      float v[4], acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      load_vox4<kBF16>(grid, self, C, q, v);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        if (!has[d]) continue;
+        float u[4];
+        load_vox4<kBF16>(grid, nbr[d], C, q, u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += fminf(fmaxf(v[i] - u[i], -delta), delta);
+      }
+      float4 out = gin;
+      // sparse mode adds the TV gradient only where the data gradient is non-zero
+      if (dense_mode || gin.x != 0.0f) out.x = gin.x + scale * acc[0];
+      if (dense_mode || gin.y != 0.0f) out.y = gin.y + scale * acc[1];
+      if (dense_mode || gin.z != 0.0f) out.z = gin.z + scale * acc[2];
+      if (dense_mode || gin.w != 0.0f) out.w = gin.w + scale * acc[3];
+      *gp = out;
+    }
+  } else {
+    for (int c = 0; c < C; ++c) {
+      float* gp = g_grid + self * C + c;
+      const float gin = *gp;
+      if (!dense_mode && gin == 0.0f) continue;
+      const float v = load_val<kBF16>(grid, self * C + c);
+      float acc = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 6; ++d)
+        if (has[d]) acc += fminf(fmaxf(v - load_val<kBF16>(grid, nbr[d] * C + c), -delta), delta);
+      *gp = gin + scale * acc;
+    }
+  }
+}
+
+constexpr int kMaxMulti = 4;
+
+struct TvGridArgs {
+  const void* grid;
+  float* g_grid;
+  uint8_t* touched;
+  float scale;
+  int C;
+  int bf16;
+};
+struct TvMulti {
+  TvGridArgs a[kMaxMulti];
+  int count;
+};
+
+// One block per brick of all grids (they share the geometry).
+__global__ void __launch_bounds__(512) tv_kernel(TvMulti M, BrickGeom g, float delta, int dense_mode) {
   const int64_t nb = g.num_bricks();
   const int t = threadIdx.x;
   const int lx = compact3(t), ly = compact3(t >> 1), lz = compact3(t >> 2);
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    if (!dense_mode && touched && touched[b] == 0) continue;
-    if (dense_mode && touched && t == 0) touched[b] = 1;
     const int bx = (int)(b % g.nb[0]);
     const int by = (int)((b / g.nb[0]) % g.nb[1]);
     const int bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
     const int x = bx * 8 + lx, y = by * 8 + ly, z = bz * 8 + lz;
-    if (x >= g.G[0] || y >= g.G[1] || z >= g.G[2]) continue;
-    const int64_t self = b * kBrickVox + t;
-    int64_t nbr[6];
-    bool has[6];
-    has[0] = x > 0;
-    has[1] = x + 1 < g.G[0];
-    has[2] = y > 0;
-    has[3] = y + 1 < g.G[1];
-    has[4] = z > 0;
-    has[5] = z + 1 < g.G[2];
-    nbr[0] = has[0] ? voxel_slot(g, x - 1, y, z) : self;
-    nbr[1] = has[1] ? voxel_slot(g, x + 1, y, z) : self;
-    nbr[2] = has[2] ? voxel_slot(g, x, y - 1, z) : self;
-    nbr[3] = has[3] ? voxel_slot(g, x, y + 1, z) : self;
-    nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
-    nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
-    if (C % 4 == 0) {
-      for (int q = 0; q < C / 4; ++q) {
-        float4* gp = reinterpret_cast<float4*>(g_grid + self * C) + q;
-        const float4 gin = *gp;
-        const bool any = gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
-        if (!dense_mode && !any) continue;
-        float v[4], acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        load_vox4<kBF16>(grid, self, C, q, v);
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-          if (!has[d]) continue;
-          float u[4];
-          load_vox4<kBF16>(grid, nbr[d], C, q, u);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) acc[i] += fminf(fmaxf(v[i] - u[i], -delta), delta);
-        }
-        float4 out = gin;
-        // sparse mode adds the TV gradient only where the data gradient is non-zero
-        if (dense_mode || gin.x != 0.0f) out.x = gin.x + scale * acc[0];
-        if (dense_mode || gin.y != 0.0f) out.y = gin.y + scale * acc[1];
-        if (dense_mode || gin.z != 0.0f) out.z = gin.z + scale * acc[2];
-        if (dense_mode || gin.w != 0.0f) out.w = gin.w + scale * acc[3];
-        *gp = out;
-      }
-    } else {
-      for (int c = 0; c < C; ++c) {
-        float* gp = g_grid + self * C + c;
-        const float gin = *gp;
-        if (!dense_mode && gin == 0.0f) continue;
-        const float v = load_val<kBF16>(grid, self * C + c);
-        float acc = 0.0f;
-#pragma unroll
-        for (int d = 0; d < 6; ++d)
-          if (has[d]) acc += fminf(fmaxf(v - load_val<kBF16>(grid, nbr[d] * C + c), -delta), delta);
-        *gp = gin + scale * acc;
-      }
+    const bool inside = x < g.G[0] && y < g.G[1] && z < g.G[2];
+    for (int i = 0; i < M.count; ++i) {
+      const TvGridArgs& A = M.a[i];
+      if (!dense_mode && A.touched && A.touched[b] == 0) continue;
+      if (dense_mode && A.touched && t == 0) A.touched[b] = 1;
+      if (!inside) continue;
+      if (A.bf16)
+        tv_voxel<true>(A.grid, g, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, x, y, z);
+      else
+        tv_voxel<false>(A.grid, g, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, x, y, z);
     }
   }
 }
@@ -421,7 +449,45 @@ __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v,
   changed = true;
 }
 
-// One block per flagged block of entries (bricks of grids), float4 body.
+// Adam over entries [base, end) of one array, float4 body (base a multiple of 4).
+__device__ __forceinline__ void adam_range(float* __restrict__ p, uint16_t* __restrict__ shadow,
+                                           float* __restrict__ g, float* __restrict__ m,
+                                           float* __restrict__ v, int64_t base, int64_t end,
+                                           const AdamArgs& a, int zero_grad) {
+  for (int64_t i = base + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
+    if (i + 4 <= end) {
+      float4 gg = *reinterpret_cast<float4*>(g + i);
+      if (gg.x == 0.0f && gg.y == 0.0f && gg.z == 0.0f && gg.w == 0.0f) continue;
+      float4 pp = *reinterpret_cast<float4*>(p + i);
+      float4 mm = *reinterpret_cast<float4*>(m + i);
+      float4 vv = *reinterpret_cast<float4*>(v + i);
+      bool ch = false;
+      adam_one(pp.x, gg.x, mm.x, vv.x, a, ch);
+      adam_one(pp.y, gg.y, mm.y, vv.y, a, ch);
+      adam_one(pp.z, gg.z, mm.z, vv.z, a, ch);
+      adam_one(pp.w, gg.w, mm.w, vv.w, a, ch);
+      *reinterpret_cast<float4*>(p + i) = pp;
+      *reinterpret_cast<float4*>(m + i) = mm;
+      *reinterpret_cast<float4*>(v + i) = vv;
+      if (zero_grad) *reinterpret_cast<float4*>(g + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (shadow) {
+        uint2 sh;
+        sh.x = (uint32_t)f32_to_bf16_bits(pp.x) | ((uint32_t)f32_to_bf16_bits(pp.y) << 16);
+        sh.y = (uint32_t)f32_to_bf16_bits(pp.z) | ((uint32_t)f32_to_bf16_bits(pp.w) << 16);
+        *reinterpret_cast<uint2*>(shadow + i) = sh;
+      }
+    } else {
+      for (int64_t e = i; e < end; ++e) {
+        bool ch = false;
+        adam_one(p[e], g[e], m[e], v[e], a, ch);
+        if (zero_grad) g[e] = 0.0f;
+        if (shadow && ch) shadow[e] = f32_to_bf16_bits(p[e]);
+      }
+    }
+  }
+}
+
+// One block per flagged block of entries (bricks of grids).
 __global__ void __launch_bounds__(256) adam_blocks_kernel(float* __restrict__ p,
                                                           uint16_t* __restrict__ shadow,
                                                           float* __restrict__ g,
@@ -433,43 +499,47 @@ __global__ void __launch_bounds__(256) adam_blocks_kernel(float* __restrict__ p,
   const int64_t nblk = (n + block_elems - 1) / block_elems;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     if (touched && touched[b] == 0) continue;
-    const int64_t base = b * block_elems;
-    const int64_t end = min(base + block_elems, n);
-    // block_elems and base are multiples of 4 (checked on the host)
-    for (int64_t i = base + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
-      if (i + 4 <= end) {
-        float4 gg = *reinterpret_cast<float4*>(g + i);
-        if (gg.x == 0.0f && gg.y == 0.0f && gg.z == 0.0f && gg.w == 0.0f) continue;
-        float4 pp = *reinterpret_cast<float4*>(p + i);
-        float4 mm = *reinterpret_cast<float4*>(m + i);
-        float4 vv = *reinterpret_cast<float4*>(v + i);
-        bool ch = false;
-        adam_one(pp.x, gg.x, mm.x, vv.x, a, ch);
-        adam_one(pp.y, gg.y, mm.y, vv.y, a, ch);
-        adam_one(pp.z, gg.z, mm.z, vv.z, a, ch);
-        adam_one(pp.w, gg.w, mm.w, vv.w, a, ch);
-        *reinterpret_cast<float4*>(p + i) = pp;
-        *reinterpret_cast<float4*>(m + i) = mm;
-        *reinterpret_cast<float4*>(v + i) = vv;
-        if (zero_grad) *reinterpret_cast<float4*>(g + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (shadow) {
-          uint2 sh;
-          sh.x = (uint32_t)f32_to_bf16_bits(pp.x) | ((uint32_t)f32_to_bf16_bits(pp.y) << 16);
-          sh.y = (uint32_t)f32_to_bf16_bits(pp.z) | ((uint32_t)f32_to_bf16_bits(pp.w) << 16);
-          *reinterpret_cast<uint2*>(shadow + i) = sh;
-        }
-      } else {
-        for (int64_t e = i; e < end; ++e) {
-          bool ch = false;
-          adam_one(p[e], g[e], m[e], v[e], a, ch);
-          if (zero_grad) g[e] = 0.0f;
-          if (shadow && ch) shadow[e] = f32_to_bf16_bits(p[e]);
-        }
-      }
-    }
+    // block_elems and the block starts are multiples of 4 (checked on the host)
+    adam_range(p, shadow, g, m, v, b * block_elems, min((b + 1) * block_elems, n), a, zero_grad);
     if (touched && zero_grad) {
       __syncthreads();
       if (threadIdx.x == 0) touched[b] = 0;
+    }
+  }
+}
+
+struct AdamArray {
+  float* p;
+  uint16_t* shadow;
+  float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  uint8_t* touched;
+  int64_t block_elems;
+  int64_t first_block;   // prefix of the block counts of the arrays before it
+  AdamArgs a;
+};
+struct AdamMulti {
+  AdamArray x[kMaxMulti];
+  int count;
+  int64_t total_blocks;
+};
+
+// Blocks of all arrays in one index space (array i owns blocks
+// [first_block_i, first_block_i + ceil(n_i / block_elems_i))).
+__global__ void __launch_bounds__(256) adam_multi_kernel(AdamMulti M, int zero_grad) {
+  for (int64_t b = blockIdx.x; b < M.total_blocks; b += gridDim.x) {
+    int i = 0;
+    while (i + 1 < M.count && b >= M.x[i + 1].first_block) ++i;
+    const AdamArray& A = M.x[i];
+    const int64_t lb = b - A.first_block;
+    if (A.touched && A.touched[lb] == 0) continue;
+    adam_range(A.p, A.shadow, A.g, A.m, A.v, lb * A.block_elems,
+               min((lb + 1) * A.block_elems, A.n), A.a, zero_grad);
+    if (A.touched && zero_grad) {
+      __syncthreads();
+      if (threadIdx.x == 0) A.touched[lb] = 0;
     }
   }
 }
@@ -598,18 +668,26 @@ extern "C" int dvgo_sample_grid_bwd(const float* g_out, const dvgo_grid_desc* gd
 extern "C" int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3], int32_t C,
                                 float weight, float delta, int dense_mode, uint8_t* touched,
                                 float* g_grid, void* stream) {
-  DVGO_CHECK_ARG(grid && G && g_grid && C >= 1 && delta > 0.0f);
-  DVGO_CHECK_ARG(dtype == DVGO_F32 || dtype == DVGO_BF16);
+  dvgo_tv_grid one{grid, dtype, C, weight, touched, g_grid};
+  return dvgo_tv_add_grad_multi(&one, 1, G, delta, dense_mode, stream);
+}
+
+extern "C" int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, const int32_t G[3],
+                                      float delta, int dense_mode, void* stream) {
+  DVGO_CHECK_ARG(grids && count >= 1 && count <= kMaxMulti && G && delta > 0.0f);
   DVGO_CHECK_ARG(G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
   BrickGeom g = make_geom(G);
-  double N = (double)G[0] * G[1] * G[2];
-  float scale = (float)((double)weight * 2.0 / (N * C));
-  cudaStream_t st = as_stream(stream);
-  int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 16);
-  if (dtype == DVGO_F32)
-    tv_kernel<false><<<nb, 512, 0, st>>>(grid, g, C, scale, delta, dense_mode, touched, g_grid);
-  else
-    tv_kernel<true><<<nb, 512, 0, st>>>(grid, g, C, scale, delta, dense_mode, touched, g_grid);
+  const double N = (double)G[0] * G[1] * G[2];
+  TvMulti M{};
+  M.count = count;
+  for (int i = 0; i < count; ++i) {
+    const dvgo_tv_grid& q = grids[i];
+    DVGO_CHECK_ARG(q.grid && q.g_grid && q.C >= 1 && (q.dtype == DVGO_F32 || q.dtype == DVGO_BF16));
+    M.a[i] = TvGridArgs{q.grid, q.g_grid, q.touched, (float)((double)q.weight * 2.0 / (N * q.C)), q.C,
+                        q.dtype == DVGO_BF16 ? 1 : 0};
+  }
+  const int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 16);
+  tv_kernel<<<nb, 512, 0, as_stream(stream)>>>(M, g, delta, dense_mode);
   return launch_status();
 }
 
@@ -665,4 +743,34 @@ extern "C" int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g
   int r = dvgo_sample_grid_bwd(g_out_a, gd, C_a, xyz, idx, n_cap, n_dev, g_grid_a, touched_a, stream);
   if (r != DVGO_OK) return r;
   return dvgo_sample_grid_bwd(g_out_b, gd, C_b, xyz, idx, n_cap, n_dev, g_grid_b, touched_b, stream);
+}
+
+extern "C" int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1,
+                                    float beta2, float eps, int64_t step, int zero_grad,
+                                    void* stream) {
+  DVGO_CHECK_ARG(params && count >= 1 && count <= kMaxMulti && step >= 1);
+  AdamMulti M{};
+  M.count = 0;
+  int64_t total = 0;
+  const float inv_c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
+  const float inv_c2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
+  for (int i = 0; i < count; ++i) {
+    const dvgo_adam_param& q = params[i];
+    DVGO_CHECK_ARG(q.n >= 0);
+    if (q.n == 0) continue;
+    DVGO_CHECK_ARG(q.p && q.g && q.m && q.v);
+    DVGO_CHECK_ARG((uintptr_t)q.p % 16 == 0 && (uintptr_t)q.g % 16 == 0 && (uintptr_t)q.m % 16 == 0 &&
+                   (uintptr_t)q.v % 16 == 0 && (!q.p_shadow || (uintptr_t)q.p_shadow % 8 == 0));
+    const int64_t be = q.touched ? q.block_elems : 4096;
+    DVGO_CHECK_ARG(be > 0 && be % 4 == 0);
+    AdamArray& A = M.x[M.count++];
+    A = AdamArray{q.p, q.p_shadow, q.g, q.m, q.v, q.n, q.touched, be, total,
+                  AdamArgs{q.lr, beta1, beta2, eps, inv_c1, inv_c2}};
+    total += (q.n + be - 1) / be;
+  }
+  if (M.count == 0) return DVGO_OK;
+  M.total_blocks = total;
+  const int grid = (int)std::min<int64_t>(total, (int64_t)kNumSMs * 8);
+  adam_multi_kernel<<<grid, 256, 0, as_stream(stream)>>>(M, zero_grad);
+  return launch_status();
 }

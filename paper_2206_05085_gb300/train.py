@@ -187,14 +187,17 @@ class Trainer:
     def regularize_and_step(self, tv_dense: bool):
         rp = self.rp
         self.it += 1
-        for gp, tvw in ((self.density, rp.tv_w_density), (self.feature, rp.tv_w_feature)):
-            if tvw > 0:
-                grid, dt = gp.render_view
-                L.tv_add_grad(grid, dt, self.G, gp.C, tvw, rp.tv_delta, tv_dense, gp.touched, gp.g)
-            L.adam_step(gp.p, gp.shadow, gp.g, gp.m, gp.v, gp.p.numel(), gp.touched,
-                        512 * gp.C, rp.lr_grid, rp.beta1, rp.beta2, rp.eps, self.it, True)
-        L.adam_step(self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
-                    rp.lr_mlp, rp.beta1, rp.beta2, rp.eps, self.it, True)
+        grids = ((self.density, rp.tv_w_density), (self.feature, rp.tv_w_feature))
+        # TV of both grids in one launch (they share the geometry), then one
+        # Adam launch for both grids and the colour MLP
+        tv = [(*gp.render_view, gp.C, tvw, gp.touched, gp.g) for gp, tvw in grids if tvw > 0]
+        if tv:
+            L.tv_add_grad_multi(tv, self.G, rp.tv_delta, tv_dense)
+        params = [(gp.p, gp.shadow, gp.g, gp.m, gp.v, gp.p.numel(), gp.touched, 512 * gp.C,
+                   rp.lr_grid) for gp, _ in grids]
+        params.append((self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
+                       rp.lr_mlp))
+        L.adam_step_multi(params, rp.beta1, rp.beta2, rp.eps, self.it, True)
 
     def step(self, rays_o, rays_d, target, tv_dense: bool = False, sample: bool = True):
         """One full training iteration; returns the device loss tensor [3]."""

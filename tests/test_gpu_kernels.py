@@ -563,6 +563,72 @@ def test_tv_add_grad(L, C, dense_mode, bf16):
         assert np.all(host(touched) == 1)
 
 
+@pytest.mark.parametrize("dense_mode", [True, False])
+def test_tv_add_grad_multi(L, dense_mode):
+    """Two grids of one shape in one launch = two single TV calls (oracle)."""
+    rng = np.random.default_rng(21)
+    G = (19, 23, 10)
+    nb = [(g + 7) // 8 for g in G]
+    cases = []
+    for C, bf16, w in ((1, False, 0.7), (12, True, 0.3)):
+        grid = rng.normal(0, 1.2, (G[2], G[1], G[0], C)).astype(np.float32)
+        if bf16:
+            grid = synth.bf16_round(grid)
+        g0 = np.where(rng.uniform(size=grid.shape) < 0.2, rng.normal(size=grid.shape), 0.0).astype(np.float32)
+        t = np.zeros((nb[2], nb[1], nb[0]), np.uint8)
+        zz, yy, xx = np.nonzero(np.abs(g0).sum(-1) > 0)
+        t[zz // 8, yy // 8, xx // 8] = 1
+        gb = _bricked(L, g0, G, C)
+        tb = dev(t.reshape(-1))
+        gridb = _bricked(L, grid, G, C, torch.bfloat16 if bf16 else torch.float32)
+        cases.append((grid, g0, C, w, bf16, gridb, gb, tb))
+    L.tv_add_grad_multi([(gridb, L.BF16 if bf16 else L.F32, C, w, tb, gb)
+                         for grid, g0, C, w, bf16, gridb, gb, tb in cases], G, 1.0, dense_mode)
+    for grid, g0, C, w, bf16, gridb, gb, tb in cases:
+        out = torch.empty(G[2], G[1], G[0], C, device="cuda")
+        L.grid_unpack(gb, out, G, C, L.F32)
+        assert rel_err(host(out), oracle.tv_add_grad(grid, g0, w, 1.0, dense_mode)) < TOL32
+        if dense_mode:
+            assert np.all(host(tb) == 1)
+
+
+def test_adam_step_multi(L):
+    """Two bricked grids (flagged blocks) and a flat odd-length vector in one
+    launch = three single Adam calls (oracle)."""
+    rng = np.random.default_rng(12)
+    arrays = []
+    for C, nb in ((1, 30), (12, 17)):
+        n = nb * 512 * C
+        p = rng.normal(size=n).astype(np.float32)
+        m = rng.normal(0, 0.1, n).astype(np.float32)
+        v = rng.uniform(0, 0.1, n).astype(np.float32)
+        g = np.zeros(n, np.float32)
+        flags = (rng.uniform(size=nb) < 0.5).astype(np.uint8)
+        for b in np.nonzero(flags)[0]:
+            blk = slice(b * 512 * C, (b + 1) * 512 * C)
+            g[blk] = np.where(rng.uniform(size=512 * C) < 0.7, rng.normal(size=512 * C), 0.0)
+        arrays.append((p, g, m, v, flags, 512 * C, 0.1))
+    n = 22019
+    arrays.append((rng.normal(size=n).astype(np.float32), rng.normal(size=n).astype(np.float32),
+                   rng.normal(0, 0.1, n).astype(np.float32), rng.uniform(0, 0.1, n).astype(np.float32),
+                   None, 0, 1e-3))
+    dev_arrays = [(dev(p), dev(g), dev(m), dev(v), None if f is None else dev(f))
+                  for p, g, m, v, f, be, lr in arrays]
+    L.adam_step_multi([(tp, None, tg, tm, tv, tp.numel(), tf, be, lr)
+                       for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays)],
+                      0.9, 0.99, 1e-15, 5, True)
+    for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays):
+        rp, rm, rv = oracle.adam(p, g, m, v, lr, 0.9, 0.99, 1e-15, 5)
+        assert rel_err(host(tp), rp) < TOL32
+        assert rel_err(host(tm), rm) < TOL32
+        assert rel_err(host(tv), rv) < TOL32
+        z = g == 0
+        assert np.array_equal(host(tp)[z], p[z])
+        assert np.all(host(tg) == 0)
+        if f is not None:
+            assert np.all(host(tf) == 0)
+
+
 @pytest.mark.parametrize("sparse", [True, False])
 def test_adam_step(L, sparse):
     rng = np.random.default_rng(11)
