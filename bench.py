@@ -309,7 +309,9 @@ MLP_BWD_FLOP = 2 * (2 * 3 * 128 + 2 * 128 * 128 + 128 * 40 + 128 * 12)
 # (FP32-accurate) backward recomputes the second layer only.
 MLP_BWD_FLOP_RECOMPUTE = MLP_BWD_FLOP + 2 * (39 * 128 + 128 * 128)
 MLP_BWD_FLOP_TC = MLP_BWD_FLOP + 2 * 128 * 128
-KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2}
+# kernels launched per C-ABI call (others launch one); the FP32 tensor-core MLP
+# backward runs a bound kernel, the backward and the partial-gradient reduction
+KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1}
 
 
 def roofline(res, peaks):
@@ -575,8 +577,10 @@ def main():
     cfg, rp = res["cfg"], res["rp"]
     value = res["samples"] / (res["total_ms"] * 1e-3)
     e2e = res["e2e_samples"] / (res["e2e_total_ms"] * 1e-3)
-    launches_per_step = sum(v["calls_per_step"] * KERNELS_PER_CALL.get(k, 1)
-                            for k, v in res["kt"].items())
+    per_call = dict(KERNELS_PER_CALL)
+    if res["prec"] == "f32tc":
+        per_call["dvgo_rgbnet_bwd"] = 3
+    launches_per_step = sum(v["calls_per_step"] * per_call.get(k, 1) for k, v in res["kt"].items())
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "ray-samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["total_ms"] / args.steps, 4),

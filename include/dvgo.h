@@ -364,7 +364,18 @@ typedef struct {
 } dvgo_tv_grid;
 
 int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, const int32_t G[3], float delta,
-                           int dense_mode, void* stream);
+                           int dense_mode, const int32_t* brick_list, const int32_t* brick_count,
+                           void* stream);
+
+/* Compacted list of the flagged bricks: list[0 .. *count) = the indices b
+ * with touched[b] != 0, in no particular order (list holds nb entries;
+ * count is one int32 on the device, written here).  Given to
+ * dvgo_tv_add_grad_multi (brick_list / brick_count, sparse mode; NULL =
+ * visit every brick and test its flag) and to dvgo_adam_step_multi
+ * (block_list / block_count of a bricked array), the kernels visit only those
+ * bricks, spread evenly over persistent blocks. */
+int dvgo_touched_compact(const uint8_t* touched, int64_t nb, int32_t* list, int32_t* count,
+                         void* stream);
 
 /* ------------------------------------------------------------------ Adam */
 /* Fused Adam (Sec. 3 "Re-implement Adam optimizer"): for each entry with a
@@ -393,6 +404,8 @@ typedef struct {
   uint8_t* touched;
   int64_t block_elems;
   float lr;
+  const int32_t* block_list;   /* optional (with touched): the flagged blocks, see dvgo_touched_compact */
+  const int32_t* block_count;
 } dvgo_adam_param;
 
 int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,

@@ -54,7 +54,8 @@ class TvGrid(ctypes.Structure):
 
 class AdamParam(ctypes.Structure):
     _fields_ = [("p", P), ("p_shadow", P), ("g", P), ("m", P), ("v", P), ("n", I64),
-                ("touched", P), ("block_elems", I64), ("lr", F)]
+                ("touched", P), ("block_elems", I64), ("lr", F), ("block_list", P),
+                ("block_count", P)]
 
 
 class DvgoError(RuntimeError):
@@ -104,7 +105,8 @@ def _declare(L):
         "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
         "dvgo_tv_add_grad": ([P, INT, P, I32, F, F, INT, P, P, P], INT),
         "dvgo_adam_step": ([P, P, P, P, P, I64, P, I64, F, F, F, F, I64, INT, P], INT),
-        "dvgo_tv_add_grad_multi": ([P, I32, P, F, INT, P], INT),
+        "dvgo_tv_add_grad_multi": ([P, I32, P, F, INT, P, P, P], INT),
+        "dvgo_touched_compact": ([P, I64, P, P, P], INT),
         "dvgo_adam_step_multi": ([P, I32, F, F, F, I64, INT, P], INT),
         "dvgo_device_status": ([P], INT),
         "dvgo_proposal_fwd": ([P, P, I64, P, P, P, P], INT),
@@ -134,7 +136,7 @@ def exported_names():
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
         "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
-        "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi"]
+        "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact"]
 
 
 def ptr(t):
@@ -305,19 +307,27 @@ def tv_add_grad(grid, dtype, G, C, weight, delta, dense_mode, touched, g_grid, s
           ptr(touched), ptr(g_grid), _stream(stream))
 
 
-def tv_add_grad_multi(grids, G, delta, dense_mode, stream=None):
+def tv_add_grad_multi(grids, G, delta, dense_mode, brick_list=None, brick_count=None, stream=None):
     """grids: list of (grid, dtype, C, weight, touched, g_grid)."""
     arr = (TvGrid * len(grids))(*[TvGrid(ptr(g), dt, C, w, ptr(t), ptr(gg))
                                   for g, dt, C, w, t, gg in grids])
     _call("dvgo_tv_add_grad_multi", arr, len(grids), _vec3(G, I32), delta, int(dense_mode),
+          ptr(brick_list), ptr(brick_count), _stream(stream))
+
+
+def touched_compact(touched, nb, brick_list, brick_count, stream=None):
+    _call("dvgo_touched_compact", ptr(touched), nb, ptr(brick_list), ptr(brick_count),
           _stream(stream))
 
 
 def adam_step_multi(params, beta1, beta2, eps, step, zero_grad, stream=None):
-    """params: list of (p, p_shadow, g, m, v, n, touched, block_elems, lr)."""
-    arr = (AdamParam * len(params))(*[AdamParam(ptr(p), ptr(sh), ptr(g), ptr(m), ptr(v), n, ptr(t),
-                                                be, lr)
-                                      for p, sh, g, m, v, n, t, be, lr in params])
+    """params: list of (p, p_shadow, g, m, v, n, touched, block_elems, lr[, block_list,
+    block_count])."""
+    def one(t):
+        p, sh, g, m, v, n, tch, be, lr = t[:9]
+        bl, bc = (t[9], t[10]) if len(t) > 9 else (None, None)
+        return AdamParam(ptr(p), ptr(sh), ptr(g), ptr(m), ptr(v), n, ptr(tch), be, lr, ptr(bl), ptr(bc))
+    arr = (AdamParam * len(params))(*[one(t) for t in params])
     _call("dvgo_adam_step_multi", arr, len(params), beta1, beta2, eps, step, int(zero_grad),
           _stream(stream))
 

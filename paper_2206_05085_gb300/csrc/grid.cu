@@ -358,23 +358,25 @@ __device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const Br
   nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
   nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
   if (C % 4 == 0) {
+    // per group of 4 channels: the gradient, the value and the six neighbours
+    // are loaded together (no load waits on another)
     for (int q = 0; q < C / 4; ++q) {
       float4* gp = reinterpret_cast<float4*>(g_grid + self * C) + q;
       const float4 gin = *gp;
-      const bool any = gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
-      if (!dense_mode && !any) continue;
-      float v[4], acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float v[4], u[6][4];
       load_vox4<kBF16>(grid, self, C, q, v);
 #pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        if (!has[d]) continue;
-        float u[4];
-        load_vox4<kBF16>(grid, nbr[d], C, q, u);
+      for (int d = 0; d < 6; ++d) load_vox4<kBF16>(grid, nbr[d], C, q, u[d]);
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] += fminf(fmaxf(v[i] - u[i], -delta), delta);
-      }
-      float4 out = gin;
+      for (int d = 0; d < 6; ++d)
+        if (has[d])
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i] += fminf(fmaxf(v[i] - u[d][i], -delta), delta);
       // sparse mode adds the TV gradient only where the data gradient is non-zero
+      const bool any = gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
+      if (!dense_mode && !any) continue;
+      float4 out = gin;
       if (dense_mode || gin.x != 0.0f) out.x = gin.x + scale * acc[0];
       if (dense_mode || gin.y != 0.0f) out.y = gin.y + scale * acc[1];
       if (dense_mode || gin.z != 0.0f) out.z = gin.z + scale * acc[2];
@@ -385,12 +387,15 @@ __device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const Br
     for (int c = 0; c < C; ++c) {
       float* gp = g_grid + self * C + c;
       const float gin = *gp;
-      if (!dense_mode && gin == 0.0f) continue;
       const float v = load_val<kBF16>(grid, self * C + c);
+      float u[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) u[d] = load_val<kBF16>(grid, nbr[d] * C + c);
+      if (!dense_mode && gin == 0.0f) continue;
       float acc = 0.0f;
 #pragma unroll
       for (int d = 0; d < 6; ++d)
-        if (has[d]) acc += fminf(fmaxf(v - load_val<kBF16>(grid, nbr[d] * C + c), -delta), delta);
+        if (has[d]) acc += fminf(fmaxf(v - u[d], -delta), delta);
       *gp = gin + scale * acc;
     }
   }
@@ -409,14 +414,18 @@ struct TvGridArgs {
 struct TvMulti {
   TvGridArgs a[kMaxMulti];
   int count;
+  const int32_t* list;    // flagged bricks (sparse mode) or NULL
+  const int32_t* list_n;
 };
 
-// One block per brick of all grids (they share the geometry).
-__global__ void __launch_bounds__(512) tv_kernel(TvMulti M, BrickGeom g, float delta, int dense_mode) {
-  const int64_t nb = g.num_bricks();
+// One block per brick of all grids (they share the geometry): every brick, or
+// the bricks of the compacted list.
+__global__ void __launch_bounds__(512, 2) tv_kernel(TvMulti M, BrickGeom g, float delta, int dense_mode) {
+  const int64_t nb = M.list ? (int64_t)*M.list_n : g.num_bricks();
   const int t = threadIdx.x;
   const int lx = compact3(t), ly = compact3(t >> 1), lz = compact3(t >> 2);
-  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+  for (int64_t i = blockIdx.x; i < nb; i += gridDim.x) {
+    const int64_t b = M.list ? (int64_t)M.list[i] : i;
     const int bx = (int)(b % g.nb[0]);
     const int by = (int)((b / g.nb[0]) % g.nb[1]);
     const int bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
@@ -517,23 +526,29 @@ struct AdamArray {
   int64_t n;
   uint8_t* touched;
   int64_t block_elems;
-  int64_t first_block;   // prefix of the block counts of the arrays before it
+  const int32_t* list;     // flagged blocks (or NULL: every block)
+  const int32_t* list_n;
   AdamArgs a;
 };
 struct AdamMulti {
   AdamArray x[kMaxMulti];
   int count;
-  int64_t total_blocks;
 };
 
-// Blocks of all arrays in one index space (array i owns blocks
-// [first_block_i, first_block_i + ceil(n_i / block_elems_i))).
+// Blocks of all arrays in one index space: array i owns the next
+// |list_i| (or ceil(n_i / block_elems_i)) indices.
 __global__ void __launch_bounds__(256) adam_multi_kernel(AdamMulti M, int zero_grad) {
-  for (int64_t b = blockIdx.x; b < M.total_blocks; b += gridDim.x) {
-    int i = 0;
-    while (i + 1 < M.count && b >= M.x[i + 1].first_block) ++i;
+  int64_t first[kMaxMulti + 1];
+  first[0] = 0;
+  for (int i = 0; i < M.count; ++i) {
     const AdamArray& A = M.x[i];
-    const int64_t lb = b - A.first_block;
+    first[i + 1] = first[i] + (A.list ? (int64_t)*A.list_n : (A.n + A.block_elems - 1) / A.block_elems);
+  }
+  for (int64_t b = blockIdx.x; b < first[M.count]; b += gridDim.x) {
+    int i = 0;
+    while (i + 1 < M.count && b >= first[i + 1]) ++i;
+    const AdamArray& A = M.x[i];
+    const int64_t lb = A.list ? (int64_t)A.list[b - first[i]] : b - first[i];
     if (A.touched && A.touched[lb] == 0) continue;
     adam_range(A.p, A.shadow, A.g, A.m, A.v, lb * A.block_elems,
                min((lb + 1) * A.block_elems, A.n), A.a, zero_grad);
@@ -669,11 +684,12 @@ extern "C" int dvgo_tv_add_grad(const void* grid, int dtype, const int32_t G[3],
                                 float weight, float delta, int dense_mode, uint8_t* touched,
                                 float* g_grid, void* stream) {
   dvgo_tv_grid one{grid, dtype, C, weight, touched, g_grid};
-  return dvgo_tv_add_grad_multi(&one, 1, G, delta, dense_mode, stream);
+  return dvgo_tv_add_grad_multi(&one, 1, G, delta, dense_mode, nullptr, nullptr, stream);
 }
 
 extern "C" int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, const int32_t G[3],
-                                      float delta, int dense_mode, void* stream) {
+                                      float delta, int dense_mode, const int32_t* brick_list,
+                                      const int32_t* brick_count, void* stream) {
   DVGO_CHECK_ARG(grids && count >= 1 && count <= kMaxMulti && G && delta > 0.0f);
   DVGO_CHECK_ARG(G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
   BrickGeom g = make_geom(G);
@@ -686,7 +702,13 @@ extern "C" int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, 
     M.a[i] = TvGridArgs{q.grid, q.g_grid, q.touched, (float)((double)q.weight * 2.0 / (N * q.C)), q.C,
                         q.dtype == DVGO_BF16 ? 1 : 0};
   }
-  const int nb = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 16);
+  const bool use_list = !dense_mode && brick_list && brick_count;
+  M.list = use_list ? brick_list : nullptr;
+  M.list_n = use_list ? brick_count : nullptr;
+  // with the list: persistent blocks over the flagged bricks; without: one
+  // block per brick (blocks of unflagged bricks retire at once)
+  const int nb = use_list ? (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 2)
+                          : (int)std::min<int64_t>(g.num_bricks(), (int64_t)1 << 30);
   tv_kernel<<<nb, 512, 0, as_stream(stream)>>>(M, g, delta, dense_mode);
   return launch_status();
 }
@@ -752,6 +774,7 @@ extern "C" int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count
   AdamMulti M{};
   M.count = 0;
   int64_t total = 0;
+  bool lists = false;
   const float inv_c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
   const float inv_c2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
   for (int i = 0; i < count; ++i) {
@@ -763,14 +786,48 @@ extern "C" int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count
                    (uintptr_t)q.v % 16 == 0 && (!q.p_shadow || (uintptr_t)q.p_shadow % 8 == 0));
     const int64_t be = q.touched ? q.block_elems : 4096;
     DVGO_CHECK_ARG(be > 0 && be % 4 == 0);
+    const bool use_list = q.touched && q.block_list && q.block_count;
+    lists |= use_list;
     AdamArray& A = M.x[M.count++];
-    A = AdamArray{q.p, q.p_shadow, q.g, q.m, q.v, q.n, q.touched, be, total,
+    A = AdamArray{q.p, q.p_shadow, q.g, q.m, q.v, q.n, q.touched, be,
+                  use_list ? q.block_list : nullptr, use_list ? q.block_count : nullptr,
                   AdamArgs{q.lr, beta1, beta2, eps, inv_c1, inv_c2}};
     total += (q.n + be - 1) / be;
   }
   if (M.count == 0) return DVGO_OK;
-  M.total_blocks = total;
-  const int grid = (int)std::min<int64_t>(total, (int64_t)kNumSMs * 8);
+  // with lists the block count is on the device: persistent blocks; else one
+  // block per block of entries
+  const int grid = lists ? (int)std::min<int64_t>(total, (int64_t)kNumSMs * 8)
+                         : (int)std::min<int64_t>(total, (int64_t)1 << 30);
   adam_multi_kernel<<<grid, 256, 0, as_stream(stream)>>>(M, zero_grad);
+  return launch_status();
+}
+
+__global__ void __launch_bounds__(256) touched_compact_kernel(const uint8_t* __restrict__ touched,
+                                                              int64_t nb, int32_t* __restrict__ list,
+                                                              int32_t* __restrict__ count) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const bool on = touched[b] != 0;
+    // one counter update per warp
+    const unsigned act = __activemask();
+    const unsigned mask = __ballot_sync(act, on);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader && mask) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(act, base, leader);
+    if (on) list[base + __popc(mask & ((1u << lane) - 1))] = (int32_t)b;
+  }
+}
+
+extern "C" int dvgo_touched_compact(const uint8_t* touched, int64_t nb, int32_t* list, int32_t* count,
+                                    void* stream) {
+  DVGO_CHECK_ARG(nb >= 0 && count);
+  cudaStream_t st = as_stream(stream);
+  cudaMemsetAsync(count, 0, sizeof(int32_t), st);
+  if (nb == 0) return launch_status();
+  DVGO_CHECK_ARG(touched && list && nb < ((int64_t)1 << 31));
+  touched_compact_kernel<<<grid_for(nb, 256, 4), 256, 0, st>>>(touched, nb, list, count);
   return launch_status();
 }

@@ -139,6 +139,9 @@ class Trainer:
             self.act = torch.empty(L.rgbnet_act_bytes(S, L.F32_TC), dtype=torch.uint8, device=dev)
         self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
+        nb = self.density.touched.numel()
+        self.brick_list = torch.empty(nb, **i32)
+        self.brick_count = torch.zeros(1, **i32)
 
     # --------------------------------------------------------------- forward
     def sample(self, rays_o, rays_d):
@@ -188,13 +191,21 @@ class Trainer:
         rp = self.rp
         self.it += 1
         grids = ((self.density, rp.tv_w_density), (self.feature, rp.tv_w_feature))
+        nb = self.density.touched.numel()
+        # The trilinear adjoints flag the same bricks in both grids; their
+        # compacted list drives the sparse TV and Adam (dense TV flags every
+        # brick, so then the list is taken after it).
+        if not tv_dense:
+            L.touched_compact(self.density.touched, nb, self.brick_list, self.brick_count)
         # TV of both grids in one launch (they share the geometry), then one
         # Adam launch for both grids and the colour MLP
         tv = [(*gp.render_view, gp.C, tvw, gp.touched, gp.g) for gp, tvw in grids if tvw > 0]
         if tv:
-            L.tv_add_grad_multi(tv, self.G, rp.tv_delta, tv_dense)
+            L.tv_add_grad_multi(tv, self.G, rp.tv_delta, tv_dense, self.brick_list, self.brick_count)
+        if tv_dense:
+            L.touched_compact(self.density.touched, nb, self.brick_list, self.brick_count)
         params = [(gp.p, gp.shadow, gp.g, gp.m, gp.v, gp.p.numel(), gp.touched, 512 * gp.C,
-                   rp.lr_grid) for gp, _ in grids]
+                   rp.lr_grid, self.brick_list, self.brick_count) for gp, _ in grids]
         params.append((self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
                        rp.lr_mlp))
         L.adam_step_multi(params, rp.beta1, rp.beta2, rp.eps, self.it, True)

@@ -563,8 +563,21 @@ def test_tv_add_grad(L, C, dense_mode, bf16):
         assert np.all(host(touched) == 1)
 
 
+def test_touched_compact(L):
+    rng = np.random.default_rng(23)
+    for nb in (1, 31, 1000, 70001):
+        flags = (rng.uniform(size=nb) < 0.3).astype(np.uint8)
+        lst = torch.full((nb,), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.full((1,), 77, dtype=torch.int32, device="cuda")
+        L.touched_compact(dev(flags), nb, lst, cnt)
+        c = int(host(cnt)[0])
+        assert c == int(flags.sum())
+        assert np.array_equal(np.sort(host(lst)[:c]), np.nonzero(flags)[0])
+
+
+@pytest.mark.parametrize("use_list", [False, True])
 @pytest.mark.parametrize("dense_mode", [True, False])
-def test_tv_add_grad_multi(L, dense_mode):
+def test_tv_add_grad_multi(L, dense_mode, use_list):
     """Two grids of one shape in one launch = two single TV calls (oracle)."""
     rng = np.random.default_rng(21)
     G = (19, 23, 10)
@@ -582,8 +595,15 @@ def test_tv_add_grad_multi(L, dense_mode):
         tb = dev(t.reshape(-1))
         gridb = _bricked(L, grid, G, C, torch.bfloat16 if bf16 else torch.float32)
         cases.append((grid, g0, C, w, bf16, gridb, gb, tb))
+    lst = cnt = None
+    if use_list:   # the two grids' flags are the same here only by chance; list from the union
+        union = np.maximum(host(cases[0][7]), host(cases[1][7]))
+        lst = torch.empty(len(union), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        L.touched_compact(dev(union), len(union), lst, cnt)
     L.tv_add_grad_multi([(gridb, L.BF16 if bf16 else L.F32, C, w, tb, gb)
-                         for grid, g0, C, w, bf16, gridb, gb, tb in cases], G, 1.0, dense_mode)
+                         for grid, g0, C, w, bf16, gridb, gb, tb in cases], G, 1.0, dense_mode,
+                        lst, cnt)
     for grid, g0, C, w, bf16, gridb, gb, tb in cases:
         out = torch.empty(G[2], G[1], G[0], C, device="cuda")
         L.grid_unpack(gb, out, G, C, L.F32)
@@ -592,7 +612,8 @@ def test_tv_add_grad_multi(L, dense_mode):
             assert np.all(host(tb) == 1)
 
 
-def test_adam_step_multi(L):
+@pytest.mark.parametrize("use_list", [False, True])
+def test_adam_step_multi(L, use_list):
     """Two bricked grids (flagged blocks) and a flat odd-length vector in one
     launch = three single Adam calls (oracle)."""
     rng = np.random.default_rng(12)
@@ -614,9 +635,16 @@ def test_adam_step_multi(L):
                    None, 0, 1e-3))
     dev_arrays = [(dev(p), dev(g), dev(m), dev(v), None if f is None else dev(f))
                   for p, g, m, v, f, be, lr in arrays]
-    L.adam_step_multi([(tp, None, tg, tm, tv, tp.numel(), tf, be, lr)
-                       for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays)],
-                      0.9, 0.99, 1e-15, 5, True)
+    params = []
+    for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays):
+        entry = [tp, None, tg, tm, tv, tp.numel(), tf, be, lr]
+        if use_list and f is not None:
+            lst = torch.empty(len(f), dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+            L.touched_compact(tf, len(f), lst, cnt)
+            entry += [lst, cnt]
+        params.append(tuple(entry))
+    L.adam_step_multi(params, 0.9, 0.99, 1e-15, 5, True)
     for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays):
         rp, rm, rv = oracle.adam(p, g, m, v, lr, 0.9, 0.99, 1e-15, 5)
         assert rel_err(host(tp), rp) < TOL32
