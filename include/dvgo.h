@@ -287,8 +287,11 @@ int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
  * DVGO_F32_TC: act is the buffer its forward filled for the same list and
  * count (required; rgb ignored); the backward also writes its header (first
  * 256 bytes) and the per-CTA partial gradients stored after the tile
- * images, and sums those partials in a fixed order (deterministic).  The BF16 form ignores act and rgb (it recomputes on
- * the tensor cores). */
+ * images, and sums those partials in a fixed order (deterministic).
+ * DVGO_BF16: rgb is ignored (the tensor cores recompute the forward); act,
+ * if given (dvgo_rgbnet_act_bytes(n_cap, DVGO_BF16) bytes), holds per-CTA
+ * partial gradients summed in a fixed order; without it the backward adds
+ * into g_params with atomics. */
 int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                     const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
                     const int64_t* n_dev, const float* params, int precision, const float* act,
@@ -297,8 +300,9 @@ int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, co
 /* Bytes of the act buffer dvgo_rgbnet_fwd / _bwd need for n_cap list
  * positions: n_cap * 1024 for DVGO_F32 (optional there); for DVGO_F32_TC
  * 256 + 90112 per 128-position tile + 152 * 22019 * 4 (one partial
- * parameter gradient per SM); 0 for DVGO_BF16; -1 for a bad precision or
- * n_cap < 0. */
+ * parameter gradient per SM); for DVGO_BF16 152 * 22019 * 4 (optional: with
+ * it the backward sums per-CTA partial gradients in a fixed order instead of
+ * using atomics); -1 for a bad precision or n_cap < 0. */
 int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision);
 
 /* ------------------------------------------------------- learned proposal */

@@ -10,7 +10,7 @@ int dvgo_rgbnet_bwd_f32(const float*, const float*, const float*, const float*, 
 int dvgo_rgbnet_fwd_bf16(const float*, const float*, const int32_t*, const int32_t*, int64_t,
                          const int64_t*, const float*, float*, cudaStream_t);
 int dvgo_rgbnet_bwd_bf16(const float*, const float*, const float*, const float*, const float*, const int32_t*,
-                         const int32_t*, int64_t, const int64_t*, const float*, float*, float*,
+                         const int32_t*, int64_t, const int64_t*, const float*, float*, float*, float*,
                          cudaStream_t);
 int dvgo_mlp_status_read_and_clear(cudaStream_t);
 int dvgo_rgbnet_fwd_f32tc(const float*, const float*, const int32_t*, const int32_t*, int64_t,
@@ -74,8 +74,9 @@ extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const f
     return dvgo_rgbnet_bwd_f32(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, act,
                                rgb, g_params, g_k0, st);
   if (precision == DVGO_BF16)
+    // act (optional): per-CTA partial gradient rows (deterministic sum, no contended atomics)
     return dvgo_rgbnet_bwd_bf16(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
-                                g_params, g_k0, st);
+                                g_params, g_k0, const_cast<float*>(act), st);
   if (precision == DVGO_F32_TC) {
     DVGO_CHECK_ARG(act != nullptr);
     // the backward writes its gradient bound into the first bytes of act
@@ -89,7 +90,7 @@ extern "C" int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision) {
   if (n_cap < 0) return -1;
   if (precision == DVGO_F32) return n_cap * 1024;
   if (precision == DVGO_F32_TC) return rgbnet_act_bytes_tc(n_cap);
-  if (precision == DVGO_BF16) return 0;
+  if (precision == DVGO_BF16) return (int64_t)kNumSMs * kNumParams * (int64_t)sizeof(float);
   return -1;
 }
 

@@ -44,6 +44,7 @@ struct MlpIO {
   const float* w;
   float* g_params;
   float* g_in;           // rgbnet: g_k0
+  float* part;           // backward: per-CTA partial gradient rows of NP floats (NULL: atomics)
 };
 
 template <int H_, int OUT_>
@@ -414,6 +415,13 @@ __global__ void __launch_bounds__(288, 1) mlp_bwd_bf16_kernel(MlpIO io) {
   const uint32_t tmem = fs->tmem_slot;
   const uint32_t sm_w1 = tc::smem_u32(sm + Lo::oW1), sm_w2 = tc::smem_u32(sm + Lo::oW2);
 
+  // output-layer gradient partials of the epilogue threads (zero in the issuer warp)
+  float dW3acc[OUT * NCH];
+#pragma unroll
+  for (int i = 0; i < OUT * NCH; ++i) dW3acc[i] = 0.0f;
+  float db3acc[OUT];
+#pragma unroll
+  for (int c = 0; c < OUT; ++c) db3acc[c] = 0.0f;
   if (warp == 8) {
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
@@ -495,12 +503,6 @@ __global__ void __launch_bounds__(288, 1) mlp_bwd_bf16_kernel(MlpIO io) {
     uint8_t* grp = sm + Lo::oGroup + w * Lo::kGroupBytes;
     const uint32_t lane_base = tmem + 128 * w + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t ph = 0;
-    float dW3acc[OUT * NCH];
-#pragma unroll
-    for (int i = 0; i < OUT * NCH; ++i) dW3acc[i] = 0.0f;
-    float db3acc[OUT];
-#pragma unroll
-    for (int c = 0; c < OUT; ++c) db3acc[c] = 0.0f;
     auto signal = [&]() {
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
@@ -629,20 +631,98 @@ __global__ void __launch_bounds__(288, 1) mlp_bwd_bf16_kernel(MlpIO io) {
       tc::fence_before_sync();
       named_bar(1 + w);                           // TMEM region and X free for the next tile
     }
-    // output-layer partials of this thread
+    if (!io.part) {
+      // output-layer partials of this thread
 #pragma unroll
-    for (int c = 0; c < OUT; ++c)
+      for (int c = 0; c < OUT; ++c)
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch)
-        atomicAdd(io.g_params + Net::oW3 + c * H + ch * 32 + lane, dW3acc[c * NCH + ch]);
+        for (int ch = 0; ch < NCH; ++ch)
+          atomicAdd(io.g_params + Net::oW3 + c * H + ch * 32 + lane, dW3acc[c * NCH + ch]);
 #pragma unroll
-    for (int c = 0; c < OUT; ++c) atomicAdd(io.g_params + Net::oB3 + c, db3acc[c]);
+      for (int c = 0; c < OUT; ++c) atomicAdd(io.g_params + Net::oB3 + c, db3acc[c]);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const bool ok = fs->error == 0;
-  if (ok && warp < 4 && ntiles > blockIdx.x) {
+  if (io.part && warp < 8) {
+    // output-layer partials of each epilogue warp into shared memory (every
+    // group buffer is free once all warps have passed the barrier above)
+    float* pr = reinterpret_cast<float*>(sm + Lo::oGroup);   // [8 warps][OUT][NCH][32]
+    float* pr3 = pr + 8 * OUT * NCH * 32;                     // [8 warps][OUT]
+#pragma unroll
+    for (int c = 0; c < OUT; ++c)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) pr[((warp * OUT + c) * NCH + ch) * 32 + lane] = dW3acc[c * NCH + ch];
+#pragma unroll
+    for (int c = 0; c < OUT; ++c) {
+      float v = db3acc[c];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) pr3[warp * OUT + c] = v;
+    }
+  }
+  __syncthreads();
+  if (io.part) {
+    // This CTA's gradient into its own partial row (no atomics); a second
+    // kernel sums the rows in CTA order.
+    float* P = io.part + (size_t)blockIdx.x * Net::NP;
+    const bool has = ntiles > blockIdx.x;
+    const float* pr = reinterpret_cast<const float*>(sm + Lo::oGroup);
+    const float* pr3 = pr + 8 * OUT * NCH * 32;
+    for (int e = tid; has && e < OUT * H; e += blockDim.x) {
+      const int c = e / H, o = e % H, ch = o >> 5, l = o & 31;
+      float v = 0.0f;
+      for (int w8 = 0; w8 < 8; ++w8) v += pr[((w8 * OUT + c) * NCH + ch) * 32 + l];
+      P[Net::oW3 + e] = v;
+    }
+    if (has && tid < OUT) {
+      float v = 0.0f;
+      for (int w8 = 0; w8 < 8; ++w8) v += pr3[w8 * OUT + tid];
+      P[Net::oB3 + tid] = v;
+    }
+    if (has && warp < 4 && warp * 32 < H) {
+      // TMEM lane = output neuron o; rows through a 32 x 33 shared-memory
+      // transpose so that each store covers 32 consecutive parameters
+      float* tp = reinterpret_cast<float*>(sm + Lo::oGroup) + 8 * OUT * NCH * 32 + 64 + warp * 32 * 33;
+      const int o0 = warp * 32;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const float keep = ok ? 1.0f : 0.0f;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {
+        float v[32];
+        tc::tmem_ld32(lane_base + cDW2 + ch * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i] * keep;
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) P[Net::oW2 + (o0 + r) * H + ch * 32 + lane] = tp[r * 33 + lane];
+        __syncwarp();
+      }
+      {
+        float v[16];
+        tc::tmem_ld16(lane_base + cDW2 + H, v);
+        P[Net::oB2 + o0 + lane] = v[0] * keep;
+      }
+      {
+        float v[32], u[16];
+        tc::tmem_ld32(lane_base + cDW1, v);
+        tc::tmem_ld16(lane_base + cDW1 + 32, u);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i] * keep;
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) P[Net::oW1 + (o0 + r) * kIn + lane] = tp[r * 33 + lane];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tp[lane * 33 + i] = u[i] * keep;
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) {
+          if (lane < kIn - 32) P[Net::oW1 + (o0 + r) * kIn + 32 + lane] = tp[r * 33 + lane];
+          else if (lane == kIn - 32) P[Net::oB1 + o0 + r] = tp[r * 33 + lane];
+        }
+      }
+    }
+  } else if (ok && warp < 4 && ntiles > blockIdx.x) {
     // TMEM lane = output neuron o (rows o >= H are padding)
     const int o = tid;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -679,6 +759,20 @@ __global__ void __launch_bounds__(288, 1) mlp_bwd_bf16_kernel(MlpIO io) {
   if (warp == 8) tc::tmem_dealloc(tmem, 512);
 }
 
+// g_params += sum over the CTAs that had tiles of their partial rows, in CTA order.
+__global__ void __launch_bounds__(256) bf16_partials_reduce_kernel(const float* __restrict__ part, int nrows,
+                                                                   int np, int64_t n_cap,
+                                                                   const int64_t* __restrict__ n_dev,
+                                                                   float* __restrict__ g_params) {
+  const int64_t n = mlp_count(n_cap, n_dev);
+  const int rows = (int)std::min<int64_t>(nrows, (n + kTile - 1) / kTile);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int b = 0; b < rows; ++b) acc += part[(size_t)b * np + p];
+    g_params[p] += acc;
+  }
+}
+
 template <class Net>
 static int launch_fwd(const MlpIO& io, cudaStream_t st) {
   const size_t smem = Layout<Net>::kFwdOperands + sizeof(F32Side<Net>);
@@ -704,6 +798,9 @@ static int launch_bwd(const MlpIO& io, cudaStream_t st) {
   int grid = (int)std::min<int64_t>((io.n_cap + kTile - 1) / kTile, kNumSMs);
   if (grid < 1) return DVGO_OK;
   mlp_bwd_bf16_kernel<Net><<<grid, 288, smem, st>>>(io);
+  if (io.part)
+    bf16_partials_reduce_kernel<<<(Net::NP + 255) / 256, 256, 0, st>>>(io.part, grid, Net::NP, io.n_cap,
+                                                                      io.n_dev, io.g_params);
   return launch_status();
 }
 
@@ -729,7 +826,7 @@ int dvgo_rgbnet_fwd_bf16(const float* k0, const float* rays_d, const int32_t* ra
 int dvgo_rgbnet_bwd_bf16(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                          const float* rays_d, const int32_t* ray_id, const int32_t* idx,
                          int64_t n_cap, const int64_t* n_dev, const float* params,
-                         float* g_params, float* g_k0, cudaStream_t st) {
+                         float* g_params, float* g_k0, float* part, cudaStream_t st) {
   MlpIO io{};
   io.k0 = k0;
   io.rays_d = rays_d;
@@ -743,6 +840,7 @@ int dvgo_rgbnet_bwd_bf16(const float* g_rgb, const float* g_color, const float* 
   io.w = w;
   io.g_params = g_params;
   io.g_in = g_k0;
+  io.part = part;
   return launch_bwd<RgbNet>(io, st);
 }
 

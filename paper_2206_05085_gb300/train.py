@@ -132,11 +132,11 @@ class Trainer:
         self.g_k0 = torch.empty(S, FEAT, **f32)
         # FP32 forms: what the colour-MLP forward saves for its backward (hidden
         # activations, or the split layer inputs of each 128-sample tile)
-        self.act = None
+        # (BF16 form: the backward's per-CTA partial gradients)
         if self.precision == L.F32:
             self.act = torch.empty(S, 256, **f32)
-        elif self.precision == L.F32_TC:
-            self.act = torch.empty(L.rgbnet_act_bytes(S, L.F32_TC), dtype=torch.uint8, device=dev)
+        else:
+            self.act = torch.empty(L.rgbnet_act_bytes(S, self.precision), dtype=torch.uint8, device=dev)
         self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
         nb = self.density.touched.numel()

@@ -438,8 +438,10 @@ def test_rgbnet_fwd_bwd(L, precision, n):
     rest = np.setdiff1d(np.arange(n), idx)
     assert np.all(got[rest] == -1.0)
     # backward recomputing the forward, and (FP32 form) from stored activations
-    for use_act in ((False, True) if precision == "f32" else (precision == "f32tc",)):
+    for use_act in ((False, True) if precision in ("f32", "bf16") else (True,)):
         act = act_tc
+        if use_act and precision == "bf16":   # per-CTA partial gradients instead of atomics
+            act = torch.empty(L.rgbnet_act_bytes(n, prec), dtype=torch.uint8, device="cuda")
         if use_act and precision == "f32":
             act = torch.empty(n, 256, device="cuda")
             L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb,
