@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BF16 / learned-proposal comparison")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step's kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup+steps with no clock sampling or CPU baseline (for ncu)")
     return ap.parse_args()
@@ -233,6 +235,22 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         return None
 
+    # The step as one CUDA graph over fixed input buffers (each timed step
+    # copies its batch into them, device to device, inside the timed region);
+    # --no-graph launches the kernels one by one.
+    graph, g_in = None, None
+    if not args.no_graph:
+        graph, g_in = tr.capture(*batches[0], tv_dense=args.tv_dense)
+        torch.cuda.synchronize()
+
+    def one_step(o, d, t):
+        if graph is None:
+            return tr.step(o, d, t, tv_dense=args.tv_dense)
+        for dst, src in zip(g_in, (o, d, t)):
+            dst.copy_(src, non_blocking=True)
+        graph.replay()
+        return tr.loss
+
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -249,7 +267,7 @@ def run_ours(args, rank, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        tr.step(o, d, t, tv_dense=args.tv_dense)
+        one_step(o, d, t)
         e1.record(stream)
         ev.append((e0, e1))
         samples += S_of[b]
@@ -272,9 +290,14 @@ def run_ours(args, rank, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for dst, src in zip(dev_in, pinned[b]):
+        dst_in = dev_in if graph is None else g_in
+        for dst, src in zip(dst_in, pinned[b]):
             dst.copy_(src, non_blocking=True)
-        loss = tr.step(dev_in[0], dev_in[1], dev_in[2], tv_dense=args.tv_dense)
+        if graph is None:
+            loss = tr.step(dst_in[0], dst_in[1], dst_in[2], tv_dense=args.tv_dense)
+        else:
+            graph.replay()
+            loss = tr.loss
         loss_host.copy_(loss, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
@@ -593,6 +616,7 @@ def main():
                                      "f32": "FP32 on the CUDA cores",
                                      "bf16": "BF16 on tcgen05"}[res["prec"]],
                    "tv_dense": bool(args.tv_dense), "l2": "flushed (256 MB memset) before each timed step",
+                   "launch": "one CUDA graph per step" if not args.no_graph else "eager kernel launches",
                    "parallelism": "replicas" if args.gpus > 1 else "single"},
         "e2e": {"value": round(e2e, 1), "unit": "ray-samples/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": 12},

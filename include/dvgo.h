@@ -415,6 +415,12 @@ typedef struct {
 int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,
                          float eps, int64_t step, int zero_grad, void* stream);
 
+/* Same, with the step count on the device: *step (int64) is incremented by
+ * one, then used as t (so a captured CUDA graph of a training step can be
+ * replayed step after step). */
+int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,
+                             float eps, int64_t* step, int zero_grad, void* stream);
+
 /* Reads and clears the device status word that kernels with bounded waits
  * set (DVGO_ERR_TIMEOUT) instead of hanging.  Synchronises the stream. */
 int dvgo_device_status(void* stream);

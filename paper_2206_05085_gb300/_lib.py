@@ -108,6 +108,7 @@ def _declare(L):
         "dvgo_tv_add_grad_multi": ([P, I32, P, F, INT, P, P, P], INT),
         "dvgo_touched_compact": ([P, I64, P, P, P], INT),
         "dvgo_adam_step_multi": ([P, I32, F, F, F, I64, INT, P], INT),
+        "dvgo_adam_step_multi_dev": ([P, I32, F, F, F, P, INT, P], INT),
         "dvgo_device_status": ([P], INT),
         "dvgo_proposal_fwd": ([P, P, I64, P, P, P, P], INT),
         "dvgo_proposal_bwd": ([P, P, P, I64, P, P, P, P], INT),
@@ -136,7 +137,8 @@ def exported_names():
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
         "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
-        "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact"]
+        "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact",
+        "dvgo_adam_step_multi_dev"]
 
 
 def ptr(t):
@@ -330,6 +332,17 @@ def adam_step_multi(params, beta1, beta2, eps, step, zero_grad, stream=None):
     arr = (AdamParam * len(params))(*[one(t) for t in params])
     _call("dvgo_adam_step_multi", arr, len(params), beta1, beta2, eps, step, int(zero_grad),
           _stream(stream))
+
+
+def adam_step_multi_dev(params, beta1, beta2, eps, step_dev, zero_grad, stream=None):
+    """adam_step_multi with the step count in device memory (incremented here)."""
+    def one(t):
+        p, sh, g, m, v, n, tch, be, lr = t[:9]
+        bl, bc = (t[9], t[10]) if len(t) > 9 else (None, None)
+        return AdamParam(ptr(p), ptr(sh), ptr(g), ptr(m), ptr(v), n, ptr(tch), be, lr, ptr(bl), ptr(bc))
+    arr = (AdamParam * len(params))(*[one(t) for t in params])
+    _call("dvgo_adam_step_multi_dev", arr, len(params), beta1, beta2, eps, ptr(step_dev),
+          int(zero_grad), _stream(stream))
 
 
 def adam_step(p, p_shadow, g, m, v, n, touched, block_elems, lr, beta1, beta2, eps, step,

@@ -533,11 +533,25 @@ struct AdamArray {
 struct AdamMulti {
   AdamArray x[kMaxMulti];
   int count;
+  const int64_t* step;   // if set: t on the device, bias corrections formed in the kernel
 };
 
 // Blocks of all arrays in one index space: array i owns the next
 // |list_i| (or ceil(n_i / block_elems_i)) indices.
 __global__ void __launch_bounds__(256) adam_multi_kernel(AdamMulti M, int zero_grad) {
+  if (M.step) {   // bias corrections of the device-side step count (beta1, beta2 shared by all arrays)
+    __shared__ float corr[2];
+    if (threadIdx.x == 0) {
+      const double t = (double)*M.step;
+      corr[0] = (float)(1.0 / (1.0 - pow((double)M.x[0].a.b1, t)));
+      corr[1] = (float)(1.0 / (1.0 - pow((double)M.x[0].a.b2, t)));
+    }
+    __syncthreads();
+    for (int i = 0; i < M.count; ++i) {
+      M.x[i].a.inv_c1 = corr[0];
+      M.x[i].a.inv_c2 = corr[1];
+    }
+  }
   int64_t first[kMaxMulti + 1];
   first[0] = 0;
   for (int i = 0; i < M.count; ++i) {
@@ -767,12 +781,32 @@ extern "C" int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g
   return dvgo_sample_grid_bwd(g_out_b, gd, C_b, xyz, idx, n_cap, n_dev, g_grid_b, touched_b, stream);
 }
 
+__global__ void step_increment_kernel(int64_t* step) { *step += 1; }
+
+static int adam_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2, float eps,
+                      int64_t step, int64_t* step_dev, int zero_grad, void* stream);
+
 extern "C" int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1,
                                     float beta2, float eps, int64_t step, int zero_grad,
                                     void* stream) {
-  DVGO_CHECK_ARG(params && count >= 1 && count <= kMaxMulti && step >= 1);
+  DVGO_CHECK_ARG(step >= 1);
+  return adam_multi(params, count, beta1, beta2, eps, step, nullptr, zero_grad, stream);
+}
+
+extern "C" int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t count, float beta1,
+                                        float beta2, float eps, int64_t* step, int zero_grad,
+                                        void* stream) {
+  DVGO_CHECK_ARG(step);
+  step_increment_kernel<<<1, 1, 0, as_stream(stream)>>>(step);
+  return adam_multi(params, count, beta1, beta2, eps, 1, step, zero_grad, stream);
+}
+
+static int adam_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2, float eps,
+                      int64_t step, int64_t* step_dev, int zero_grad, void* stream) {
+  DVGO_CHECK_ARG(params && count >= 1 && count <= kMaxMulti);
   AdamMulti M{};
   M.count = 0;
+  M.step = step_dev;
   int64_t total = 0;
   bool lists = false;
   const float inv_c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));

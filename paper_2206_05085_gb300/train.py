@@ -142,6 +142,7 @@ class Trainer:
         nb = self.density.touched.numel()
         self.brick_list = torch.empty(nb, **i32)
         self.brick_count = torch.zeros(1, **i32)
+        self.step_dev = torch.zeros(1, dtype=torch.int64, device=dev)   # Adam's t
 
     # --------------------------------------------------------------- forward
     def sample(self, rays_o, rays_d):
@@ -208,7 +209,8 @@ class Trainer:
                    rp.lr_grid, self.brick_list, self.brick_count) for gp, _ in grids]
         params.append((self.mlp, None, self.mlp_g, self.mlp_m, self.mlp_v, self.mlp.numel(), None, 0,
                        rp.lr_mlp))
-        L.adam_step_multi(params, rp.beta1, rp.beta2, rp.eps, self.it, True)
+        # the step count t lives on the device (so that a captured step can be replayed)
+        L.adam_step_multi_dev(params, rp.beta1, rp.beta2, rp.eps, self.step_dev, True)
 
     def step(self, rays_o, rays_d, target, tv_dense: bool = False, sample: bool = True):
         """One full training iteration; returns the device loss tensor [3]."""
@@ -216,6 +218,26 @@ class Trainer:
         self.backward(rays_d)
         self.regularize_and_step(tv_dense)
         return self.loss
+
+    def capture(self, rays_o, rays_d, target, tv_dense: bool = False):
+        """Record one training step (sampling through the optimizer) as a CUDA
+        graph over fixed device input buffers.  Returns (graph, inputs): copy a
+        batch into inputs = (rays_o, rays_d, target), then graph.replay() runs
+        one step (the Adam step count advances on the device).  Two eager
+        warm-up steps on the given batch run first (they update the state)."""
+        self.g_in = tuple(torch.empty_like(x) for x in (rays_o, rays_d, target))
+        for dst, src in zip(self.g_in, (rays_o, rays_d, target)):
+            dst.copy_(src)
+        side = torch.cuda.Stream(device=self.dev)
+        side.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                self.step(*self.g_in, tv_dense=tv_dense)
+        torch.cuda.current_stream(self.dev).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.step(*self.g_in, tv_dense=tv_dense)
+        return graph, self.g_in
 
     # ------------------------------------------------------------- helpers
     def dense(self, gp: GridParam, which: str = "p") -> torch.Tensor:

@@ -646,7 +646,12 @@ def test_adam_step_multi(L, use_list):
             L.touched_compact(tf, len(f), lst, cnt)
             entry += [lst, cnt]
         params.append(tuple(entry))
-    L.adam_step_multi(params, 0.9, 0.99, 1e-15, 5, True)
+    if use_list:   # the device-side step count: 4 -> 5
+        step = torch.tensor([4], dtype=torch.int64, device="cuda")
+        L.adam_step_multi_dev(params, 0.9, 0.99, 1e-15, step, True)
+        assert int(host(step)[0]) == 5
+    else:
+        L.adam_step_multi(params, 0.9, 0.99, 1e-15, 5, True)
     for (tp, tg, tm, tv, tf), (p, g, m, v, f, be, lr) in zip(dev_arrays, arrays):
         rp, rm, rv = oracle.adam(p, g, m, v, lr, 0.9, 0.99, 1e-15, 5)
         assert rel_err(host(tp), rp) < TOL32

@@ -147,3 +147,36 @@ def test_step_unbounded_contracted(T):
     cfg = dataclasses.replace(synth.CFG3, grid=96)
     gpu, fb, opt, cfg, rp, P = _run(T, cfg, 256, "f32", tv_dense=False, ray_stride=32)
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
+
+
+def test_captured_step_replays_like_eager(T):
+    """A training step captured as a CUDA graph and replayed on new batches
+    leaves the same state as the same steps launched one by one."""
+    cfg = synth.CFG1
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    batches = []
+    for seed in (1, 2, 3):
+        o, d = synth.rays(cfg, seed=seed, n_rays=1024)
+        t = synth.target_rgb(cfg, seed=seed, n_rays=1024)
+        batches.append(tuple(torch.from_numpy(a).cuda() for a in (o, d, t)))
+    eager = T.Trainer(cfg, rp, D, Fg, P, n_rays=1024, precision="f32tc")
+    for b in (batches[0], batches[0], batches[1], batches[2]):
+        eager.step(*b)
+    graphed = T.Trainer(cfg, rp, D, Fg, P, n_rays=1024, precision="f32tc")
+    graph, inputs = graphed.capture(*batches[0])       # two eager steps on batch 0
+    for b in batches[1:]:
+        for dst, src in zip(inputs, b):
+            dst.copy_(src)
+        graph.replay()
+    torch.cuda.synchronize()
+    assert int(graphed.step_dev.item()) == 4 == int(eager.step_dev.item())
+    # the grid adjoints sum with atomics, so the two runs differ only by that
+    # summation order: the loss and the MLP to FP32 rounding, the grids by far
+    # less than one Adam step (lr = 0.1)
+    for a, b in ((eager.loss, graphed.loss), (eager.mlp, graphed.mlp)):
+        a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
+        assert np.max(np.abs(a - b)) <= 1e-5 * max(np.max(np.abs(a)), 1e-30)
+    for a, b in ((eager.density.p, graphed.density.p), (eager.feature.p, graphed.feature.p)):
+        a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
+        assert np.max(np.abs(a - b)) <= 1e-3 * rp.lr_grid
