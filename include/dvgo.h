@@ -415,9 +415,10 @@ typedef struct {
 int dvgo_adam_step_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,
                          float eps, int64_t step, int zero_grad, void* stream);
 
-/* Same, with the step count on the device: *step (int64) is incremented by
- * one, then used as t (so a captured CUDA graph of a training step can be
- * replayed step after step). */
+/* Same, with the step count on the device: step points to two int64 words;
+ * step[0] (t) is incremented by one and used, step[1] receives the two FP32
+ * bias corrections of the new t (scratch).  A captured CUDA graph of a
+ * training step can then be replayed step after step. */
 int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t count, float beta1, float beta2,
                              float eps, int64_t* step, int zero_grad, void* stream);
 

@@ -539,18 +539,12 @@ struct AdamMulti {
 // Blocks of all arrays in one index space: array i owns the next
 // |list_i| (or ceil(n_i / block_elems_i)) indices.
 __global__ void __launch_bounds__(256) adam_multi_kernel(AdamMulti M, int zero_grad) {
-  if (M.step) {   // bias corrections of the device-side step count (beta1, beta2 shared by all arrays)
-    __shared__ float corr[2];
-    if (threadIdx.x == 0) {
-      const double t = (double)*M.step;
-      corr[0] = (float)(1.0 / (1.0 - pow((double)M.x[0].a.b1, t)));
-      corr[1] = (float)(1.0 / (1.0 - pow((double)M.x[0].a.b2, t)));
-    }
-    __syncthreads();
-    for (int i = 0; i < M.count; ++i) {
-      M.x[i].a.inv_c1 = corr[0];
-      M.x[i].a.inv_c2 = corr[1];
-    }
+  // bias corrections of the device-side step count, formed once by step_increment_kernel
+  float corr[2] = {0.0f, 0.0f};
+  if (M.step) {
+    const float* c = reinterpret_cast<const float*>(M.step + 1);
+    corr[0] = c[0];
+    corr[1] = c[1];
   }
   int64_t first[kMaxMulti + 1];
   first[0] = 0;
@@ -564,8 +558,13 @@ __global__ void __launch_bounds__(256) adam_multi_kernel(AdamMulti M, int zero_g
     const AdamArray& A = M.x[i];
     const int64_t lb = A.list ? (int64_t)A.list[b - first[i]] : b - first[i];
     if (A.touched && A.touched[lb] == 0) continue;
-    adam_range(A.p, A.shadow, A.g, A.m, A.v, lb * A.block_elems,
-               min((lb + 1) * A.block_elems, A.n), A.a, zero_grad);
+    AdamArgs a = A.a;
+    if (M.step) {
+      a.inv_c1 = corr[0];
+      a.inv_c2 = corr[1];
+    }
+    adam_range(A.p, A.shadow, A.g, A.m, A.v, lb * A.block_elems, min((lb + 1) * A.block_elems, A.n), a,
+               zero_grad);
     if (A.touched && zero_grad) {
       __syncthreads();
       if (threadIdx.x == 0) A.touched[lb] = 0;
@@ -781,7 +780,14 @@ extern "C" int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g
   return dvgo_sample_grid_bwd(g_out_b, gd, C_b, xyz, idx, n_cap, n_dev, g_grid_b, touched_b, stream);
 }
 
-__global__ void step_increment_kernel(int64_t* step) { *step += 1; }
+// step[0] += 1; step[1] holds the two FP32 bias corrections of the new t.
+__global__ void step_increment_kernel(int64_t* step, float beta1, float beta2) {
+  const int64_t t = step[0] + 1;
+  step[0] = t;
+  float* c = reinterpret_cast<float*>(step + 1);
+  c[0] = (float)(1.0 / (1.0 - pow((double)beta1, (double)t)));
+  c[1] = (float)(1.0 / (1.0 - pow((double)beta2, (double)t)));
+}
 
 static int adam_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2, float eps,
                       int64_t step, int64_t* step_dev, int zero_grad, void* stream);
@@ -797,7 +803,7 @@ extern "C" int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t c
                                         float beta2, float eps, int64_t* step, int zero_grad,
                                         void* stream) {
   DVGO_CHECK_ARG(step);
-  step_increment_kernel<<<1, 1, 0, as_stream(stream)>>>(step);
+  step_increment_kernel<<<1, 1, 0, as_stream(stream)>>>(step, beta1, beta2);
   return adam_multi(params, count, beta1, beta2, eps, 1, step, zero_grad, stream);
 }
 

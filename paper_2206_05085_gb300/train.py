@@ -142,7 +142,7 @@ class Trainer:
         nb = self.density.touched.numel()
         self.brick_list = torch.empty(nb, **i32)
         self.brick_count = torch.zeros(1, **i32)
-        self.step_dev = torch.zeros(1, dtype=torch.int64, device=dev)   # Adam's t
+        self.step_dev = torch.zeros(2, dtype=torch.int64, device=dev)   # Adam's t (+ scratch)
 
     # --------------------------------------------------------------- forward
     def sample(self, rays_o, rays_d):

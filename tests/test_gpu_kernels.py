@@ -647,7 +647,7 @@ def test_adam_step_multi(L, use_list):
             entry += [lst, cnt]
         params.append(tuple(entry))
     if use_list:   # the device-side step count: 4 -> 5
-        step = torch.tensor([4], dtype=torch.int64, device="cuda")
+        step = torch.tensor([4, 0], dtype=torch.int64, device="cuda")
         L.adam_step_multi_dev(params, 0.9, 0.99, 1e-15, step, True)
         assert int(host(step)[0]) == 5
     else:

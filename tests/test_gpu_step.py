@@ -170,7 +170,7 @@ def test_captured_step_replays_like_eager(T):
             dst.copy_(src)
         graph.replay()
     torch.cuda.synchronize()
-    assert int(graphed.step_dev.item()) == 4 == int(eager.step_dev.item())
+    assert int(graphed.step_dev[0].item()) == 4 == int(eager.step_dev[0].item())
     # the grid adjoints sum with atomics, so the two runs differ only by that
     # summation order: the loss and the MLP to FP32 rounding, the grids by far
     # less than one Adam step (lr = 0.1)
