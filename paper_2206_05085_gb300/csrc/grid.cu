@@ -214,35 +214,74 @@ __global__ void __launch_bounds__(256) scatter_bwd_kernel(const float* __restric
   }
 }
 
-// Density (1 channel) and feature (12 channels) adjoints in one pass.
+// Density (1 channel) and feature (12 channels) adjoints in one pass,
+// warp-aggregated: a warp takes 32 consecutive list positions, and two
+// neighbouring lanes whose samples lie in the same grid cell (consecutive
+// samples of a ray often do) are merged - the first lane adds the second
+// lane's weighted gradients to its own and issues one set of reductions for
+// both.  Pairs are formed greedily along each run of equal cells.
 __global__ void __launch_bounds__(256) scatter_bwd_1_12_kernel(
     const float* __restrict__ g_a, float* __restrict__ grid_a, uint8_t* __restrict__ touched_a,
     const float* __restrict__ g_b, float* __restrict__ grid_b, uint8_t* __restrict__ touched_b, TriArgs T,
     const float* __restrict__ xyz, const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* n_dev) {
   const int64_t n = live_n(n_cap, n_dev);
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j0 = warp0 * 32; j0 < n; j0 += nwarps * 32) {
+    const int64_t j = j0 + lane;
+    const bool valid = j < n;
     Corners c;
-    corners(T, xyz, s, c);
-    const float ga = __ldg(g_a + s);
-    float gb[12];
+    float ga = 0.0f, gb[12];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(g_b + s * 12) + q);
-      gb[4 * q] = v.x;
-      gb[4 * q + 1] = v.y;
-      gb[4 * q + 2] = v.z;
-      gb[4 * q + 3] = v.w;
+    for (int i = 0; i < 12; ++i) gb[i] = 0.0f;
+    int64_t key = -1 - lane;   // distinct for invalid lanes
+    if (valid) {
+      const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+      corners(T, xyz, s, c);
+      ga = __ldg(g_a + s);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(g_b + s * 12) + q);
+        gb[4 * q] = v.x;
+        gb[4 * q + 1] = v.y;
+        gb[4 * q + 2] = v.z;
+        gb[4 * q + 3] = v.w;
+      }
+      key = c.slot[0];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        c.w[k] = 0.0f;
+        c.slot[k] = 0;
+      }
     }
+    // lanes continuing the previous lane's cell; greedy pairing along runs
+    const int64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned same = __ballot_sync(0xffffffffu, lane > 0 && prev == key);
+    unsigned absorbed = 0u;
+    for (int i = 1; i < 32; ++i)
+      if (((same >> i) & 1u) && !((absorbed >> (i - 1)) & 1u)) absorbed |= 1u << i;
+    // the next lane's weights and gradients (used when it is absorbed into this one)
+    float wn[8], gan, gbn[12];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wn[k] = __shfl_down_sync(0xffffffffu, c.w[k], 1);
+    gan = __shfl_down_sync(0xffffffffu, ga, 1);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) gbn[i] = __shfl_down_sync(0xffffffffu, gb[i], 1);
+    if (!valid || ((absorbed >> lane) & 1u)) continue;
+    const bool pair = lane < 31 && ((absorbed >> (lane + 1)) & 1u);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      atomicAdd(grid_a + c.slot[k], c.w[k] * ga);
+      const float w0 = c.w[k], w1 = pair ? wn[k] : 0.0f;
+      atomicAdd(grid_a + c.slot[k], fmaf(w1, gan, w0 * ga));
       float4* p = reinterpret_cast<float4*>(grid_b + c.slot[k] * 12);
 #pragma unroll
       for (int q = 0; q < 3; ++q)
-        atomicAdd(p + q, make_float4(c.w[k] * gb[4 * q], c.w[k] * gb[4 * q + 1], c.w[k] * gb[4 * q + 2],
-                                     c.w[k] * gb[4 * q + 3]));
+        atomicAdd(p + q, make_float4(fmaf(w1, gbn[4 * q], w0 * gb[4 * q]),
+                                     fmaf(w1, gbn[4 * q + 1], w0 * gb[4 * q + 1]),
+                                     fmaf(w1, gbn[4 * q + 2], w0 * gb[4 * q + 2]),
+                                     fmaf(w1, gbn[4 * q + 3], w0 * gb[4 * q + 3])));
     }
     mark_touched(touched_a, T, c);
     mark_touched(touched_b, T, c);

@@ -143,6 +143,46 @@ def test_trilinear_adjoint_along_rays(L, C):
     assert np.all(got_t[tb])
 
 
+def test_trilinear_adjoint_pair_along_rays(L):
+    """The paired adjoint on ray-ordered samples (neighbouring list positions
+    often share a cell, so the warp merges them) against the oracle."""
+    rng = np.random.default_rng(45)
+    G = (40, 33, 37)
+    lo, hi = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0])
+    vs = 2.0 / 32
+    pts = []
+    for r in range(400):
+        o = rng.uniform(-0.9, 0.9, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        k = int(rng.choice([1, 2, 3, 33, 90]))
+        step = vs * rng.choice([0.1, 0.25, 0.5, 1.0])
+        pts.append(np.clip(o + d * step * np.arange(k)[:, None], -1.05, 1.05))
+    xyz = np.concatenate(pts).astype(np.float32)
+    n = len(xyz)
+    live = np.sort(rng.choice(n, int(0.9 * n), replace=False)).astype(np.int32)
+    ga = rng.normal(size=(n, 1)).astype(np.float32)
+    gb = rng.normal(size=(n, 12)).astype(np.float32)
+    gd = L.GridDesc.make(lo, hi, G)
+    nb = L.grid_num_bricks(G)
+    outs = [(torch.zeros(L.grid_bricked_elems(G, C), device="cuda"),
+             torch.zeros(nb, dtype=torch.uint8, device="cuda")) for C in (1, 12)]
+    n_dev = torch.tensor([len(live)], dtype=torch.int64, device="cuda")
+    L.sample_grid_bwd2(dev(ga), 1, outs[0][0], outs[0][1], dev(gb), 12, outs[1][0], outs[1][1], gd,
+                       dev(xyz), dev(live), n, n_dev)
+    for (g_grid, touched), C, g in zip(outs, (1, 12), (ga, gb)):
+        gg = torch.empty(G[2], G[1], G[0], C, device="cuda")
+        L.grid_unpack(g_grid, gg, G, C, L.F32)
+        ref = oracle.trilinear_adjoint(g[live], (G[2], G[1], G[0], C), lo, hi, xyz[live])
+        assert rel_err(host(gg), ref) < TOL32
+        nz = np.abs(ref).sum(-1) > 0
+        nbv = [(q + 7) // 8 for q in G]
+        tb = np.zeros((nbv[2], nbv[1], nbv[0]), bool)
+        zz, yy, xx = np.nonzero(nz)
+        tb[zz // 8, yy // 8, xx // 8] = True
+        assert np.all(host(touched).reshape(nbv[2], nbv[1], nbv[0]).astype(bool)[tb])
+
+
 def test_trilinear_adjoint_pair(L):
     """The paired density / feature adjoint equals the two single ones."""
     rng = np.random.default_rng(44)

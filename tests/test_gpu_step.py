@@ -172,11 +172,15 @@ def test_captured_step_replays_like_eager(T):
     torch.cuda.synchronize()
     assert int(graphed.step_dev[0].item()) == 4 == int(eager.step_dev[0].item())
     # the grid adjoints sum with atomics, so the two runs differ only by that
-    # summation order: the loss and the MLP to FP32 rounding, the grids by far
-    # less than one Adam step (lr = 0.1)
+    # summation order: the loss and the MLP to FP32 rounding; grid entries by
+    # far less than one Adam step (lr = 0.1), except the very few whose tiny
+    # gradient (a near-cancelling sum) changes sign with the order - Adam
+    # moves those by up to lr either way
     for a, b in ((eager.loss, graphed.loss), (eager.mlp, graphed.mlp)):
         a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
         assert np.max(np.abs(a - b)) <= 1e-5 * max(np.max(np.abs(a)), 1e-30)
     for a, b in ((eager.density.p, graphed.density.p), (eager.feature.p, graphed.feature.p)):
         a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
-        assert np.max(np.abs(a - b)) <= 1e-3 * rp.lr_grid
+        d = np.abs(a - b)
+        assert np.mean(d > 1e-3 * rp.lr_grid) < 1e-4
+        assert np.max(d) <= 2 * rp.lr_grid
