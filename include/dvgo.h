@@ -197,6 +197,13 @@ int dvgo_alpha_weights_fwd(const float* raw, const int64_t* ray_off, int64_t R, 
                            float interval, float T_stop, float* w, float* T, int32_t* n_live,
                            float* T_end, void* stream);
 
+/* The whole compositing forward of a ray batch in one call:
+ * dvgo_alpha_weights_fwd (raw -> w, T, n_live, T_end) followed by
+ * dvgo_composite_rgb_fwd (color).  Its adjoint is dvgo_composite_bwd. */
+int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_off, int64_t R,
+                       float shift, float interval, float T_stop, const float bg[3], float* color,
+                       float* w, float* T, int32_t* n_live, float* T_end, void* stream);
+
 /* Colour accumulation: color[r] = sum_{i < n_live[r]} w_i rgb_i + T_end[r] bg. */
 int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_off,
                            const int32_t* n_live, const float* T_end, int64_t R, const float bg[3],
@@ -392,6 +399,13 @@ int dvgo_touched_compact(const uint8_t* touched, int64_t nb, int32_t* list, int3
 int dvgo_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v, int64_t n,
                    uint8_t* touched, int64_t block_elems, float lr, float beta1, float beta2,
                    float eps, int64_t step, int zero_grad, void* stream);
+
+/* The sparse Adam step of a bricked grid (Sec. 3): dvgo_adam_step with the
+ * grid's brick flags (one uint8 per brick of 512 voxels, C channels each, so
+ * block_elems = 512 C); a NULL touched visits every brick and skips g == 0. */
+int dvgo_grid_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v,
+                        const int32_t G[3], int32_t C, uint8_t* touched, float lr, float beta1,
+                        float beta2, float eps, int64_t step, int zero_grad, void* stream);
 
 /* Several parameter arrays in one launch (density grid, feature grid, colour
  * MLP): params[i] behaves as dvgo_adam_step(params[i].p, .p_shadow, .g, .m,

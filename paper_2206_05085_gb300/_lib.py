@@ -94,6 +94,8 @@ def _declare(L):
         "dvgo_live_samples": ([P, P, I64, P, P, P, SZ, P], INT),
         "dvgo_alpha_weights_fwd": ([P, P, I64, F, F, F, P, P, P, P, P], INT),
         "dvgo_composite_rgb_fwd": ([P, P, P, P, P, I64, P, P, P], INT),
+        "dvgo_composite_fwd": ([P, P, P, I64, F, F, F, P, P, P, P, P, P, P], INT),
+        "dvgo_grid_adam_step": ([P, P, P, P, P, P, I32, P, F, F, F, F, I64, INT, P], INT),
         "dvgo_composite_bwd": ([P, P, P, P, P, P, P, I64, F, F, P, P, P, P], INT),
         "dvgo_distortion_fwd": ([P, P, P, P, P, I64, P, P], INT),
         "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
@@ -138,7 +140,7 @@ def exported_names():
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
         "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
         "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact",
-        "dvgo_adam_step_multi_dev"]
+        "dvgo_adam_step_multi_dev", "dvgo_composite_fwd", "dvgo_grid_adam_step"]
 
 
 def ptr(t):
@@ -250,6 +252,18 @@ def alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_
 def composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream=None):
     _call("dvgo_composite_rgb_fwd", ptr(w), ptr(rgb), ptr(ray_off), ptr(n_live), ptr(T_end), R,
           _vec3(bg, F), ptr(color), _stream(stream))
+
+
+def composite_fwd(raw, rgb, ray_off, R, shift, interval, T_stop, bg, color, w, T, n_live, T_end,
+                  stream=None):
+    _call("dvgo_composite_fwd", ptr(raw), ptr(rgb), ptr(ray_off), R, shift, interval, T_stop,
+          _vec3(bg, F), ptr(color), ptr(w), ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
+
+
+def grid_adam_step(p, p_shadow, g, m, v, G, C, touched, lr, beta1, beta2, eps, step, zero_grad,
+                   stream=None):
+    _call("dvgo_grid_adam_step", ptr(p), ptr(p_shadow), ptr(g), ptr(m), ptr(v), _vec3(G, I32), C,
+          ptr(touched), lr, beta1, beta2, eps, step, int(zero_grad), _stream(stream))
 
 
 def composite_bwd(g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, bg, g_raw,

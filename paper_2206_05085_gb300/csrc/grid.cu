@@ -910,3 +910,12 @@ extern "C" int dvgo_touched_compact(const uint8_t* touched, int64_t nb, int32_t*
   touched_compact_kernel<<<grid_for(nb, 256, 4), 256, 0, st>>>(touched, nb, list, count);
   return launch_status();
 }
+
+extern "C" int dvgo_grid_adam_step(float* p, uint16_t* p_shadow, float* g, float* m, float* v,
+                                   const int32_t G[3], int32_t C, uint8_t* touched, float lr, float beta1,
+                                   float beta2, float eps, int64_t step, int zero_grad, void* stream) {
+  DVGO_CHECK_ARG(G && C >= 1 && G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
+  const int64_t n = make_geom(G).num_bricks() * kBrickVox * C;
+  return dvgo_adam_step(p, p_shadow, g, m, v, n, touched, (int64_t)kBrickVox * C, lr, beta1, beta2, eps,
+                        step, zero_grad, stream);
+}

@@ -563,3 +563,13 @@ extern "C" int dvgo_composite_distortion_bwd(const float* g_color, float g_L, co
       g_raw);
   return launch_status();
 }
+
+extern "C" int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_off, int64_t R,
+                                  float shift, float interval, float T_stop, const float bg[3],
+                                  float* color, float* w, float* T, int32_t* n_live, float* T_end,
+                                  void* stream) {
+  const int r = dvgo_alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end,
+                                       stream);
+  if (r != DVGO_OK) return r;
+  return dvgo_composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream);
+}

@@ -742,6 +742,32 @@ def test_adam_step(L, sparse):
     assert rel_err(host(tq), rq) < TOL32
 
 
+def test_grid_adam_step(L):
+    """dvgo_grid_adam_step: the bricked-grid form (geometry instead of a
+    flat length; one flag per brick) = the oracle's Adam on the same data."""
+    rng = np.random.default_rng(13)
+    G, C = (21, 9, 17), 12
+    n = L.grid_bricked_elems(G, C)
+    nb = L.grid_num_bricks(G)
+    assert n == nb * 512 * C
+    p = rng.normal(size=n).astype(np.float32)
+    m = rng.normal(0, 0.1, n).astype(np.float32)
+    v = rng.uniform(0, 0.1, n).astype(np.float32)
+    g = np.zeros(n, np.float32)
+    flags = (rng.uniform(size=nb) < 0.5).astype(np.uint8)
+    for b in np.nonzero(flags)[0]:
+        blk = slice(b * 512 * C, (b + 1) * 512 * C)
+        g[blk] = np.where(rng.uniform(size=512 * C) < 0.7, rng.normal(size=512 * C), 0.0)
+    tp, tg, tm, tv, tf = dev(p), dev(g), dev(m), dev(v), dev(flags)
+    L.grid_adam_step(tp, None, tg, tm, tv, G, C, tf, 0.1, 0.9, 0.99, 1e-15, 3, True)
+    rp, rm, rv = oracle.adam(p, g, m, v, 0.1, 0.9, 0.99, 1e-15, 3)
+    assert rel_err(host(tp), rp) < TOL32
+    assert rel_err(host(tm), rm) < TOL32
+    assert rel_err(host(tv), rv) < TOL32
+    assert np.array_equal(host(tp)[g == 0], p[g == 0])
+    assert np.all(host(tg) == 0) and np.all(host(tf) == 0)
+
+
 def test_invalid_arguments_raise(L):
     with pytest.raises(L.DvgoError):
         L.distortion_fwd(None, None, None, None, None, 5, None)
