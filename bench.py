@@ -167,6 +167,9 @@ def per_kernel_times(tr, batches, flush, reps=5):
     try:
         for r in range(reps):
             flush.zero_()
+            # the host enqueues the whole step while the GPU spins (~1 ms), so
+            # that no interval includes host-side launch time
+            torch.cuda._sleep(2_000_000)
             seen.clear()
             o, d, t = batches[r % len(batches)]
             tr.step(o, d, t)

@@ -60,9 +60,6 @@ constexpr float kSH = 16.0f;     // hidden-activation scale
 constexpr float kRange = 32768.0f;
 constexpr uint32_t kSpin = 1u << 24;
 
-// forward shared memory
-constexpr uint32_t fW1h = 0, fW1l = fW1h + kW1Bytes, fW2h = fW1l + kW1Bytes,
-                   fW2l = fW2h + kW2Bytes, fImg = fW2l + kW2Bytes, fEnd = fImg + kImage;
 // backward shared memory
 constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
                    bW1l = bW1h + kW1sBytes, bImg = bW1l + kW1sBytes, bGh = bImg + kImage,
@@ -79,7 +76,6 @@ struct Side {
   uint64_t bar_mma;
   uint32_t tmem_slot;
 };
-static_assert(fEnd + sizeof(Side) <= 227 * 1024, "forward shared memory");
 static_assert(bEnd + sizeof(Side) <= 227 * 1024, "backward shared memory");
 
 // Largest value of v over the block (all threads call it).
@@ -174,18 +170,99 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint3
 }
 
 // Output-layer constants (exact FP32).
-__device__ __forceinline__ void load_out_layer(const float* __restrict__ params, Side* fs) {
+template <class SideT>
+__device__ __forceinline__ void load_out_layer(const float* __restrict__ params, SideT* fs) {
   for (int o = threadIdx.x; o < kHid; o += blockDim.x)
     fs->ob[o] = make_float4(params[kOffB2 + o], params[kOffW3 + o], params[kOffW3 + kHid + o],
                             params[kOffW3 + 2 * kHid + o]);
   if (threadIdx.x < 4) fs->b3[threadIdx.x] = threadIdx.x < kOut ? params[kOffB3 + threadIdx.x] : 0.0f;
 }
 
-// W2 (scaled by s) as split K-major core matrices [o][i].
+// This thread's share of max |p[e]|, e < count (float4 loads, four in
+// flight per thread, when p is 16-byte aligned and count a multiple of 4).
+__device__ __forceinline__ float abs_max_part(const float* __restrict__ p, int count) {
+  float m = 0.0f;
+  if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (count & 3) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const int n4 = count >> 2;
+    for (int e0 = threadIdx.x; e0 < n4; e0 += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < n4 ? __ldg(p4 + e) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+    }
+  } else {
+    for (int e = threadIdx.x; e < count; e += blockDim.x) m = fmaxf(m, fabsf(__ldg(p + e)));
+  }
+  return m;
+}
+
+// Rows o of W1 | b1 | 0 (width K = 8 kb, the bias in column kIn when K > kIn),
+// scaled by s, as split K-major core matrices [o][k]; 8 columns per chunk.
+template <int K>
+__device__ __forceinline__ void load_w1(const float* __restrict__ params, uint8_t* hi, uint8_t* lo, uint32_t sbo,
+                                        float s) {
+  constexpr int kB = K / 8, kChunks = kHid * kB;
+  float dummy = 0.0f;
+  for (int c0 = threadIdx.x; c0 < kChunks; c0 += 2 * blockDim.x) {
+    float v[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int c = c0 + u * blockDim.x, o = c / kB, k8 = (c % kB) * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = k8 + i;
+        v[u][i] = c >= kChunks ? 0.0f
+                               : (k < kIn ? __ldg(params + kOffW1 + o * kIn + k)
+                                          : (k == kIn ? __ldg(params + kOffB1 + o) : 0.0f));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int c = c0 + u * blockDim.x;
+      if (c < kChunks) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[u][i] *= s;
+        st_split8(hi, lo, c / kB, (c % kB) * 8, sbo, v[u], dummy);
+      }
+    }
+  }
+}
+
+// W2 (scaled by s) as split K-major core matrices [o][i]; 8 columns per chunk.
 __device__ __forceinline__ void load_w2(const float* __restrict__ params, uint8_t* hi, uint8_t* lo, float s) {
-  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
-    const int o = e / kHid, i = e % kHid;
-    st_split1(hi, lo, tc::cm_off(o, i, kSboH), s * params[kOffW2 + e]);
+  const float* w = params + kOffW2;
+  float dummy = 0.0f;
+  if ((reinterpret_cast<uintptr_t>(w) & 15u) != 0) {
+    for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x)
+      st_split1(hi, lo, tc::cm_off(e / kHid, e % kHid, kSboH), s * __ldg(w + e));
+    return;
+  }
+  constexpr int kChunks = kHid * kHid / 8;
+  for (int c0 = threadIdx.x; c0 < kChunks; c0 += 4 * blockDim.x) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * blockDim.x;
+      if (c < kChunks) {
+        a[u] = __ldg(reinterpret_cast<const float4*>(w + 8 * c));
+        b[u] = __ldg(reinterpret_cast<const float4*>(w + 8 * c + 4));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * blockDim.x;
+      if (c < kChunks) {
+        float v[8] = {s * a[u].x, s * a[u].y, s * a[u].z, s * a[u].w,
+                      s * b[u].x, s * b[u].y, s * b[u].z, s * b[u].w};
+        st_split8(hi, lo, c >> 4, (c & 15) * 8, kSboH, v, dummy);
+      }
+    }
   }
 }
 
@@ -196,12 +273,9 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_mlp_tc_statu
 using namespace x3;
 
 // ------------------------------------------------------------------ forward
-// 512 threads: the four warps w, w + 4, w + 8, w + 12 share TMEM lane quarter
-// w & 3 (tile rows 32 (w & 3) .. + 31); warp quarter q = w / 4 takes hidden
-// columns 32 q .. 32 q + 31 and a quarter of the input columns.  The next
-// tile's inputs are loaded in three dependent steps spread over the current
-// tile (list index; feature row and ray id; direction), so their latency
-// hides behind the MMAs.
+// Row inputs of the forward: the next tile's inputs are loaded in three
+// dependent steps spread over the current tile (list index; feature row and
+// ray id; direction), so their latency hides behind other work.
 struct RowIn {
   int64_t s;       // sample index (-1 past the list end)
   int32_t r;       // ray id
@@ -268,178 +342,295 @@ __device__ __forceinline__ void quarter_x(const RowIn& in, int q, float v[16]) {
   }
 }
 
-__global__ void __launch_bounds__(512, 1) rgbnet_fwd_tc_kernel(
+// Forward shared memory: split W1 and W2 (resident), two X buffers, and the
+// staging copy of a tile's split H1 for the image.
+constexpr uint32_t gW1h = 0, gW1l = gW1h + kW1Bytes, gW2h = gW1l + kW1Bytes, gW2l = gW2h + kW2Bytes,
+                   gX0 = gW2l + kW2Bytes, gXBuf = 2 * kXBytes, gStage = gX0 + 2 * gXBuf,
+                   gEnd = gStage + 2 * kHBytes;
+
+struct FwdSide {
+  float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
+  float b3[4];
+  float red[32];         // block_max scratch: one entry per warp (17 warps)
+  uint64_t x_full[2];    // X of the tile in buffer b written (16 warp arrivals)
+  uint64_t l1_full[2];   // layer-1 MMAs of buffer b done (X buffer b free again)
+  uint64_t h1_full[2];   // H1 of buffer b stored in tensor memory (16 warp arrivals)
+  uint64_t l2_full[2];   // layer-2 MMAs of buffer b done
+  uint64_t fin;          // every MMA of the kernel done
+  uint32_t tmem_slot;
+  int abort;             // a wait gave up: later waits return at once
+};
+static_assert(gEnd + sizeof(FwdSide) + 2 * 4 * kTile * kOut * sizeof(float) <= 227 * 1024,
+              "forward shared memory");
+
+// Bounded wait shared by all roles of the forward; after the first timeout
+// every later wait returns false immediately, so that all threads still
+// reach the same barriers and the kernel ends.
+__device__ __forceinline__ bool fwd_wait(FwdSide* fs, uint64_t* bar, uint32_t parity) {
+  if (*reinterpret_cast<volatile int*>(&fs->abort)) return false;
+  if (tc::mbar_wait(bar, parity, kSpin)) return true;
+  *reinterpret_cast<volatile int*>(&fs->abort) = 1;
+  set_status(DVGO_ERR_TIMEOUT);
+  return false;
+}
+
+// 544 threads.  Warps 0-15 compute (warp w: TMEM lane quarter w & 3 = tile
+// rows 32 (w & 3) .. + 31, column quarter w / 4 = hidden columns 32 (w / 4)
+// .. + 31 and a quarter of the input columns); warp 16 issues the MMAs, so
+// that the tensor core runs while the compute warps work on other tiles.
+// Two tiles are in flight, in tensor-memory buffers b = 0, 1 of 256 columns:
+// columns 0-127 take D1 and then, in place, H1 split into FP16 hi / lo (the
+// A operand of layer 2, read from tensor memory), columns 128-255 take D2.
+// Column quarter q of H1 sits in columns 32 q .. 32 q + 31 of the buffer:
+// hi terms of k = 32 q .. 32 q + 31 packed two per column in the first 16,
+// lo terms in the next 16 (so each thread overwrites only the D1 columns it
+// has read).  X (the layer-1 A operand) is double-buffered in shared memory.
+// The tile image in the act buffer (the layout the backward loads) is written
+// by bulk copies that the MMA warp issues: X from its buffer, H1 from a
+// shared-memory staging copy that the compute warps fill beside the TMEM one.
+// Before the layer-1 MMAs of tile k are committed the MMA thread waits until
+// those copies have read their sources, so l1_full(k) also tells the compute
+// warps that the staging area and X buffer k & 1 may be rewritten.
+//
+// Order per tile k of this CTA (b = k & 1):
+//   compute: wait l1_full(k) -> H1(k) into TMEM and the image -> arrive
+//            h1_full(k); write X(k + 1) -> arrive x_full(k + 1); wait
+//            l2_full(k - 1) -> output layer and sigmoid of tile k - 1.
+//   MMA:     wait h1_full(k - 1) -> layer 2 of k - 1 -> commit l2_full(k - 1);
+//            wait x_full(k) (and l2_full(k - 2): buffer b's H1 read) -> layer 1
+//            of k -> commit l1_full(k).
+__global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
     const float* __restrict__ k0, const float* __restrict__ rays_d, const int32_t* __restrict__ ray_id,
     const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* __restrict__ n_dev,
     const float* __restrict__ params, float* __restrict__ rgb, uint8_t* __restrict__ act) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  Side* fs = reinterpret_cast<Side*>(sm + fEnd);
-  float* zx = reinterpret_cast<float*>(sm + fEnd + sizeof(Side));   // [4][128][3] output-layer partials
+  FwdSide* fs = reinterpret_cast<FwdSide*>(sm + gEnd);
+  float* zx_all = reinterpret_cast<float*>(sm + gEnd + sizeof(FwdSide));  // [2][4][128][3]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int qw = warp >> 2, row = (warp & 3) * 32 + lane;
+  const int lq = warp & 3, qw = warp >> 2, row = lq * 32 + lane;   // compute warps
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
-  if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 256);
+  const int64_t nt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // the first tile's row inputs are fetched while the weights are prepared
+  RowIn in;
+  if (warp < 16 && nt > 0) row_in_l1(in, idx, (int64_t)blockIdx.x * kTile + row, n);
+  if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
   if (tid == 0) {
-    tc::mbar_init(&fs->bar_h, 1);     // layer-1 MMAs done
-    tc::mbar_init(&fs->bar_mma, 1);   // layer-2 MMAs done
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&fs->x_full[b], 16);
+      tc::mbar_init(&fs->l1_full[b], 1);
+      tc::mbar_init(&fs->h1_full[b], 16);
+      tc::mbar_init(&fs->l2_full[b], 1);
+    }
+    tc::mbar_init(&fs->fin, 1);
+    fs->abort = 0;
   }
   // weights: W1 | b1 (column 39) and W2, split, each with its own scale
-  float m1 = 0.0f, m2 = 0.0f;
-  for (int e = tid; e < kHid * kIn + kHid; e += blockDim.x) m1 = fmaxf(m1, fabsf(params[kOffW1 + e]));
-  for (int e = tid; e < kHid * kHid; e += blockDim.x) m2 = fmaxf(m2, fabsf(params[kOffW2 + e]));
+  const float m1 = abs_max_part(params + kOffW1, kHid * kIn + kHid);
+  const float m2 = abs_max_part(params + kOffW2, kHid * kHid);
   const float sW1 = pow2_scale(block_max(m1, fs->red));
   const float sW2 = pow2_scale(block_max(m2, fs->red));
-  for (int e = tid; e < kHid * kK1; e += blockDim.x) {
-    const int o = e / kK1, k = e % kK1;
-    const float v = k < kIn ? params[kOffW1 + o * kIn + k] : (k == kIn ? params[kOffB1 + o] : 0.0f);
-    st_split1(sm + fW1h, sm + fW1l, tc::cm_off(o, k, kSboX), sW1 * v);
-  }
-  load_w2(params, sm + fW2h, sm + fW2l, sW2);
+  if (warp < 16 && nt > 0) row_in_l2(in, k0, ray_id, qw == 0);
+  load_w1<kK1>(params, sm + gW1h, sm + gW1l, kSboX, sW1);
+  load_w2(params, sm + gW2h, sm + gW2l, sW2);
   load_out_layer(params, fs);
-  const float inv1 = 1.0f / (kSX * sW1), inv2 = 1.0f / (kSH * sW2);
+  if (warp < 16 && nt > 0) row_in_l3(in, rays_d);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t sW1h = tc::smem_u32(sm + fW1h), sW1l = tc::smem_u32(sm + fW1l);
-  const uint32_t sW2h = tc::smem_u32(sm + fW2h), sW2l = tc::smem_u32(sm + fW2l);
-  uint8_t* img = sm + fImg;
-  const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
-  const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
-  const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
   uint8_t* act_img = act + kActHeader;
-  uint32_t ph1 = 0, ph2 = 0;
-  bool ok = true;
   float vmax = 0.0f;
-  const int64_t step = gridDim.x;
+  auto tile_of = [&](int64_t k) { return (int64_t)blockIdx.x + k * (int64_t)gridDim.x; };
 
-  // Software pipeline over this CTA's tiles t0, t1 = t0 + step, ...  While
-  // the layer-2 MMAs of tile t run, the threads write X of tile t + step and
-  // issue its layer-1 MMAs; while those run, they finish tile t's output layer.
-  // The X and H1 parts of each tile image are stored by separate bulk copies,
-  // so X of the next tile may be written as soon as the X copy has read it.
-  RowIn in, nxt;   // inputs of the tile whose X is written next / the one after
-  auto load_rows = [&](RowIn& r, int64_t tile) {
-    row_in_l1(r, idx, tile * kTile + row, n);
-    row_in_l2(r, k0, ray_id, qw == 0);
-    row_in_l3(r, rays_d);
-  };
-  auto write_x = [&](const RowIn& r) {
-    float x[16];
-    quarter_x(r, qw, x);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) x[i] *= kSX;
-    const int fb = x_first_block(qw);
-    st_split8(img + iXh, img + iXl, row, fb * 8, kSboX, x, vmax);
-    if (x_num_blocks(qw) == 2) st_split8(img + iXh, img + iXl, row, fb * 8 + 8, kSboX, x + 8, vmax);
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-  };
-  auto issue_l1 = [&](int64_t tile) {   // thread 0
-    tc::fence_after_sync();
-    mma3(tmem, sXh, sXl, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
-    tc::mma_commit(&fs->bar_h);
-    tc::bulk_s2g(act_img + (size_t)tile * kImage + iXh, img + iXh, 2 * kXBytes);
-  };
-  // H1 = relu(D1) of a tile, split; then its layer-2 MMAs and the H1 copy
-  auto layer1_out = [&](int64_t tile) -> bool {
-    bool r = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph1, kSpin));
-    ph1 ^= 1;
-    if (!r) return false;
-    tc::fence_after_sync();
-    {
-      float v[32];
-      tc::tmem_ld32(lane_base + 32 * qw, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = kSH * fmaxf(v[i] * inv1, 0.0f);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(img + iHh, img + iHl, row, 32 * qw + q * 8, kSboH, v + 8 * q, vmax);
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
+  if (warp == 16) {
+    // ------------------------------------------------------------ MMA warp
+    const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
+    const uint32_t sW1h = tc::smem_u32(sm + gW1h), sW1l = tc::smem_u32(sm + gW1l);
+    const uint32_t sW2h = tc::smem_u32(sm + gW2h), sW2l = tc::smem_u32(sm + gW2l);
+    // lane 0 polls; the outcome is the warp's
+    auto wait0 = [&](uint64_t* bar, uint32_t parity) -> bool {
+      int r = 0;
+      if (lane == 0) r = fwd_wait(fs, bar, parity) ? 1 : 0;
+      return __shfl_sync(0xffffffffu, r, 0) != 0;
+    };
+    auto layer2 = [&](int64_t k) {
+      const uint32_t b = (uint32_t)(k & 1), buf = tmem + 256u * b;
+      if (!wait0(&fs->h1_full[b], (uint32_t)(k >> 1) & 1u)) return;
       tc::fence_after_sync();
-      mma3(tmem + 128, sHh, sHl, 256, 128, kSboH, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
-      tc::mma_commit(&fs->bar_mma);
-      tc::bulk_s2g(act_img + (size_t)tile * kImage + iHh, img + iHh, 2 * kHBytes);
-    }
-    return true;
-  };
-
-  int64_t t = blockIdx.x;
-  if (t < ntiles) {
-    load_rows(in, t);
-    write_x(in);
-    int64_t s_t = in.s;
-    if (tid == 0) issue_l1(t);
-    load_rows(in, t + step);
-    ok = layer1_out(t);
-    while (ok) {
-      const int64_t tn = t + step;
-      const bool more = tn < ntiles;
-      // X (and layer 1) of the next tile, once its X region has been read out
-      if (more) {
-        if (tid == 0) tc::bulk_wait_read_allow1();   // the older group: X copy of tile t
-        __syncthreads();
-        write_x(in);
-        if (tid == 0) issue_l1(tn);
+      if (lane == 0) {
+        tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iHh, sm + gStage, 2 * kHBytes);
+        uint64_t dbh = tc::smem_desc(sW2h, 128, kSboH), dbl = tc::smem_desc(sW2l, 128, kSboH);
+#pragma unroll 1
+        for (uint32_t j = 0; j < kHid / 16; ++j) {
+          const uint32_t ah = buf + 32u * (j >> 1) + 8u * (j & 1u), al = ah + 16u;
+          tc::mma_ts(buf + 128u, ah, dbh, id128, j > 0 ? 1u : 0u);
+          tc::mma_ts(buf + 128u, ah, dbl, id128, 1u);
+          tc::mma_ts(buf + 128u, al, dbh, id128, 1u);
+          dbh += 256 >> 4;
+          dbl += 256 >> 4;
+        }
+        tc::mma_commit(&fs->l2_full[b]);
       }
-      const int64_t s_n = in.s;
-      if (more) row_in_l1(nxt, idx, (tn + step) * kTile + row, n);
-      // output layer of tile t
-      ok = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, ph2, kSpin));
-      ph2 ^= 1;
-      if (!ok) break;
+      __syncwarp();
+    };
+    auto layer1 = [&](int64_t k) {
+      const uint32_t b = (uint32_t)(k & 1), buf = tmem + 256u * b;
+      if (!wait0(&fs->x_full[b], (uint32_t)(k >> 1) & 1u)) return;
+      // buffer b's H1 (tile k - 2) has been read by its layer-2 MMAs
+      if (k >= 2 && !wait0(&fs->l2_full[b], (uint32_t)((k - 2) >> 1) & 1u)) return;
       tc::fence_after_sync();
-      if (more) row_in_l2(nxt, k0, ray_id, qw == 0);
+      if (lane == 0) {
+        uint8_t* xb = sm + gX0 + b * gXBuf;
+        tc::bulk_wait_read();   // staging (H1 of k - 1) and X buffer b's older copy are read
+        tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iXh, xb, 2 * kXBytes);
+        const uint32_t xs = tc::smem_u32(xb);
+        mma3(buf, xs, xs + kXBytes, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
+        tc::mma_commit(&fs->l1_full[b]);
+      }
+      __syncwarp();
+    };
+    // issue order: L1(0), then per k: L2(k - 1) as soon as H1(k - 1) is in, L1(k)
+    if (nt > 0) layer1(0);
+    for (int64_t k = 1; k < nt; ++k) {
+      layer2(k - 1);
+      layer1(k);
+    }
+    if (nt > 0) layer2(nt - 1);
+    // every MMA and copy this thread issued has finished before the memory is released
+    if (lane == 0) {
+      tc::mma_commit(&fs->fin);
+      tc::mbar_wait(&fs->fin, 0, kSpin);
+      tc::bulk_wait_all();
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------- compute warps
+    const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
+    const float inv1 = kSH / (kSX * sW1), inv2 = 1.0f / (kSH * sW2);
+    const int fb = x_first_block(qw), nb = x_num_blocks(qw);
+    auto load_rows = [&](int64_t k) {
+      row_in_l1(in, idx, tile_of(k) * kTile + row, n);
+      row_in_l2(in, k0, ray_id, qw == 0);
+      row_in_l3(in, rays_d);
+    };
+    // X of tile k (rows loaded in `in`) into buffer k & 1 and the image
+    auto write_x = [&](int64_t k) {
+      float x[16];
+      quarter_x(in, qw, x);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] *= kSX;
+      uint8_t* xs = sm + gX0 + (k & 1) * gXBuf;
+      st_split8(xs, xs + kXBytes, row, fb * 8, kSboX, x, vmax);
+      if (nb == 2) st_split8(xs, xs + kXBytes, row, fb * 8 + 8, kSboX, x + 8, vmax);
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fs->x_full[k & 1]);
+    };
+    // H1 of tile k: relu(D1) scaled, split, into TMEM (in place) and the staging area
+    auto layer1_out = [&](int64_t k) {
+      const uint32_t b = (uint32_t)(k & 1);
+      const uint32_t taddr = tmem + 256u * b + lane_off + 32u * qw;
+      fwd_wait(fs, &fs->l1_full[b], (uint32_t)(k >> 1) & 1u);
+      tc::fence_after_sync();
+      uint32_t hl[32];
+      {
+        float v[32];
+        tc::tmem_ld32(taddr, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float a = fmaxf(v[2 * c] * inv1, 0.0f), bb = fmaxf(v[2 * c + 1] * inv1, 0.0f);
+          vmax = fmaxf(vmax, fmaxf(a, bb));
+          const __half2 h2 = __floats2half2_rn(a, bb);
+          const float2 hf = __half22float2(h2);
+          const __half2 l2 = __floats2half2_rn(a - hf.x, bb - hf.y);
+          hl[c] = *reinterpret_cast<const uint32_t*>(&h2);
+          hl[16 + c] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+      }
+      tc::tmem_st32(taddr, hl);
+      uint8_t* st = sm + gStage;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t off = tc::cm_off(row, 32 * qw + 8 * q, kSboH);
+        *reinterpret_cast<uint4*>(st + off) = make_uint4(hl[4 * q], hl[4 * q + 1], hl[4 * q + 2], hl[4 * q + 3]);
+        *reinterpret_cast<uint4*>(st + kHBytes + off) =
+            make_uint4(hl[16 + 4 * q], hl[17 + 4 * q], hl[18 + 4 * q], hl[19 + 4 * q]);
+      }
+      tc::fence_proxy_async_smem();
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fs->h1_full[b]);
+    };
+    // output layer and sigmoid of tile k (sample index s of this row)
+    auto layer2_out = [&](int64_t k, int64_t s) {
+      const uint32_t b = (uint32_t)(k & 1);
+      fwd_wait(fs, &fs->l2_full[b], (uint32_t)(k >> 1) & 1u);
+      tc::fence_after_sync();
       float z3[kOut] = {0.0f, 0.0f, 0.0f};
       {
         float v[32];
-        tc::tmem_ld32(lane_base + 128 + 32 * qw, v);
+        tc::tmem_ld32(tmem + 256u * b + 128u + lane_off + 32u * qw, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int o = 32 * qw + i;
-          const float4 q = fs->ob[o];
+          const float4 q = fs->ob[32 * qw + i];
           const float h = fmaxf(fmaf(v[i], inv2, q.x), 0.0f);
           z3[0] = fmaf(q.y, h, z3[0]);
           z3[1] = fmaf(q.z, h, z3[1]);
           z3[2] = fmaf(q.w, h, z3[2]);
         }
       }
+      float* zx = zx_all + b * (4 * kTile * kOut);
 #pragma unroll
       for (int c = 0; c < kOut; ++c) zx[(qw * kTile + row) * kOut + c] = z3[c];
-      // the H1 region is free once tile t's H1 copy has read it
-      if (tid == 0) tc::bulk_wait_read_allow1();    // pending: the X copy of tile tn at most
-      tc::fence_before_sync();
-      __syncthreads();
-      if (qw == 0 && s_t >= 0) {
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) {
-          const float* zc = zx + row * kOut + c;
-          const float z = ((zc[0] + zc[kTile * kOut]) + zc[2 * kTile * kOut]) + zc[3 * kTile * kOut];
-          rgb[3 * s_t + c] = sigmoid_f(fs->b3[c] + z);
-        }
+      tc::named_sync(1 + lq, 128);
+      if (qw < kOut && s >= 0) {   // quarter qw finishes output channel qw
+        const float* zc = zx + row * kOut + qw;
+        const float z = ((zc[0] + zc[kTile * kOut]) + zc[2 * kTile * kOut]) + zc[3 * kTile * kOut];
+        rgb[3 * s + qw] = sigmoid_f(fs->b3[qw] + z);
       }
-      if (!more) break;
-      if (more) row_in_l3(nxt, rays_d);
-      ok = layer1_out(tn);
-      in = nxt;
-      s_t = s_n;
-      t = tn;
+    };
+    auto idx_of = [&](int64_t k) -> int64_t {
+      const int64_t j = tile_of(k) * kTile + row;
+      return j < n ? (idx ? (int64_t)__ldg(idx + j) : j) : -1;
+    };
+    // Per tile k: H1(k); X(k + 1); output layer of k - 1.  The three dependent
+    // loads of a tile's rows (list index; feature row and ray id; direction)
+    // are spread over the two iterations before its X is written.
+    int64_t s_prev = -1, s_cur = -1, s_nn = -1;   // this row's sample in tiles k - 1, k, k + 2
+    if (nt > 0) {
+      write_x(0);
+      s_cur = in.s;
+      if (nt > 1) load_rows(1);
+      if (nt > 2) s_nn = idx_of(2);
     }
+    for (int64_t k = 0; k < nt; ++k) {
+      layer1_out(k);
+      int64_t s_next = -1;
+      if (k + 1 < nt) {
+        write_x(k + 1);
+        s_next = in.s;
+      }
+      if (k + 2 < nt) {
+        in.s = s_nn;
+        row_in_l2(in, k0, ray_id, qw == 0);
+      }
+      if (k >= 1) layer2_out(k - 1, s_prev);
+      if (k + 2 < nt) row_in_l3(in, rays_d);
+      if (k + 3 < nt) s_nn = idx_of(k + 3);
+      s_prev = s_cur;
+      s_cur = s_next;
+    }
+    if (nt > 0) layer2_out(nt - 1, s_prev);
+    __syncwarp();
   }
-  if (tid == 0) tc::bulk_wait_all();
-  if (!ok && tid == 0) set_status(DVGO_ERR_TIMEOUT);
   if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------- upstream gradient bound
@@ -510,16 +701,38 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const int qw = warp >> 2, row = (warp & 3) * 32 + lane;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
+  const uint8_t* img_g = act + kActHeader;
+  uint8_t* img = sm + bImg;
+  bool inflight_h = false, inflight_x = false;   // thread 0: copies not yet waited for
+  auto load_h = [&](int64_t tile) {
+    tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
+    tc::bulk_g2s(img + iHh, img_g + (size_t)tile * kImage + iHh, 2 * kHBytes, &fs->bar_h);
+    inflight_h = true;
+  };
+  auto load_x = [&](int64_t tile) {
+    tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
+    tc::bulk_g2s(img + iXh, img_g + (size_t)tile * kImage + iXh, 2 * kXBytes, &fs->bar_x);
+    inflight_x = true;
+  };
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
   if (tid == 0) {
     tc::mbar_init(&fs->bar_h, 1);
     tc::mbar_init(&fs->bar_x, 1);
     tc::mbar_init(&fs->bar_mma, 1);
+    // the first image and upstream rows are fetched while the weights are prepared
+    if ((int64_t)blockIdx.x < ntiles) {
+      load_h(blockIdx.x);
+      load_x(blockIdx.x);
+    }
   }
+  UpIn cur, nxt;
+  up_l1(cur, idx, (int64_t)blockIdx.x * kTile + row, n);
   // scales: W2 and W1[:, 0:16] per matrix; G2 from the upstream bound, G1 from G2's
-  float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
-  for (int e = tid; e < kHid * 16; e += blockDim.x) m1 = fmaxf(m1, fabsf(params[kOffW1 + (e >> 4) * kIn + (e & 15)]));
-  for (int e = tid; e < kHid * kHid; e += blockDim.x) m2 = fmaxf(m2, fabsf(params[kOffW2 + e]));
+  float m1 = 0.0f, m3 = 0.0f;
+#pragma unroll 4
+  for (int e = tid; e < kHid * 16; e += blockDim.x)
+    m1 = fmaxf(m1, fabsf(__ldg(params + kOffW1 + (e >> 4) * kIn + (e & 15))));
+  const float m2 = abs_max_part(params + kOffW2, kHid * kHid);
   for (int o = tid; o < kHid; o += blockDim.x) {
     float a = 0.0f;
 #pragma unroll
@@ -536,16 +749,13 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const float w21 = mw2 * (float)kHid;
   const float S2 = pow2_scale(0.25f * gmax * mw3);
   const float S1 = pow2_scale(0.25f * gmax * mw3 * w21);
+  up_l2(cur, g_rgb, w, ray_id);
   // W1[:, 0:16] as split [o][k] rows for g_X = G1 W1[:, 0:16]
-  for (int e = tid; e < kHid * 16; e += blockDim.x) {
-    const int o = e >> 4, k = e & 15;
-    st_split1(sm + bW1h, sm + bW1l, tc::cm_off(o, k, kSboW1s), sW1 * params[kOffW1 + o * kIn + k]);
-  }
+  load_w1<16>(params, sm + bW1h, sm + bW1l, kSboW1s, sW1);
   load_w2(params, sm + bW2h, sm + bW2l, sW2);
   load_out_layer(params, fs);
+  up_l3(cur, g_rgb, g_color);
   const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
-  const uint8_t* img_g = act + kActHeader;
-  uint8_t* img = sm + bImg;
   float* zx = reinterpret_cast<float*>(sm + bGh);  // [4][128][3] output-layer partials (G is free then)
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -566,31 +776,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   uint32_t ph_in = 0, ph_mma = 0;
   bool ok = true, dw_started = false;
   float vmax = 0.0f;   // largest magnitude split (range check)
-  bool inflight_h = false, inflight_x = false;   // thread 0: copies not yet waited for
-  auto load_h = [&](int64_t tile) {
-    tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
-    tc::bulk_g2s(img + iHh, img_g + (size_t)tile * kImage + iHh, 2 * kHBytes, &fs->bar_h);
-    inflight_h = true;
-  };
-  auto load_x = [&](int64_t tile) {
-    tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
-    tc::bulk_g2s(img + iXh, img_g + (size_t)tile * kImage + iXh, 2 * kXBytes, &fs->bar_x);
-    inflight_x = true;
-  };
-  if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
-    load_h(blockIdx.x);
-    load_x(blockIdx.x);
-  }
   auto mma_wait = [&]() -> bool {
     const bool r = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, ph_mma, kSpin));
     ph_mma ^= 1;
     tc::fence_after_sync();
     return r;
   };
-  UpIn cur, nxt;
-  up_l1(cur, idx, (int64_t)blockIdx.x * kTile + row, n);
-  up_l2(cur, g_rgb, w, ray_id);
-  up_l3(cur, g_rgb, g_color);
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int64_t tn = t + gridDim.x;   // this CTA's next tile
     const bool valid = cur.s >= 0;
@@ -858,14 +1049,14 @@ int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
 int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
                           const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
                           float* rgb, float* act, cudaStream_t st) {
-  const size_t smem = fEnd + sizeof(Side) + 4 * kTile * kOut * sizeof(float);
+  const size_t smem = gEnd + sizeof(FwdSide) + 2 * 4 * kTile * kOut * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(rgbnet_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_fwd_tc_kernel<<<grid, 512, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
+  rgbnet_fwd_tc_kernel<<<grid, 544, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
                                                 reinterpret_cast<uint8_t*>(act));
   return launch_status();
 }
