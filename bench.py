@@ -605,7 +605,7 @@ def main():
     e2e = res["e2e_samples"] / (res["e2e_total_ms"] * 1e-3)
     per_call = dict(KERNELS_PER_CALL)
     if res["prec"] == "f32tc":
-        per_call["dvgo_rgbnet_bwd"] = 3
+        per_call["dvgo_rgbnet_bwd"] = 2
     launches_per_step = sum(v["calls_per_step"] * per_call.get(k, 1) for k, v in res["kt"].items())
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "ray-samples/s", "n_gpus": args.gpus,

@@ -633,29 +633,6 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// ------------------------------------------------- upstream gradient bound
-// act header word 0 (zeroed by the host) <- max over the list of |g_rgb|.
-__global__ void __launch_bounds__(256) grad_bound_kernel(const float* __restrict__ g_rgb,
-                                                         const float* __restrict__ g_color,
-                                                         const float* __restrict__ w,
-                                                         const int32_t* __restrict__ ray_id,
-                                                         const int32_t* __restrict__ idx, int64_t n_cap,
-                                                         const int64_t* __restrict__ n_dev,
-                                                         unsigned int* __restrict__ out) {
-  __shared__ float red[8];
-  const int64_t n = mlp_count(n_cap, n_dev);
-  float m = 0.0f;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
-    float g[3];
-    upstream_rgb_grad(g_rgb, g_color, w, ray_id, s, g);
-    m = fmaxf(m, fmaxf(fabsf(g[0]), fmaxf(fabsf(g[1]), fabsf(g[2]))));
-  }
-  m = block_max(m, red);
-  if (threadIdx.x == 0) atomicMax(out, __float_as_uint(m));
-}
-
 // ----------------------------------------------------------------- backward
 // Same thread layout as the forward (512 threads, four warp quarters per TMEM
 // lane quarter, quarter q on hidden columns 32 q .. 32 q + 31).  The upstream colour
@@ -743,7 +720,31 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const float mw2 = block_max(m2, fs->red);
   const float mw3 = block_max(m3, fs->red);
   const float sW1 = pow2_scale(mw1), sW2 = pow2_scale(mw2);
-  const float gmax = __uint_as_float(*reinterpret_cast<const unsigned int*>(act));
+  // Largest upstream colour gradient over this CTA's own tiles.  S2 and S1
+  // need only be uniform within the CTA: its partial gradient row carries
+  // its own scale.
+  float gm = 0.0f;
+  {
+    const int64_t nt = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t cnt = nt * kTile;
+    for (int64_t e0 = tid; e0 < cnt; e0 += 4 * (int64_t)blockDim.x) {
+      int64_t sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + u * (int64_t)blockDim.x;
+        const int64_t j = ((int64_t)blockIdx.x + (e / kTile) * gridDim.x) * kTile + e % kTile;
+        sv[u] = (e < cnt && j < n) ? (idx ? (int64_t)__ldg(idx + j) : j) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (sv[u] < 0) continue;
+        float g[kOut];
+        upstream_rgb_grad(g_rgb, g_color, w, ray_id, sv[u], g);
+        gm = fmaxf(gm, fmaxf(fabsf(g[0]), fmaxf(fabsf(g[1]), fabsf(g[2]))));
+      }
+    }
+  }
+  const float gmax = block_max(gm, fs->red);
   // |g_z2[s]| <= max_o sum_c |W3[c][o]| * max_c |g_z3[s][c]| and g_z3 <= g_rgb / 4;
   // |g_h1[s]| <= 128 max|W2| max|g_z2[s]|.  S2 / S1: the scales of the largest bounds.
   const float w21 = mw2 * (float)kHid;
@@ -1019,16 +1020,30 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// g_params += sum over the CTAs that had tiles of their partial rows, in CTA order.
+// g_params += sum of the partial rows of the CTAs that had tiles: block =
+// 32 parameters x 8 row groups; each group sums its rows in order, then the
+// eight group sums are added in order (a fixed association: deterministic).
 __global__ void __launch_bounds__(256) partials_reduce_kernel(const float* __restrict__ part, int nrows,
                                                               int64_t n_cap, const int64_t* __restrict__ n_dev,
                                                               float* __restrict__ g_params) {
+  __shared__ float acc[8][33];
   const int64_t n = mlp_count(n_cap, n_dev);
   const int rows = (int)std::min<int64_t>(nrows, (n + kTile - 1) / kTile);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kNumParams; p += gridDim.x * blockDim.x) {
-    float acc = 0.0f;
-    for (int b = 0; b < rows; ++b) acc += part[(size_t)b * kNumParams + p];
-    g_params[p] += acc;
+  const int j = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + j;
+  const int per = (rows + 7) / 8, b0 = grp * per, b1 = std::min(rows, b0 + per);
+  float a = 0.0f;
+  if (p < kNumParams) {
+#pragma unroll 8
+    for (int b = b0; b < b1; ++b) a += __ldg(part + (size_t)b * kNumParams + p);
+  }
+  acc[grp][j] = a;
+  __syncthreads();
+  if (grp == 0 && p < kNumParams) {
+    float t = acc[0][j];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += acc[q][j];
+    g_params[p] += t;
   }
 }
 
@@ -1036,7 +1051,7 @@ __global__ void __launch_bounds__(256) partials_reduce_kernel(const float* __res
 
 using namespace dvgo;
 
-// act layout: [256-byte header | one 90112-byte image per 128-position tile |
+// act layout: [256 reserved bytes | one 90112-byte image per 128-position tile |
 // kNumSMs partial gradient rows of kNumParams floats]
 static int64_t act_images_end(int64_t n_cap) {
   return (int64_t)kActHeader + (n_cap + kTile - 1) / kTile * (int64_t)kImage;
@@ -1071,14 +1086,11 @@ int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float*
     cudaFuncSetAttribute(rgbnet_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  cudaMemsetAsync(act, 0, sizeof(unsigned int), st);
-  grad_bound_kernel<<<grid_for(n_cap, 256, 4), 256, 0, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev,
-                                                             reinterpret_cast<unsigned int*>(act));
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
   float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(act) + act_images_end(n_cap));
   rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
                                                 reinterpret_cast<const uint8_t*>(act), part, g_k0);
-  partials_reduce_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
+  partials_reduce_kernel<<<(kNumParams + 31) / 32, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
   return launch_status();
 }
 
