@@ -65,7 +65,7 @@ constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
                    bW1l = bW1h + kW1sBytes, bImg = bW1l + kW1sBytes, bGh = bImg + kImage,
                    bGl = bGh + kHBytes, bEnd = bGl + kHBytes;
 // tensor-memory columns of the backward
-constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256;
+constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 304, cGH = 384;
 
 struct Side {
   float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
@@ -118,28 +118,6 @@ __device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Multiply row `row` (K values, split) by the power of two r <= 1, re-splitting.
-template <int K>
-__device__ __forceinline__ void rescale_row(uint8_t* hi, uint8_t* lo, int row, uint32_t sbo, float r,
-                                            float& vmax) {
-#pragma unroll 2
-  for (int k8 = 0; k8 < K; k8 += 8) {
-    const uint32_t off = tc::cm_off(row, k8, sbo);
-    const uint4 qh = *reinterpret_cast<const uint4*>(hi + off);
-    const uint4 ql = *reinterpret_cast<const uint4*>(lo + off);
-    const uint32_t wh[4] = {qh.x, qh.y, qh.z, qh.w}, wl[4] = {ql.x, ql.y, ql.z, ql.w};
-    float v[8];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __half2 h2 = *reinterpret_cast<const __half2*>(&wh[i]);
-      const __half2 l2 = *reinterpret_cast<const __half2*>(&wl[i]);
-      v[2 * i] = r * (__low2float(h2) + __low2float(l2));
-      v[2 * i + 1] = r * (__high2float(h2) + __high2float(l2));
-    }
-    st_split8(hi, lo, row, k8, sbo, v, vmax);
-  }
-}
-
 // One scaled, split element (setup only).
 __device__ __forceinline__ void st_split1(uint8_t* hi, uint8_t* lo, uint32_t off, float v) {
   const __half h = __float2half_rn(v);
@@ -167,6 +145,43 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint3
     dbh += ib;
     dbl += ib;
   }
+}
+
+// D (+)= A B^T over K = 16 * ksteps with A (128 rows) in tensor memory as
+// split terms: K-chunk q of 32 columns at a_tmem + 32 q, its hi terms packed
+// two per column in the first 16 columns and its lo terms in the next 16.
+__device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh, uint32_t bl, uint32_t b_step,
+                                        uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
+                                        bool accumulate) {
+  uint64_t dbh = tc::smem_desc(bh, b_lbo, b_sbo), dbl = tc::smem_desc(bl, b_lbo, b_sbo);
+  const uint64_t ib = b_step >> 4;
+#pragma unroll 1
+  for (int j = 0; j < ksteps; ++j) {
+    const uint32_t ah = a_tmem + 32u * (uint32_t)(j >> 1) + 8u * (uint32_t)(j & 1), al = ah + 16u;
+    tc::mma_ts(d, ah, dbh, idesc, (accumulate || j > 0) ? 1u : 0u);
+    tc::mma_ts(d, ah, dbl, idesc, 1u);
+    tc::mma_ts(d, al, dbh, idesc, 1u);
+    dbh += ib;
+    dbl += ib;
+  }
+}
+
+// Values 8 g .. 8 g + 7 of a 32-column K-chunk (already scaled) into its
+// tensor-memory split layout at chunk column taddr (the split_pack32 layout).
+__device__ __forceinline__ void tmem_st_split8(uint32_t taddr, int g, const float* v, float& vmax) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float a = v[2 * i], b = v[2 * i + 1];
+    vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
+    const __half2 h2 = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h2);
+    const __half2 l2 = __floats2half2_rn(a - hf.x, b - hf.y);
+    h[i] = *reinterpret_cast<const uint32_t*>(&h2);
+    l[i] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  tc::tmem_st4(taddr + 4u * (uint32_t)g, h[0], h[1], h[2], h[3]);
+  tc::tmem_st4(taddr + 16u + 4u * (uint32_t)g, l[0], l[1], l[2], l[3]);
 }
 
 // Output-layer constants (exact FP32).
@@ -461,16 +476,7 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
       tc::fence_after_sync();
       if (lane == 0) {
         tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iHh, sm + gStage, 2 * kHBytes);
-        uint64_t dbh = tc::smem_desc(sW2h, 128, kSboH), dbl = tc::smem_desc(sW2l, 128, kSboH);
-#pragma unroll 1
-        for (uint32_t j = 0; j < kHid / 16; ++j) {
-          const uint32_t ah = buf + 32u * (j >> 1) + 8u * (j & 1u), al = ah + 16u;
-          tc::mma_ts(buf + 128u, ah, dbh, id128, j > 0 ? 1u : 0u);
-          tc::mma_ts(buf + 128u, ah, dbl, id128, 1u);
-          tc::mma_ts(buf + 128u, al, dbh, id128, 1u);
-          dbh += 256 >> 4;
-          dbl += 256 >> 4;
-        }
+        mma3_ts(buf + 128u, buf, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
         tc::mma_commit(&fs->l2_full[b]);
       }
       __syncwarp();
@@ -852,20 +858,14 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
     }
     __syncthreads();   // zx (inside the G buffer) is read; G may be written
-    // this sample's gradient scales; its H1 and X rows carry the compensation
+    // this sample's gradient scales (for g_h1 and g_X); the weight-gradient
+    // products take the CTA-wide S2, S1 instead
     const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
-    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;   // S2 / sG2 <= 1
+    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
     const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
     const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
+    const float fU1 = S1 / (sG2 * sW2);              //                  -> S1 g_h1
     const float invX = 1.0f / (sG1 * sW1);           // g_X
-    if (S2 != sG2) rescale_row<32>(img + iHh + qw * 128 * 4, img + iHl + qw * 128 * 4, row, kSboH, S2 / sG2, vmax);
-    if (S1 != sG1) {
-      const int fb = x_first_block(qw);
-      if (x_num_blocks(qw) == 2)
-        rescale_row<16>(img + iXh + fb * 128, img + iXl + fb * 128, row, kSboX, S1 / sG1, vmax);
-      else
-        rescale_row<8>(img + iXh + fb * 128, img + iXl + fb * 128, row, kSboX, S1 / sG1, vmax);
-    }
     // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
     {
       float v[32], g[32];
@@ -879,11 +879,18 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         g[i] = z2 > 0.0f ? gs : 0.0f;
         v[i] = fmaxf(z2, 0.0f);
       }
-      float sg[32];
+      // the dW2 operand: shared memory, scale S2; the g_h1 operand: tensor
+      // memory over D2, scale sG2
 #pragma unroll
-      for (int i = 0; i < 32; ++i) sg[i] = sG2 * g[i];
+      for (int q = 0; q < 4; ++q) {
+        float t[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, sg + 8 * q, vmax);
+        for (int i = 0; i < 8; ++i) t[i] = S2 * g[8 * q + i];
+        st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, t, vmax);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = sG2 * g[8 * q + i];
+        tmem_st_split8(lane_base + cTmp + 32 * qw, q, t, vmax);
+      }
       db2acc += reduce_scatter32(g, lane);
 #pragma unroll
       for (int c = 0; c < kOut; ++c) {
@@ -893,38 +900,48 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         dW3acc[c] += reduce_scatter32(p, lane);
       }
     }
+    tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {   // dW2 += G2^T H1;  g_h1 = G2 W2
+    if (tid == 0) {   // dW2 += G2^T H1;  g_h1 = G2 W2 (A from tensor memory)
       tc::fence_after_sync();
       mma3(tmem + cDW2, sGh, sGl, 2 * kSboH, kSboH, 128, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
            tc::idesc_f16(128, kHid, 1, 1), dw_started);
-      mma3(tmem + cTmp, sGh, sGl, 256, 128, kSboH, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
-           tc::idesc_f16(128, kHid, 0, 1), false);
+      mma3_ts(tmem + cGH, tmem + cTmp, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
+              tc::idesc_f16(128, kHid, 0, 1), false);
       tc::mma_commit(&fs->bar_mma);
     }
     up_l3(nxt, g_rgb, g_color);
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
-    // G1 = g_h1 * (H1 > 0), rescaled to sG1
+    // G1 = g_h1 * (H1 > 0): at S1 in shared memory (dW1), at sG1 in tensor memory (g_X)
     {
       float v[32];
-      tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
+      tc::tmem_ld32(lane_base + cGH + 32 * qw, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] * fG1 : 0.0f;
+      for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] : 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, v + 8 * q, vmax);
+      for (int q = 0; q < 4; ++q) {
+        float t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = fU1 * v[8 * q + i];
+        st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, t, vmax);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = fG1 * v[8 * q + i];
+        tmem_st_split8(lane_base + cGH + 32 * qw, q, t, vmax);
+      }
     }
+    tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16]
+    if (tid == 0) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
       tc::fence_after_sync();
       mma3(tmem + cDW1, sGh, sGl, 2 * kSboH, kSboH, 128, sXh, sXl, 2 * kSboX, kSboX, 128, kTile / 16,
            tc::idesc_f16(128, kK1, 1, 1), dw_started);
-      mma3(tmem + cTmp, sGh, sGl, 256, 128, kSboH, sW1h, sW1l, 2 * kSboW1s, kSboW1s, 128, kHid / 16,
-           tc::idesc_f16(128, 16, 0, 1), false);
+      mma3_ts(tmem + cGX, tmem + cGH, sW1h, sW1l, 2 * kSboW1s, kSboW1s, 128, kHid / 16,
+              tc::idesc_f16(128, 16, 0, 1), false);
       tc::mma_commit(&fs->bar_mma);
       dw_started = true;
     }
@@ -932,7 +949,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
     if (qw == 0) {
       float gx[16];
-      tc::tmem_ld16(lane_base + cTmp, gx);
+      tc::tmem_ld16(lane_base + cGX, gx);
       if (valid) {
         float4* dst = reinterpret_cast<float4*>(g_k0 + s * kFeat);
         dst[0] = make_float4(gx[0] * invX, gx[1] * invX, gx[2] * invX, gx[3] * invX);
