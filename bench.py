@@ -195,6 +195,20 @@ def by_entry_point(calls):
     return out
 
 
+def reduce_over_ranks(total_ms, e2e_ms, samples, device):
+    """Whole-job figures of an N-rank run: the slowest rank's times (max)
+    and the samples of all ranks (sum); unchanged without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, e2e_ms, samples
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([samples], dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return float(t[0]), float(t[1]), float(s[0])
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2206_05085_gb300 import build as B
@@ -311,15 +325,7 @@ def run_ours(args, rank, world):
     kt = by_entry_point(calls)
     counts = kernel_flops_bytes(tr)
     S, S_live = counts["S"], counts["S_live"]
-    if world > 1:
-        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
-        s = torch.tensor([samples], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(s)
-        samples = float(s[0])
-    else:
-        e2e_total = sum(e2e_ms)
+    total_ms, e2e_total, samples = reduce_over_ranks(total_ms, sum(e2e_ms), samples, "cuda")
     return dict(total_ms=total_ms, samples=samples, e2e_total_ms=e2e_total,
                 e2e_samples=samples, kt=kt, calls=calls, counts=counts, clocks=clock_info, S=S,
                 S_live=S_live, h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
