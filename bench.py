@@ -195,6 +195,28 @@ def by_entry_point(calls):
     return out
 
 
+def l2_read_gbs(mb=32, reps=40):
+    """L2 read rate: one launch of the library's read probe over a buffer well
+    inside L2 (152 x 4 blocks, each pass over the whole buffer; the best of
+    three launches after a warm-up).  The denominator of the gathers' logical
+    (per-corner) traffic."""
+    import torch
+    from paper_2206_05085_gb300 import _lib as L
+    nbytes = mb << 20
+    buf = torch.ones(nbytes // 4, device="cuda")
+    sink = torch.zeros(152 * 4, device="cuda")
+    L.read_probe(buf, nbytes, 2, sink)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.read_probe(buf, nbytes, reps, sink)
+        e1.record()
+        e1.synchronize()
+        best = max(best, nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def reduce_over_ranks(total_ms, e2e_ms, samples, device):
     """Whole-job figures of an N-rank run: the slowest rank's times (max)
     and the samples of all ranks (sum); unchanged without a process group."""
@@ -322,11 +344,12 @@ def run_ours(args, rank, world):
     clock_info = clocks.stop() if clocks else None
 
     calls = per_kernel_times(tr, batches[:1], flush, reps=5)
+    l2_gbs = l2_read_gbs()
     kt = by_entry_point(calls)
     counts = kernel_flops_bytes(tr)
     S, S_live = counts["S"], counts["S_live"]
     total_ms, e2e_total, samples = reduce_over_ranks(total_ms, sum(e2e_ms), samples, "cuda")
-    return dict(total_ms=total_ms, samples=samples, e2e_total_ms=e2e_total,
+    return dict(total_ms=total_ms, steps=args.steps, l2_gbs=l2_gbs, samples=samples, e2e_total_ms=e2e_total,
                 e2e_samples=samples, kt=kt, calls=calls, counts=counts, clocks=clock_info, S=S,
                 S_live=S_live, h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
 
@@ -405,6 +428,8 @@ def memory_kernels(res, peaks):
         "dvgo_distortion_bwd#0": SL * 16 + R * 12,
         # w, rgb, m, ds in per live sample; colour and L_r out per ray
         "dvgo_composite_distortion_fwd#0": SL * 24 + R * 32,
+        # ... with the photometric loss: target in, g_color out per ray
+        "dvgo_composite_distortion_loss_fwd#0": SL * 24 + R * 56,
         # g_w, raw, T, rgb in and g_raw out per live sample, g_raw zeroed past the halt
         "dvgo_composite_bwd#0": SL * 28 + (S - SL) * 4 + R * 24,
         # w, m (twice), ds, raw, T, rgb in and g_raw out per live sample
@@ -425,6 +450,7 @@ def memory_kernels(res, peaks):
         # both grids in one launch (the colour MLP's 22019 entries ride along: 32 B each)
         "dvgo_tv_add_grad_multi#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (e + 4),
         "dvgo_adam_step_multi#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (28 + sh) + 22019 * 32,
+        "dvgo_adam_step_multi_dev#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (28 + sh) + 22019 * 32,
     }
     peak = peaks.get("hbm_gbs", 6701.5)
     out = {}
@@ -437,12 +463,33 @@ def memory_kernels(res, peaks):
                     "frac": round(gbs / peak, 3)}
     tot_b = sum(v["bytes"] for v in out.values())
     tot_ms = sum(v["ms"] for v in out.values())
+    # logical gather traffic (8 corners x channels per sample) against the L2 read rate
+    l2 = res.get("l2_gbs")
+    gather = {}
+    for key, n, ch in (("dvgo_sample_grid_fwd#0", S, 1), ("dvgo_sample_grid_fwd#1", SL, F)):
+        if key in calls and l2:
+            b = n * 8 * ch * e
+            gbs = b / (calls[key] * 1e-3) / 1e9
+            gather[key] = {"logical_bytes": int(b), "effective_gbs": round(gbs, 1),
+                           "frac_of_l2": round(gbs / l2, 3)}
+    # what one iteration must move: every touched grid point (13 channels) is read
+    # by the forward, re-read by the adjoint, its FP32 gradient read-modify-written
+    # and its Adam state (p, g, m, v in; p, m, v out) moved once; step index and
+    # ray id per sample written once, read twice; rays, colours, targets, loss per ray
+    V_t = Bl * 512
+    it_b = V_t * (1 + F) * (e + e + 8 + 28 + sh) + S * 24 + R * 48
+    step_ms = res["total_ms"] / max(res.get("steps", 1), 1)
+    it_gbs = it_b / (step_ms * 1e-3) / 1e9
     return {"peak_gbs": peak, "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks
             else "6701.5 GB/s (earlier measurement on this pool)",
             "counts": c, "kernels": out,
             "all": {"bytes": tot_b, "ms": round(tot_ms, 4),
                     "achieved_gbs": round(tot_b / (tot_ms * 1e-3) / 1e9, 1),
-                    "frac": round(tot_b / (tot_ms * 1e-3) / 1e9 / peak, 3)}}
+                    "frac": round(tot_b / (tot_ms * 1e-3) / 1e9 / peak, 3)},
+            "l2_read_gbs": round(l2, 1) if l2 else None,
+            "gather_effective": gather,
+            "iteration": {"bytes": int(it_b), "touched_points": int(V_t), "ms": round(step_ms, 4),
+                          "achieved_gbs": round(it_gbs, 1), "frac": round(it_gbs / peak, 3)}}
 
 
 def traffic_for(name, prec, units):
@@ -576,6 +623,51 @@ def cpu_baseline(workload, max_seconds=20.0):
                       f"single-threaded FP64 C oracle, {el:.1f} s"}
 
 
+def _oracle_worker(job):
+    """One spawned process: the FP64 oracle's forward + backward over its
+    share of 64-ray slices until the time budget is spent."""
+    workload, slices, max_seconds = job
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from oracle_step import forward_backward
+    from paper_2206_05085_gb300 import synth
+    oracle.build()
+    cfg = synth.CONFIGS[workload]
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    if precision_of(workload) == "bf16":
+        D, Fg, P = synth.bf16_round(D), synth.bf16_round(Fg), synth.bf16_round(P)
+    o, d = synth.rays(cfg, seed=0)
+    t = synth.target_rgb(cfg, seed=0)
+    samples, rays, t0 = 0, 0, time.perf_counter()
+    for a, b in slices:
+        fb = forward_backward(cfg, rp, D, Fg, P, o[a:b], d[a:b], t[a:b])
+        samples += fb["smp"].S
+        rays += b - a
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    return samples, rays, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(workload, max_seconds=20.0):
+    """The same oracle on every host core: one spawned process per core, each
+    on its own slices of the workload's rays (the oracle itself unchanged)."""
+    import multiprocessing
+    from paper_2206_05085_gb300 import synth
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    R, n = synth.CONFIGS[workload].n_rays, 64
+    slices = [(a, min(a + n, R)) for a in range(0, R, n)]
+    jobs = [(workload, slices[i::cores], max_seconds) for i in range(cores)]
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    samples = sum(r[0] for r in res)
+    rays = sum(r[1] for r in res)
+    el = max(r[2] for r in res)
+    return {"value": samples / el, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{rays} of {R} rays of {workload}, forward+backward, FP64 C oracle, "
+                      f"{cores} processes, {el:.1f} s"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -639,6 +731,7 @@ def main():
         line["forms"] = forms_report(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
     print(json.dumps(line))
 
 

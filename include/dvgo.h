@@ -252,6 +252,19 @@ int dvgo_composite_distortion_bwd(const float* g_color, float g_L, const float* 
                                   float shift, float interval, const float bg[3], float* g_raw,
                                   void* stream);
 
+/* dvgo_composite_distortion_fwd and dvgo_rgb_loss (with L_r) in one launch:
+ * color, L_r, g_color and loss_out exactly as those two calls define them
+ * (the loss sums are added in a different but fixed order: deterministic).
+ * ws: dvgo_composite_loss_workspace_size(R) bytes, 16-byte aligned, zeroed
+ * by the caller before its first use; every call leaves it zeroed again. */
+size_t dvgo_composite_loss_workspace_size(int64_t R);
+int dvgo_composite_distortion_loss_fwd(const float* w, const float* rgb, const float* m,
+                                       const float* ds, const int64_t* ray_off,
+                                       const int32_t* n_live, const float* T_end, int64_t R,
+                                       const float bg[3], const float* target, float lambda_dist,
+                                       float* color, float* L_r, float* g_color, float* loss_out,
+                                       void* ws, void* stream);
+
 /* Photometric loss and its gradient: loss_out[0] = mean over R x 3 of
  * (color - target)^2, loss_out[1] = mean_r L_r (0 if L_r is NULL),
  * loss_out[2] = loss_out[0] + lambda_dist loss_out[1]; g_color =
@@ -439,6 +452,13 @@ int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t count, float
 /* Reads and clears the device status word that kernels with bounded waits
  * set (DVGO_ERR_TIMEOUT) instead of hanging.  Synchronises the stream. */
 int dvgo_device_status(void* stream);
+
+/* Measurement aid (not a step of the method): sink_len blocks of 512 threads
+ * each read the first bytes/16 float4 of buf (16-byte aligned) reps times and
+ * add a checksum into sink[block] (f32 [sink_len], caller-zeroed).  A buffer
+ * well inside L2 gives the L2 read rate the gathers' corner reads see. */
+int dvgo_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink, int32_t sink_len,
+                    void* stream);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,9 @@ def _declare(L):
         "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
         "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
         "dvgo_composite_distortion_fwd": ([P, P, P, P, P, P, P, I64, P, P, P, P], INT),
+        "dvgo_composite_loss_workspace_size": ([I64], SZ),
+        "dvgo_read_probe": ([P, I64, I32, P, I32, P], INT),
+        "dvgo_composite_distortion_loss_fwd": ([P, P, P, P, P, P, P, I64, P, P, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
         "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
@@ -140,7 +143,9 @@ def exported_names():
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
         "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
         "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact",
-        "dvgo_adam_step_multi_dev", "dvgo_composite_fwd", "dvgo_grid_adam_step"]
+        "dvgo_adam_step_multi_dev", "dvgo_composite_fwd", "dvgo_grid_adam_step",
+        "dvgo_composite_loss_workspace_size", "dvgo_composite_distortion_loss_fwd",
+        "dvgo_read_probe"]
 
 
 def ptr(t):
@@ -277,6 +282,17 @@ def composite_distortion_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, color
           ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(color), ptr(L_r), _stream(stream))
 
 
+def composite_loss_workspace_size(R):
+    return int(lib().dvgo_composite_loss_workspace_size(R))
+
+
+def composite_distortion_loss_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, target, lambda_dist,
+                                  color, L_r, g_color, loss_out, ws, stream=None):
+    _call("dvgo_composite_distortion_loss_fwd", ptr(w), ptr(rgb), ptr(m), ptr(ds), ptr(ray_off),
+          ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(target), lambda_dist, ptr(color), ptr(L_r),
+          ptr(g_color), ptr(loss_out), ptr(ws), _stream(stream))
+
+
 def composite_distortion_bwd(g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift,
                              interval, bg, g_raw, stream=None):
     _call("dvgo_composite_distortion_bwd", ptr(g_color), g_L, ptr(w), ptr(raw), ptr(T), ptr(rgb),
@@ -363,6 +379,10 @@ def adam_step(p, p_shadow, g, m, v, n, touched, block_elems, lr, beta1, beta2, e
               zero_grad, stream=None):
     _call("dvgo_adam_step", ptr(p), ptr(p_shadow), ptr(g), ptr(m), ptr(v), n, ptr(touched),
           block_elems, lr, beta1, beta2, eps, step, int(zero_grad), _stream(stream))
+
+
+def read_probe(buf, nbytes, reps, sink, stream=None):
+    _call("dvgo_read_probe", ptr(buf), nbytes, reps, ptr(sink), sink.numel(), _stream(stream))
 
 
 def device_status(stream=None):

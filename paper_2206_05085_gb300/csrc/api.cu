@@ -94,6 +94,33 @@ extern "C" int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision) {
   return -1;
 }
 
+// Read-bandwidth probe: every block reads buf[0 .. n4) (float4) reps times
+// with coalesced 16-byte loads and folds the values into sink[block] (so the
+// loads are kept).  With n4 * 16 bytes well inside L2 it measures the L2 read
+// rate that the gathers' repeated corner reads see.
+__global__ void __launch_bounds__(512) read_probe_kernel(const float4* __restrict__ buf, int64_t n4,
+                                                         int reps, float* __restrict__ sink) {
+  float acc = 0.0f;
+  for (int r = 0; r < reps; ++r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const float4 v = __ldcg(buf + i);   // cached in L2 only
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sink + blockIdx.x, acc);
+}
+
+extern "C" int dvgo_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink,
+                               int32_t sink_len, void* stream) {
+  DVGO_CHECK_ARG(buf && sink && bytes >= 16 && reps >= 1 && sink_len >= 1);
+  DVGO_CHECK_ARG((reinterpret_cast<uintptr_t>(buf) & 15u) == 0);
+  read_probe_kernel<<<sink_len, 512, 0, as_stream(stream)>>>(reinterpret_cast<const float4*>(buf),
+                                                            bytes / 16, reps, sink);
+  return launch_status();
+}
+
 extern "C" int dvgo_device_status(void* stream) {
   const int a = dvgo_mlp_status_read_and_clear(as_stream(stream));
   const int b = dvgo_mlp_tc_status_read_and_clear(as_stream(stream));

@@ -256,11 +256,27 @@ __global__ void __launch_bounds__(256) distortion_bwd_kernel(
 // ------------------------------------------------ fused per-ray tails
 // Colour accumulation and the distortion loss of the live samples in one pass
 // over each ray (both read w; same arithmetic as the two kernels above).
+// With kLoss the photometric loss of dvgo_rgb_loss is formed too: each ray's
+// squared error and g_color beside its colour, per-block partial sums, and
+// the last block to finish (a ticket counter it resets) adds the partials in
+// block order (deterministic).
+struct LossTail {
+  const float* target;
+  float lambda_dist;
+  float* g_color;
+  float* loss_out;
+  unsigned int* ticket;
+  float* part;       // [gridDim.x][2]
+};
+
+template <bool kLoss>
 __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     const float* __restrict__ w, const float* __restrict__ rgb, const float* __restrict__ m,
     const float* __restrict__ ds, const int64_t* __restrict__ ray_off, const int32_t* __restrict__ n_live,
     const float* __restrict__ T_end, int64_t R, float bg0, float bg1, float bg2,
-    float* __restrict__ color, float* __restrict__ L_r) {
+    float* __restrict__ color, float* __restrict__ L_r, LossTail lt) {
+  float sq = 0.0f, dsum = 0.0f;   // lane 0: this warp's rays
+  const float gscale = 2.0f / (3.0f * (float)R);
   DVGO_WARP_LOOP(R) {
     int64_t b;
     int n, N;
@@ -295,10 +311,74 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     acc = warp_sum(acc);
     if (lane == 0) {
       const float te = T_end[r];
-      color[3 * r] = a0 + te * bg0;
-      color[3 * r + 1] = a1 + te * bg1;
-      color[3 * r + 2] = a2 + te * bg2;
+      const float c0 = a0 + te * bg0, c1 = a1 + te * bg1, c2 = a2 + te * bg2;
+      color[3 * r] = c0;
+      color[3 * r + 1] = c1;
+      color[3 * r + 2] = c2;
       L_r[r] = acc;
+      if constexpr (kLoss) {
+        const float e0 = c0 - __ldg(lt.target + 3 * r), e1 = c1 - __ldg(lt.target + 3 * r + 1),
+                    e2 = c2 - __ldg(lt.target + 3 * r + 2);
+        lt.g_color[3 * r] = gscale * e0;
+        lt.g_color[3 * r + 1] = gscale * e1;
+        lt.g_color[3 * r + 2] = gscale * e2;
+        sq += (e0 * e0 + e1 * e1) + e2 * e2;
+        dsum += acc;
+      }
+    }
+  }
+  if constexpr (kLoss) {
+    __shared__ float s1[8], s2[8];
+    __shared__ bool last;
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      s1[wid] = sq;
+      s2[wid] = dsum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = 0.0f, d = 0.0f;
+      for (int i = 0; i < 8; ++i) {
+        a += s1[i];
+        d += s2[i];
+      }
+      lt.part[2 * blockIdx.x] = a;
+      lt.part[2 * blockIdx.x + 1] = d;
+      __threadfence();
+      last = atomicAdd(lt.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      // thread t adds blocks t, t + 256, ... in order; the warp and block
+      // steps below always pair the same partners
+      float a = 0.0f, d = 0.0f;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        a += __ldcg(lt.part + 2 * b);
+        d += __ldcg(lt.part + 2 * b + 1);
+      }
+      a = warp_sum(a);
+      d = warp_sum(d);
+      __syncthreads();
+      if (lane == 0) {
+        s1[wid] = a;
+        s2[wid] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        a = 0.0f;
+        d = 0.0f;
+        for (int i = 0; i < 8; ++i) {
+          a += s1[i];
+          d += s2[i];
+        }
+        const float lr = a / (3.0f * (float)R);
+        const float ld = d / (float)R;
+        lt.loss_out[0] = lr;
+        lt.loss_out[1] = ld;
+        lt.loss_out[2] = lr + lt.lambda_dist * ld;
+        *lt.ticket = 0u;   // ready for the next call
+      }
     }
   }
 }
@@ -544,8 +624,31 @@ extern "C" int dvgo_composite_distortion_fwd(const float* w, const float* rgb, c
   DVGO_CHECK_ARG(R >= 0);
   if (R == 0) return DVGO_OK;
   DVGO_CHECK_ARG(w && rgb && m && ds && ray_off && T_end && bg && color && L_r);
-  composite_distortion_fwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
-      w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r);
+  composite_distortion_fwd_kernel<false><<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r, LossTail{});
+  return launch_status();
+}
+
+// workspace: a ticket counter (16 bytes) and two partial sums per block
+extern "C" size_t dvgo_composite_loss_workspace_size(int64_t R) {
+  return 16 + (size_t)2 * sizeof(float) * (size_t)warp_grid(R < 1 ? 1 : R);
+}
+
+extern "C" int dvgo_composite_distortion_loss_fwd(const float* w, const float* rgb, const float* m,
+                                                  const float* ds, const int64_t* ray_off,
+                                                  const int32_t* n_live, const float* T_end, int64_t R,
+                                                  const float bg[3], const float* target,
+                                                  float lambda_dist, float* color, float* L_r,
+                                                  float* g_color, float* loss_out, void* ws,
+                                                  void* stream) {
+  DVGO_CHECK_ARG(R > 0);
+  DVGO_CHECK_ARG(w && rgb && m && ds && ray_off && T_end && bg && color && L_r && target && g_color &&
+                 loss_out && ws);
+  DVGO_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 15u) == 0);
+  LossTail lt{target, lambda_dist, g_color, loss_out, reinterpret_cast<unsigned int*>(ws),
+              reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 16)};
+  composite_distortion_fwd_kernel<true><<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r, lt);
   return launch_status();
 }
 

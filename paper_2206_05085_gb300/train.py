@@ -139,6 +139,8 @@ class Trainer:
             self.act = torch.empty(L.rgbnet_act_bytes(S, self.precision), dtype=torch.uint8, device=dev)
         self.ws_sample = torch.empty(L.sample_rays_workspace_size(R), dtype=torch.uint8, device=dev)
         self.ws_live = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device=dev)
+        # zeroed once: the loss pass leaves its ticket counter at zero after every call
+        self.ws_loss = torch.zeros(L.composite_loss_workspace_size(R), dtype=torch.uint8, device=dev)
         nb = self.density.touched.numel()
         self.brick_list = torch.empty(nb, **i32)
         self.brick_count = torch.zeros(1, **i32)
@@ -167,10 +169,11 @@ class Trainer:
                           self.k0)
         L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
                      self.precision, self.rgb, self.act)
-        # colour accumulation and distortion loss in one pass over each ray
-        L.composite_distortion_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
-                                   self.n_live, self.T_end, R, rp.bg, self.color, self.L_r)
-        L.rgb_loss(self.color, target, self.L_r, R, rp.lambda_dist, self.loss, self.g_color)
+        # colour accumulation, distortion loss and the photometric loss in one pass
+        # over each ray
+        L.composite_distortion_loss_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
+                                        self.n_live, self.T_end, R, rp.bg, target, rp.lambda_dist,
+                                        self.color, self.L_r, self.g_color, self.loss, self.ws_loss)
 
     # -------------------------------------------------------------- backward
     def backward(self, rays_d):

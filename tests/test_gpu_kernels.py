@@ -395,6 +395,51 @@ def test_composite_distortion_fused(L):
         assert rel_err(host(g_raw), gr) < TOL32
 
 
+@pytest.mark.parametrize("R_rays", [37, 5000])
+def test_composite_distortion_loss_fused(L, R_rays):
+    """One launch = compositing + distortion + photometric loss: colour, L_r
+    and g_color bit-equal to the separate calls, the loss against the oracle's
+    mean squared error; repeated calls give the same bits and leave the
+    workspace's ticket at zero (several blocks reach the last-block sum)."""
+    rng = np.random.default_rng(R_rays)
+    counts = rng.integers(0, 40, R_rays)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(off[-1])
+    raw = (rng.normal(size=S) * 2.0 + 1.0).astype(np.float32)
+    rgb = rng.uniform(0, 1, (S, 3)).astype(np.float32)
+    m = np.zeros(S, np.float32)
+    for r in range(R_rays):
+        m[off[r]:off[r + 1]] = np.sort(rng.uniform(0, 1, counts[r]))
+    ds = rng.uniform(0.001, 0.01, S).astype(np.float32)
+    target = rng.uniform(0, 1, (R_rays, 3)).astype(np.float32)
+    bg = np.array([1.0, 1.0, 1.0], np.float32)
+    sh, lam = shift32(), 0.01
+    w, T = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+    n_live = torch.empty(R_rays, dtype=torch.int32, device="cuda")
+    T_end = torch.empty(R_rays, device="cuda")
+    L.alpha_weights_fwd(dev(raw), dev(off), R_rays, sh, 0.5, 1e-3, w, T, n_live, T_end)
+    args = (w, dev(rgb), dev(m), dev(ds), dev(off), n_live, T_end, R_rays, bg)
+    c1, l1 = torch.empty(R_rays, 3, device="cuda"), torch.empty(R_rays, device="cuda")
+    L.composite_distortion_fwd(*args, c1, l1)
+    loss1, g1 = torch.empty(3, device="cuda"), torch.empty(R_rays, 3, device="cuda")
+    L.rgb_loss(c1, dev(target), l1, R_rays, lam, loss1, g1)
+    ws = torch.zeros(L.composite_loss_workspace_size(R_rays), dtype=torch.uint8, device="cuda")
+    outs = []
+    for _ in range(3):
+        c2, l2 = torch.empty(R_rays, 3, device="cuda"), torch.empty(R_rays, device="cuda")
+        loss2, g2 = torch.empty(3, device="cuda"), torch.empty(R_rays, 3, device="cuda")
+        L.composite_distortion_loss_fwd(*args, dev(target), lam, c2, l2, g2, loss2, ws)
+        outs.append(host(loss2))
+        assert torch.equal(c1, c2) and torch.equal(l1, l2) and torch.equal(g1, g2)
+        assert int(host(ws[:4].view(torch.int32))[0]) == 0
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    ref = oracle.composite(raw, rgb, off, sh, 0.5, 1e-3, bg)
+    mse = np.mean((ref["color"] - target) ** 2)
+    Ld = np.mean(oracle.distortion(ref["w"], m, ds, off, ref["n_live"]))
+    assert rel_err(outs[0], np.array([mse, Ld, mse + lam * Ld])) < TOL32
+    assert rel_err(outs[0], host(loss1)) < 1e-6
+
+
 def test_distortion(L):
     rng = np.random.default_rng(4)
     counts = COUNTS
