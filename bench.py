@@ -417,12 +417,19 @@ def memory_kernels(res, peaks):
     e = 2 if prec == "bf16" else 4          # bytes per grid element the renderer reads
     sh = 2 if prec == "bf16" else 0         # BF16 shadow written by Adam
     ent_d, ent_f = Bl * 512, Bl * 512 * F   # grid entries in the touched bricks
+    # the feature query is the step's only dvgo_sample_grid_fwd once the density
+    # query is fused into the weights pass, else the second one
+    fused_density = "dvgo_density_alpha_fwd#0" in calls
+    dens_key = None if fused_density else "dvgo_sample_grid_fwd#0"
+    feat_key = "dvgo_sample_grid_fwd#0" if fused_density else "dvgo_sample_grid_fwd#1"
     algo = {
         # xyz + value out per sample, each distinct corner voxel once
-        "dvgo_sample_grid_fwd#0": S * (12 + 4) + Va * e,
-        "dvgo_sample_grid_fwd#1": SL * (4 + 12 + 4 * F) + Vl * e * F,
+        feat_key: SL * (4 + 12 + 4 * F) + Vl * e * F,
         # raw in, w and T out per sample; ray_off, n_live, T_end per ray
         "dvgo_alpha_weights_fwd#0": S * 12 + R * 16,
+        # the density query fused in: xyz in per sample up to the halt, each distinct
+        # queried voxel once; raw, w, T out per sample
+        "dvgo_density_alpha_fwd#0": SL * 12 + Vl * e + S * 12 + R * 16,
         "dvgo_composite_rgb_fwd#0": SL * 16 + R * 28,
         "dvgo_distortion_fwd#0": SL * 12 + R * 16,
         "dvgo_distortion_bwd#0": SL * 16 + R * 12,
@@ -452,6 +459,8 @@ def memory_kernels(res, peaks):
         "dvgo_adam_step_multi#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (28 + sh) + 22019 * 32,
         "dvgo_adam_step_multi_dev#0": (ent_d + ent_f) * 4 + Vl * (1 + F) * (28 + sh) + 22019 * 32,
     }
+    if dens_key:
+        algo[dens_key] = S * (12 + 4) + Va * e
     peak = peaks.get("hbm_gbs", 6701.5)
     out = {}
     for key, b in algo.items():
@@ -466,7 +475,9 @@ def memory_kernels(res, peaks):
     # logical gather traffic (8 corners x channels per sample) against the L2 read rate
     l2 = res.get("l2_gbs")
     gather = {}
-    for key, n, ch in (("dvgo_sample_grid_fwd#0", S, 1), ("dvgo_sample_grid_fwd#1", SL, F)):
+    queries = [(feat_key, SL, F)] + ([(dens_key, S, 1)] if dens_key else
+                                     [("dvgo_density_alpha_fwd#0", SL, 1)])
+    for key, n, ch in queries:
         if key in calls and l2:
             b = n * 8 * ch * e
             gbs = b / (calls[key] * 1e-3) / 1e9

@@ -204,6 +204,16 @@ int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_of
                        float shift, float interval, float T_stop, const float bg[3], float* color,
                        float* w, float* T, int32_t* n_live, float* T_end, void* stream);
 
+/* dvgo_sample_grid_fwd of a one-channel density grid fused with
+ * dvgo_alpha_weights_fwd: raw[S], w[S], T[S], n_live[R], T_end[R] as those
+ * two calls define them, except that samples at or past a ray's halting
+ * index are not queried (their raw is written as 0; nothing downstream reads
+ * it).  xyz [S][3] f32 in ray order (the sampler's output). */
+int dvgo_density_alpha_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd, const float* xyz,
+                           const int64_t* ray_off, int64_t R, float shift, float interval,
+                           float T_stop, float* raw, float* w, float* T, int32_t* n_live,
+                           float* T_end, void* stream);
+
 /* Colour accumulation: color[r] = sum_{i < n_live[r]} w_i rgb_i + T_end[r] bg. */
 int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_off,
                            const int32_t* n_live, const float* T_end, int64_t R, const float bg[3],

@@ -103,6 +103,7 @@ def _declare(L):
         "dvgo_composite_distortion_fwd": ([P, P, P, P, P, P, P, I64, P, P, P, P], INT),
         "dvgo_composite_loss_workspace_size": ([I64], SZ),
         "dvgo_read_probe": ([P, I64, I32, P, I32, P], INT),
+        "dvgo_density_alpha_fwd": ([P, INT, P, P, P, I64, F, F, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_loss_fwd": ([P, P, P, P, P, P, P, I64, P, P, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
@@ -145,7 +146,7 @@ def exported_names():
         "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact",
         "dvgo_adam_step_multi_dev", "dvgo_composite_fwd", "dvgo_grid_adam_step",
         "dvgo_composite_loss_workspace_size", "dvgo_composite_distortion_loss_fwd",
-        "dvgo_read_probe"]
+        "dvgo_read_probe", "dvgo_density_alpha_fwd"]
 
 
 def ptr(t):
@@ -249,6 +250,12 @@ def live_samples(ray_off, seg_len, R, live_idx, live_count, ws, stream=None):
 
 
 # ------------------------------------------------------------ rendering
+def density_alpha_fwd(grid, dtype, gd, xyz, ray_off, R, shift, interval, T_stop, raw, w, T, n_live,
+                      T_end, stream=None):
+    _call("dvgo_density_alpha_fwd", ptr(grid), dtype, ctypes.byref(gd), ptr(xyz), ptr(ray_off), R,
+          shift, interval, T_stop, ptr(raw), ptr(w), ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
+
+
 def alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end, stream=None):
     _call("dvgo_alpha_weights_fwd", ptr(raw), ptr(ray_off), R, shift, interval, T_stop, ptr(w),
           ptr(T), ptr(n_live), ptr(T_end), _stream(stream))

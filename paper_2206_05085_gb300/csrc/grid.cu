@@ -691,6 +691,102 @@ extern "C" int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_d
   return launch_status();
 }
 
+// ------------------------------------------------- density query + weights
+// dvgo_sample_grid_fwd of the density (one channel) fused with the weights
+// pass (dvgo_alpha_weights_fwd): one warp per ray, 32 samples at a time; each
+// lane queries its sample's density, the warp scans log T, and the ray stops
+// at the halt, so no sample past it is queried.  Same arithmetic as the two
+// separate kernels.
+template <bool kBF16>
+__global__ void __launch_bounds__(256) density_alpha_kernel(
+    const void* __restrict__ grid, TriArgs Tr, const float* __restrict__ xyz,
+    const int64_t* __restrict__ ray_off, int64_t R, float shift, float interval, float T_stop,
+    float* __restrict__ raw, float* __restrict__ w, float* __restrict__ T,
+    int32_t* __restrict__ n_live, float* __restrict__ T_end) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp0; r < R; r += nwarps) {
+    const int64_t b = ray_off[r];
+    const int N = (int)(ray_off[r + 1] - b);
+    Kahan carry;  // log T before the current chunk
+    int stop = N;
+    float t_end = 1.0f;
+    int c0 = 0;
+    for (; c0 < N; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < N;
+      float rv = 0.0f;
+      if (valid) {
+        Corners c;
+        corners(Tr, xyz, b + i, c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if constexpr (kBF16)
+            rv += c.w[k] * bf16_bits_to_f32(__ldg(reinterpret_cast<const uint16_t*>(grid) + c.slot[k]));
+          else
+            rv += c.w[k] * __ldg(reinterpret_cast<const float*>(grid) + c.slot[k]);
+        }
+        raw[b + i] = rv;
+      }
+      const float la = valid ? -interval * softplus_f(rv + shift) : 0.0f;
+      const float incl = warp_incl_sum(la);
+      const float logT = __fadd_rn(carry.s, __fsub_rn(incl - la, carry.c));
+      const float Ti = expf(logT);
+      const unsigned below = __ballot_sync(0xffffffffu, valid && Ti < T_stop);
+      const int first = below ? __ffs(below) - 1 : 32;
+      if (below) {
+        stop = c0 + first;
+        t_end = __shfl_sync(0xffffffffu, Ti, first);
+      }
+      if (valid) {
+        if (lane < first) {
+          w[b + i] = Ti * -expm1f(la);
+          T[b + i] = Ti;
+        } else {
+          w[b + i] = 0.0f;
+          T[b + i] = t_end;
+        }
+      }
+      if (below) break;
+      carry.add(__shfl_sync(0xffffffffu, incl, 31));
+    }
+    if (stop == N) t_end = expf(__fsub_rn(carry.s, carry.c));
+    for (c0 += 32; c0 < N; c0 += 32) {
+      const int i = c0 + lane;
+      if (i < N) {
+        raw[b + i] = 0.0f;   // past the halt: not queried
+        w[b + i] = 0.0f;
+        T[b + i] = t_end;
+      }
+    }
+    if (lane == 0) {
+      n_live[r] = stop;
+      T_end[r] = t_end;
+    }
+  }
+}
+
+extern "C" int dvgo_density_alpha_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd,
+                                      const float* xyz, const int64_t* ray_off, int64_t R,
+                                      float shift, float interval, float T_stop, float* raw, float* w,
+                                      float* T, int32_t* n_live, float* T_end, void* stream) {
+  DVGO_CHECK_ARG(gd && R >= 0 && interval > 0.0f && T_stop >= 0.0f);
+  DVGO_CHECK_ARG(dtype == DVGO_F32 || dtype == DVGO_BF16);
+  if (R == 0) return DVGO_OK;
+  DVGO_CHECK_ARG(grid && xyz && ray_off && raw && w && T && n_live && T_end);
+  TriArgs Tr;
+  DVGO_CHECK_ARG(make_tri(Tr, gd));
+  const int g = grid_for(R * 32, 256, 16);
+  if (dtype == DVGO_F32)
+    density_alpha_kernel<false><<<g, 256, 0, as_stream(stream)>>>(grid, Tr, xyz, ray_off, R, shift, interval,
+                                                                   T_stop, raw, w, T, n_live, T_end);
+  else
+    density_alpha_kernel<true><<<g, 256, 0, as_stream(stream)>>>(grid, Tr, xyz, ray_off, R, shift, interval,
+                                                                  T_stop, raw, w, T, n_live, T_end);
+  return launch_status();
+}
+
 extern "C" int dvgo_sample_grid_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd,
                                     int32_t C, const float* xyz, const int32_t* idx, int64_t n_cap,
                                     const int64_t* n_dev, float* out, void* stream) {

@@ -158,11 +158,10 @@ class Trainer:
         rp, R, S = self.rp, self.R, self.S_cap
         if sample:
             self.sample(rays_o, rays_d)
-        S_dev = self.ray_off[R:]
+        # density query and weights in one pass over each ray, up to its halt
         dgrid, ddt = self.density.render_view
-        L.sample_grid_fwd(dgrid, ddt, self.gd, 1, self.xyz, None, S, S_dev, self.raw)
-        L.alpha_weights_fwd(self.raw, self.ray_off, R, self.shift, rp.interval, rp.T_stop, self.w,
-                            self.T, self.n_live, self.T_end)
+        L.density_alpha_fwd(dgrid, ddt, self.gd, self.xyz, self.ray_off, R, self.shift, rp.interval,
+                            rp.T_stop, self.raw, self.w, self.T, self.n_live, self.T_end)
         L.live_samples(self.ray_off, self.n_live, R, self.live_idx, self.live_count, self.ws_live)
         fgrid, fdt = self.feature.render_view
         L.sample_grid_fwd(fgrid, fdt, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,

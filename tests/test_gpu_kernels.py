@@ -395,6 +395,55 @@ def test_composite_distortion_fused(L):
         assert rel_err(host(g_raw), gr) < TOL32
 
 
+@pytest.mark.parametrize("bf16", [False, True])
+def test_density_alpha_fused(L, bf16):
+    """Density query + weights in one pass = dvgo_sample_grid_fwd then
+    dvgo_alpha_weights_fwd (bit-equal w, T, n_live, T_end; raw equal before
+    each ray's halt), on rays sampled through a blob scene so that many halt."""
+    rng = np.random.default_rng(50 + bf16)
+    G = (40, 40, 40)
+    lo, hi = np.array([-1.0] * 3), np.array([1.0] * 3)
+    ax = np.linspace(-1, 1, 40)
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    dense = (30.0 * np.exp(-(xx ** 2 + yy ** 2 + zz ** 2) / 0.1) - 3.0).astype(np.float32)[..., None]
+    if bf16:
+        dense = synth.bf16_round(dense)
+    R = 700
+    counts = rng.integers(0, 100, R)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    pts = []
+    for r in range(R):
+        o = rng.uniform(-0.5, 0.5, 3) * np.array([1, 1, 0]) + np.array([0, 0, -0.99])
+        d = np.array([0.0, 0.0, 1.0]) + rng.normal(0, 0.2, 3)
+        d /= np.linalg.norm(d)
+        pts.append(np.clip(o + d * 0.02 * np.arange(counts[r])[:, None], -1, 1))
+    xyz = np.concatenate(pts).astype(np.float32)
+    S = len(xyz)
+    gd = L.GridDesc.make(lo, hi, G)
+    grid = _bricked(L, dense, G, 1, torch.bfloat16 if bf16 else torch.float32)
+    dt = L.BF16 if bf16 else L.F32
+    sh = shift32()
+    outs = []
+    for fused in (False, True):
+        raw, w, T = (torch.full((S,), -9.0, device="cuda") for _ in range(3))
+        n_live = torch.empty(R, dtype=torch.int32, device="cuda")
+        T_end = torch.empty(R, device="cuda")
+        if fused:
+            L.density_alpha_fwd(grid, dt, gd, dev(xyz), dev(off), R, sh, 0.5, 1e-3, raw, w, T, n_live, T_end)
+        else:
+            L.sample_grid_fwd(grid, dt, gd, 1, dev(xyz), None, S, None, raw)
+            L.alpha_weights_fwd(raw, dev(off), R, sh, 0.5, 1e-3, w, T, n_live, T_end)
+        outs.append([host(x) for x in (raw, w, T, n_live, T_end)])
+    (r0, w0, T0, n0, e0), (r1, w1, T1, n1, e1) = outs
+    assert np.array_equal(n0, n1) and np.array_equal(e0, e1)
+    assert np.array_equal(w0, w1) and np.array_equal(T0, T1)
+    halted = int(np.sum(n0 < np.diff(off)))
+    assert halted > 50   # (93 of the 700 rays halt in the FP64 oracle)
+    for r in range(R):
+        k = slice(off[r], off[r] + n0[r])
+        assert np.array_equal(r0[k], r1[k])
+
+
 @pytest.mark.parametrize("R_rays", [37, 5000])
 def test_composite_distortion_loss_fused(L, R_rays):
     """One launch = compositing + distortion + photometric loss: colour, L_r
