@@ -363,7 +363,9 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
     bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
                                           step_k, s_mid, s_len);
   } else {
-    const int block = 128;
+    // one warp of rays per block, so that the sequential marches spread over
+    // every SM (8192 rays: 256 blocks)
+    const int block = 32;
     int g = (int)ceil_div(R, block);
     contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -466,7 +468,9 @@ extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d
     bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
                                           step_k, s_mid, s_len);
   } else {
-    const int block = 128;
+    // one warp of rays per block, so that the sequential marches spread over
+    // every SM (8192 rays: 256 blocks)
+    const int block = 32;
     int g = (int)ceil_div(R, block);
     contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
