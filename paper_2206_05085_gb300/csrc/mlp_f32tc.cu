@@ -46,7 +46,7 @@ namespace x3 {
 constexpr int kK1 = 48;                           // padded input width
 constexpr uint32_t kSboX = (kK1 / 8) * 128;       // 768: 8-row group stride, 48-wide rows
 constexpr uint32_t kSboH = (kHid / 8) * 128;      // 2048: 128-wide rows
-constexpr uint32_t kSboW1s = (16 / 8) * 128;      // 256: 16-wide rows (W1[:, 0:16])
+constexpr uint32_t kSboW1s = (32 / 8) * 128;      // 512: W1[:, 0:16] hi and lo side by side per 8 rows
 constexpr uint32_t kXBytes = kTile * kK1 * 2;     // one term of X
 constexpr uint32_t kHBytes = kTile * kHid * 2;    // one term of H1 or G
 constexpr uint32_t kW1Bytes = kHid * kK1 * 2;
@@ -62,10 +62,10 @@ constexpr uint32_t kSpin = 1u << 24;
 
 // backward shared memory
 constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
-                   bW1l = bW1h + kW1sBytes, bImg = bW1l + kW1sBytes, bGh = bImg + kImage,
+                   bImg = bW1h + 2 * kW1sBytes, bGh = bImg + kImage,
                    bGl = bGh + kHBytes, bEnd = bGl + kHBytes;
 // tensor-memory columns of the backward
-constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 304, cGH = 384;
+constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 320, cGH = 384;
 
 struct Side {
   float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
@@ -758,7 +758,9 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const float S1 = pow2_scale(0.25f * gmax * mw3 * w21);
   up_l2(cur, g_rgb, w, ray_id);
   // W1[:, 0:16] as split [o][k] rows for g_X = G1 W1[:, 0:16]
-  load_w1<16>(params, sm + bW1h, sm + bW1l, kSboW1s, sW1);
+  // W1[:, 0:16] split, hi and lo core matrices side by side in each 8-row
+  // group, so that [hi | lo] is one 32-wide B operand of g_X
+  load_w1<16>(params, sm + bW1h, sm + bW1h + 256, kSboW1s, sW1);
   load_w2(params, sm + bW2h, sm + bW2l, sW2);
   load_out_layer(params, fs);
   up_l3(cur, g_rgb, g_color);
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
   const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t sW1h = tc::smem_u32(sm + bW1h), sW1l = tc::smem_u32(sm + bW1l);
+  const uint32_t sW1h = tc::smem_u32(sm + bW1h);
   const uint32_t sW2h = tc::smem_u32(sm + bW2h), sW2l = tc::smem_u32(sm + bW2l);
   const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
@@ -940,8 +942,17 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       tc::fence_after_sync();
       mma3(tmem + cDW1, sGh, sGl, 2 * kSboH, kSboH, 128, sXh, sXl, 2 * kSboX, kSboX, 128, kTile / 16,
            tc::idesc_f16(128, kK1, 1, 1), dw_started);
-      mma3_ts(tmem + cGX, tmem + cGH, sW1h, sW1l, 2 * kSboW1s, kSboW1s, 128, kHid / 16,
-              tc::idesc_f16(128, 16, 0, 1), false);
+      {   // per K step: G1h [W1h | W1l] (N = 32: hi*hi in columns 0-15, hi*lo in 16-31), G1l W1h
+        const uint32_t id32 = tc::idesc_f16(128, 32, 0, 1), id16 = tc::idesc_f16(128, 16, 0, 1);
+        uint64_t db = tc::smem_desc(sW1h, kSboW1s, 128);
+#pragma unroll 1
+        for (uint32_t j = 0; j < kHid / 16; ++j) {
+          const uint32_t ah = tmem + cGH + 32u * (j >> 1) + 8u * (j & 1u), al = ah + 16u;
+          tc::mma_ts(tmem + cGX, ah, db, id32, j > 0 ? 1u : 0u);
+          tc::mma_ts(tmem + cGX, al, db, id16, 1u);
+          db += (2 * kSboW1s) >> 4;
+        }
+      }
       tc::mma_commit(&fs->bar_mma);
       dw_started = true;
     }
@@ -949,7 +960,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
     if (qw == 0) {
       float gx[16];
-      tc::tmem_ld16(lane_base + cGX, gx);
+      {
+        float gd[32];
+        tc::tmem_ld32(lane_base + cGX, gd);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) gx[i] = gd[i] + gd[16 + i];
+      }
       if (valid) {
         float4* dst = reinterpret_cast<float4*>(g_k0 + s * kFeat);
         dst[0] = make_float4(gx[0] * invX, gx[1] * invX, gx[2] * invX, gx[3] * invX);
