@@ -397,6 +397,16 @@ __device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const Br
   nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
   nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
   if (C % 4 == 0) {
+    // sparse mode: a voxel whose data gradient is zero in every channel gets
+    // no TV gradient, so its value and neighbours are not loaded at all
+    if (!dense_mode) {
+      bool any = false;
+      for (int q = 0; q < C / 4; ++q) {
+        const float4 gin = reinterpret_cast<const float4*>(g_grid + self * C)[q];
+        any = any || gin.x != 0.0f || gin.y != 0.0f || gin.z != 0.0f || gin.w != 0.0f;
+      }
+      if (!any) return;
+    }
     // per group of 4 channels: the gradient, the value and the six neighbours
     // are loaded together (no load waits on another)
     for (int q = 0; q < C / 4; ++q) {
@@ -426,11 +436,11 @@ __device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const Br
     for (int c = 0; c < C; ++c) {
       float* gp = g_grid + self * C + c;
       const float gin = *gp;
+      if (!dense_mode && gin == 0.0f) continue;   // no TV gradient here: nothing to load
       const float v = load_val<kBF16>(grid, self * C + c);
       float u[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) u[d] = load_val<kBF16>(grid, nbr[d] * C + c);
-      if (!dense_mode && gin == 0.0f) continue;
       float acc = 0.0f;
 #pragma unroll
       for (int d = 0; d < 6; ++d)
