@@ -252,47 +252,72 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
   }
 }
 
-// Exclusive scan of int32 counts into int64 offsets off[0..n] (one block).
-__global__ void scan_counts_kernel(const int32_t* __restrict__ counts, int64_t n,
-                                   int64_t* __restrict__ off, int64_t* __restrict__ total_out) {
+// Exclusive scan of int32 counts into int64 offsets off[0..n] (one block of
+// 1024 threads).  Each pass covers 8192 counts: thread t takes 8 consecutive
+// ones (two 16-byte loads when aligned), scans them in registers, and the
+// block scans the per-thread totals; a running carry joins the passes.
+__global__ void __launch_bounds__(1024) scan_counts_kernel(const int32_t* __restrict__ counts, int64_t n,
+                                                           int64_t* __restrict__ off,
+                                                           int64_t* __restrict__ total_out) {
   __shared__ int64_t warp_tot[32];
-  const int t = threadIdx.x;
-  const int nt = blockDim.x;
-  int64_t chunk = (n + nt - 1) / nt;
-  int64_t b = (int64_t)t * chunk, e = b + chunk;
-  if (b > n) b = n;
-  if (e > n) e = n;
-  int64_t local = 0;
-  for (int64_t i = b; i < e; ++i) local += counts[i];
-  // block exclusive scan of local
-  int lane = t & 31, wid = t >> 5;
-  int64_t incl = local;
+  __shared__ int64_t pass_total;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const bool vec = (reinterpret_cast<uintptr_t>(counts) & 15u) == 0;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += 8 * (int64_t)blockDim.x) {
+    const int64_t i0 = base + 8 * (int64_t)t;
+    int32_t c[8];
+    if (vec && i0 + 8 <= n) {
+      const int4 a = __ldg(reinterpret_cast<const int4*>(counts + i0));
+      const int4 b = __ldg(reinterpret_cast<const int4*>(counts + i0 + 4));
+      c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+      c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    } else {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_tot[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int nw = nt >> 5;
-    int64_t v = lane < nw ? warp_tot[lane] : 0;
+      for (int k = 0; k < 8; ++k) c[k] = i0 + k < n ? __ldg(counts + i0 + k) : 0;
+    }
+    int64_t loc[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      loc[k] = s;
+      s += c[k];
+    }
+    int64_t incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int64_t y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
+      const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (lane < nw) warp_tot[lane] = v;  // inclusive warp totals
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = (int)(blockDim.x >> 5);
+      int64_t v = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane < nw) warp_tot[lane] = v;   // inclusive warp totals
+      if (lane == nw - 1) pass_total = v;
+    }
+    __syncthreads();
+    const int64_t ex = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + incl - s;
+    if (i0 + 8 <= n && (reinterpret_cast<uintptr_t>(off + i0) & 15u) == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; k += 2)
+        *reinterpret_cast<longlong2*>(off + i0 + k) = make_longlong2(ex + loc[k], ex + loc[k + 1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (i0 + k < n) off[i0 + k] = ex + loc[k];
+    }
+    carry += pass_total;
+    __syncthreads();   // warp_tot and pass_total are rewritten by the next pass
   }
-  __syncthreads();
-  int64_t run = (wid > 0 ? warp_tot[wid - 1] : 0) + incl - local;
-  for (int64_t i = b; i < e; ++i) {
-    off[i] = run;
-    run += counts[i];
-  }
-  if (t == nt - 1) {
-    off[n] = run;
-    if (total_out) *total_out = run;
+  if (t == 0) {
+    off[n] = carry;
+    if (total_out) *total_out = carry;
   }
 }
 
