@@ -357,6 +357,56 @@ __device__ __forceinline__ void quarter_x(const RowIn& in, int q, float v[16]) {
   }
 }
 
+// Column c (0..7) of quarter q (1..3) of the input row for a ray with
+// direction d: q1 sin p = c + 1; q2 sin p = 9 + c (c < 3), cos p = c - 3;
+// q3 cos p = 5 + c (c < 7), the constant 1 (c = 7); argument 2^f d_a, p = 4 a + f.
+__device__ __forceinline__ float enc_col(int q, int c, float d0, float d1, float d2) {
+  if (q == 3 && c == 7) return 1.0f;
+  const bool is_cos = q == 3 || (q == 2 && c >= 3);
+  const int p = q == 1 ? c + 1 : (q == 2 ? (c < 3 ? 9 + c : c - 3) : 5 + c);
+  const float da = (p >> 2) == 0 ? d0 : ((p >> 2) == 1 ? d1 : d2);
+  float sv, cv;
+  sincosf(da * (float)(1 << (p & 3)), &sv, &cv);
+  return is_cos ? cv : sv;
+}
+
+// quarter_x for q = 1..3, with the direction encoding evaluated once per
+// distinct ray of the warp's 32 rows (consecutive samples mostly share a ray):
+// for up to 8 distinct rays, lane 8 j' + c evaluates column c of the j-th
+// ray (4 rays per round) and each row collects its 8 columns by shuffles.
+__device__ __forceinline__ void quarter_x_shared(const RowIn& in, int q, int lane, float v[16]) {
+  const int key = in.s >= 0 ? in.r : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  const unsigned leaders = __ballot_sync(0xffffffffu, lane == leader);
+  const int nd = __popc(leaders);
+  if (nd > 8) {   // warp-uniform
+    quarter_x(in, q, v);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+  const int rank = __popc(leaders & ((1u << leader) - 1u));
+  for (int r0 = 0; r0 < nd; r0 += 4) {
+    const int j = min(r0 + (lane >> 3), nd - 1), c = lane & 7;
+    const int src = (int)__fns(leaders, 0, j + 1);
+    const float d0 = __shfl_sync(0xffffffffu, in.d[0], src);
+    const float d1 = __shfl_sync(0xffffffffu, in.d[1], src);
+    const float d2 = __shfl_sync(0xffffffffu, in.d[2], src);
+    const float val = enc_col(q, c, d0, d1, d2);
+    const bool mine = rank >= r0 && rank < r0 + 4;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const float t = __shfl_sync(0xffffffffu, val, ((rank - r0) & 3) * 8 + cc);
+      if (mine) v[cc] = t;
+    }
+  }
+  if (in.s < 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+  }
+}
+
 // Forward shared memory: split W1 and W2 (resident), two X buffers, and the
 // staging copy of a tile's split H1 for the image.
 constexpr uint32_t gW1h = 0, gW1l = gW1h + kW1Bytes, gW2h = gW1l + kW1Bytes, gW2l = gW2h + kW2Bytes,
@@ -524,7 +574,10 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
     // X of tile k (rows loaded in `in`) into buffer k & 1 and the image
     auto write_x = [&](int64_t k) {
       float x[16];
-      quarter_x(in, qw, x);
+      if (qw == 0)
+        quarter_x(in, 0, x);
+      else
+        quarter_x_shared(in, qw, lane, x);
 #pragma unroll
       for (int i = 0; i < 16; ++i) x[i] *= kSX;
       uint8_t* xs = sm + gX0 + (k & 1) * gXBuf;
