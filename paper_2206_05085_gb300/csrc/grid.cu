@@ -507,33 +507,68 @@ __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v,
   changed = true;
 }
 
-// Adam over entries [base, end) of one array, float4 body (base a multiple of 4).
+// One float4 group of Adam entries at i (p, m, v loaded by the caller when g
+// is non-zero anywhere in the group).
+__device__ __forceinline__ void adam_group(float* __restrict__ p, uint16_t* __restrict__ shadow,
+                                           float* __restrict__ g, float* __restrict__ m,
+                                           float* __restrict__ v, int64_t i, float4 gg, float4 pp,
+                                           float4 mm, float4 vv, const AdamArgs& a, int zero_grad) {
+  bool ch = false;
+  adam_one(pp.x, gg.x, mm.x, vv.x, a, ch);
+  adam_one(pp.y, gg.y, mm.y, vv.y, a, ch);
+  adam_one(pp.z, gg.z, mm.z, vv.z, a, ch);
+  adam_one(pp.w, gg.w, mm.w, vv.w, a, ch);
+  *reinterpret_cast<float4*>(p + i) = pp;
+  *reinterpret_cast<float4*>(m + i) = mm;
+  *reinterpret_cast<float4*>(v + i) = vv;
+  if (zero_grad) *reinterpret_cast<float4*>(g + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (shadow) {
+    uint2 sh;
+    sh.x = (uint32_t)f32_to_bf16_bits(pp.x) | ((uint32_t)f32_to_bf16_bits(pp.y) << 16);
+    sh.y = (uint32_t)f32_to_bf16_bits(pp.z) | ((uint32_t)f32_to_bf16_bits(pp.w) << 16);
+    *reinterpret_cast<uint2*>(shadow + i) = sh;
+  }
+}
+
+__device__ __forceinline__ bool nonzero4(float4 v) {
+  return v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f;
+}
+
+// Adam over entries [base, end) of one array, float4 body (base a multiple of
+// 4).  Two groups per thread and step: both gradients are loaded, then the
+// state of whichever is non-zero, so their loads are in flight together.
 __device__ __forceinline__ void adam_range(float* __restrict__ p, uint16_t* __restrict__ shadow,
                                            float* __restrict__ g, float* __restrict__ m,
                                            float* __restrict__ v, int64_t base, int64_t end,
                                            const AdamArgs& a, int zero_grad) {
-  for (int64_t i = base + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
+  const int64_t stride = 4 * (int64_t)blockDim.x;
+  int64_t i = base + 4 * (int64_t)threadIdx.x;
+  for (; i + stride + 4 <= end; i += 2 * stride) {
+    const int64_t j = i + stride;
+    const float4 g0 = *reinterpret_cast<const float4*>(g + i);
+    const float4 g1 = *reinterpret_cast<const float4*>(g + j);
+    const bool n0 = nonzero4(g0), n1 = nonzero4(g1);
+    float4 p0, m0, v0, p1, m1, v1;
+    if (n0) {
+      p0 = *reinterpret_cast<const float4*>(p + i);
+      m0 = *reinterpret_cast<const float4*>(m + i);
+      v0 = *reinterpret_cast<const float4*>(v + i);
+    }
+    if (n1) {
+      p1 = *reinterpret_cast<const float4*>(p + j);
+      m1 = *reinterpret_cast<const float4*>(m + j);
+      v1 = *reinterpret_cast<const float4*>(v + j);
+    }
+    if (n0) adam_group(p, shadow, g, m, v, i, g0, p0, m0, v0, a, zero_grad);
+    if (n1) adam_group(p, shadow, g, m, v, j, g1, p1, m1, v1, a, zero_grad);
+  }
+  for (; i < end; i += stride) {
     if (i + 4 <= end) {
-      float4 gg = *reinterpret_cast<float4*>(g + i);
-      if (gg.x == 0.0f && gg.y == 0.0f && gg.z == 0.0f && gg.w == 0.0f) continue;
-      float4 pp = *reinterpret_cast<float4*>(p + i);
-      float4 mm = *reinterpret_cast<float4*>(m + i);
-      float4 vv = *reinterpret_cast<float4*>(v + i);
-      bool ch = false;
-      adam_one(pp.x, gg.x, mm.x, vv.x, a, ch);
-      adam_one(pp.y, gg.y, mm.y, vv.y, a, ch);
-      adam_one(pp.z, gg.z, mm.z, vv.z, a, ch);
-      adam_one(pp.w, gg.w, mm.w, vv.w, a, ch);
-      *reinterpret_cast<float4*>(p + i) = pp;
-      *reinterpret_cast<float4*>(m + i) = mm;
-      *reinterpret_cast<float4*>(v + i) = vv;
-      if (zero_grad) *reinterpret_cast<float4*>(g + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (shadow) {
-        uint2 sh;
-        sh.x = (uint32_t)f32_to_bf16_bits(pp.x) | ((uint32_t)f32_to_bf16_bits(pp.y) << 16);
-        sh.y = (uint32_t)f32_to_bf16_bits(pp.z) | ((uint32_t)f32_to_bf16_bits(pp.w) << 16);
-        *reinterpret_cast<uint2*>(shadow + i) = sh;
-      }
+      const float4 gg = *reinterpret_cast<const float4*>(g + i);
+      if (!nonzero4(gg)) continue;
+      adam_group(p, shadow, g, m, v, i, gg, *reinterpret_cast<const float4*>(p + i),
+                 *reinterpret_cast<const float4*>(m + i), *reinterpret_cast<const float4*>(v + i), a,
+                 zero_grad);
     } else {
       for (int64_t e = i; e < end; ++e) {
         bool ch = false;
