@@ -184,3 +184,64 @@ def test_captured_step_replays_like_eager(T):
         d = np.abs(a - b)
         assert np.mean(d > 1e-3 * rp.lr_grid) < 1e-4
         assert np.max(d) <= 2 * rp.lr_grid
+
+
+def test_full_size_step_sampled_outputs(T):
+    """The benchmark's own configuration - dvgo_160 at 8192 rays, the FP32 form
+    with the colour MLP on the tensor cores, one replay of the captured step -
+    checked where the oracle can follow it: the whole sample list (bit-exact
+    against the oracle's sampler), the per-ray and per-sample outputs of 48
+    sampled rays (oracle run on those rays, gradients rescaled to the batch's
+    1/R), and the loss as the mean of the per-ray terms."""
+    import oracle
+    from oracle_step import forward_backward, sample, shift32
+    from paper_2206_05085_gb300 import _lib as L
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg, seed=0)
+    tgt = synth.target_rgb(cfg, seed=0)
+    R = cfg.n_rays
+    tr = T.Trainer(cfg, rp, D, Fg, P, n_rays=R, precision="f32tc")
+    to, td, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (o, d, tgt))
+    graph, _ = tr.capture(to, td, tt)        # its two eager warm-up steps change the state
+    for gp, dense, C in ((tr.density, D, 1), (tr.feature, Fg, 12)):
+        L.grid_pack(torch.from_numpy(np.ascontiguousarray(dense, np.float32)).cuda(), gp.p, tr.G, C, L.F32)
+        gp.m.zero_()
+        gp.v.zero_()
+    tr.mlp.copy_(torch.from_numpy(P).cuda())
+    tr.mlp_m.zero_()
+    tr.mlp_v.zero_()
+    tr.step_dev.zero_()
+    graph.replay()
+    ray_off = host(tr.ray_off)
+    S = int(ray_off[-1])
+    n_live = host(tr.n_live)
+    color, L_r, loss = host(tr.color), host(tr.L_r), host(tr.loss)
+    w, rgb, g_raw, g_k0, xyz = (host(x[:S]) for x in (tr.w, tr.rgb, tr.g_raw, tr.g_k0, tr.xyz))
+    # the whole sample list
+    mask = oracle.build_mask(D, shift32(rp.alpha_init), rp.interval, rp.mask_thres)
+    smp = sample(cfg, rp, o, d, mask)
+    assert np.array_equal(ray_off, smp.ray_off)
+    assert np.array_equal(xyz, smp.xyz)
+    # the loss from the per-ray terms (FP64 on the host)
+    mse = np.mean((color.astype(np.float64) - tgt) ** 2)
+    ld = np.mean(L_r.astype(np.float64))
+    assert rel_err(loss, np.array([mse, ld, mse + rp.lambda_dist * ld])) < 1e-5
+    # 48 sampled rays against the oracle on those rays alone
+    rng = np.random.default_rng(7)
+    sel = np.sort(rng.choice(R, 48, replace=False))
+    fb = forward_backward(cfg, rp, D, Fg, P, o[sel], d[sel], tgt[sel])
+    assert np.array_equal(n_live[sel], fb["n_live"])
+    assert rel_err(color[sel], fb["color"]) < 1e-5
+    assert rel_err(L_r[sel], fb["L_r"]) < 1e-5
+    rows = np.concatenate([np.arange(ray_off[r], ray_off[r + 1]) for r in sel]).astype(np.int64)
+    live = fb["live"]
+    scale = len(sel) / R                     # the oracle's gradients carry 1/48, the batch's 1/8192
+    assert rel_err(w[rows], fb["w"]) < 1e-5
+    assert rel_err(rgb[rows][live], fb["rgb"][live]) < 1e-5
+    assert rel_err(g_raw[rows][live], fb["g_raw"][live] * scale) < 1e-5
+    # g_k0 per live sample, except samples whose ReLU input sits within rounding of 0
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"], False)
+    keep = zmin >= 1e-6
+    assert rel_err(g_k0[rows][live][keep], fb["g_k0"][keep] * scale) < 1e-5
