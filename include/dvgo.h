@@ -150,7 +150,10 @@ size_t dvgo_sample_rays_workspace_size(int64_t R);
  * dense uint8 grid (may be NULL).  Outputs (capacity S_cap >= R*max_steps
  * is required, so the list never overflows): ray_off [R+1] (ray_off[R] is
  * the sample count S), xyz [S_cap][3], ray_id, step_k [S_cap] int32,
- * s_mid, s_len [S_cap] f32.  ws: dvgo_sample_rays_workspace_size(R) bytes. */
+ * s_mid, s_len [S_cap] f32.  ws: dvgo_sample_rays_workspace_size(R) bytes of
+ * device scratch owned by the caller (per-ray counts, then per-ray keep bits
+ * of the first 1024 steps, which the second pass reads instead of repeating
+ * the occupancy lookups; longer marches repeat them).  Needs no clearing. */
 int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
                      const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
                      const uint8_t* mask, int64_t S_cap, int64_t* ray_off, float* xyz,

@@ -90,10 +90,19 @@ __device__ __forceinline__ void load_ray(const float* __restrict__ ro, const flo
   }
 }
 
-// Mode 0, pass 1: one warp per ray counts the kept samples.
+// Steps per ray whose keep bits pass 1 records for pass 2: one word of 32
+// steps per lane of the ray's warp (1024 steps).  Longer marches recompute
+// the keep test in pass 2.
+constexpr int kBitWords = 32;
+
+// Mode 0, pass 1: one warp per ray counts the kept samples.  With bits,
+// the warp also stores each 32-step chunk's keep ballot (lane j holds chunk
+// j's word; one coalesced store per ray), so that pass 2 need not repeat the
+// occupancy lookups.
 __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
                                   const float* __restrict__ rd, int64_t R,
-                                  const uint8_t* __restrict__ mask, int32_t* __restrict__ counts) {
+                                  const uint8_t* __restrict__ mask, int32_t* __restrict__ counts,
+                                  uint32_t* __restrict__ bits) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -102,6 +111,7 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
     load_ray(ro, rd, r, o, d);
     RaySpan sp = ray_span(A, o, d);
     int cnt = 0;
+    uint32_t mine = 0;
     for (int k0 = 0; k0 < sp.n; k0 += 32) {
       int k = k0 + lane;
       bool keep = false;
@@ -110,16 +120,23 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
         point_at(A, o, d, sp.tlo, k, x);
         keep = keep_point(A, mask, x);
       }
-      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == (k0 >> 5)) mine = bal;
+      cnt += __popc(bal);
     }
     if (lane == 0) counts[r] = cnt;
+    if (bits && 32 * lane < sp.n) bits[r * kBitWords + lane] = mine;
   }
 }
 
 // Mode 0, pass 2: one warp per ray writes the kept samples in step order.
+// With bits (only when max_steps <= 32 kBitWords = 1024) the keep decisions are
+// pass 1's ballots; without, the keep test is evaluated again (same FP32
+// operations, same result).
 __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
                                  const float* __restrict__ rd, int64_t R,
                                  const uint8_t* __restrict__ mask,
+                                 const uint32_t* __restrict__ bits,
                                  const int64_t* __restrict__ ray_off, float* __restrict__ xyz,
                                  int32_t* __restrict__ ray_id, int32_t* __restrict__ step_k,
                                  float* __restrict__ s_mid, float* __restrict__ s_len) {
@@ -134,15 +151,24 @@ __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
     float span = __fsub_rn(sp.thi, sp.tlo);
     float slen = __fdiv_rn(A.s.step, span);
     int64_t pos = ray_off[r];
+    uint32_t mine = 0;
+    if (bits && 32 * lane < sp.n) mine = bits[r * kBitWords + lane];
     for (int k0 = 0; k0 < sp.n; k0 += 32) {
       int k = k0 + lane;
       bool keep = false;
       float x[3];
-      if (k < sp.n) {
-        point_at(A, o, d, sp.tlo, k, x);
-        keep = keep_point(A, mask, x);
+      unsigned bal;
+      if (bits) {
+        bal = __shfl_sync(0xffffffffu, mine, k0 >> 5);
+        keep = (bal >> lane) & 1u;
+        if (keep) point_at(A, o, d, sp.tlo, k, x);
+      } else {
+        if (k < sp.n) {
+          point_at(A, o, d, sp.tlo, k, x);
+          keep = keep_point(A, mask, x);
+        }
+        bal = __ballot_sync(0xffffffffu, keep);
       }
-      unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) {
         int64_t s = pos + __popc(bal & lt_mask);
         xyz[3 * s + 0] = x[0];
@@ -355,8 +381,14 @@ static bool fill_args(SamplerArgs& A, const dvgo_grid_desc* g, const dvgo_sample
 
 using namespace dvgo;
 
-extern "C" size_t dvgo_sample_rays_workspace_size(int64_t R) {
+// Workspace: per-ray counts ((R+1) int32, padded to 256 bytes), then the
+// per-ray keep bits of pass 1 (R x kBitWords uint32).
+static size_t counts_bytes(int64_t R) {
   return (size_t)((R + 1) * sizeof(int32_t) + 255) / 256 * 256;
+}
+
+extern "C" size_t dvgo_sample_rays_workspace_size(int64_t R) {
+  return counts_bytes(R) + (size_t)R * kBitWords * sizeof(uint32_t);
 }
 
 extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
@@ -383,9 +415,12 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
   if (smp->mode == 0) {
     const int block = 256;
     int g = grid_for(R * 32, block, 16);
-    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts);
+    uint32_t* bits = smp->max_steps <= 32 * kBitWords
+                         ? reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + counts_bytes(R))
+                         : nullptr;
+    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, bits);
     scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
+    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, bits, ray_off, xyz, ray_id,
                                           step_k, s_mid, s_len);
   } else {
     // one warp of rays per block, so that the sequential marches spread over
@@ -488,10 +523,10 @@ extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d
   if (smp->mode == 0) {
     const int block = 256;
     int g = grid_for(R * 32, block, 16);
-    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts);
+    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr);
     scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, ray_off, xyz, ray_id,
-                                          step_k, s_mid, s_len);
+    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+                                          ray_id, step_k, s_mid, s_len);
   } else {
     // one warp of rays per block, so that the sequential marches spread over
     // every SM (8192 rays: 256 blocks)

@@ -277,6 +277,29 @@ def test_sampler_bit_exact(L, name):
     _check_samples(got, ref)
 
 
+@pytest.mark.parametrize("step_scale", [0.55, 0.45])
+def test_sampler_long_march(L, step_scale):
+    """Step caps either side of the 1024-step limit of the recorded keep bits
+    (0.55: max_steps 1010, kept samples up to step ~640, so about 20 bit words
+    per ray; 0.45: max_steps 1232, the second pass evaluates the keep test
+    again)."""
+    import dataclasses
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    step = float(np.float32(rp.step * step_scale))
+    diag = np.sqrt(3.0) * (cfg.bbox_max - cfg.bbox_min)
+    rp = dataclasses.replace(rp, step=step, max_steps=int(np.ceil(diag / step)) + 8)
+    assert (rp.max_steps <= 1024) == (step_scale > 0.5)
+    o, d = synth.rays(cfg, n_rays=400)
+    D = synth.density_grid(cfg)
+    mask_np = oracle.build_mask(D, shift32(), rp.interval, rp.mask_thres)
+    got = _gpu_sample(L, cfg, rp, o, d, dev(mask_np))
+    from oracle_step import sample
+    ref = sample(cfg, rp, o, d, mask_np)
+    assert ref.S > 0 and int(np.max(ref.step_k)) > 512
+    _check_samples(got, ref)
+
+
 def test_sampler_edge_cases(L):
     cfg = synth.CFG2
     rp = synth.render_params(cfg)
