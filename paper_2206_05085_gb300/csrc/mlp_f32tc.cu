@@ -12,11 +12,12 @@
 // (largest |w| s in [2^13, 2^14)), layer inputs by 2^6, hidden activations
 // by 2^4, and the backward's gradient rows G2 = g_z2 and G1 = g_z1 per sample
 // from a bound on that sample's output-layer gradient, so that every sample's
-// input gradient keeps FP32 relative accuracy however small it is.  In the
-// weight-gradient products (sums over samples) the per-sample factor is undone
-// on the other operand: row s of H1 (X) is multiplied by S / s_s, with S the
-// smallest per-sample scale of the whole list (from a first kernel's bound on
-// the upstream gradient), so the accumulator carries the single factor S.
+// input gradient keeps FP32 relative accuracy however small it is.  The
+// weight-gradient products (sums over samples) need one factor for all rows:
+// they read a second copy of each gradient row, the same FP16 terms times
+// S / s_s, with S the scale of the largest bound over the CTA's samples, so
+// the accumulator carries the single factor S (a row far below the largest
+// loses only terms below FP16's subnormal range, 2^-38 of the largest row).
 // Every scale is an exact power of two, undone exactly in the epilogues.  A
 // value whose scaled magnitude reaches 2^15 sets DVGO_ERR_RANGE.
 //
@@ -166,22 +167,39 @@ __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh
   }
 }
 
-// Values 8 g .. 8 g + 7 of a 32-column K-chunk (already scaled) into its
-// tensor-memory split layout at chunk column taddr (the split_pack32 layout).
-__device__ __forceinline__ void tmem_st_split8(uint32_t taddr, int g, const float* v, float& vmax) {
-  uint32_t h[4], l[4];
+// 32 values times s split into the tensor-memory chunk layout: hi terms of
+// value pairs in words 0-15, lo terms in words 16-31 (one tcgen05.st).
+__device__ __forceinline__ void split32(const float (&v)[32], float s, uint32_t (&hl)[32],
+                                        float& vmax) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float a = v[2 * i], b = v[2 * i + 1];
+  for (int c = 0; c < 16; ++c) {
+    const float a = s * v[2 * c], b = s * v[2 * c + 1];
     vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
     const __half2 h2 = __floats2half2_rn(a, b);
     const float2 hf = __half22float2(h2);
     const __half2 l2 = __floats2half2_rn(a - hf.x, b - hf.y);
-    h[i] = *reinterpret_cast<const uint32_t*>(&h2);
-    l[i] = *reinterpret_cast<const uint32_t*>(&l2);
+    hl[c] = *reinterpret_cast<const uint32_t*>(&h2);
+    hl[16 + c] = *reinterpret_cast<const uint32_t*>(&l2);
   }
-  tc::tmem_st4(taddr + 4u * (uint32_t)g, h[0], h[1], h[2], h[3]);
-  tc::tmem_st4(taddr + 16u + 4u * (uint32_t)g, l[0], l[1], l[2], l[3]);
+}
+
+// The split terms of split32 times r (a power of two <= 1, exact in FP16
+// down to its subnormal range) as the hi / lo core-matrix rows of columns
+// k0 .. k0 + 31 of row `row` in shared memory.
+__device__ __forceinline__ void st_terms32(uint8_t* hi, uint8_t* lo, int row, int k0, const uint32_t (&hl)[32],
+                                           __half2 r) {
+  auto m = [&](uint32_t x) {
+    const __half2 y = __hmul2(*reinterpret_cast<const __half2*>(&x), r);
+    return *reinterpret_cast<const uint32_t*>(&y);
+  };
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t off = tc::cm_off(row, k0 + 8 * q, kSboH);
+    *reinterpret_cast<uint4*>(hi + off) =
+        make_uint4(m(hl[4 * q]), m(hl[4 * q + 1]), m(hl[4 * q + 2]), m(hl[4 * q + 3]));
+    *reinterpret_cast<uint4*>(lo + off) =
+        make_uint4(m(hl[16 + 4 * q]), m(hl[17 + 4 * q]), m(hl[18 + 4 * q]), m(hl[19 + 4 * q]));
+  }
 }
 
 // Output-layer constants (exact FP32).
@@ -919,7 +937,6 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
     const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
     const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
-    const float fU1 = S1 / (sG2 * sW2);              //                  -> S1 g_h1
     const float invX = 1.0f / (sG1 * sW1);           // g_X
     // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
     {
@@ -934,26 +951,16 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         g[i] = z2 > 0.0f ? gs : 0.0f;
         v[i] = fmaxf(z2, 0.0f);
       }
-      // the dW2 operand: shared memory, scale S2; the g_h1 operand: tensor
-      // memory over D2, scale sG2
+      // db2 and dW3 sums over the tile's rows first (v is then dead)
+      db2acc += reduce_scatter32_keep<false>(g, 1.0f, lane);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float t[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = S2 * g[8 * q + i];
-        st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, t, vmax);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = sG2 * g[8 * q + i];
-        tmem_st_split8(lane_base + cTmp + 32 * qw, q, t, vmax);
-      }
-      db2acc += reduce_scatter32(g, lane);
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) {
-        float p[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) p[i] = gz3[c] * v[i];
-        dW3acc[c] += reduce_scatter32(p, lane);
-      }
+      for (int c = 0; c < kOut; ++c) dW3acc[c] += reduce_scatter32_keep<true>(v, gz3[c], lane);
+      // the g_h1 operand: tensor memory over D2, scale sG2; the dW2 operand:
+      // the same terms times S2 / sG2 in shared memory (scale S2)
+      uint32_t hl[32];
+      split32(g, sG2, hl, vmax);
+      tc::tmem_st32(lane_base + cTmp + 32 * qw, hl);
+      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(S2 / sG2));
     }
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
@@ -976,16 +983,10 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       tc::tmem_ld32(lane_base + cGH + 32 * qw, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float t[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = fU1 * v[8 * q + i];
-        st_split8(sm + bGh, sm + bGl, row, 32 * qw + q * 8, kSboH, t, vmax);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = fG1 * v[8 * q + i];
-        tmem_st_split8(lane_base + cGH + 32 * qw, q, t, vmax);
-      }
+      uint32_t hl[32];
+      split32(v, fG1, hl, vmax);
+      tc::tmem_st32(lane_base + cGH + 32 * qw, hl);
+      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(S1 / sG1));
     }
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
