@@ -45,7 +45,8 @@ __device__ int g_mlp_tc_status;  // first error a kernel of this file met
 namespace x3 {
 
 constexpr int kK1 = 48;                           // padded input width
-constexpr uint32_t kSboX = (kK1 / 8) * 128;       // 768: 8-row group stride, 48-wide rows
+constexpr uint32_t kSboX = (kK1 / 8) * 128;       // 768: one term of an 8-row group, 48-wide rows
+constexpr uint32_t kSboXs = 2 * kSboX;            // 1536: X's 8-row group, hi then lo terms
 constexpr uint32_t kSboH = (kHid / 8) * 128;      // 2048: 128-wide rows
 constexpr uint32_t kSboW1s = (32 / 8) * 128;      // 512: W1[:, 0:16] hi and lo side by side per 8 rows
 constexpr uint32_t kXBytes = kTile * kK1 * 2;     // one term of X
@@ -53,8 +54,10 @@ constexpr uint32_t kHBytes = kTile * kHid * 2;    // one term of H1 or G
 constexpr uint32_t kW1Bytes = kHid * kK1 * 2;
 constexpr uint32_t kW1sBytes = kHid * 16 * 2;
 constexpr uint32_t kW2Bytes = kHid * kHid * 2;
-constexpr uint32_t kImage = 2 * kXBytes + 2 * kHBytes;  // [Xh | Xl | H1h | H1l]
-constexpr uint32_t iXh = 0, iXl = kXBytes, iHh = 2 * kXBytes, iHl = 2 * kXBytes + kHBytes;
+// Tile image [X | H1h | H1l]: X's hi and lo core matrices side by side in
+// each 8-row group (so that [Xh | Xl] is one 96-wide operand of dW1).
+constexpr uint32_t kImage = 2 * kXBytes + 2 * kHBytes;
+constexpr uint32_t iX = 0, iHh = 2 * kXBytes, iHl = 2 * kXBytes + kHBytes;
 constexpr uint32_t kActHeader = 256;
 constexpr float kSX = 64.0f;     // input scale
 constexpr float kSH = 16.0f;     // hidden-activation scale
@@ -66,7 +69,7 @@ constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
                    bImg = bW1h + 2 * kW1sBytes, bGh = bImg + kImage,
                    bGl = bGh + kHBytes, bEnd = bGl + kHBytes;
 // tensor-memory columns of the backward
-constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 320, cGH = 384;
+constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 352, cGH = 384;
 
 struct Side {
   float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
@@ -558,9 +561,9 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
       if (lane == 0) {
         uint8_t* xb = sm + gX0 + b * gXBuf;
         tc::bulk_wait_read();   // staging (H1 of k - 1) and X buffer b's older copy are read
-        tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iXh, xb, 2 * kXBytes);
+        tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iX, xb, 2 * kXBytes);
         const uint32_t xs = tc::smem_u32(xb);
-        mma3(buf, xs, xs + kXBytes, 256, 128, kSboX, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
+        mma3(buf, xs, xs + kSboX, 256, 128, kSboXs, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
         tc::mma_commit(&fs->l1_full[b]);
       }
       __syncwarp();
@@ -599,8 +602,8 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
 #pragma unroll
       for (int i = 0; i < 16; ++i) x[i] *= kSX;
       uint8_t* xs = sm + gX0 + (k & 1) * gXBuf;
-      st_split8(xs, xs + kXBytes, row, fb * 8, kSboX, x, vmax);
-      if (nb == 2) st_split8(xs, xs + kXBytes, row, fb * 8 + 8, kSboX, x + 8, vmax);
+      st_split8(xs, xs + kSboX, row, fb * 8, kSboXs, x, vmax);
+      if (nb == 2) st_split8(xs, xs + kSboX, row, fb * 8 + 8, kSboXs, x + 8, vmax);
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&fs->x_full[k & 1]);
@@ -765,7 +768,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   };
   auto load_x = [&](int64_t tile) {
     tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
-    tc::bulk_g2s(img + iXh, img_g + (size_t)tile * kImage + iXh, 2 * kXBytes, &fs->bar_x);
+    tc::bulk_g2s(img + iX, img_g + (size_t)tile * kImage + iX, 2 * kXBytes, &fs->bar_x);
     inflight_x = true;
   };
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
@@ -845,7 +848,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sW1h = tc::smem_u32(sm + bW1h);
   const uint32_t sW2h = tc::smem_u32(sm + bW2h), sW2l = tc::smem_u32(sm + bW2l);
-  const uint32_t sXh = tc::smem_u32(img + iXh), sXl = tc::smem_u32(img + iXl);
+  const uint32_t sX = tc::smem_u32(img + iX);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
   const uint32_t sGh = tc::smem_u32(sm + bGh), sGl = tc::smem_u32(sm + bGl);
   float dW3acc[kOut], db2acc = 0.0f, db3acc[kOut];
@@ -994,8 +997,19 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     __syncthreads();
     if (tid == 0) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
       tc::fence_after_sync();
-      mma3(tmem + cDW1, sGh, sGl, 2 * kSboH, kSboH, 128, sXh, sXl, 2 * kSboX, kSboX, 128, kTile / 16,
-           tc::idesc_f16(128, kK1, 1, 1), dw_started);
+      {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
+        const uint32_t id96 = tc::idesc_f16(128, 2 * kK1, 1, 1), id48 = tc::idesc_f16(128, kK1, 1, 1);
+        uint64_t dah = tc::smem_desc(sGh, kSboH, 128), dal = tc::smem_desc(sGl, kSboH, 128);
+        uint64_t dbx = tc::smem_desc(sX, kSboXs, 128);
+#pragma unroll 1
+        for (int k = 0; k < kTile / 16; ++k) {
+          tc::mma_bf16(tmem + cDW1, dah, dbx, id96, (dw_started || k > 0) ? 1u : 0u);
+          tc::mma_bf16(tmem + cDW1, dal, dbx, id48, 1u);
+          dah += (2 * kSboH) >> 4;
+          dal += (2 * kSboH) >> 4;
+          dbx += (2 * kSboXs) >> 4;
+        }
+      }
       {   // per K step: G1h [W1h | W1l] (N = 32: hi*hi in columns 0-15, hi*lo in 16-31), G1l W1h
         const uint32_t id32 = tc::idesc_f16(128, 32, 0, 1), id16 = tc::idesc_f16(128, 16, 0, 1);
         uint64_t db = tc::smem_desc(sW1h, kSboW1s, 128);
@@ -1077,9 +1091,16 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     float* tp = reinterpret_cast<float*>(sm + bImg) + warp * 32 * 33;
     const float u2 = ok ? 1.0f / (S2 * kSH) : 0.0f, u1 = ok ? 1.0f / (S1 * kSX) : 0.0f;
     const int o0 = (warp & 3) * 32;
-    auto flush32 = [&](uint32_t col, float scale, int base, int stride) {
+    // columns col (plus columns col2, when given) of this warp's 32 lanes
+    auto flush32 = [&](uint32_t col, float scale, int base, int stride, uint32_t col2 = 0) {
       float v[32];
       tc::tmem_ld32(lane_base + col, v);
+      if (col2) {
+        float v2[32];
+        tc::tmem_ld32(lane_base + col2, v2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += v2[i];
+      }
 #pragma unroll
       for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i] * scale;
       __syncwarp();
@@ -1087,13 +1108,15 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       __syncwarp();
     };
     flush32(cDW2 + 32 * qw, u2, kOffW2 + 32 * qw, kHid);
+    // dW1 | db1: the sum of the hi*hi + lo*hi columns and the hi*lo columns
     if (qw == 0) {
-      flush32(cDW1, u1, kOffW1, kIn);                           // W1[:, 0:32]
+      flush32(cDW1, u1, kOffW1, kIn, cDW1 + kK1);              // W1[:, 0:32]
     } else if (qw == 1) {
-      float v[16];
+      float v[16], v2[16];
       tc::tmem_ld16(lane_base + cDW1 + 32, v);                  // W1[:, 32:39] and b1 (column 39)
+      tc::tmem_ld16(lane_base + cDW1 + kK1 + 32, v2);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tp[lane * 33 + i] = v[i] * u1;
+      for (int i = 0; i < 8; ++i) tp[lane * 33 + i] = (v[i] + v2[i]) * u1;
       __syncwarp();
       for (int r = 0; r < 32; ++r) {
         if (lane < kIn - 32) P[kOffW1 + (o0 + r) * kIn + 32 + lane] = tp[r * 33 + lane];
