@@ -365,7 +365,7 @@ MLP_BWD_FLOP = 2 * (2 * 3 * 128 + 2 * 128 * 128 + 128 * 40 + 128 * 12)
 MLP_BWD_FLOP_RECOMPUTE = MLP_BWD_FLOP + 2 * (39 * 128 + 128 * 128)
 MLP_BWD_FLOP_TC = MLP_BWD_FLOP + 2 * 128 * 128
 # kernels launched per C-ABI call (others launch one); the FP32 tensor-core MLP
-# backward runs a bound kernel, the backward and the partial-gradient reduction
+# backward runs the backward and the partial-gradient reduction
 KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1}
 
 

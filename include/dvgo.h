@@ -318,9 +318,10 @@ int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
  * position j; with it (and rgb, the forward's output, may be NULL) the
  * backward reads the hidden activations instead of recomputing them.
  * DVGO_F32_TC: act is the buffer its forward filled for the same list and
- * count (required; rgb ignored); the backward also writes the per-CTA
- * partial gradients stored after the tile images, and sums those partials
- * in a fixed order (deterministic).
+ * count, and rgb that forward's output (both required: the output layer's
+ * sigmoid derivative is y (1 - y) with y = rgb[s], not recomputed); the
+ * backward also writes the per-CTA partial gradients stored after the tile
+ * images, and sums those partials in a fixed order (deterministic).
  * DVGO_BF16: rgb is ignored (the tensor cores recompute the forward); act,
  * if given (dvgo_rgbnet_act_bytes(n_cap, DVGO_BF16) bytes), holds per-CTA
  * partial gradients summed in a fixed order; without it the backward adds

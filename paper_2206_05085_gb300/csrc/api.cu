@@ -15,8 +15,9 @@ int dvgo_rgbnet_bwd_bf16(const float*, const float*, const float*, const float*,
 int dvgo_mlp_status_read_and_clear(cudaStream_t);
 int dvgo_rgbnet_fwd_f32tc(const float*, const float*, const int32_t*, const int32_t*, int64_t,
                           const int64_t*, const float*, float*, float*, cudaStream_t);
-int dvgo_rgbnet_bwd_f32tc(const float*, const float*, const float*, const int32_t*, const int32_t*,
-                          int64_t, const int64_t*, const float*, float*, float*, float*, cudaStream_t);
+int dvgo_rgbnet_bwd_f32tc(const float*, const float*, const float*, const float*, const int32_t*,
+                          const int32_t*, int64_t, const int64_t*, const float*, float*, float*, float*,
+                          cudaStream_t);
 int64_t rgbnet_act_bytes_tc(int64_t);
 int dvgo_mlp_tc_status_read_and_clear(cudaStream_t);
 
@@ -78,9 +79,10 @@ extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const f
     return dvgo_rgbnet_bwd_bf16(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
                                 g_params, g_k0, const_cast<float*>(act), st);
   if (precision == DVGO_F32_TC) {
-    DVGO_CHECK_ARG(act != nullptr);
-    // the backward writes its gradient bound into the first bytes of act
-    return dvgo_rgbnet_bwd_f32tc(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
+    // act: the forward's tile images (read) and the per-CTA partial rows
+    // (written); rgb: the forward's output, for the sigmoid derivative
+    DVGO_CHECK_ARG(act != nullptr && rgb != nullptr);
+    return dvgo_rgbnet_bwd_f32tc(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev, params,
                                  const_cast<float*>(act), g_params, g_k0, st);
   }
   return DVGO_ERR_INVALID_ARG;

@@ -13,11 +13,11 @@
 // by 2^4, and the backward's gradient rows G2 = g_z2 and G1 = g_z1 per sample
 // from a bound on that sample's output-layer gradient, so that every sample's
 // input gradient keeps FP32 relative accuracy however small it is.  The
-// weight-gradient products (sums over samples) need one factor for all rows:
-// they read a second copy of each gradient row, the same FP16 terms times
-// S / s_s, with S the scale of the largest bound over the CTA's samples, so
-// the accumulator carries the single factor S (a row far below the largest
-// loses only terms below FP16's subnormal range, 2^-38 of the largest row).
+// weight-gradient products (sums over samples) need one factor for all rows,
+// S, the scale of the largest bound over the CTA's samples: dW2 reads H1 with
+// row s multiplied by S / s_s, dW1 a second copy of G1's terms times S / s_s
+// (a row far below the largest loses only terms below FP16's subnormal range,
+// 2^-38 of the largest row).
 // Every scale is an exact power of two, undone exactly in the epilogues.  A
 // value whose scaled magnitude reaches 2^15 sets DVGO_ERR_RANGE.
 //
@@ -26,11 +26,14 @@
 //   relu(D1) -> D2 = H1 W2^T -> z2 = D2 + b2 -> output layer and sigmoid on
 //   the CUDA cores in FP32.  The split X and H1 of the tile (90112 bytes, the
 //   shared-memory image) go to the act buffer with one bulk copy.
-// Backward, per tile: bulk-load the tile's image; D2 = H1 W2^T again; on the
-//   CUDA cores z3, g_z3, dW3, db3, g_h2 and G2 = g_z2 (and db2 = sum of G2);
-//   then dW2 += G2^T H1 and g_h1 = G2 W2; G1 = g_h1 * (H1 > 0);
-//   dW1 (+db1 through X's ones column) += G1^T X and g_X = G1 W1[:, 0:16]
-//   (-> g_k0).  dW2 and dW1 stay in tensor memory for the whole kernel.
+// Backward, per tile: bulk-load the tile's image; D2^T = W2 H1^T again (one
+//   hidden unit per TMEM lane, so that sums over the tile's rows stay in a
+//   thread's registers); on the CUDA cores g_z3 = g_rgb y (1 - y) from the
+//   forward's output y, G2 = g_z2, dW3, db2 and db3; then dW2 += G2^T H1 and
+//   g_h1 = G2 W2 (one shared-memory copy of G2 serves both); G1 = g_h1 *
+//   (H1 > 0); dW1 (+db1 through X's ones column) += G1^T X and g_X =
+//   G1 W1[:, 0:16] (-> g_k0).  dW2 and dW1 stay in tensor memory for the
+//   whole kernel.
 // Every wait on an mbarrier is bounded (DVGO_ERR_TIMEOUT).
 #include <cuda_fp16.h>
 
@@ -72,8 +75,7 @@ constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
 constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 352, cGH = 384;
 
 struct Side {
-  float4 ob[kHid];   // per hidden unit o: (b2[o], W3[0][o], W3[1][o], W3[2][o])
-  float b3[4];
+  float4 smp[kTile];  // per tile row: (g_z3[0..2], the row's gradient scale sG2)
   float red[16];
   uint64_t bar_h;     // H1 terms of a tile image landed
   uint64_t bar_x;     // X terms landed
@@ -189,12 +191,14 @@ __device__ __forceinline__ void split32(const float (&v)[32], float s, uint32_t 
 // The split terms of split32 times r (a power of two <= 1, exact in FP16
 // down to its subnormal range) as the hi / lo core-matrix rows of columns
 // k0 .. k0 + 31 of row `row` in shared memory.
+__device__ __forceinline__ uint32_t hmul2_u32(uint32_t x, __half2 r) {
+  const __half2 y = __hmul2(*reinterpret_cast<const __half2*>(&x), r);
+  return *reinterpret_cast<const uint32_t*>(&y);
+}
+template <bool kScale = true>
 __device__ __forceinline__ void st_terms32(uint8_t* hi, uint8_t* lo, int row, int k0, const uint32_t (&hl)[32],
                                            __half2 r) {
-  auto m = [&](uint32_t x) {
-    const __half2 y = __hmul2(*reinterpret_cast<const __half2*>(&x), r);
-    return *reinterpret_cast<const uint32_t*>(&y);
-  };
+  auto m = [&](uint32_t x) { return kScale ? hmul2_u32(x, r) : x; };
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t off = tc::cm_off(row, k0 + 8 * q, kSboH);
@@ -723,7 +727,7 @@ struct UpIn {
   int64_t s;       // sample index (-1 past the list end)
   int32_t r;
   float ws;
-  float g[kOut];
+  float g[kOut];   // the upstream colour gradient, then (up_l3) g_z3
 };
 
 __device__ __forceinline__ void up_l1(UpIn& u, const int32_t* __restrict__ idx, int64_t j, int64_t n) {
@@ -740,18 +744,26 @@ __device__ __forceinline__ void up_l2(UpIn& u, const float* __restrict__ g_rgb, 
     u.r = __ldg(ray_id + u.s);
   }
 }
+// g_z3 = g_rgb * y (1 - y) with y = rgb[s], the forward's sigmoid output.
 __device__ __forceinline__ void up_l3(UpIn& u, const float* __restrict__ g_rgb,
-                                      const float* __restrict__ g_color) {
-  if (u.s < 0 || g_rgb) return;
+                                      const float* __restrict__ g_color, const float* __restrict__ rgb) {
+  if (u.s < 0) return;
+  float y[kOut];
 #pragma unroll
-  for (int c = 0; c < kOut; ++c) u.g[c] = u.ws * __ldg(g_color + 3 * (int64_t)u.r + c);
+  for (int c = 0; c < kOut; ++c) y[c] = __ldg(rgb + 3 * u.s + c);
+  if (!g_rgb) {
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) u.g[c] = u.ws * __ldg(g_color + 3 * (int64_t)u.r + c);
+  }
+#pragma unroll
+  for (int c = 0; c < kOut; ++c) u.g[c] = u.g[c] * y[c] * (1.0f - y[c]);
 }
 
 __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
-    const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx, int64_t n_cap,
-    const int64_t* __restrict__ n_dev, const float* __restrict__ params, const uint8_t* __restrict__ act,
-    float* __restrict__ part, float* __restrict__ g_k0) {
+    const float* __restrict__ rgb, const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx,
+    int64_t n_cap, const int64_t* __restrict__ n_dev, const float* __restrict__ params,
+    const uint8_t* __restrict__ act, float* __restrict__ part, float* __restrict__ g_k0) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + bEnd);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -836,10 +848,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   // group, so that [hi | lo] is one 32-wide B operand of g_X
   load_w1<16>(params, sm + bW1h, sm + bW1h + 256, kSboW1s, sW1);
   load_w2(params, sm + bW2h, sm + bW2l, sW2);
-  load_out_layer(params, fs);
-  up_l3(cur, g_rgb, g_color);
+  up_l3(cur, g_rgb, g_color, rgb);
   const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
-  float* zx = reinterpret_cast<float*>(sm + bGh);  // [4][128][3] output-layer partials (G is free then)
+  // this thread's hidden unit in the transposed layer-2 products (TMEM lane)
+  const int oh = (warp & 3) * 32 + lane;
+  const float b2o = __ldg(params + kOffB2 + oh), w3o0 = __ldg(params + kOffW3 + oh),
+              w3o1 = __ldg(params + kOffW3 + kHid + oh), w3o2 = __ldg(params + kOffW3 + 2 * kHid + oh);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -868,12 +882,24 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int64_t tn = t + gridDim.x;   // this CTA's next tile
     const bool valid = cur.s >= 0;
-    float gup[kOut] = {0.0f, 0.0f, 0.0f};
+    float gz3[kOut] = {0.0f, 0.0f, 0.0f};
     if (valid) {
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) gup[c] = cur.g[c];
+      for (int c = 0; c < kOut; ++c) gz3[c] = cur.g[c];
     }
     const int64_t s = cur.s;
+    // this sample's gradient scales (for g_h1 and g_X); the weight-gradient
+    // products take the CTA-wide S2, S1 instead
+    const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
+    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
+    const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
+    const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
+    const float invX = 1.0f / (sG1 * sW1);           // g_X
+    if (qw == 0) {
+      fs->smp[row] = make_float4(gz3[0], gz3[1], gz3[2], sG2);
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
+    }
     up_l1(nxt, idx, tn * kTile + row, n);
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_in, kSpin) &&
                            tc::mbar_wait(&fs->bar_x, ph_in, kSpin));
@@ -893,91 +919,71 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         if ((int16_t)(wd[i] >> 16) > 0) m1b |= 1u << (k + 1);
       }
     }
-    if (tid == 0) {   // D2 = H1 W2^T
+    if (tid == 0) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
       tc::fence_after_sync();
-      mma3(tmem + cTmp, sHh, sHl, 256, 128, kSboH, sW2h, sW2l, 256, 128, kSboH, kHid / 16,
-           tc::idesc_f16(128, kHid, 0, 0), false);
+      mma3(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH, kHid / 16,
+           tc::idesc_f16(128, kTile, 0, 0), false);
       tc::mma_commit(&fs->bar_mma);
     }
     up_l2(nxt, g_rgb, w, ray_id);
     if (!(ok = mma_wait())) break;
-    // output layer: z3 from both halves, g_z3, db3
+    // Hidden unit oh over the tile rows 32 qw .. 32 qw + 31: G2 = (W3^T g_z3)
+    // * (z2 > 0), and the sums over rows dW3 += g_z3 h2^T, db2 += G2 in
+    // registers.  G2 times the row's scale sG2 goes to shared memory as
+    // [unit][row] core matrices: the K-major A operand of dW2 and the
+    // MN-major A operand of g_h1.
     {
-      float zp[kOut] = {0.0f, 0.0f, 0.0f};
-      {
-        float v[32];
-        tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int o = 32 * qw + i;
-          const float4 q = fs->ob[o];
-          const float h = fmaxf(fmaf(v[i], inv2, q.x), 0.0f);
-          zp[0] = fmaf(q.y, h, zp[0]);
-          zp[1] = fmaf(q.z, h, zp[1]);
-          zp[2] = fmaf(q.w, h, zp[2]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) zx[(qw * kTile + row) * kOut + c] = zp[c];
-    }
-    __syncthreads();
-    float gz3[kOut];
-#pragma unroll
-    for (int c = 0; c < kOut; ++c) {
-      const float* zc = zx + row * kOut + c;
-      const float z3 = fs->b3[c] + (((zc[0] + zc[kTile * kOut]) + zc[2 * kTile * kOut]) + zc[3 * kTile * kOut]);
-      const float y = sigmoid_f(z3);
-      gz3[c] = gup[c] * y * (1.0f - y);
-    }
-    if (qw == 0) {
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
-    }
-    __syncthreads();   // zx (inside the G buffer) is read; G may be written
-    // this sample's gradient scales (for g_h1 and g_X); the weight-gradient
-    // products take the CTA-wide S2, S1 instead
-    const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
-    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
-    const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
-    const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
-    const float invX = 1.0f / (sG1 * sW1);           // g_X
-    // G2 = (W3^T g_z3) * (z2 > 0); dW3 += g_z3 h2^T; db2 += G2 (sums over the tile's rows)
-    {
-      float v[32], g[32];
+      float v[32];
       tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const int o = 32 * qw + i;
-        const float4 q = fs->ob[o];
-        const float z2 = fmaf(v[i], inv2, q.x);
-        const float gs = fmaf(gz3[2], q.w, fmaf(gz3[1], q.z, gz3[0] * q.y));
-        g[i] = z2 > 0.0f ? gs : 0.0f;
-        v[i] = fmaxf(z2, 0.0f);
+        const float4 q = fs->smp[32 * qw + i];
+        const float z2 = fmaf(v[i], inv2, b2o);
+        const float gs = fmaf(w3o2, q.z, fmaf(w3o1, q.y, w3o0 * q.x));
+        const float g = z2 > 0.0f ? gs : 0.0f;
+        const float h = fmaxf(z2, 0.0f);
+        db2acc += g;
+        dW3acc[0] = fmaf(q.x, h, dW3acc[0]);
+        dW3acc[1] = fmaf(q.y, h, dW3acc[1]);
+        dW3acc[2] = fmaf(q.z, h, dW3acc[2]);
+        v[i] = g * q.w;
       }
-      // db2 and dW3 sums over the tile's rows first (v is then dead)
-      db2acc += reduce_scatter32_keep<false>(g, 1.0f, lane);
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) dW3acc[c] += reduce_scatter32_keep<true>(v, gz3[c], lane);
-      // the g_h1 operand: tensor memory over D2, scale sG2; the dW2 operand:
-      // the same terms times S2 / sG2 in shared memory (scale S2)
       uint32_t hl[32];
-      split32(g, sG2, hl, vmax);
-      tc::tmem_st32(lane_base + cTmp + 32 * qw, hl);
-      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(S2 / sG2));
+      split32(v, 1.0f, hl, vmax);
+      st_terms32<false>(sm + bGh, sm + bGl, oh, 32 * qw, hl, __float2half2_rn(1.0f));
     }
-    tc::tmem_wait_st();
+    // H1 row r to the scale kSH S2 / sG2[r], so that dW2 = sum_r G2[r]^T H1[r]
+    // carries the single factor kSH S2 (four threads per row, 32 columns each)
+    {
+      const int hr = tid >> 2, hc = (tid & 3) * 32;
+      const __half2 r2 = __float2half2_rn(S2 / fs->smp[hr].w);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        uint8_t* base = img + (u ? iHl : iHh);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint4* p = reinterpret_cast<uint4*>(base + tc::cm_off(hr, hc + 8 * q, kSboH));
+          uint4 x = *p;
+          x.x = hmul2_u32(x.x, r2);
+          x.y = hmul2_u32(x.y, r2);
+          x.z = hmul2_u32(x.z, r2);
+          x.w = hmul2_u32(x.w, r2);
+          *p = x;
+        }
+      }
+    }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {   // dW2 += G2^T H1;  g_h1 = G2 W2 (A from tensor memory)
+    if (tid == 0) {   // dW2 += G2^T H1 (A K-major);  g_h1 = G2 W2 (A MN-major)
       tc::fence_after_sync();
-      mma3(tmem + cDW2, sGh, sGl, 2 * kSboH, kSboH, 128, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
-           tc::idesc_f16(128, kHid, 1, 1), dw_started);
-      mma3_ts(tmem + cGH, tmem + cTmp, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
-              tc::idesc_f16(128, kHid, 0, 1), false);
+      mma3(tmem + cDW2, sGh, sGl, 256, 128, kSboH, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
+           tc::idesc_f16(128, kHid, 0, 1), dw_started);
+      mma3(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
+           tc::idesc_f16(128, kHid, 1, 1), false);
       tc::mma_commit(&fs->bar_mma);
     }
-    up_l3(nxt, g_rgb, g_color);
+    up_l3(nxt, g_rgb, g_color, rgb);
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
     // G1 = g_h1 * (H1 > 0): at S1 in shared memory (dW1), at sG1 in tensor memory (g_X)
@@ -1075,12 +1081,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   tc::fence_after_sync();
   float* P = part + (size_t)blockIdx.x * kNumParams;
   const bool has_tiles = (int64_t)blockIdx.x < ntiles;
-  if (has_tiles && (warp & 3) == 0) {   // warp 4 q: W3[:, 32 q + lane] and b2[32 q + lane]
+  if (has_tiles && qw == 0) {   // warp l: W3[:, 32 l + lane] and b2[32 l + lane] over the 4 row quarters
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const float v = ((pr[((warp + 0) * 4 + c) * 32 + lane] + pr[((warp + 1) * 4 + c) * 32 + lane]) +
-                       pr[((warp + 2) * 4 + c) * 32 + lane]) + pr[((warp + 3) * 4 + c) * 32 + lane];
-      P[(c < kOut ? kOffW3 + c * kHid : kOffB2) + 32 * qw + lane] = v;
+      const float v = ((pr[((warp + 0) * 4 + c) * 32 + lane] + pr[((warp + 4) * 4 + c) * 32 + lane]) +
+                       pr[((warp + 8) * 4 + c) * 32 + lane]) + pr[((warp + 12) * 4 + c) * 32 + lane];
+      P[(c < kOut ? kOffW3 + c * kHid : kOffB2) + 32 * warp + lane] = v;
     }
   }
   if (has_tiles && tid < kOut) P[kOffB3 + tid] = ((pr3[tid] + pr3[kOut + tid]) + pr3[2 * kOut + tid]) + pr3[3 * kOut + tid];
@@ -1187,7 +1193,7 @@ int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* r
 }
 
 int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float* w,
-                          const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
+                          const float* rgb, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
                           const int64_t* n_dev, const float* params, float* act, float* g_params,
                           float* g_k0, cudaStream_t st) {
   const size_t smem = bEnd + sizeof(Side);
@@ -1198,8 +1204,9 @@ int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float*
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
   float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(act) + act_images_end(n_cap));
-  rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, ray_id, idx, n_cap, n_dev, params,
-                                                reinterpret_cast<const uint8_t*>(act), part, g_k0);
+  rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev,
+                                                params, reinterpret_cast<const uint8_t*>(act), part,
+                                                g_k0);
   partials_reduce_kernel<<<(kNumParams + 31) / 32, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
   return launch_status();
 }

@@ -135,7 +135,7 @@ class RGBNet(torch.autograd.Function):
         g_params = torch.zeros_like(params)
         g_k0 = torch.empty_like(k0)
         L.rgbnet_bwd(g_rgb.contiguous(), None, None, k0, rays_d, ray_id, None, S, None, params,
-                     ctx.prec, g_params, g_k0, ctx.act, rgb if ctx.prec == L.F32 else None)
+                     ctx.prec, g_params, g_k0, ctx.act, None if ctx.prec == L.BF16 else rgb)
         return g_k0, g_params, None, None, None
 
 

@@ -658,7 +658,7 @@ def test_rgbnet_tc_compositing_gradient_wide_range(L):
     g_params = torch.zeros(len(params), device="cuda")
     g_k0 = torch.zeros(n, 12, device="cuda")
     L.rgbnet_bwd(None, dev(g_color), dev(w), dev(k0), dev(d), dev(ray_id), None, n, None,
-                 dev(params), L.F32_TC, g_params, g_k0, act)
+                 dev(params), L.F32_TC, g_params, g_k0, act, rgb)
     assert L.device_status() == 0
     x = oracle.rgbnet_input(k0, d[ray_id])
     assert rel_err(host(rgb), oracle.mlp_fwd(synth.RGBNET_DIMS, params, x, True)) < TOL32
