@@ -879,33 +879,48 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     tc::fence_after_sync();
     return r;
   };
+  // The MMAs are issued by one thread of warp 4; while the tensor core runs
+  // a product, the other warps do the work that does not feed it (this
+  // row's gradient scales, the layer-1 relu mask), warp 4 after its issue.
+  constexpr int kIssuer = 128;
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int64_t tn = t + gridDim.x;   // this CTA's next tile
     const bool valid = cur.s >= 0;
-    float gz3[kOut] = {0.0f, 0.0f, 0.0f};
-    if (valid) {
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) gz3[c] = cur.g[c];
-    }
     const int64_t s = cur.s;
-    // this sample's gradient scales (for g_h1 and g_X); the weight-gradient
-    // products take the CTA-wide S2, S1 instead
-    const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
-    const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
-    const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
-    const float fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
-    const float invX = 1.0f / (sG1 * sW1);           // g_X
-    if (qw == 0) {
-      fs->smp[row] = make_float4(gz3[0], gz3[1], gz3[2], sG2);
+    float fG1 = 0.0f, invX = 0.0f, r1 = 0.0f;
+    // g_z3 of this row's sample and its gradient scales (for g_h1 and g_X);
+    // the weight-gradient products take the CTA-wide S2, S1 instead
+    auto prologue = [&]() {
+      float gz3[kOut] = {0.0f, 0.0f, 0.0f};
+      if (valid) {
 #pragma unroll
-      for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
-    }
+        for (int c = 0; c < kOut; ++c) gz3[c] = cur.g[c];
+      }
+      const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
+      const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
+      const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
+      fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
+      invX = 1.0f / (sG1 * sW1);           // g_X
+      r1 = S1 / sG1;                       // G1 terms -> the dW1 copy
+      if (qw == 0) {
+        fs->smp[row] = make_float4(gz3[0], gz3[1], gz3[2], sG2);
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
+      }
+    };
     up_l1(nxt, idx, tn * kTile + row, n);
     ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_in, kSpin) &&
                            tc::mbar_wait(&fs->bar_x, ph_in, kSpin));
     if (!ok) break;
     ph_in ^= 1;
     inflight_h = inflight_x = false;
+    if (tid == kIssuer) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
+      tc::fence_after_sync();
+      mma3(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH, kHid / 16,
+           tc::idesc_f16(128, kTile, 0, 0), false);
+      tc::mma_commit(&fs->bar_mma);
+    }
+    if (warp != kIssuer / 32) prologue();
     // relu mask of layer 1 on this quarter's columns (H1 > 0 <=> hi > 0)
     uint32_t m1b = 0u;
 #pragma unroll
@@ -919,19 +934,14 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         if ((int16_t)(wd[i] >> 16) > 0) m1b |= 1u << (k + 1);
       }
     }
-    if (tid == 0) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
-      tc::fence_after_sync();
-      mma3(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH, kHid / 16,
-           tc::idesc_f16(128, kTile, 0, 0), false);
-      tc::mma_commit(&fs->bar_mma);
-    }
     up_l2(nxt, g_rgb, w, ray_id);
     if (!(ok = mma_wait())) break;
     // Hidden unit oh over the tile rows 32 qw .. 32 qw + 31: G2 = (W3^T g_z3)
     // * (z2 > 0), and the sums over rows dW3 += g_z3 h2^T, db2 += G2 in
-    // registers.  G2 times the row's scale sG2 goes to shared memory as
-    // [unit][row] core matrices: the K-major A operand of dW2 and the
-    // MN-major A operand of g_h1.
+    // registers.  G2 goes out twice: at the CTA-wide scale S2 into tensor
+    // memory over this thread's D2 columns (lane = unit, K = row: the A
+    // operand of dW2), and at each row's own scale sG2 into shared memory as
+    // [unit][row] core matrices (the MN-major A operand of g_h1).
     {
       float v[32];
       tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
@@ -946,43 +956,29 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         dW3acc[0] = fmaf(q.x, h, dW3acc[0]);
         dW3acc[1] = fmaf(q.y, h, dW3acc[1]);
         dW3acc[2] = fmaf(q.z, h, dW3acc[2]);
-        v[i] = g * q.w;
+        v[i] = g;
       }
       uint32_t hl[32];
+      split32(v, S2, hl, vmax);
+      tc::tmem_st32(lane_base + cTmp + 32 * qw, hl);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] *= fs->smp[32 * qw + i].w;
       split32(v, 1.0f, hl, vmax);
       st_terms32<false>(sm + bGh, sm + bGl, oh, 32 * qw, hl, __float2half2_rn(1.0f));
     }
-    // H1 row r to the scale kSH S2 / sG2[r], so that dW2 = sum_r G2[r]^T H1[r]
-    // carries the single factor kSH S2 (four threads per row, 32 columns each)
-    {
-      const int hr = tid >> 2, hc = (tid & 3) * 32;
-      const __half2 r2 = __float2half2_rn(S2 / fs->smp[hr].w);
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        uint8_t* base = img + (u ? iHl : iHh);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint4* p = reinterpret_cast<uint4*>(base + tc::cm_off(hr, hc + 8 * q, kSboH));
-          uint4 x = *p;
-          x.x = hmul2_u32(x.x, r2);
-          x.y = hmul2_u32(x.y, r2);
-          x.z = hmul2_u32(x.z, r2);
-          x.w = hmul2_u32(x.w, r2);
-          *p = x;
-        }
-      }
-    }
+    tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {   // dW2 += G2^T H1 (A K-major);  g_h1 = G2 W2 (A MN-major)
+    if (tid == kIssuer) {   // dW2 += G2^T H1 (A from tensor memory);  g_h1 = G2 W2 (A MN-major)
       tc::fence_after_sync();
-      mma3(tmem + cDW2, sGh, sGl, 256, 128, kSboH, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
-           tc::idesc_f16(128, kHid, 0, 1), dw_started);
+      mma3_ts(tmem + cDW2, tmem + cTmp, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
+              tc::idesc_f16(128, kHid, 0, 1), dw_started);
       mma3(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
            tc::idesc_f16(128, kHid, 1, 1), false);
       tc::mma_commit(&fs->bar_mma);
     }
+    if (warp == kIssuer / 32) prologue();
     up_l3(nxt, g_rgb, g_color, rgb);
     if (!(ok = mma_wait())) break;
     if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
@@ -995,13 +991,13 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       uint32_t hl[32];
       split32(v, fG1, hl, vmax);
       tc::tmem_st32(lane_base + cGH + 32 * qw, hl);
-      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(S1 / sG1));
+      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(r1));
     }
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
+    if (tid == kIssuer) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
       tc::fence_after_sync();
       {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
         const uint32_t id96 = tc::idesc_f16(128, 2 * kK1, 1, 1), id48 = tc::idesc_f16(128, kK1, 1, 1);
