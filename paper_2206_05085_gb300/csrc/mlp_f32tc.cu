@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   for (int i = 0; i < kOut; ++i) dW3acc[i] = 0.0f;
 #pragma unroll
   for (int c = 0; c < kOut; ++c) db3acc[c] = 0.0f;
-  uint32_t ph_in = 0, ph_mma = 0;
+  uint32_t ph_h = 0, ph_x = 0, ph_mma = 0;
   bool ok = true, dw_started = false;
   float vmax = 0.0f;   // largest magnitude split (range check)
   auto mma_wait = [&]() -> bool {
@@ -909,11 +909,10 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
       }
     };
     up_l1(nxt, idx, tn * kTile + row, n);
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_in, kSpin) &&
-                           tc::mbar_wait(&fs->bar_x, ph_in, kSpin));
+    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_h, kSpin));
     if (!ok) break;
-    ph_in ^= 1;
-    inflight_h = inflight_x = false;
+    ph_h ^= 1;
+    inflight_h = false;
     if (tid == kIssuer) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
       tc::fence_after_sync();
       mma3(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH, kHid / 16,
@@ -996,7 +995,11 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    // the tile's X (the B operand of dW1, loaded since the previous tile's dW1) has landed
+    ok = __syncthreads_and(tid != kIssuer || tc::mbar_wait(&fs->bar_x, ph_x, kSpin));
+    if (!ok) break;
+    ph_x ^= 1;
+    inflight_x = false;
     if (tid == kIssuer) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
       tc::fence_after_sync();
       {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
@@ -1049,8 +1052,8 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   }
   // a load still in flight (only after a failed wait) must land before exit
   if (!ok && tid == 0) {
-    if (inflight_h) tc::mbar_wait(&fs->bar_h, ph_in, kSpin);
-    if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_in, kSpin);
+    if (inflight_h) tc::mbar_wait(&fs->bar_h, ph_h, kSpin);
+    if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_x, kSpin);
     set_status(DVGO_ERR_TIMEOUT);
   }
   if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
