@@ -441,6 +441,9 @@ def memory_kernels(res, peaks):
         "dvgo_composite_bwd#0": SL * 28 + (S - SL) * 4 + R * 24,
         # w, m (twice), ds, raw, T, rgb in and g_raw out per live sample
         "dvgo_composite_distortion_bwd#0": SL * 40 + (S - SL) * 4 + R * 24,
+        # both in one pass: w, rgb, m, ds, raw, T in and g_raw out per live sample
+        # (g_raw zeroed past the halt); target in, colour, L_r, g_color out per ray
+        "dvgo_composite_distortion_loss_fwd_bwd#0": SL * 32 + S * 4 + R * 56,
         # g, xyz, index per live sample; FP32 gradient read-modify-write per distinct voxel
         "dvgo_sample_grid_bwd#0": SL * (4 + 12 + 4) + Vl * 8,
         "dvgo_sample_grid_bwd#1": SL * (4 * F + 12 + 4) + Vl * 8 * F,

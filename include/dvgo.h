@@ -278,6 +278,20 @@ int dvgo_composite_distortion_loss_fwd(const float* w, const float* rgb, const f
                                        float* color, float* L_r, float* g_color, float* loss_out,
                                        void* ws, void* stream);
 
+/* dvgo_composite_distortion_loss_fwd and then, for each ray in the same warp
+ * with the g_color just formed, dvgo_composite_distortion_bwd (g_L, raw, T,
+ * shift, interval as that call takes them): color, L_r, g_color, loss_out
+ * and g_raw [S] bit-equal to the two calls, in one launch (one pass of the
+ * per-ray tail of a training step).  ws as for the forward call. */
+int dvgo_composite_distortion_loss_fwd_bwd(const float* w, const float* rgb, const float* m,
+                                           const float* ds, const int64_t* ray_off,
+                                           const int32_t* n_live, const float* T_end, int64_t R,
+                                           const float bg[3], const float* target,
+                                           float lambda_dist, float g_L, const float* raw,
+                                           const float* T, float shift, float interval,
+                                           float* color, float* L_r, float* g_color,
+                                           float* loss_out, float* g_raw, void* ws, void* stream);
+
 /* Photometric loss and its gradient: loss_out[0] = mean over R x 3 of
  * (color - target)^2, loss_out[1] = mean_r L_r (0 if L_r is NULL),
  * loss_out[2] = loss_out[0] + lambda_dist loss_out[1]; g_color =

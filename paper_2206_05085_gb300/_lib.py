@@ -106,6 +106,8 @@ def _declare(L):
         "dvgo_density_alpha_fwd": ([P, INT, P, P, P, I64, F, F, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_loss_fwd": ([P, P, P, P, P, P, P, I64, P, P, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P], INT),
+        "dvgo_composite_distortion_loss_fwd_bwd": ([P, P, P, P, P, P, P, I64, P, P, F, F, P, P, F, F,
+                                                    P, P, P, P, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
         "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
         "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
@@ -143,6 +145,7 @@ def exported_names():
         "dvgo_proposal_bwd", "dvgo_proposal_xent", "dvgo_proposal_select", "dvgo_compact_samples",
         "dvgo_sample_rays_noalloc_max_rays", "dvgo_sample_rays_noalloc", "dvgo_rgbnet_act_bytes",
         "dvgo_sample_grid_bwd2", "dvgo_composite_distortion_fwd", "dvgo_composite_distortion_bwd",
+        "dvgo_composite_distortion_loss_fwd_bwd",
         "dvgo_tv_add_grad_multi", "dvgo_adam_step_multi", "dvgo_touched_compact",
         "dvgo_adam_step_multi_dev", "dvgo_composite_fwd", "dvgo_grid_adam_step",
         "dvgo_composite_loss_workspace_size", "dvgo_composite_distortion_loss_fwd",
@@ -298,6 +301,15 @@ def composite_distortion_loss_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, 
     _call("dvgo_composite_distortion_loss_fwd", ptr(w), ptr(rgb), ptr(m), ptr(ds), ptr(ray_off),
           ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(target), lambda_dist, ptr(color), ptr(L_r),
           ptr(g_color), ptr(loss_out), ptr(ws), _stream(stream))
+
+
+def composite_distortion_loss_fwd_bwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, target,
+                                      lambda_dist, g_L, raw, T, shift, interval, color, L_r,
+                                      g_color, loss_out, g_raw, ws, stream=None):
+    _call("dvgo_composite_distortion_loss_fwd_bwd", ptr(w), ptr(rgb), ptr(m), ptr(ds), ptr(ray_off),
+          ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(target), lambda_dist, g_L, ptr(raw), ptr(T),
+          shift, interval, ptr(color), ptr(L_r), ptr(g_color), ptr(loss_out), ptr(g_raw), ptr(ws),
+          _stream(stream))
 
 
 def composite_distortion_bwd(g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift,

@@ -253,6 +253,88 @@ __global__ void __launch_bounds__(256) distortion_bwd_kernel(
   }
 }
 
+// Compositing adjoint with the distortion gradient formed in place, for ray
+// r (samples b .. b + N, the first n live) given its totals W and WM of w and
+// w m (Kahan): chunks from the last to the first, Kahan-compensated suffix
+// sums W_{>i}, WM_{>i} give g_w_i (W_{<i} = W - W_{>i} - w_i), which enters
+// the reverse affine scan of the colour adjoint directly (g_w is never
+// stored).  One warp; every lane calls it.
+__device__ __forceinline__ void composite_distortion_bwd_ray(
+    int lane, int64_t b, int n, int N, float gc0, float gc1, float gc2, float Wt, float WMt, float g_L,
+    const float* __restrict__ w, const float* __restrict__ raw, const float* __restrict__ T,
+    const float* __restrict__ rgb, const float* __restrict__ m, const float* __restrict__ ds,
+    float shift, float interval, float bg0, float bg1, float bg2, float* __restrict__ g_raw) {
+  const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+  Kahan sW, sWM;                                     // sums over the chunks after the current one
+  float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;   // R_{n-1} = g_T
+  const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
+  for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
+    const int k = c0 + lane;
+    const bool valid = k < n;
+    float wi = 0.0f, mi = 0.0f, di = 0.0f, rk = 0.0f, Tk = 0.0f, la = 0.0f;
+    float c_rgb = 0.0f;
+    if (valid) {
+      const int64_t s = b + k;
+      wi = __ldg(w + s);
+      mi = __ldg(m + s) - m0;
+      di = __ldg(ds + s);
+      rk = __ldg(raw + s);
+      Tk = __ldg(T + s);
+      c_rgb = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
+    }
+    // inclusive suffix sums within the chunk (lane .. 31)
+    float sw = wi, swm = wi * mi;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float a = __shfl_down_sync(0xffffffffu, sw, o);
+      const float c = __shfl_down_sync(0xffffffffu, swm, o);
+      if (lane + o < 32) {
+        sw += a;
+        swm += c;
+      }
+    }
+    const float Wgt = __fadd_rn(sW.s, __fsub_rn(sw - wi, sW.c));
+    const float WMgt = __fadd_rn(sWM.s, __fsub_rn(swm - wi * mi, sWM.c));
+    const float Wlt = Wt - Wgt - wi;
+    const float WMlt = WMt - WMgt - wi * mi;
+    const float gw = g_L * (2.0f * (mi * (Wlt - Wgt) - WMlt + WMgt) + (2.0f / 3.0f) * wi * di);
+    float A = 1.0f, B = 0.0f, gk = 0.0f;
+    if (valid) {
+      la = -interval * softplus_f(rk + shift);
+      const float al = -expm1f(la);
+      gk = c_rgb + gw;
+      A = 1.0f - al;
+      B = gk * al;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float A2 = __shfl_down_sync(0xffffffffu, A, o);
+      const float B2 = __shfl_down_sync(0xffffffffu, B, o);
+      if (lane + o < 32) {
+        B = A * B2 + B;
+        A = A * A2;
+      }
+    }
+    float An = __shfl_down_sync(0xffffffffu, A, 1);
+    float Bn = __shfl_down_sync(0xffffffffu, B, 1);
+    if (lane == 31) {
+      An = 1.0f;
+      Bn = 0.0f;
+    }
+    const float Rk = An * carry + Bn;
+    if (valid) {
+      const float Tk1 = Tk * expf(la);
+      g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
+    }
+    const float A0 = __shfl_sync(0xffffffffu, A, 0);
+    const float B0 = __shfl_sync(0xffffffffu, B, 0);
+    carry = A0 * carry + B0;
+    sW.add(__shfl_sync(0xffffffffu, sw, 0));
+    sWM.add(__shfl_sync(0xffffffffu, swm, 0));
+  }
+  for (int k = n + lane; k < N; k += 32) g_raw[b + k] = 0.0f;
+}
+
 // ------------------------------------------------ fused per-ray tails
 // Colour accumulation and the distortion loss of the live samples in one pass
 // over each ray (both read w; same arithmetic as the two kernels above).
@@ -260,6 +342,17 @@ __global__ void __launch_bounds__(256) distortion_bwd_kernel(
 // squared error and g_color beside its colour, per-block partial sums, and
 // the last block to finish (a ticket counter it resets) adds the partials in
 // block order (deterministic).
+// With kBwd (and kLoss) the compositing adjoint of each ray follows its
+// forward pass in the same warp (composite_distortion_bwd_ray with the g_color
+// just formed): one pass of the per-ray tail for the whole step.
+struct BwdTail {
+  float g_L;
+  const float* raw;
+  const float* T;
+  float shift, interval;
+  float* g_raw;
+};
+
 struct LossTail {
   const float* target;
   float lambda_dist;
@@ -269,12 +362,13 @@ struct LossTail {
   float* part;       // [gridDim.x][2]
 };
 
-template <bool kLoss>
+template <bool kLoss, bool kBwd = false>
 __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     const float* __restrict__ w, const float* __restrict__ rgb, const float* __restrict__ m,
     const float* __restrict__ ds, const int64_t* __restrict__ ray_off, const int32_t* __restrict__ n_live,
     const float* __restrict__ T_end, int64_t R, float bg0, float bg1, float bg2,
-    float* __restrict__ color, float* __restrict__ L_r, LossTail lt) {
+    float* __restrict__ color, float* __restrict__ L_r, LossTail lt, BwdTail bt = BwdTail{}) {
+  static_assert(kLoss || !kBwd, "the adjoint needs the loss gradient");
   float sq = 0.0f, dsum = 0.0f;   // lane 0: this warp's rays
   const float gscale = 2.0f / (3.0f * (float)R);
   DVGO_WARP_LOOP(R) {
@@ -283,7 +377,7 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     ray_range(ray_off, n_live, r, b, n, N);
     const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, acc = 0.0f;
-    Kahan cW, cWM;
+    Kahan cW, cWM, tW, tWM;
     for (int c0 = 0; c0 < n; c0 += 32) {
       const int i = c0 + lane;
       const bool valid = i < n;
@@ -304,11 +398,16 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
       acc += 2.0f * wi * (mi * Wlt - WMlt) + wi * wi * di * (1.0f / 3.0f);
       cW.add(__shfl_sync(0xffffffffu, iw, 31));
       cWM.add(__shfl_sync(0xffffffffu, iwm, 31));
+      if constexpr (kBwd) {   // the adjoint's totals, summed as its own kernel sums them
+        tW.add(warp_sum(wi));
+        tWM.add(warp_sum(wi * mi));
+      }
     }
     a0 = warp_sum(a0);
     a1 = warp_sum(a1);
     a2 = warp_sum(a2);
     acc = warp_sum(acc);
+    float gc0 = 0.0f, gc1 = 0.0f, gc2 = 0.0f;
     if (lane == 0) {
       const float te = T_end[r];
       const float c0 = a0 + te * bg0, c1 = a1 + te * bg1, c2 = a2 + te * bg2;
@@ -319,12 +418,23 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
       if constexpr (kLoss) {
         const float e0 = c0 - __ldg(lt.target + 3 * r), e1 = c1 - __ldg(lt.target + 3 * r + 1),
                     e2 = c2 - __ldg(lt.target + 3 * r + 2);
-        lt.g_color[3 * r] = gscale * e0;
-        lt.g_color[3 * r + 1] = gscale * e1;
-        lt.g_color[3 * r + 2] = gscale * e2;
+        gc0 = gscale * e0;
+        gc1 = gscale * e1;
+        gc2 = gscale * e2;
+        lt.g_color[3 * r] = gc0;
+        lt.g_color[3 * r + 1] = gc1;
+        lt.g_color[3 * r + 2] = gc2;
         sq += (e0 * e0 + e1 * e1) + e2 * e2;
         dsum += acc;
       }
+    }
+    if constexpr (kBwd) {
+      gc0 = __shfl_sync(0xffffffffu, gc0, 0);
+      gc1 = __shfl_sync(0xffffffffu, gc1, 0);
+      gc2 = __shfl_sync(0xffffffffu, gc2, 0);
+      composite_distortion_bwd_ray(lane, b, n, N, gc0, gc1, gc2, __fsub_rn(tW.s, tW.c),
+                                   __fsub_rn(tWM.s, tWM.c), bt.g_L, w, bt.raw, bt.T, rgb, m, ds,
+                                   bt.shift, bt.interval, bg0, bg1, bg2, bt.g_raw);
     }
   }
   if constexpr (kLoss) {
@@ -383,11 +493,8 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
   }
 }
 
-// Compositing adjoint with the distortion gradient formed in place: one
-// forward pass for the ray's totals W and WM, then chunks from the last to the
-// first: Kahan-compensated suffix sums W_{>i}, WM_{>i} give g_w_i (W_{<i} =
-// W - W_{>i} - w_i), which enters the reverse affine scan of the colour
-// adjoint directly (g_w is never stored).
+// The adjoint for each ray: one forward pass for the totals W and WM, then
+// composite_distortion_bwd_ray.
 __global__ void __launch_bounds__(256) composite_distortion_bwd_kernel(
     const float* __restrict__ g_color, float g_L, const float* __restrict__ w,
     const float* __restrict__ raw, const float* __restrict__ T, const float* __restrict__ rgb,
@@ -409,75 +516,9 @@ __global__ void __launch_bounds__(256) composite_distortion_bwd_kernel(
       tW.add(warp_sum(wi));
       tWM.add(warp_sum(wi * mi));
     }
-    const float Wt = __fsub_rn(tW.s, tW.c), WMt = __fsub_rn(tWM.s, tWM.c);
-    Kahan sW, sWM;                                     // sums over the chunks after the current one
-    float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;   // R_{n-1} = g_T
-    const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
-    for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
-      const int k = c0 + lane;
-      const bool valid = k < n;
-      float wi = 0.0f, mi = 0.0f, di = 0.0f, rk = 0.0f, Tk = 0.0f, la = 0.0f;
-      float c_rgb = 0.0f;
-      if (valid) {
-        const int64_t s = b + k;
-        wi = __ldg(w + s);
-        mi = __ldg(m + s) - m0;
-        di = __ldg(ds + s);
-        rk = __ldg(raw + s);
-        Tk = __ldg(T + s);
-        c_rgb = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
-      }
-      // inclusive suffix sums within the chunk (lane .. 31)
-      float sw = wi, swm = wi * mi;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float a = __shfl_down_sync(0xffffffffu, sw, o);
-        const float c = __shfl_down_sync(0xffffffffu, swm, o);
-        if (lane + o < 32) {
-          sw += a;
-          swm += c;
-        }
-      }
-      const float Wgt = __fadd_rn(sW.s, __fsub_rn(sw - wi, sW.c));
-      const float WMgt = __fadd_rn(sWM.s, __fsub_rn(swm - wi * mi, sWM.c));
-      const float Wlt = Wt - Wgt - wi;
-      const float WMlt = WMt - WMgt - wi * mi;
-      const float gw = g_L * (2.0f * (mi * (Wlt - Wgt) - WMlt + WMgt) + (2.0f / 3.0f) * wi * di);
-      float A = 1.0f, B = 0.0f, gk = 0.0f;
-      if (valid) {
-        la = -interval * softplus_f(rk + shift);
-        const float al = -expm1f(la);
-        gk = c_rgb + gw;
-        A = 1.0f - al;
-        B = gk * al;
-      }
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float A2 = __shfl_down_sync(0xffffffffu, A, o);
-        const float B2 = __shfl_down_sync(0xffffffffu, B, o);
-        if (lane + o < 32) {
-          B = A * B2 + B;
-          A = A * A2;
-        }
-      }
-      float An = __shfl_down_sync(0xffffffffu, A, 1);
-      float Bn = __shfl_down_sync(0xffffffffu, B, 1);
-      if (lane == 31) {
-        An = 1.0f;
-        Bn = 0.0f;
-      }
-      const float Rk = An * carry + Bn;
-      if (valid) {
-        const float Tk1 = Tk * expf(la);
-        g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
-      }
-      const float A0 = __shfl_sync(0xffffffffu, A, 0);
-      const float B0 = __shfl_sync(0xffffffffu, B, 0);
-      carry = A0 * carry + B0;
-      sW.add(__shfl_sync(0xffffffffu, sw, 0));
-      sWM.add(__shfl_sync(0xffffffffu, swm, 0));
-    }
-    for (int k = n + lane; k < N; k += 32) g_raw[b + k] = 0.0f;
+    composite_distortion_bwd_ray(lane, b, n, N, gc0, gc1, gc2, __fsub_rn(tW.s, tW.c),
+                                 __fsub_rn(tWM.s, tWM.c), g_L, w, raw, T, rgb, m, ds, shift, interval,
+                                 bg0, bg1, bg2, g_raw);
   }
 }
 
@@ -649,6 +690,23 @@ extern "C" int dvgo_composite_distortion_loss_fwd(const float* w, const float* r
               reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 16)};
   composite_distortion_fwd_kernel<true><<<warp_grid(R), 256, 0, as_stream(stream)>>>(
       w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r, lt);
+  return launch_status();
+}
+
+extern "C" int dvgo_composite_distortion_loss_fwd_bwd(
+    const float* w, const float* rgb, const float* m, const float* ds, const int64_t* ray_off,
+    const int32_t* n_live, const float* T_end, int64_t R, const float bg[3], const float* target,
+    float lambda_dist, float g_L, const float* raw, const float* T, float shift, float interval,
+    float* color, float* L_r, float* g_color, float* loss_out, float* g_raw, void* ws, void* stream) {
+  DVGO_CHECK_ARG(R > 0);
+  DVGO_CHECK_ARG(w && rgb && m && ds && ray_off && T_end && bg && color && L_r && target && g_color &&
+                 loss_out && ws && raw && T && g_raw);
+  DVGO_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 15u) == 0);
+  LossTail lt{target, lambda_dist, g_color, loss_out, reinterpret_cast<unsigned int*>(ws),
+              reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 16)};
+  BwdTail bt{g_L, raw, T, shift, interval, g_raw};
+  composite_distortion_fwd_kernel<true, true><<<warp_grid(R), 256, 0, as_stream(stream)>>>(
+      w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r, lt, bt);
   return launch_status();
 }
 

@@ -151,10 +151,12 @@ class Trainer:
         L.sample_rays(rays_o, rays_d, self.R, self.gd, self.sd, self.mask, self.S_cap, self.ray_off,
                       self.xyz, self.ray_id, self.step_k, self.s_mid, self.s_len, self.ws_sample)
 
-    def forward(self, rays_o, rays_d, target, sample: bool = True):
+    def forward(self, rays_o, rays_d, target, sample: bool = True, tail_adjoint: bool = False):
         """Forward pass.  sample=False renders the sample list already in the
         buffers (ray_off, xyz, ray_id, step_k, s_mid, s_len), e.g. the samples
-        a proposal network selected."""
+        a proposal network selected.  tail_adjoint: the compositing adjoint of
+        each ray (g_raw) runs in the same pass as its loss (then backward takes
+        tail_done=True)."""
         rp, R, S = self.rp, self.R, self.S_cap
         if sample:
             self.sample(rays_o, rays_d)
@@ -169,18 +171,27 @@ class Trainer:
         L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
                      self.precision, self.rgb, self.act)
         # colour accumulation, distortion loss and the photometric loss in one pass
-        # over each ray
-        L.composite_distortion_loss_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
-                                        self.n_live, self.T_end, R, rp.bg, target, rp.lambda_dist,
-                                        self.color, self.L_r, self.g_color, self.loss, self.ws_loss)
+        # over each ray (with tail_adjoint, followed in the same warp by the ray's
+        # compositing adjoint)
+        if tail_adjoint:
+            L.composite_distortion_loss_fwd_bwd(
+                self.w, self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live, self.T_end, R,
+                rp.bg, target, rp.lambda_dist, rp.lambda_dist / R, self.raw, self.T, self.shift,
+                rp.interval, self.color, self.L_r, self.g_color, self.loss, self.g_raw, self.ws_loss)
+        else:
+            L.composite_distortion_loss_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
+                                            self.n_live, self.T_end, R, rp.bg, target,
+                                            rp.lambda_dist, self.color, self.L_r, self.g_color,
+                                            self.loss, self.ws_loss)
 
     # -------------------------------------------------------------- backward
-    def backward(self, rays_d):
+    def backward(self, rays_d, tail_done: bool = False):
         rp, R, S = self.rp, self.R, self.S_cap
         # compositing adjoint with the distortion gradient formed inside its reverse scan
-        L.composite_distortion_bwd(self.g_color, rp.lambda_dist / R, self.w, self.raw, self.T,
-                                   self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live, R,
-                                   self.shift, rp.interval, rp.bg, self.g_raw)
+        if not tail_done:
+            L.composite_distortion_bwd(self.g_color, rp.lambda_dist / R, self.w, self.raw, self.T,
+                                       self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live,
+                                       R, self.shift, rp.interval, rp.bg, self.g_raw)
         L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.live_idx, S,
                      self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
                      self.act, self.rgb)
@@ -216,8 +227,8 @@ class Trainer:
 
     def step(self, rays_o, rays_d, target, tv_dense: bool = False, sample: bool = True):
         """One full training iteration; returns the device loss tensor [3]."""
-        self.forward(rays_o, rays_d, target, sample=sample)
-        self.backward(rays_d)
+        self.forward(rays_o, rays_d, target, sample=sample, tail_adjoint=True)
+        self.backward(rays_d, tail_done=True)
         self.regularize_and_step(tv_dense)
         return self.loss
 

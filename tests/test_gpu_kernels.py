@@ -505,6 +505,17 @@ def test_composite_distortion_loss_fused(L, R_rays):
         assert torch.equal(c1, c2) and torch.equal(l1, l2) and torch.equal(g1, g2)
         assert int(host(ws[:4].view(torch.int32))[0]) == 0
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    # with the compositing adjoint in the same pass: every output bit-equal to the two calls
+    gr1 = torch.empty(S, device="cuda")
+    L.composite_distortion_bwd(g1, lam / R_rays, w, dev(raw), T, dev(rgb), dev(m), dev(ds), dev(off),
+                               n_live, R_rays, sh, 0.5, bg, gr1)
+    c3, l3 = torch.empty(R_rays, 3, device="cuda"), torch.empty(R_rays, device="cuda")
+    loss3, g3, gr3 = torch.empty(3, device="cuda"), torch.empty(R_rays, 3, device="cuda"), torch.empty(S, device="cuda")
+    L.composite_distortion_loss_fwd_bwd(*args, dev(target), lam, lam / R_rays, dev(raw), T, sh, 0.5,
+                                        c3, l3, g3, loss3, gr3, ws)
+    assert torch.equal(c1, c3) and torch.equal(l1, l3) and torch.equal(g1, g3)
+    assert torch.equal(gr1, gr3)
+    assert np.array_equal(outs[0], host(loss3))
     ref = oracle.composite(raw, rgb, off, sh, 0.5, 1e-3, bg)
     mse = np.mean((ref["color"] - target) ** 2)
     Ld = np.mean(oracle.distortion(ref["w"], m, ds, off, ref["n_live"]))
