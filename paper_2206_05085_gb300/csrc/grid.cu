@@ -535,8 +535,9 @@ __device__ __forceinline__ bool nonzero4(float4 v) {
 }
 
 // Adam over entries [base, end) of one array, float4 body (base a multiple of
-// 4).  Two groups per thread and step: both gradients are loaded, then the
-// state of whichever is non-zero, so their loads are in flight together.
+// 4).  Two groups per thread and step, gradient and state loaded together
+// (one memory round trip per step; the state of an all-zero group is read
+// but neither updated nor written).
 __device__ __forceinline__ void adam_range(float* __restrict__ p, uint16_t* __restrict__ shadow,
                                            float* __restrict__ g, float* __restrict__ m,
                                            float* __restrict__ v, int64_t base, int64_t end,
@@ -548,17 +549,12 @@ __device__ __forceinline__ void adam_range(float* __restrict__ p, uint16_t* __re
     const float4 g0 = *reinterpret_cast<const float4*>(g + i);
     const float4 g1 = *reinterpret_cast<const float4*>(g + j);
     const bool n0 = nonzero4(g0), n1 = nonzero4(g1);
-    float4 p0, m0, v0, p1, m1, v1;
-    if (n0) {
-      p0 = *reinterpret_cast<const float4*>(p + i);
-      m0 = *reinterpret_cast<const float4*>(m + i);
-      v0 = *reinterpret_cast<const float4*>(v + i);
-    }
-    if (n1) {
-      p1 = *reinterpret_cast<const float4*>(p + j);
-      m1 = *reinterpret_cast<const float4*>(m + j);
-      v1 = *reinterpret_cast<const float4*>(v + j);
-    }
+    const float4 p0 = *reinterpret_cast<const float4*>(p + i);
+    const float4 m0 = *reinterpret_cast<const float4*>(m + i);
+    const float4 v0 = *reinterpret_cast<const float4*>(v + i);
+    const float4 p1 = *reinterpret_cast<const float4*>(p + j);
+    const float4 m1 = *reinterpret_cast<const float4*>(m + j);
+    const float4 v1 = *reinterpret_cast<const float4*>(v + j);
     if (n0) adam_group(p, shadow, g, m, v, i, g0, p0, m0, v0, a, zero_grad);
     if (n1) adam_group(p, shadow, g, m, v, j, g1, p1, m1, v1, a, zero_grad);
   }
