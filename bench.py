@@ -354,7 +354,7 @@ def run_ours(args, rank, world):
                 S_live=S_live, h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
 
 
-# Algorithmic work per unit ("Kernels and their rooflines").
+# Algorithmic work per unit of each kernel (the roofline numerators).
 # Colour MLP, per live sample: forward 2*(39*128 + 128*128 + 128*3) FLOP; backward
 # (activations stored by the forward, nothing recomputed) g_z2 + dW3 (2*3*128 each),
 # dW2 and g_h1 (128*128 each), dW1 (128*40), g_k0 (128*12), all x2.
