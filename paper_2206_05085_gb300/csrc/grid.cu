@@ -30,13 +30,13 @@ struct Corners {
   int ix, iy, iz;    // lower corner
 };
 
-__device__ __forceinline__ void corners(const TriArgs& T, const float* __restrict__ xyz, int64_t s,
-                                        Corners& c) {
+// Corners and weights of the position pos (already loaded).
+__device__ __forceinline__ void corners_at(const TriArgs& T, const float pos[3], Corners& c) {
   int i0[3];
   float f[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float u = (__ldg(xyz + 3 * s + a) - T.lo[a]) * T.scale[a];
+    float u = (pos[a] - T.lo[a]) * T.scale[a];
     u = fminf(fmaxf(u, 0.0f), (float)(T.g.G[a] - 1));
     int i = (int)floorf(u);
     i = min(i, T.g.G[a] - 2);
@@ -54,6 +54,12 @@ __device__ __forceinline__ void corners(const TriArgs& T, const float* __restric
   }
 }
 
+__device__ __forceinline__ void corners(const TriArgs& T, const float* __restrict__ xyz, int64_t s,
+                                        Corners& c) {
+  const float pos[3] = {__ldg(xyz + 3 * s), __ldg(xyz + 3 * s + 1), __ldg(xyz + 3 * s + 2)};
+  corners_at(T, pos, c);
+}
+
 __device__ __forceinline__ int64_t live_n(int64_t n_cap, const int64_t* n_dev) {
   if (!n_dev) return n_cap;
   int64_t n = *n_dev;
@@ -61,6 +67,10 @@ __device__ __forceinline__ int64_t live_n(int64_t n_cap, const int64_t* n_dev) {
 }
 
 // ---------------------------------------------------------------- gather
+// One sample per thread and step of a grid-stride loop over a grid that
+// stays resident; the next sample's position and the index after it are
+// loaded before this sample's corners, so that the index -> position ->
+// corners chain of one sample overlaps the corner loads of the previous one.
 template <int C, bool kBF16>
 __global__ void __launch_bounds__(256) gather_fwd_kernel(const void* __restrict__ grid, TriArgs T,
                                                          const float* __restrict__ xyz,
@@ -68,11 +78,22 @@ __global__ void __launch_bounds__(256) gather_fwd_kernel(const void* __restrict_
                                                          int64_t n_cap, const int64_t* n_dev,
                                                          float* __restrict__ out) {
   const int64_t n = live_n(n_cap, n_dev);
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = idx ? (int64_t)__ldg(idx + j) : j;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  auto sample_of = [&](int64_t k) -> int64_t { return idx ? (int64_t)__ldg(idx + k) : k; };
+  int64_t s = sample_of(j);
+  float pos[3] = {__ldg(xyz + 3 * s), __ldg(xyz + 3 * s + 1), __ldg(xyz + 3 * s + 2)};
+  int64_t s_next = j + stride < n ? sample_of(j + stride) : -1;
+  for (; j < n; j += stride) {
+    float pos_next[3] = {0.0f, 0.0f, 0.0f};
+    if (s_next >= 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pos_next[a] = __ldg(xyz + 3 * s_next + a);
+    }
+    const int64_t s_after = j + 2 * stride < n ? sample_of(j + 2 * stride) : -1;
     Corners c;
-    corners(T, xyz, s, c);
+    corners_at(T, pos, c);
     float acc[C];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
@@ -125,6 +146,10 @@ __global__ void __launch_bounds__(256) gather_fwd_kernel(const void* __restrict_
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) o[ch] = acc[ch];
     }
+    s = s_next;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pos[a] = pos_next[a];
+    s_next = s_after;
   }
 }
 
@@ -839,6 +864,20 @@ extern "C" int dvgo_sample_grid_fwd(const void* grid, int dtype, const dvgo_grid
   cudaStream_t st = as_stream(stream);
   const int block = 256;
   int g = grid_for(n_cap, block, 16);
+  if (C == 1 || C == 12) {   // the specialised kernels loop: one resident wave of blocks
+    static int per_sm[2][2] = {{0, 0}, {0, 0}};
+    const int di = dtype == DVGO_F32 ? 0 : 1, ci = C == 1 ? 0 : 1;
+    if (!per_sm[di][ci]) {
+      const void* fn = di == 0 ? (ci == 0 ? (const void*)gather_fwd_kernel<1, false>
+                                          : (const void*)gather_fwd_kernel<12, false>)
+                               : (ci == 0 ? (const void*)gather_fwd_kernel<1, true>
+                                          : (const void*)gather_fwd_kernel<12, true>);
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, 0) != cudaSuccess || b < 1) b = 1;
+      per_sm[di][ci] = b;
+    }
+    g = (int)std::min<int64_t>(ceil_div(n_cap, block), (int64_t)kNumSMs * per_sm[di][ci]);
+  }
   if (dtype == DVGO_F32) {
     if (C == 1) gather_fwd_kernel<1, false><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
     else if (C == 12) gather_fwd_kernel<12, false><<<g, block, 0, st>>>(grid, T, xyz, idx, n_cap, n_dev, out);
