@@ -104,6 +104,35 @@ def test_trilinear_fwd_bwd(L, C, bf16):
 
 
 @pytest.mark.parametrize("C", [1, 12])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_trilinear_fwd_many_samples_per_thread(L, C, bf16):
+    """The specialised gathers loop over a resident wave of blocks with the
+    next sample's index and position prefetched: enough listed samples that
+    every thread takes several steps (and a ragged last one), through an
+    index list in random order, count on the device."""
+    rng = np.random.default_rng(100 + C + bf16)
+    G = (37, 29, 33)
+    lo, hi = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0])
+    dense = rng.normal(size=(G[2], G[1], G[0], C)).astype(np.float32)
+    if bf16:
+        dense = synth.bf16_round(dense)
+    n = 1_300_003
+    xyz = rng.uniform(-1.0, 1.0, (n, 3)).astype(np.float32)
+    gd = L.GridDesc.make(lo, hi, G)
+    grid = _bricked(L, dense, G, C, torch.bfloat16 if bf16 else torch.float32)
+    idx = rng.permutation(n).astype(np.int32)
+    m = n - 7
+    n_dev = torch.tensor([m], dtype=torch.int64, device="cuda")
+    out = torch.full((n, C), -7.0, device="cuda")
+    L.sample_grid_fwd(grid, L.BF16 if bf16 else L.F32, gd, C, dev(xyz), dev(idx), n, n_dev, out)
+    got = host(out)
+    ref = oracle.trilinear(dense, lo, hi, xyz)
+    sel = idx[:m]
+    assert rel_err(got[sel], ref[sel]) < TOL32
+    assert np.all(got[idx[m:]] == -7.0)
+
+
+@pytest.mark.parametrize("C", [1, 12])
 def test_trilinear_adjoint_along_rays(L, C):
     """Ray-ordered samples (the layout the renderer produces): consecutive list
     positions share corner voxels, so the scatter's per-warp aggregation table
