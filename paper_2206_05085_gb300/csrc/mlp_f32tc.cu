@@ -718,11 +718,14 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
 }
 
 // ----------------------------------------------------------------- backward
-// Same thread layout as the forward (512 threads, four warp quarters per TMEM
-// lane quarter, quarter q on hidden columns 32 q .. 32 q + 31).  The upstream colour
-// gradient of the next tile is loaded in three dependent steps over the
-// current tile, and the next tile's image is copied in as soon as the MMAs
-// that read each part have completed.
+// 512 threads: warp w covers TMEM lane quarter w & 3 and column quarter
+// q = w / 4.  In the products with the tile rows on the TMEM lanes (g_h1,
+// g_X) a thread holds row 32 (w & 3) + lane and hidden columns 32 q .. + 31;
+// in the transposed layer 2 (D2^T) it holds hidden unit 32 (w & 3) + lane
+// and tile rows 32 q .. + 31.  The upstream colour gradient of the next
+// tile is loaded in three dependent steps over the current tile, and the
+// next tile's image is copied in as soon as the MMAs that read each part
+// have completed (H1 after dW2, X before the next dW1).
 struct UpIn {
   int64_t s;       // sample index (-1 past the list end)
   int32_t r;
