@@ -6,7 +6,9 @@
 // round-to-nearest intrinsics (no FMA contraction), in the operation order
 // stated in dvgo.h / below, so the integer results are reproducible bit for
 // bit by any IEEE FP32 implementation of the same formulas.
-#include <atomic>
+#include <cuda.h>
+
+#include <mutex>
 
 #include "common.cuh"
 
@@ -471,23 +473,65 @@ constexpr int64_t kNoAllocMaxRays = 1 << 20;
 static __device__ __align__(256) int32_t g_noalloc_counts[kNoAllocMaxRays + 1];
 
 constexpr int kNoAllocMaxDevices = 64;
-static std::atomic<int32_t*> g_noalloc_ptr[kNoAllocMaxDevices];
 
-// Device address of g_noalloc_counts on the current device.  In host code
-// the array's name is only a host-side stand-in, so the address is looked
-// up once per device, with that device current, and cached.
+// The array's device address, cached per device together with the identity
+// of the context it was looked up in.  A context that is torn down and
+// created again (cudaDeviceReset, or a driver-API context switch) gets a new
+// identity, so the address is looked up again there instead of being reused.
+struct NoAllocSlot {
+  int32_t* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+static NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identity of the calling thread's current context (false if there is none
+// or the driver does not provide the query).
+static bool current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_counts in the current context.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// (cudaGetSymbolAddress, with the device current) on the first call in a
+// context and cached; later calls in the same context reuse it.
 static int noalloc_counts(int32_t** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DVGO_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return DVGO_ERR_UNSUPPORTED;
-  int32_t* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-  if (!p) {
-    void* addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_noalloc_counts) != cudaSuccess || !addr) return DVGO_ERR_CUDA;
-    p = static_cast<int32_t*>(addr);
-    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocSlot& slot = g_noalloc_slot[dev];
+  unsigned long long id = 0;
+  if (slot.ptr && current_ctx_id(&id) && id == slot.ctx_id) {
+    *out = slot.ptr;
+    return DVGO_OK;
   }
-  *out = p;
+  void* addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_noalloc_counts) != cudaSuccess || !addr) return DVGO_ERR_CUDA;
+  // without a context identity the address is not cached (looked up every call)
+  slot.ptr = current_ctx_id(&id) ? static_cast<int32_t*>(addr) : nullptr;
+  slot.ctx_id = id;
+  *out = static_cast<int32_t*>(addr);
   return DVGO_OK;
 }
 
