@@ -167,12 +167,15 @@ int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_t R,
  * dvgo_sample_rays without ws/ws_bytes.  Its scratch is a fixed array inside
  * the library, present on every GPU that loads the library until the
  * process exits, limited to R <= dvgo_sample_rays_noalloc_max_rays()
- * (1,048,576 rays; larger R returns DVGO_ERR_SHAPE).  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress) and
- * caches it, so make that first call before any stream capture.  All calls
- * share the one array: calls that overlap on the GPU (other streams, other
- * threads) race and must be serialised by the caller.  No allocation of any
- * kind is made. */
+ * (1,048,576 rays; larger R returns DVGO_ERR_SHAPE).  The first call in a
+ * context (per device, and again after that device's context was destroyed
+ * and re-created, e.g. by cudaDeviceReset) looks the array's device address
+ * up (cudaGetSymbolAddress) and caches it with the context's identity, so
+ * make the first call on a device, and the first call after a reset, before
+ * any stream capture.  The array needs no clearing: each call writes every
+ * count it reads.  All calls share the one array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.  No allocation of any kind is made. */
 int64_t dvgo_sample_rays_noalloc_max_rays(void);
 int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d, int64_t R,
                              const dvgo_grid_desc* grid, const dvgo_sampler_desc* smp,
@@ -314,11 +317,18 @@ int dvgo_rgb_loss(const float* color, const float* target, const float* L_r, int
  *                product, like FP32 arithmetic).  Inputs must stay below
  *                512 in magnitude and hidden activations below 2048, else
  *                dvgo_device_status reports DVGO_ERR_RANGE;
- *   DVGO_BF16    BF16 operands on the tensor cores, FP32 accumulation.
- * act: DVGO_F32 may be NULL, else see dvgo_rgbnet_bwd; DVGO_F32_TC
- * required, dvgo_rgbnet_act_bytes(n_cap, DVGO_F32_TC) bytes, 16-byte
- * aligned (the forward stores each 128-sample tile's split layer inputs
- * for the backward); DVGO_BF16 ignored. */
+ *   DVGO_BF16    the BF16 form: the parameters are used as their BF16
+ *                values (the stored precision of this form) and every
+ *                tensor-core operand is BF16 with FP32 accumulation; weight
+ *                matrices are one BF16 term, every other operand (layer
+ *                inputs, hidden activations, gradient rows) two BF16 terms
+ *                hi + lo (16 significant bits), so no value is rounded to
+ *                BF16 between layers.  Same kernels and workspace as
+ *                DVGO_F32_TC; no range limit.
+ * act: DVGO_F32 may be NULL, else see dvgo_rgbnet_bwd; DVGO_F32_TC and
+ * DVGO_BF16 required, dvgo_rgbnet_act_bytes(n_cap, precision) bytes,
+ * 16-byte aligned (the forward stores each 128-sample tile's split layer
+ * inputs for the backward). */
 int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
                     const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
                     int precision, float* rgb, float* act, void* stream);
@@ -331,26 +341,21 @@ int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32_t* ray_id,
  * dvgo_rgbnet_fwd for the same list, row j = [h1 (128) | h2 (128)] of list
  * position j; with it (and rgb, the forward's output, may be NULL) the
  * backward reads the hidden activations instead of recomputing them.
- * DVGO_F32_TC: act is the buffer its forward filled for the same list and
- * count, and rgb that forward's output (both required: the output layer's
- * sigmoid derivative is y (1 - y) with y = rgb[s], not recomputed); the
- * backward also writes the per-CTA partial gradients stored after the tile
- * images, and sums those partials in a fixed order (deterministic).
- * DVGO_BF16: rgb is ignored (the tensor cores recompute the forward); act,
- * if given (dvgo_rgbnet_act_bytes(n_cap, DVGO_BF16) bytes), holds per-CTA
- * partial gradients summed in a fixed order; without it the backward adds
- * into g_params with atomics. */
+ * DVGO_F32_TC and DVGO_BF16: act is the buffer its forward filled for the
+ * same list and count, and rgb that forward's output (both required: the
+ * output layer's sigmoid derivative is y (1 - y) with y = rgb[s], not
+ * recomputed); the backward also writes the per-CTA partial gradients
+ * stored after the tile images, and sums those partials in a fixed order
+ * (deterministic). */
 int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const float* w, const float* k0,
                     const float* rays_d, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
                     const int64_t* n_dev, const float* params, int precision, const float* act,
                     const float* rgb, float* g_params, float* g_k0, void* stream);
 
 /* Bytes of the act buffer dvgo_rgbnet_fwd / _bwd need for n_cap list
- * positions: n_cap * 1024 for DVGO_F32 (optional there); for DVGO_F32_TC
- * 256 + 90112 per 128-position tile + 152 * 22019 * 4 (one partial
- * parameter gradient per SM); for DVGO_BF16 152 * 22019 * 4 (optional: with
- * it the backward sums per-CTA partial gradients in a fixed order instead of
- * using atomics); -1 for a bad precision or n_cap < 0. */
+ * positions: n_cap * 1024 for DVGO_F32 (optional there); for DVGO_F32_TC and
+ * DVGO_BF16 256 + 90112 per 128-position tile + 152 * 22019 * 4 (one partial
+ * parameter gradient per SM); -1 for a bad precision or n_cap < 0. */
 int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision);
 
 /* ------------------------------------------------------- learned proposal */
@@ -358,9 +363,11 @@ int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision);
  * compositing weight lies, so that far fewer samples are rendered.  It is
  * trained on the plain renderer's own weights and the plain dense render
  * stays the fallback.  Network: position encoding [x, sin(2^f x_a),
- * cos(2^f x_a)], f < 6 (39 values) -> ReLU 64 -> ReLU 64 -> 1 logit, BF16
- * operands on the tensor cores with FP32 accumulation.  params: f32 flat
- * W1[64][39], b1, W2[64][64], b2, W3[1][64], b3 (6785 values). */
+ * cos(2^f x_a)], f < 6 (39 values) -> ReLU 64 -> ReLU 64 -> 1 logit, in the
+ * BF16 form of dvgo_rgbnet_fwd: parameters used as their BF16 values, BF16
+ * tensor-core operands (weights one term, inputs, activations and gradient
+ * rows two terms) with FP32 accumulation.  params: f32 flat W1[64][39], b1,
+ * W2[64][64], b2, W3[1][64], b3 (6785 values). */
 int dvgo_proposal_fwd(const float* xyz, const int32_t* idx, int64_t n_cap, const int64_t* n_dev,
                       const float* params, float* logits, void* stream);
 /* Accumulates g_params (+=) from the per-sample logit gradients. */

@@ -95,9 +95,9 @@ def _declare(L):
         getattr(L, nm).argtypes = [P, P, P, P, P, I64, P]
     for nm in ("or_distortion_grad", "or_distortion_grad_naive"):
         getattr(L, nm).argtypes = [P, P, P, P, P, P, I64, P]
-    L.or_mlp_fwd.argtypes = [P, INT, P, P, I64, INT, INT, P]
-    L.or_mlp_bwd.argtypes = [P, INT, P, P, I64, INT, INT, P, P, P]
-    L.or_mlp_min_abs_preact.argtypes = [P, INT, P, P, I64, INT, P]
+    L.or_mlp_fwd.argtypes = [P, INT, P, P, I64, INT, P]
+    L.or_mlp_bwd.argtypes = [P, INT, P, P, I64, INT, P, P, P]
+    L.or_mlp_min_abs_preact.argtypes = [P, INT, P, P, I64, P]
     L.or_freq_encode.argtypes = [P, I64, INT, P]
     L.or_tv_loss.restype = D
     L.or_tv_loss.argtypes = [P, P, INT, D]
@@ -308,18 +308,16 @@ def distortion_grad_naive(g_L, w, m, ds, ray_off, seg_len=None):
     return _dist_grad_call(lib().or_distortion_grad_naive, g_L, w, m, ds, ray_off, seg_len)
 
 
-def mlp_fwd(dims, params, x, out_sigmoid=True, q_bf16=False):
-    """q_bf16: hidden-layer operands stored in BF16 (see dvgo_oracle.c)."""
+def mlp_fwd(dims, params, x, out_sigmoid=True):
     dims = _i32(dims)
     params, x = _f64(params), _f64(x)
     n = x.shape[0]
     out = np.zeros((n, int(dims[-1])))
-    lib().or_mlp_fwd(_p(dims), dims.size - 1, _p(params), _p(x), n, int(out_sigmoid),
-                     int(q_bf16), _p(out))
+    lib().or_mlp_fwd(_p(dims), dims.size - 1, _p(params), _p(x), n, int(out_sigmoid), _p(out))
     return out
 
 
-def mlp_bwd(dims, params, x, g_out, out_sigmoid=True, q_bf16=False):
+def mlp_bwd(dims, params, x, g_out, out_sigmoid=True):
     """Returns (g_params [P], g_x [n, dims[0]])."""
     dims = _i32(dims)
     params, x, g_out = _f64(params), _f64(x), _f64(g_out)
@@ -327,17 +325,16 @@ def mlp_bwd(dims, params, x, g_out, out_sigmoid=True, q_bf16=False):
     gp = np.zeros(params.size)
     gx = np.zeros((n, int(dims[0])))
     lib().or_mlp_bwd(_p(dims), dims.size - 1, _p(params), _p(x), n, int(out_sigmoid),
-                     int(q_bf16), _p(g_out), _p(gp), _p(gx))
+                     _p(g_out), _p(gp), _p(gx))
     return gp, gx
 
 
-def mlp_min_abs_preact(dims, params, x, q_bf16=False):
+def mlp_min_abs_preact(dims, params, x):
     """Per sample, min |pre-activation| over the hidden ReLU layers."""
     dims = _i32(dims)
     params, x = _f64(params), _f64(x)
     out = np.zeros(x.shape[0])
-    lib().or_mlp_min_abs_preact(_p(dims), dims.size - 1, _p(params), _p(x), x.shape[0],
-                                int(q_bf16), _p(out))
+    lib().or_mlp_min_abs_preact(_p(dims), dims.size - 1, _p(params), _p(x), x.shape[0], _p(out))
     return out
 
 

@@ -513,30 +513,14 @@ OR_API void or_distortion_grad_naive(const double* g_L, const double* w, const d
 /* parameter vector holds, per layer l, W_l[dims[l+1]][dims[l]] then         */
 /* b_l[dims[l+1]].  Output activation: 1 = sigmoid (colour), 0 = identity.   */
 /* ------------------------------------------------------------------------ */
-/* Round to the nearest BF16 value (ties to even), going through FP32 as a  */
-/* device does when it stores an FP32 accumulator as a BF16 operand.        */
-static double bf16q(double x) {
-  float f = (float)x;
-  uint32_t u;
-  memcpy(&u, &f, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return x;  /* inf / nan unchanged */
-  u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
-  memcpy(&f, &u, 4);
-  return (double)f;
-}
-
 static int64_t mlp_offset(const int32_t* dims, int l) {
   int64_t off = 0;
   for (int i = 0; i < l; ++i) off += (int64_t)dims[i + 1] * dims[i] + dims[i + 1];
   return off;
 }
 
-/* q_bf16 != 0 models an implementation whose hidden layers run on BF16     */
-/* tensor-core operands: the input of every layer but the last is rounded   */
-/* to BF16 before its products, and (backward) so is the gradient at the    */
-/* output of every layer but the last.  Products and sums stay FP64.         */
 OR_API void or_mlp_fwd(const int32_t* dims, int L, const double* params, const double* x, int64_t n,
-                       int out_sigmoid, int q_bf16, double* out) {
+                       int out_sigmoid, double* out) {
   int maxw = 0;
   for (int l = 0; l <= L; ++l) if (dims[l] > maxw) maxw = dims[l];
   double* h = (double*)malloc(sizeof(double) * maxw);
@@ -546,8 +530,6 @@ OR_API void or_mlp_fwd(const int32_t* dims, int L, const double* params, const d
     for (int l = 0; l < L; ++l) {
       const double* W = params + mlp_offset(dims, l);
       const double* bias = W + (int64_t)dims[l + 1] * dims[l];
-      if (q_bf16 && l < L - 1)
-        for (int i = 0; i < dims[l]; ++i) h[i] = bf16q(h[i]);
       for (int o = 0; o < dims[l + 1]; ++o) {
         double acc = bias[o];
         for (int i = 0; i < dims[l]; ++i) acc += W[(int64_t)o * dims[l] + i] * h[i];
@@ -566,8 +548,7 @@ OR_API void or_mlp_fwd(const int32_t* dims, int L, const double* params, const d
 /* Backward of or_mlp_fwd (reverse-mode chain rule, one sample at a time):   */
 /* g_params += sum_s dL/dparams, g_x[s] = dL/dx[s] (if non-NULL).            */
 OR_API void or_mlp_bwd(const int32_t* dims, int L, const double* params, const double* x, int64_t n,
-                       int out_sigmoid, int q_bf16, const double* g_out, double* g_params,
-                       double* g_x) {
+                       int out_sigmoid, const double* g_out, double* g_params, double* g_x) {
   int64_t tot = 0;
   for (int l = 0; l <= L; ++l) tot += dims[l];
   double* act = (double*)malloc(sizeof(double) * tot);  /* post-activation per layer */
@@ -584,8 +565,6 @@ OR_API void or_mlp_bwd(const int32_t* dims, int L, const double* params, const d
     for (int l = 0; l < L; ++l) {
       const double* W = params + mlp_offset(dims, l);
       const double* bias = W + (int64_t)dims[l + 1] * dims[l];
-      if (q_bf16 && l < L - 1)
-        for (int i = 0; i < dims[l]; ++i) act[base[l] + i] = bf16q(act[base[l] + i]);
       for (int o = 0; o < dims[l + 1]; ++o) {
         double acc = bias[o];
         for (int i = 0; i < dims[l]; ++i) acc += W[(int64_t)o * dims[l] + i] * act[base[l] + i];
@@ -604,8 +583,6 @@ OR_API void or_mlp_bwd(const int32_t* dims, int L, const double* params, const d
     for (int l = L - 1; l >= 0; --l) {
       const double* W = params + mlp_offset(dims, l);
       double* gW = g_params + mlp_offset(dims, l);
-      if (q_bf16 && l < L - 1)
-        for (int o = 0; o < dims[l + 1]; ++o) g[o] = bf16q(g[o]);
       double* gb = gW + (int64_t)dims[l + 1] * dims[l];
       for (int o = 0; o < dims[l + 1]; ++o) {
         gb[o] += g[o];
@@ -633,7 +610,7 @@ OR_API void or_mlp_bwd(const int32_t* dims, int L, const double* params, const d
 /* decision at the rounding level of the arithmetic, so implementations in   */
 /* different precisions may legitimately disagree there.                     */
 OR_API void or_mlp_min_abs_preact(const int32_t* dims, int L, const double* params, const double* x,
-                                  int64_t n, int q_bf16, double* out) {
+                                  int64_t n, double* out) {
   int maxw = 0;
   for (int l = 0; l <= L; ++l) if (dims[l] > maxw) maxw = dims[l];
   double* h = (double*)malloc(sizeof(double) * maxw);
@@ -644,8 +621,6 @@ OR_API void or_mlp_min_abs_preact(const int32_t* dims, int L, const double* para
     for (int l = 0; l < L - 1; ++l) {
       const double* W = params + mlp_offset(dims, l);
       const double* bias = W + (int64_t)dims[l + 1] * dims[l];
-      if (q_bf16)
-        for (int i = 0; i < dims[l]; ++i) h[i] = bf16q(h[i]);
       for (int o = 0; o < dims[l + 1]; ++o) {
         double acc = bias[o];
         for (int i = 0; i < dims[l]; ++i) acc += W[(int64_t)o * dims[l] + i] * h[i];

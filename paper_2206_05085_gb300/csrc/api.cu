@@ -7,17 +7,11 @@ int dvgo_rgbnet_fwd_f32(const float*, const float*, const int32_t*, const int32_
 int dvgo_rgbnet_bwd_f32(const float*, const float*, const float*, const float*, const float*,
                         const int32_t*, const int32_t*, int64_t, const int64_t*, const float*,
                         const float*, const float*, float*, float*, cudaStream_t);
-int dvgo_rgbnet_fwd_bf16(const float*, const float*, const int32_t*, const int32_t*, int64_t,
-                         const int64_t*, const float*, float*, cudaStream_t);
-int dvgo_rgbnet_bwd_bf16(const float*, const float*, const float*, const float*, const float*, const int32_t*,
-                         const int32_t*, int64_t, const int64_t*, const float*, float*, float*, float*,
-                         cudaStream_t);
 int dvgo_mlp_status_read_and_clear(cudaStream_t);
-int dvgo_rgbnet_fwd_f32tc(const float*, const float*, const int32_t*, const int32_t*, int64_t,
-                          const int64_t*, const float*, float*, float*, cudaStream_t);
-int dvgo_rgbnet_bwd_f32tc(const float*, const float*, const float*, const float*, const int32_t*,
-                          const int32_t*, int64_t, const int64_t*, const float*, float*, float*, float*,
-                          cudaStream_t);
+int dvgo_rgbnet_fwd_tc(const float*, const float*, const int32_t*, const int32_t*, int64_t, const int64_t*,
+                       const float*, float*, float*, bool, cudaStream_t);
+int dvgo_rgbnet_bwd_tc(const float*, const float*, const float*, const float*, const int32_t*, const int32_t*,
+                       int64_t, const int64_t*, const float*, float*, float*, float*, bool, cudaStream_t);
 int64_t rgbnet_act_bytes_tc(int64_t);
 int dvgo_mlp_tc_status_read_and_clear(cudaStream_t);
 
@@ -51,11 +45,10 @@ extern "C" int dvgo_rgbnet_fwd(const float* k0, const float* rays_d, const int32
   cudaStream_t st = as_stream(stream);
   if (precision == DVGO_F32)
     return dvgo_rgbnet_fwd_f32(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
-  if (precision == DVGO_BF16)
-    return dvgo_rgbnet_fwd_bf16(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, st);
-  if (precision == DVGO_F32_TC) {
+  if (precision == DVGO_F32_TC || precision == DVGO_BF16) {
     DVGO_CHECK_ARG(act != nullptr);
-    return dvgo_rgbnet_fwd_f32tc(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
+    return dvgo_rgbnet_fwd_tc(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act,
+                              precision == DVGO_BF16, st);
   }
   return DVGO_ERR_INVALID_ARG;
 }
@@ -74,16 +67,12 @@ extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const f
   if (precision == DVGO_F32)
     return dvgo_rgbnet_bwd_f32(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params, act,
                                rgb, g_params, g_k0, st);
-  if (precision == DVGO_BF16)
-    // act (optional): per-CTA partial gradient rows (deterministic sum, no contended atomics)
-    return dvgo_rgbnet_bwd_bf16(g_rgb, g_color, w, k0, rays_d, ray_id, idx, n_cap, n_dev, params,
-                                g_params, g_k0, const_cast<float*>(act), st);
-  if (precision == DVGO_F32_TC) {
+  if (precision == DVGO_F32_TC || precision == DVGO_BF16) {
     // act: the forward's tile images (read) and the per-CTA partial rows
     // (written); rgb: the forward's output, for the sigmoid derivative
     DVGO_CHECK_ARG(act != nullptr && rgb != nullptr);
-    return dvgo_rgbnet_bwd_f32tc(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev, params,
-                                 const_cast<float*>(act), g_params, g_k0, st);
+    return dvgo_rgbnet_bwd_tc(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev, params,
+                              const_cast<float*>(act), g_params, g_k0, precision == DVGO_BF16, st);
   }
   return DVGO_ERR_INVALID_ARG;
 }
@@ -91,8 +80,7 @@ extern "C" int dvgo_rgbnet_bwd(const float* g_rgb, const float* g_color, const f
 extern "C" int64_t dvgo_rgbnet_act_bytes(int64_t n_cap, int precision) {
   if (n_cap < 0) return -1;
   if (precision == DVGO_F32) return n_cap * 1024;
-  if (precision == DVGO_F32_TC) return rgbnet_act_bytes_tc(n_cap);
-  if (precision == DVGO_BF16) return (int64_t)kNumSMs * kNumParams * (int64_t)sizeof(float);
+  if (precision == DVGO_F32_TC || precision == DVGO_BF16) return rgbnet_act_bytes_tc(n_cap);
   return -1;
 }
 

@@ -21,6 +21,15 @@
 // Every scale is an exact power of two, undone exactly in the epilogues.  A
 // value whose scaled magnitude reaches 2^15 sets DVGO_ERR_RANGE.
 //
+// The same kernels also run the BF16 form (template parameter OpBF16): the
+// parameters are the stored BF16 values, so each weight matrix is one BF16
+// term (the products with its zero lo term are not issued) and the output
+// layer reads BF16-rounded W3, b2, b3; every other operand (layer inputs,
+// hidden activations, gradient rows) is split into two BF16 terms, hi with
+// 8 significant bits and lo with the next 8, so that no rounding to BF16
+// happens between layers.  BF16 has FP32's exponent range: the same
+// power-of-two scales are applied (harmless) and no range limit applies.
+//
 // Forward, per 128-sample tile (thread = tile row = TMEM lane):
 //   X (39 inputs, a 1 carrying b1, zero pad to 48) -> D1 = X W1^T -> H1 =
 //   relu(D1) -> D2 = H1 W2^T -> z2 = D2 + b2 -> output layer and sigmoid on
@@ -64,8 +73,60 @@ constexpr uint32_t iX = 0, iHh = 2 * kXBytes, iHl = 2 * kXBytes + kHBytes;
 constexpr uint32_t kActHeader = 256;
 constexpr float kSX = 64.0f;     // input scale
 constexpr float kSH = 16.0f;     // hidden-activation scale
-constexpr float kRange = 32768.0f;
+constexpr float kRange = 32768.0f;   // FP16 terms: scaled magnitudes must stay below 2^15
 constexpr uint32_t kSpin = 1u << 24;
+
+__device__ __forceinline__ uint32_t u32_of(__half2 v) { return *reinterpret_cast<const uint32_t*>(&v); }
+__device__ __forceinline__ uint32_t u32_of(__nv_bfloat162 v) { return *reinterpret_cast<const uint32_t*>(&v); }
+
+// Operand term formats of the split products.
+struct OpF16 {   // FP32 form: FP16 terms, every matrix split (weights too)
+  static constexpr bool kBF = false;
+  static constexpr bool kWeightLo = true;
+  static constexpr float kMaxScaled = kRange;
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N, int a_mn, int b_mn) {
+    return tc::idesc_f16(M, N, a_mn, b_mn);
+  }
+  // hi and lo terms of the pair (a, b), packed two per word
+  __device__ static __forceinline__ uint32_t split2(float a, float b, uint32_t& lo) {
+    const __half2 h2 = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h2);
+    lo = u32_of(__floats2half2_rn(a - hf.x, b - hf.y));
+    return u32_of(h2);
+  }
+  __device__ static __forceinline__ uint32_t weight2(float a, float b, uint32_t& lo) { return split2(a, b, lo); }
+  // a pair of terms times a power of two r <= 1
+  __device__ static __forceinline__ uint32_t mul2(uint32_t x, float r) {
+    const __half2 y = __hmul2(*reinterpret_cast<const __half2*>(&x), __float2half2_rn(r));
+    return u32_of(y);
+  }
+  __device__ static __forceinline__ float param(float x) { return x; }
+};
+
+struct OpBF16 {  // BF16 form: stored BF16 weights (one term), BF16 hi + lo terms elsewhere
+  static constexpr bool kBF = true;
+  static constexpr bool kWeightLo = false;
+  static constexpr float kMaxScaled = 3.0e38f;   // only an overflow to infinity is reported
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N, int a_mn, int b_mn) {
+    return tc::idesc_bf16(M, N, a_mn, b_mn);
+  }
+  __device__ static __forceinline__ uint32_t split2(float a, float b, uint32_t& lo) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h2);
+    lo = u32_of(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+    return u32_of(h2);
+  }
+  __device__ static __forceinline__ uint32_t weight2(float a, float b, uint32_t& lo) {
+    lo = 0u;
+    return u32_of(__floats2bfloat162_rn(a, b));
+  }
+  __device__ static __forceinline__ uint32_t mul2(uint32_t x, float r) {
+    const __nv_bfloat162 y =
+        __hmul2(*reinterpret_cast<const __nv_bfloat162*>(&x), __float2bfloat162_rn(r));
+    return u32_of(y);
+  }
+  __device__ static __forceinline__ float param(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+};
 
 // backward shared memory
 constexpr uint32_t bW2h = 0, bW2l = bW2h + kW2Bytes, bW1h = bW2l + kW2Bytes,
@@ -105,7 +166,9 @@ __device__ __forceinline__ float pow2_scale(float m) {
 }
 
 // Split 8 (already scaled) values into the hi / lo core-matrix rows at (row,
-// k8); vmax tracks the largest magnitude split (range check).
+// k8); vmax tracks the largest magnitude split (range check).  kWeight: the
+// values are parameters (one term in the BF16 form).
+template <class Op, bool kWeight>
 __device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int k8, uint32_t sbo,
                                           const float* v, float& vmax) {
   uint32_t h[4], l[4];
@@ -113,27 +176,28 @@ __device__ __forceinline__ void st_split8(uint8_t* hi, uint8_t* lo, int row, int
   for (int i = 0; i < 4; ++i) {
     const float a = v[2 * i], b = v[2 * i + 1];
     vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
-    const __half2 h2 = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h2);
-    const __half2 l2 = __floats2half2_rn(a - hf.x, b - hf.y);
-    h[i] = *reinterpret_cast<const uint32_t*>(&h2);
-    l[i] = *reinterpret_cast<const uint32_t*>(&l2);
+    h[i] = kWeight ? Op::weight2(a, b, l[i]) : Op::split2(a, b, l[i]);
   }
   const uint32_t off = tc::cm_off(row, k8, sbo);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// One scaled, split element (setup only).
+// One scaled, split parameter (setup only).
+template <class Op>
 __device__ __forceinline__ void st_split1(uint8_t* hi, uint8_t* lo, uint32_t off, float v) {
-  const __half h = __float2half_rn(v);
-  *reinterpret_cast<__half*>(hi + off) = h;
-  *reinterpret_cast<__half*>(lo + off) = __float2half_rn(v - __half2float(h));
+  uint32_t l;
+  const uint32_t h = Op::weight2(v, 0.0f, l);
+  *reinterpret_cast<uint16_t*>(hi + off) = (uint16_t)(h & 0xffffu);
+  *reinterpret_cast<uint16_t*>(lo + off) = (uint16_t)(l & 0xffffu);
 }
 
-// D (+)= A B^T over K = 16 * ksteps, split operands: three MMAs per K step.
-// a_step / b_step: byte advance of the descriptors' start address per step
-// (the start-address field holds address / 16, so a step adds step / 16).
+// D (+)= A B^T over K = 16 * ksteps, split operands: three MMAs per K step
+// (hi*hi, hi*lo, lo*hi; kALo / kBLo false: A's / B's lo term is zero and
+// its product is not issued).  a_step / b_step: byte advance of the
+// descriptors' start address per step (the start-address field holds
+// address / 16, so a step adds step / 16).
+template <bool kALo = true, bool kBLo = true>
 __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint32_t a_step, uint32_t a_lbo,
                                      uint32_t a_sbo, uint32_t bh, uint32_t bl, uint32_t b_step,
                                      uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
@@ -144,8 +208,8 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint3
 #pragma unroll 1
   for (int k = 0; k < ksteps; ++k) {
     tc::mma_bf16(d, dah, dbh, idesc, (accumulate || k > 0) ? 1u : 0u);
-    tc::mma_bf16(d, dah, dbl, idesc, 1u);
-    tc::mma_bf16(d, dal, dbh, idesc, 1u);
+    if (kBLo) tc::mma_bf16(d, dah, dbl, idesc, 1u);
+    if (kALo) tc::mma_bf16(d, dal, dbh, idesc, 1u);
     dah += ia;
     dal += ia;
     dbh += ib;
@@ -156,6 +220,7 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint3
 // D (+)= A B^T over K = 16 * ksteps with A (128 rows) in tensor memory as
 // split terms: K-chunk q of 32 columns at a_tmem + 32 q, its hi terms packed
 // two per column in the first 16 columns and its lo terms in the next 16.
+template <bool kBLo = true>
 __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh, uint32_t bl, uint32_t b_step,
                                         uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
                                         bool accumulate) {
@@ -165,7 +230,7 @@ __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh
   for (int j = 0; j < ksteps; ++j) {
     const uint32_t ah = a_tmem + 32u * (uint32_t)(j >> 1) + 8u * (uint32_t)(j & 1), al = ah + 16u;
     tc::mma_ts(d, ah, dbh, idesc, (accumulate || j > 0) ? 1u : 0u);
-    tc::mma_ts(d, ah, dbl, idesc, 1u);
+    if (kBLo) tc::mma_ts(d, ah, dbl, idesc, 1u);
     tc::mma_ts(d, al, dbh, idesc, 1u);
     dbh += ib;
     dbl += ib;
@@ -174,31 +239,24 @@ __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh
 
 // 32 values times s split into the tensor-memory chunk layout: hi terms of
 // value pairs in words 0-15, lo terms in words 16-31 (one tcgen05.st).
+template <class Op>
 __device__ __forceinline__ void split32(const float (&v)[32], float s, uint32_t (&hl)[32],
                                         float& vmax) {
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     const float a = s * v[2 * c], b = s * v[2 * c + 1];
     vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
-    const __half2 h2 = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h2);
-    const __half2 l2 = __floats2half2_rn(a - hf.x, b - hf.y);
-    hl[c] = *reinterpret_cast<const uint32_t*>(&h2);
-    hl[16 + c] = *reinterpret_cast<const uint32_t*>(&l2);
+    hl[c] = Op::split2(a, b, hl[16 + c]);
   }
 }
 
 // The split terms of split32 times r (a power of two <= 1, exact in FP16
-// down to its subnormal range) as the hi / lo core-matrix rows of columns
-// k0 .. k0 + 31 of row `row` in shared memory.
-__device__ __forceinline__ uint32_t hmul2_u32(uint32_t x, __half2 r) {
-  const __half2 y = __hmul2(*reinterpret_cast<const __half2*>(&x), r);
-  return *reinterpret_cast<const uint32_t*>(&y);
-}
-template <bool kScale = true>
+// down to its subnormal range, and in BF16) as the hi / lo core-matrix rows
+// of columns k0 .. k0 + 31 of row `row` in shared memory.
+template <class Op, bool kScale = true>
 __device__ __forceinline__ void st_terms32(uint8_t* hi, uint8_t* lo, int row, int k0, const uint32_t (&hl)[32],
-                                           __half2 r) {
-  auto m = [&](uint32_t x) { return kScale ? hmul2_u32(x, r) : x; };
+                                           float r) {
+  auto m = [&](uint32_t x) { return kScale ? Op::mul2(x, r) : x; };
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t off = tc::cm_off(row, k0 + 8 * q, kSboH);
@@ -209,13 +267,13 @@ __device__ __forceinline__ void st_terms32(uint8_t* hi, uint8_t* lo, int row, in
   }
 }
 
-// Output-layer constants (exact FP32).
-template <class SideT>
+// Output-layer constants (FP32; the stored BF16 values in the BF16 form).
+template <class Op, class SideT>
 __device__ __forceinline__ void load_out_layer(const float* __restrict__ params, SideT* fs) {
   for (int o = threadIdx.x; o < kHid; o += blockDim.x)
-    fs->ob[o] = make_float4(params[kOffB2 + o], params[kOffW3 + o], params[kOffW3 + kHid + o],
-                            params[kOffW3 + 2 * kHid + o]);
-  if (threadIdx.x < 4) fs->b3[threadIdx.x] = threadIdx.x < kOut ? params[kOffB3 + threadIdx.x] : 0.0f;
+    fs->ob[o] = make_float4(Op::param(params[kOffB2 + o]), Op::param(params[kOffW3 + o]),
+                            Op::param(params[kOffW3 + kHid + o]), Op::param(params[kOffW3 + 2 * kHid + o]));
+  if (threadIdx.x < 4) fs->b3[threadIdx.x] = threadIdx.x < kOut ? Op::param(params[kOffB3 + threadIdx.x]) : 0.0f;
 }
 
 // This thread's share of max |p[e]|, e < count (float4 loads, four in
@@ -244,7 +302,7 @@ __device__ __forceinline__ float abs_max_part(const float* __restrict__ p, int c
 
 // Rows o of W1 | b1 | 0 (width K = 8 kb, the bias in column kIn when K > kIn),
 // scaled by s, as split K-major core matrices [o][k]; 8 columns per chunk.
-template <int K>
+template <class Op, int K>
 __device__ __forceinline__ void load_w1(const float* __restrict__ params, uint8_t* hi, uint8_t* lo, uint32_t sbo,
                                         float s) {
   constexpr int kB = K / 8, kChunks = kHid * kB;
@@ -268,19 +326,20 @@ __device__ __forceinline__ void load_w1(const float* __restrict__ params, uint8_
       if (c < kChunks) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[u][i] *= s;
-        st_split8(hi, lo, c / kB, (c % kB) * 8, sbo, v[u], dummy);
+        st_split8<Op, true>(hi, lo, c / kB, (c % kB) * 8, sbo, v[u], dummy);
       }
     }
   }
 }
 
 // W2 (scaled by s) as split K-major core matrices [o][i]; 8 columns per chunk.
+template <class Op>
 __device__ __forceinline__ void load_w2(const float* __restrict__ params, uint8_t* hi, uint8_t* lo, float s) {
   const float* w = params + kOffW2;
   float dummy = 0.0f;
   if ((reinterpret_cast<uintptr_t>(w) & 15u) != 0) {
     for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x)
-      st_split1(hi, lo, tc::cm_off(e / kHid, e % kHid, kSboH), s * __ldg(w + e));
+      st_split1<Op>(hi, lo, tc::cm_off(e / kHid, e % kHid, kSboH), s * __ldg(w + e));
     return;
   }
   constexpr int kChunks = kHid * kHid / 8;
@@ -300,7 +359,7 @@ __device__ __forceinline__ void load_w2(const float* __restrict__ params, uint8_
       if (c < kChunks) {
         float v[8] = {s * a[u].x, s * a[u].y, s * a[u].z, s * a[u].w,
                       s * b[u].x, s * b[u].y, s * b[u].z, s * b[u].w};
-        st_split8(hi, lo, c >> 4, (c & 15) * 8, kSboH, v, dummy);
+        st_split8<Op, true>(hi, lo, c >> 4, (c & 15) * 8, kSboH, v, dummy);
       }
     }
   }
@@ -489,6 +548,7 @@ __device__ __forceinline__ bool fwd_wait(FwdSide* fs, uint64_t* bar, uint32_t pa
 //   MMA:     wait h1_full(k - 1) -> layer 2 of k - 1 -> commit l2_full(k - 1);
 //            wait x_full(k) (and l2_full(k - 2): buffer b's H1 read) -> layer 1
 //            of k -> commit l1_full(k).
+template <class Op>
 __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
     const float* __restrict__ k0, const float* __restrict__ rays_d, const int32_t* __restrict__ ray_id,
     const int32_t* __restrict__ idx, int64_t n_cap, const int64_t* __restrict__ n_dev,
@@ -521,9 +581,9 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
   const float sW1 = pow2_scale(block_max(m1, fs->red));
   const float sW2 = pow2_scale(block_max(m2, fs->red));
   if (warp < 16 && nt > 0) row_in_l2(in, k0, ray_id, qw == 0);
-  load_w1<kK1>(params, sm + gW1h, sm + gW1l, kSboX, sW1);
-  load_w2(params, sm + gW2h, sm + gW2l, sW2);
-  load_out_layer(params, fs);
+  load_w1<Op, kK1>(params, sm + gW1h, sm + gW1l, kSboX, sW1);
+  load_w2<Op>(params, sm + gW2h, sm + gW2l, sW2);
+  load_out_layer<Op>(params, fs);
   if (warp < 16 && nt > 0) row_in_l3(in, rays_d);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -536,7 +596,7 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
 
   if (warp == 16) {
     // ------------------------------------------------------------ MMA warp
-    const uint32_t id128 = tc::idesc_f16(128, kHid, 0, 0);
+    const uint32_t id128 = Op::idesc(128, kHid, 0, 0);
     const uint32_t sW1h = tc::smem_u32(sm + gW1h), sW1l = tc::smem_u32(sm + gW1l);
     const uint32_t sW2h = tc::smem_u32(sm + gW2h), sW2l = tc::smem_u32(sm + gW2l);
     // lane 0 polls; the outcome is the warp's
@@ -551,7 +611,7 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
       tc::fence_after_sync();
       if (lane == 0) {
         tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iHh, sm + gStage, 2 * kHBytes);
-        mma3_ts(buf + 128u, buf, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
+        mma3_ts<Op::kWeightLo>(buf + 128u, buf, sW2h, sW2l, 256, 128, kSboH, kHid / 16, id128, false);
         tc::mma_commit(&fs->l2_full[b]);
       }
       __syncwarp();
@@ -567,7 +627,8 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
         tc::bulk_wait_read();   // staging (H1 of k - 1) and X buffer b's older copy are read
         tc::bulk_s2g(act_img + (size_t)tile_of(k) * kImage + iX, xb, 2 * kXBytes);
         const uint32_t xs = tc::smem_u32(xb);
-        mma3(buf, xs, xs + kSboX, 256, 128, kSboXs, sW1h, sW1l, 256, 128, kSboX, kK1 / 16, id128, false);
+        mma3<true, Op::kWeightLo>(buf, xs, xs + kSboX, 256, 128, kSboXs, sW1h, sW1l, 256, 128, kSboX,
+                                  kK1 / 16, id128, false);
         tc::mma_commit(&fs->l1_full[b]);
       }
       __syncwarp();
@@ -606,8 +667,8 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
 #pragma unroll
       for (int i = 0; i < 16; ++i) x[i] *= kSX;
       uint8_t* xs = sm + gX0 + (k & 1) * gXBuf;
-      st_split8(xs, xs + kSboX, row, fb * 8, kSboXs, x, vmax);
-      if (nb == 2) st_split8(xs, xs + kSboX, row, fb * 8 + 8, kSboXs, x + 8, vmax);
+      st_split8<Op, false>(xs, xs + kSboX, row, fb * 8, kSboXs, x, vmax);
+      if (nb == 2) st_split8<Op, false>(xs, xs + kSboX, row, fb * 8 + 8, kSboXs, x + 8, vmax);
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&fs->x_full[k & 1]);
@@ -626,11 +687,7 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
         for (int c = 0; c < 16; ++c) {
           const float a = fmaxf(v[2 * c] * inv1, 0.0f), bb = fmaxf(v[2 * c + 1] * inv1, 0.0f);
           vmax = fmaxf(vmax, fmaxf(a, bb));
-          const __half2 h2 = __floats2half2_rn(a, bb);
-          const float2 hf = __half22float2(h2);
-          const __half2 l2 = __floats2half2_rn(a - hf.x, bb - hf.y);
-          hl[c] = *reinterpret_cast<const uint32_t*>(&h2);
-          hl[16 + c] = *reinterpret_cast<const uint32_t*>(&l2);
+          hl[c] = Op::split2(a, bb, hl[16 + c]);
         }
       }
       tc::tmem_st32(taddr, hl);
@@ -710,7 +767,7 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
     if (nt > 0) layer2_out(nt - 1, s_prev);
     __syncwarp();
   }
-  if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
+  if (vmax >= Op::kMaxScaled) set_status(DVGO_ERR_RANGE);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -762,6 +819,7 @@ __device__ __forceinline__ void up_l3(UpIn& u, const float* __restrict__ g_rgb,
   for (int c = 0; c < kOut; ++c) u.g[c] = u.g[c] * y[c] * (1.0f - y[c]);
 }
 
+template <class Op>
 __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
     const float* __restrict__ rgb, const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx,
@@ -849,14 +907,15 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   // W1[:, 0:16] as split [o][k] rows for g_X = G1 W1[:, 0:16]
   // W1[:, 0:16] split, hi and lo core matrices side by side in each 8-row
   // group, so that [hi | lo] is one 32-wide B operand of g_X
-  load_w1<16>(params, sm + bW1h, sm + bW1h + 256, kSboW1s, sW1);
-  load_w2(params, sm + bW2h, sm + bW2l, sW2);
+  load_w1<Op, 16>(params, sm + bW1h, sm + bW1h + 256, kSboW1s, sW1);
+  load_w2<Op>(params, sm + bW2h, sm + bW2l, sW2);
   up_l3(cur, g_rgb, g_color, rgb);
   const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
   // this thread's hidden unit in the transposed layer-2 products (TMEM lane)
   const int oh = (warp & 3) * 32 + lane;
-  const float b2o = __ldg(params + kOffB2 + oh), w3o0 = __ldg(params + kOffW3 + oh),
-              w3o1 = __ldg(params + kOffW3 + kHid + oh), w3o2 = __ldg(params + kOffW3 + 2 * kHid + oh);
+  const float b2o = Op::param(__ldg(params + kOffB2 + oh)), w3o0 = Op::param(__ldg(params + kOffW3 + oh)),
+              w3o1 = Op::param(__ldg(params + kOffW3 + kHid + oh)),
+              w3o2 = Op::param(__ldg(params + kOffW3 + 2 * kHid + oh));
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -918,8 +977,8 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     inflight_h = false;
     if (tid == kIssuer) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
       tc::fence_after_sync();
-      mma3(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH, kHid / 16,
-           tc::idesc_f16(128, kTile, 0, 0), false);
+      mma3<Op::kWeightLo, true>(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH,
+                                kHid / 16, Op::idesc(128, kTile, 0, 0), false);
       tc::mma_commit(&fs->bar_mma);
     }
     if (warp != kIssuer / 32) prologue();
@@ -961,12 +1020,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         v[i] = g;
       }
       uint32_t hl[32];
-      split32(v, S2, hl, vmax);
+      split32<Op>(v, S2, hl, vmax);
       tc::tmem_st32(lane_base + cTmp + 32 * qw, hl);
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] *= fs->smp[32 * qw + i].w;
-      split32(v, 1.0f, hl, vmax);
-      st_terms32<false>(sm + bGh, sm + bGl, oh, 32 * qw, hl, __float2half2_rn(1.0f));
+      split32<Op>(v, 1.0f, hl, vmax);
+      st_terms32<Op, false>(sm + bGh, sm + bGl, oh, 32 * qw, hl, 1.0f);
     }
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
@@ -975,9 +1034,9 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     if (tid == kIssuer) {   // dW2 += G2^T H1 (A from tensor memory);  g_h1 = G2 W2 (A MN-major)
       tc::fence_after_sync();
       mma3_ts(tmem + cDW2, tmem + cTmp, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
-              tc::idesc_f16(128, kHid, 0, 1), dw_started);
-      mma3(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH, kSboH, 128, kHid / 16,
-           tc::idesc_f16(128, kHid, 1, 1), false);
+              Op::idesc(128, kHid, 0, 1), dw_started);
+      mma3<true, Op::kWeightLo>(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH, kSboH, 128,
+                                kHid / 16, Op::idesc(128, kHid, 1, 1), false);
       tc::mma_commit(&fs->bar_mma);
     }
     if (warp == kIssuer / 32) prologue();
@@ -991,9 +1050,9 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] : 0.0f;
       uint32_t hl[32];
-      split32(v, fG1, hl, vmax);
+      split32<Op>(v, fG1, hl, vmax);
       tc::tmem_st32(lane_base + cGH + 32 * qw, hl);
-      st_terms32(sm + bGh, sm + bGl, row, 32 * qw, hl, __float2half2_rn(r1));
+      st_terms32<Op>(sm + bGh, sm + bGl, row, 32 * qw, hl, r1);
     }
     tc::tmem_wait_st();
     tc::fence_proxy_async_smem();
@@ -1006,7 +1065,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     if (tid == kIssuer) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
       tc::fence_after_sync();
       {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
-        const uint32_t id96 = tc::idesc_f16(128, 2 * kK1, 1, 1), id48 = tc::idesc_f16(128, kK1, 1, 1);
+        const uint32_t id96 = Op::idesc(128, 2 * kK1, 1, 1), id48 = Op::idesc(128, kK1, 1, 1);
         uint64_t dah = tc::smem_desc(sGh, kSboH, 128), dal = tc::smem_desc(sGl, kSboH, 128);
         uint64_t dbx = tc::smem_desc(sX, kSboXs, 128);
 #pragma unroll 1
@@ -1019,7 +1078,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
         }
       }
       {   // per K step: G1h [W1h | W1l] (N = 32: hi*hi in columns 0-15, hi*lo in 16-31), G1l W1h
-        const uint32_t id32 = tc::idesc_f16(128, 32, 0, 1), id16 = tc::idesc_f16(128, 16, 0, 1);
+        const uint32_t id32 = Op::idesc(128, 32, 0, 1), id16 = Op::idesc(128, 16, 0, 1);
         uint64_t db = tc::smem_desc(sW1h, kSboW1s, 128);
 #pragma unroll 1
         for (uint32_t j = 0; j < kHid / 16; ++j) {
@@ -1059,7 +1118,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_x, kSpin);
     set_status(DVGO_ERR_TIMEOUT);
   }
-  if (vmax >= kRange) set_status(DVGO_ERR_RANGE);
+  if (vmax >= Op::kMaxScaled) set_status(DVGO_ERR_RANGE);
   // This CTA's gradient goes to its own row of the partials array (every
   // parameter written, no atomics); a second kernel sums the rows in a fixed
   // order.  Output-layer and b2 sums of the four lane quarters meet in shared
@@ -1179,38 +1238,58 @@ int64_t rgbnet_act_bytes_tc(int64_t n_cap) {
   return act_images_end(n_cap) + (int64_t)kNumSMs * kNumParams * (int64_t)sizeof(float);
 }
 
-int dvgo_rgbnet_fwd_f32tc(const float* k0, const float* rays_d, const int32_t* ray_id,
-                          const int32_t* idx, int64_t n_cap, const int64_t* n_dev, const float* params,
-                          float* rgb, float* act, cudaStream_t st) {
+template <class Op>
+static int rgbnet_fwd_tc(const float* k0, const float* rays_d, const int32_t* ray_id, const int32_t* idx,
+                         int64_t n_cap, const int64_t* n_dev, const float* params, float* rgb, float* act,
+                         cudaStream_t st) {
   const size_t smem = gEnd + sizeof(FwdSide) + 2 * 4 * kTile * kOut * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(rgbnet_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(rgbnet_fwd_tc_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
-  rgbnet_fwd_tc_kernel<<<grid, 544, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
-                                                reinterpret_cast<uint8_t*>(act));
+  rgbnet_fwd_tc_kernel<Op><<<grid, 544, smem, st>>>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb,
+                                                    reinterpret_cast<uint8_t*>(act));
   return launch_status();
 }
 
-int dvgo_rgbnet_bwd_f32tc(const float* g_rgb, const float* g_color, const float* w,
-                          const float* rgb, const int32_t* ray_id, const int32_t* idx, int64_t n_cap,
-                          const int64_t* n_dev, const float* params, float* act, float* g_params,
-                          float* g_k0, cudaStream_t st) {
+template <class Op>
+static int rgbnet_bwd_tc(const float* g_rgb, const float* g_color, const float* w, const float* rgb,
+                         const int32_t* ray_id, const int32_t* idx, int64_t n_cap, const int64_t* n_dev,
+                         const float* params, float* act, float* g_params, float* g_k0, cudaStream_t st) {
   const size_t smem = bEnd + sizeof(Side);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(rgbnet_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(rgbnet_bwd_tc_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
   float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(act) + act_images_end(n_cap));
-  rgbnet_bwd_tc_kernel<<<grid, 512, smem, st>>>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev,
-                                                params, reinterpret_cast<const uint8_t*>(act), part,
-                                                g_k0);
+  rgbnet_bwd_tc_kernel<Op><<<grid, 512, smem, st>>>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev,
+                                                    params, reinterpret_cast<const uint8_t*>(act), part,
+                                                    g_k0);
   partials_reduce_kernel<<<(kNumParams + 31) / 32, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
   return launch_status();
+}
+
+// bf16_form: the BF16 form (stored BF16 parameters, BF16 operand terms);
+// otherwise the FP32 form (FP16 operand terms).
+int dvgo_rgbnet_fwd_tc(const float* k0, const float* rays_d, const int32_t* ray_id, const int32_t* idx,
+                       int64_t n_cap, const int64_t* n_dev, const float* params, float* rgb, float* act,
+                       bool bf16_form, cudaStream_t st) {
+  return bf16_form ? rgbnet_fwd_tc<OpBF16>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st)
+                   : rgbnet_fwd_tc<OpF16>(k0, rays_d, ray_id, idx, n_cap, n_dev, params, rgb, act, st);
+}
+
+int dvgo_rgbnet_bwd_tc(const float* g_rgb, const float* g_color, const float* w, const float* rgb,
+                       const int32_t* ray_id, const int32_t* idx, int64_t n_cap, const int64_t* n_dev,
+                       const float* params, float* act, float* g_params, float* g_k0, bool bf16_form,
+                       cudaStream_t st) {
+  return bf16_form ? rgbnet_bwd_tc<OpBF16>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev, params, act,
+                                           g_params, g_k0, st)
+                   : rgbnet_bwd_tc<OpF16>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev, params, act,
+                                          g_params, g_k0, st);
 }
 
 int dvgo_mlp_tc_status_read_and_clear(cudaStream_t st) {

@@ -2,7 +2,7 @@
 // softmax cross-entropy against the plain renderer's compositing weights,
 // inverse-CDF selection of the samples to keep, and compaction of the kept
 // samples into a new ragged list.  The proposal network itself runs in
-// mlp_bf16.cu.
+// mlp_prop.cu.
 #include "common.cuh"
 
 int dvgo_proposal_fwd_bf16(const float*, const int32_t*, int64_t, const int64_t*, const float*,

@@ -108,8 +108,8 @@ class RGBNet(torch.autograd.Function):
     """Colour MLP (39 -> ReLU 128 -> ReLU 128 -> sigmoid 3) of every sample:
     input [k0 (12), view-direction encoding of rays_d[ray_id]].  precision:
     "f32tc" (FP32 accuracy on the tensor cores, the default), "f32" (CUDA
-    cores) or "bf16".  Backward: the fused adjoint kernel (parameter and k0
-    gradients)."""
+    cores) or "bf16" (stored BF16 parameters, BF16 tensor-core operands).
+    Backward: the fused adjoint kernel (parameter and k0 gradients)."""
 
     PREC = {"f32": L.F32, "f32tc": L.F32_TC, "bf16": L.BF16}
 
@@ -121,7 +121,7 @@ class RGBNet(torch.autograd.Function):
         act = None
         if prec == L.F32:
             act = torch.empty(S, 256, dtype=torch.float32, device=k0.device)
-        elif prec == L.F32_TC:
+        else:   # tensor-core forms: tile images of the split layer inputs
             act = torch.empty(L.rgbnet_act_bytes(S, prec), dtype=torch.uint8, device=k0.device)
         L.rgbnet_fwd(k0, rays_d, ray_id, None, S, None, params, prec, rgb, act)
         ctx.save_for_backward(k0, params, rays_d, ray_id, rgb)
@@ -135,7 +135,7 @@ class RGBNet(torch.autograd.Function):
         g_params = torch.zeros_like(params)
         g_k0 = torch.empty_like(k0)
         L.rgbnet_bwd(g_rgb.contiguous(), None, None, k0, rays_d, ray_id, None, S, None, params,
-                     ctx.prec, g_params, g_k0, ctx.act, None if ctx.prec == L.BF16 else rgb)
+                     ctx.prec, g_params, g_k0, ctx.act, rgb)
         return g_k0, g_params, None, None, None
 
 

@@ -34,11 +34,9 @@ def live_of(ray_off, n_live):
     return live
 
 
-def forward_backward(cfg, rp, density, feature, params, o, d, target, bf16=False,
-                     grads=True):
+def forward_backward(cfg, rp, density, feature, params, o, d, target, grads=True):
     """density [G,G,G] f32, feature [G,G,G,12] f32, params flat f32 (the values
-    the renderer reads: BF16-rounded already for the BF16 form, whose MLP
-    also stores its hidden-layer operands in BF16: q_bf16)."""
+    the renderer reads: BF16-rounded already for the BF16 form)."""
     lo, hi = cfg.bbox_min, cfg.bbox_max
     sh = shift32(rp.alpha_init)
     mask = None
@@ -52,7 +50,7 @@ def forward_backward(cfg, rp, density, feature, params, o, d, target, bf16=False
     k0 = oracle.trilinear(feature, lo, hi, smp.xyz[live])
     x = oracle.rgbnet_input(k0, d[smp.ray_id[live]])
     p64 = params.astype(np.float64)
-    rgb_live = oracle.mlp_fwd(synth.RGBNET_DIMS, p64, x, True, q_bf16=bf16)
+    rgb_live = oracle.mlp_fwd(synth.RGBNET_DIMS, p64, x, True)
     rgb = np.zeros((smp.S, 3))
     rgb[live] = rgb_live
     comp = oracle.composite(raw, rgb, smp.ray_off, sh, rp.interval, rp.T_stop, rp.bg)
@@ -69,7 +67,7 @@ def forward_backward(cfg, rp, density, feature, params, o, d, target, bf16=False
                                  comp["n_live"])
     g_raw, g_rgb = oracle.composite_bwd(raw, rgb, smp.ray_off, sh, rp.interval, rp.T_stop, rp.bg,
                                         g_color, g_w)
-    g_params, g_x = oracle.mlp_bwd(synth.RGBNET_DIMS, p64, x, g_rgb[live], True, q_bf16=bf16)
+    g_params, g_x = oracle.mlp_bwd(synth.RGBNET_DIMS, p64, x, g_rgb[live], True)
     g_density = oracle.trilinear_adjoint(g_raw[live], density.shape, lo, hi, smp.xyz[live])
     g_feature = oracle.trilinear_adjoint(g_x[:, :12], feature.shape, lo, hi, smp.xyz[live])
     out.update(g_color=g_color, g_w=g_w, g_raw=g_raw, g_rgb=g_rgb, g_params=g_params,

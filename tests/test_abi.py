@@ -72,7 +72,9 @@ def test_host_validation_without_gpu(lib):
     assert lib.dvgo_rgbnet_act_bytes(10, 0) == 10 * 1024
     assert lib.dvgo_rgbnet_act_bytes(300, 2) == 256 + 3 * 90112 + 152 * 22019 * 4
     assert lib.dvgo_rgbnet_act_bytes(0, 2) == 256 + 152 * 22019 * 4
-    assert lib.dvgo_rgbnet_act_bytes(10, 1) == 152 * 22019 * 4
+    # the BF16 form runs the same tensor-core kernels and needs the same buffer
+    assert lib.dvgo_rgbnet_act_bytes(10, 1) == 256 + 90112 + 152 * 22019 * 4
+    assert lib.dvgo_rgbnet_fwd(p, p, p, None, 10, None, p, 1, p, None) == -1
     assert lib.dvgo_rgbnet_act_bytes(-1, 0) == -1
     assert lib.dvgo_rgbnet_act_bytes(5, 7) == -1
     assert lib.dvgo_status_string(-8) == b"value outside the range of a split-FP16 operand"

@@ -1,7 +1,9 @@
 """GPU parity of each C-ABI kernel against the FP64 oracle on seeded inputs.
 
 Tolerances: integer/index outputs bit-exact; FP32 form 1e-5 relative
-(max|x - ref| / max|ref| per tensor); BF16 form 2e-3 relative.
+(max|x - ref| / max|ref| per tensor); BF16 form 2e-3 relative.  The BF16
+form is compared with the plain FP64 oracle on the stored (BF16-rounded)
+parameters and grids; nothing in the oracle copies the kernels' rounding.
 """
 import numpy as np
 import pytest
@@ -619,7 +621,7 @@ def test_rgbnet_fwd_bwd(L, precision, n):
     prec = {"f32": L.F32, "f32tc": L.F32_TC, "bf16": L.BF16}[precision]
     tol = TOL16 if bf else TOL32
     act_tc = None
-    if precision == "f32tc":
+    if precision in ("f32tc", "bf16"):
         act_tc = torch.empty(L.rgbnet_act_bytes(n, prec), dtype=torch.uint8, device="cuda")
     p_ref = synth.bf16_round(params) if bf else params
     # every other sample through idx, count on the device
@@ -629,16 +631,14 @@ def test_rgbnet_fwd_bwd(L, precision, n):
     n_dev = torch.tensor([m], dtype=torch.int64, device="cuda")
     L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb, act_tc)
     x = oracle.rgbnet_input(k0[idx], d[ray_id[idx]])
-    ref = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True, q_bf16=bf)
+    ref = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True)
     got = host(rgb)
     assert rel_err(got[idx], ref) < tol
     rest = np.setdiff1d(np.arange(n), idx)
     assert np.all(got[rest] == -1.0)
     # backward recomputing the forward, and (FP32 form) from stored activations
-    for use_act in ((False, True) if precision in ("f32", "bf16") else (True,)):
+    for use_act in ((False, True) if precision == "f32" else (True,)):
         act = act_tc
-        if use_act and precision == "bf16":   # per-CTA partial gradients instead of atomics
-            act = torch.empty(L.rgbnet_act_bytes(n, prec), dtype=torch.uint8, device="cuda")
         if use_act and precision == "f32":
             act = torch.empty(n, 256, device="cuda")
             L.rgbnet_fwd(dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev, dev(params), prec, rgb,
@@ -648,12 +648,8 @@ def test_rgbnet_fwd_bwd(L, precision, n):
         L.rgbnet_bwd(dev(g_rgb), None, None, dev(k0), dev(d), dev(ray_id), dev(idx), n, n_dev,
                      dev(params), prec, g_params, g_k0, act, rgb if use_act else None)
         check_mlp_grads(oracle, synth.RGBNET_DIMS, p_ref, x, g_rgb[idx], host(g_params),
-                        host(g_k0)[idx], tol, bf)
+                        host(g_k0)[idx], tol, tau=2e-5 if bf else 1e-6)
     assert L.device_status() == 0
-    if bf:
-        # error of the BF16 form against the unrounded FP64 MLP (reported)
-        ref64 = oracle.mlp_fwd(synth.RGBNET_DIMS, p_ref, x, True)
-        assert rel_err(got[idx], ref64) < 2e-2
 
 
 def test_rgbnet_bwd_from_compositing_gradient(L):
@@ -680,7 +676,7 @@ def test_rgbnet_bwd_from_compositing_gradient(L):
     x = oracle.rgbnet_input(k0, d[ray_id])
     from conftest import check_mlp_grads
     check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, w[:, None] * g_color[ray_id],
-                    host(g_params), host(g_k0), TOL32, False)
+                    host(g_params), host(g_k0), TOL32)
 
 
 def test_rgbnet_tc_compositing_gradient_wide_range(L):
@@ -704,11 +700,10 @@ def test_rgbnet_tc_compositing_gradient_wide_range(L):
     assert rel_err(host(rgb), oracle.mlp_fwd(synth.RGBNET_DIMS, params, x, True)) < TOL32
     from conftest import check_mlp_grads
     g_up = w[:, None] * g_color[ray_id]
-    check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, g_up, host(g_params), host(g_k0), TOL32,
-                    False)
-    _, gx = oracle.mlp_bwd(synth.RGBNET_DIMS, params, x, g_up, True, False)
+    check_mlp_grads(oracle, synth.RGBNET_DIMS, params, x, g_up, host(g_params), host(g_k0), TOL32)
+    _, gx = oracle.mlp_bwd(synth.RGBNET_DIMS, params, x, g_up, True)
     gx = gx[:, :12]
-    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params, x, False)
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params, x)
     got = host(g_k0)
     keep = np.nonzero(zmin > 1e-6)[0]
     assert len(keep) > 0.9 * n

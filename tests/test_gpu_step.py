@@ -50,7 +50,7 @@ def _run(T, cfg, n_rays, precision, tv_dense, ray_stride=1):
     Dr = synth.bf16_round(D) if bf else D
     Fr = synth.bf16_round(Fg) if bf else Fg
     Pr = synth.bf16_round(P) if bf else P
-    fb = forward_backward(cfg, rp, Dr, Fr, Pr, o, d, tgt, bf16=bf)
+    fb = forward_backward(cfg, rp, Dr, Fr, Pr, o, d, tgt)
     fb["density0"], fb["feature0"], fb["params0"] = D, Fg, P
     opt = optimizer(rp, 1, D, Fg, P, fb, tv_dense, Dr, Fr)
     return gpu, fb, opt, cfg, rp, Pr
@@ -77,13 +77,14 @@ def _compare(gpu, fb, opt, tol, cfg, rp, params, bf16=False):
     assert rel_err(gpu["loss"], fb["loss"]) < tol
     assert rel_err(gpu["g_density"], fb["g_density"]) < tol
     from conftest import check_mlp_grads
+    # ReLU inputs within rounding of 0 (tau: the operand precision's reach)
+    tau = 1e-5 if bf16 else 1e-6
     check_mlp_grads(oracle, synth.RGBNET_DIMS, params.astype(np.float64), fb["x"],
-                    fb["g_rgb"][fb["live"]], gpu["g_mlp"], None, tol, bf16)
+                    fb["g_rgb"][fb["live"]], gpu["g_mlp"], None, tol, tau=tau)
     # Feature-grid gradient: a sample whose ReLU input sits within rounding of
     # 0 may switch that unit on in one precision and off in the other; the
     # voxels of such samples are compared separately (bounded, counted).
-    tau = 1e-5 if bf16 else 1e-6
-    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params.astype(np.float64), fb["x"], bf16)
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params.astype(np.float64), fb["x"])
     amb = zmin < tau
     gf = gpu["g_feature"]
     rf = fb["g_feature"].reshape(gf.shape)
@@ -242,6 +243,6 @@ def test_full_size_step_sampled_outputs(T):
     assert rel_err(rgb[rows][live], fb["rgb"][live]) < 1e-5
     assert rel_err(g_raw[rows][live], fb["g_raw"][live] * scale) < 1e-5
     # g_k0 per live sample, except samples whose ReLU input sits within rounding of 0
-    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"], False)
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
     keep = zmin >= 1e-6
     assert rel_err(g_k0[rows][live][keep], fb["g_k0"][keep] * scale) < 1e-5

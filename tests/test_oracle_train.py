@@ -173,47 +173,6 @@ def test_min_abs_preact_against_torch(orc):
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-15)
 
 
-def test_mlp_bf16_operands_against_torch_rounding(orc):
-    # The BF16-operand variant equals torch FP64 autograd where the input of
-    # each hidden layer and the gradient at each hidden layer's output are
-    # rounded to bfloat16 by torch's own conversion.
-    rng = np.random.default_rng(13)
-    dims = synth.RGBNET_DIMS
-    params = synth.bf16_round(synth.mlp_params(dims) * 2.0).astype(np.float64)
-    x = rng.normal(0, 0.5, size=(25, dims[0]))
-    g_out = rng.normal(size=(25, dims[-1]))
-
-    def q(t):
-        return t.to(torch.float32).to(torch.bfloat16).to(torch.float64)
-
-    p = torch.tensor(params, requires_grad=True)
-    xt = torch.tensor(x, requires_grad=True)
-    off, h = 0, xt
-    for l in range(3):
-        nW = dims[l + 1] * dims[l]
-        W = p[off:off + nW].view(dims[l + 1], dims[l])
-        b = p[off + nW:off + nW + dims[l + 1]]
-        off += nW + dims[l + 1]
-        # value rounded to bfloat16, gradient passes through unchanged
-        hin = h + (q(h) - h).detach() if l < 2 else h
-        z = torch.nn.functional.linear(hin, W, b)
-        if l < 2:
-            z.register_hook(lambda g: q(g))
-            h = torch.relu(z)
-        else:
-            h = torch.sigmoid(z)
-    (h * torch.tensor(g_out)).sum().backward()
-    out = orc.mlp_fwd(dims, params, x, True, q_bf16=True)
-    gp, gx = orc.mlp_bwd(dims, params, x, g_out, True, q_bf16=True)
-    assert rel_err(out, h.detach().numpy()) < 1e-13
-    assert rel_err(gp, p.grad.numpy()) < 1e-12
-    assert rel_err(gx, xt.grad.numpy()) < 1e-12
-    # and it differs from the unrounded MLP (BF16 steps, plus ReLU units
-    # that switch between the two)
-    gp0, _ = orc.mlp_bwd(dims, params, x, g_out, True)
-    assert 1e-4 < rel_err(gp, gp0) < 0.2
-
-
 def test_ragged_proposal_pieces_match_per_ray_dense(orc):
     rng = np.random.default_rng(14)
     counts = [0, 1, 7, 64, 300]
