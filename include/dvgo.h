@@ -227,11 +227,13 @@ int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_
 
 /* Backward of raw->alpha + compositing: with g_i = <rgb_i, g_color[r]> +
  * g_w[i] (rgb and g_w may be NULL: that term is 0) and g_T = <bg,
- * g_color[r]>, a reverse scan over the live samples gives
- * R_k = g_{k+1} alpha_{k+1} + (1 - alpha_{k+1}) R_{k+1}, R_{n-1} = g_T, and
- * g_raw[k] = interval sigmoid(raw_k + shift) T_{k+1} (g_k - R_k).  g_rgb
- * (may be NULL) receives w_k g_color[r].  Samples past the halting index get
- * zero gradients. */
+ * g_color[r]>, the reverse recurrence over the live samples
+ * R_k = g_{k+1} alpha_{k+1} + (1 - alpha_{k+1}) R_{k+1}, R_{n-1} = g_T, gives
+ * g_raw[k] = interval sigmoid(raw_k + shift) T_{k+1} (g_k - R_k).  It is
+ * evaluated as T_{k+1} g_k - S_k with the suffix sum S_k = T_{k+1} R_k =
+ * sum_{j>k} g_j w_j + g_T T_end (compensated FP32 sums, so the error does not
+ * grow with the ray's length).  g_rgb (may be NULL) receives w_k g_color[r].
+ * Samples past the halting index get zero gradients. */
 int dvgo_composite_bwd(const float* g_color, const float* g_w, const float* raw, const float* T,
                        const float* rgb, const int64_t* ray_off, const int32_t* n_live, int64_t R,
                        float shift, float interval, const float bg[3], float* g_raw, float* g_rgb,

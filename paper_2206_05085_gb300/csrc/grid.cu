@@ -8,17 +8,24 @@
 
 namespace dvgo {
 
+// Grid index of a position: u_a = (x_a - lo_a) (G_a - 1) / (hi_a - lo_a),
+// written u = x S + C with S = (G - 1)/(hi - lo) and C = -lo S, each held as
+// an unevaluated pair of floats (hi + lo parts, formed in double on the host).
 struct TriArgs {
   BrickGeom g;
-  float lo[3];
-  float scale[3];  // (G-1)/(hi-lo)
+  float s_hi[3], s_lo[3];
+  float c_hi[3], c_lo[3];
 };
 
 static bool make_tri(TriArgs& T, const dvgo_grid_desc* d) {
   for (int a = 0; a < 3; ++a) {
     if (d->G[a] < 2 || !(d->hi[a] > d->lo[a])) return false;
-    T.lo[a] = d->lo[a];
-    T.scale[a] = (float)(d->G[a] - 1) / (d->hi[a] - d->lo[a]);
+    const double S = (double)(d->G[a] - 1) / ((double)d->hi[a] - (double)d->lo[a]);
+    const double C = -(double)d->lo[a] * S;
+    T.s_hi[a] = (float)S;
+    T.s_lo[a] = (float)(S - (double)T.s_hi[a]);
+    T.c_hi[a] = (float)C;
+    T.c_lo[a] = (float)(C - (double)T.c_hi[a]);
   }
   T.g = make_geom(d->G);
   return true;
@@ -30,19 +37,42 @@ struct Corners {
   int ix, iy, iz;    // lower corner
 };
 
+// Cell and fraction along one axis.  u = x S + C is carried as s + e: the
+// product x S_hi split exactly by an FMA, the sum with C_hi split exactly by
+// the two-sum, the small terms added into e.  The fraction f = (s - i) + e
+// (s - i is exact) then has an absolute error of about one rounding of f
+// itself, instead of one rounding of u (up to G 2^-24 grid units), which a
+// steep field would multiply into the interpolated value.  Outside [0, G - 1]
+// u is clamped to the border.
+__device__ __forceinline__ void cell_1d(const TriArgs& T, int a, float x, int& i, float& f) {
+  // explicit roundings (__f*_rn are never contracted into FMAs)
+  const float p = __fmul_rn(x, T.s_hi[a]);
+  const float pe = __fmaf_rn(x, T.s_hi[a], -p);            // x S_hi = p + pe
+  const float s = __fadd_rn(p, T.c_hi[a]);
+  const float bv = __fsub_rn(s, p);
+  const float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bv)), __fsub_rn(T.c_hi[a], bv));   // p + C_hi = s + se
+  const float e = __fadd_rn(se, __fadd_rn(__fmaf_rn(x, T.s_lo[a], pe), T.c_lo[a]));
+  const float u = __fadd_rn(s, e);
+  const int Gm = T.g.G[a] - 1;
+  if (!(u > 0.0f)) {                                       // (also NaN)
+    i = 0;
+    f = 0.0f;
+  } else if (u >= (float)Gm) {
+    i = Gm - 1;
+    f = 1.0f;
+  } else {
+    i = min((int)floorf(u), Gm - 1);
+    f = __fadd_rn(__fsub_rn(s, (float)i), e);
+    f = fminf(fmaxf(f, 0.0f), 1.0f);
+  }
+}
+
 // Corners and weights of the position pos (already loaded).
 __device__ __forceinline__ void corners_at(const TriArgs& T, const float pos[3], Corners& c) {
   int i0[3];
   float f[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float u = (pos[a] - T.lo[a]) * T.scale[a];
-    u = fminf(fmaxf(u, 0.0f), (float)(T.g.G[a] - 1));
-    int i = (int)floorf(u);
-    i = min(i, T.g.G[a] - 2);
-    i0[a] = i;
-    f[a] = u - (float)i;
-  }
+  for (int a = 0; a < 3; ++a) cell_1d(T, a, pos[a], i0[a], f[a]);
   c.ix = i0[0];
   c.iy = i0[1];
   c.iz = i0[2];

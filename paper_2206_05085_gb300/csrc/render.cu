@@ -105,8 +105,14 @@ __global__ void __launch_bounds__(256) composite_rgb_kernel(
 }
 
 // -------------------------------------------------------- composite bwd
-// Reverse scan of the affine maps F_k(x) = (1 - alpha_k) x + g_k alpha_k:
-// R_k = (F_{k+1} o ... o F_{n-1})(g_T).
+// The adjoint reverse recurrence R_k = g_{k+1} alpha_{k+1} + (1 -
+// alpha_{k+1}) R_{k+1}, R_{n-1} = g_T, enters the gradient only as
+// T_{k+1} R_k, which unrolls to the suffix sum
+//   S_k = T_{k+1} R_k = sum_{j > k} g_j w_j + g_T T_end,
+// so g_raw_k = interval sigmoid(raw_k + shift) (T_{k+1} g_k - S_k).  S_k is
+// formed as a sum (per 32-sample chunk by shuffles, across chunks with a
+// compensated carry): no product of (1 - alpha) factors along the ray, so the
+// rounding error does not grow with the ray's length.
 __global__ void __launch_bounds__(256) composite_bwd_kernel(
     const float* __restrict__ g_color, const float* __restrict__ g_w, const float* __restrict__ raw,
     const float* __restrict__ T, const float* __restrict__ rgb, const int64_t* __restrict__ ray_off,
@@ -118,53 +124,44 @@ __global__ void __launch_bounds__(256) composite_bwd_kernel(
     ray_range(ray_off, n_live, r, b, n, N);
     const float gc0 = __ldg(g_color + 3 * r), gc1 = __ldg(g_color + 3 * r + 1),
                 gc2 = __ldg(g_color + 3 * r + 2);
-    float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;  // R_{n-1} = g_T
+    const float gT = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;
+    Kahan suf;   // sum of g_j w_j over the chunks after the current one, + g_T T_end
     const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
     for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
       const int k = c0 + lane;
       const bool valid = k < n;
-      float A = 1.0f, B = 0.0f, gk = 0.0f, la = 0.0f, rk = 0.0f, Tk = 0.0f;
+      float gk = 0.0f, la = 0.0f, rk = 0.0f, Tk = 0.0f, al = 0.0f;
       if (valid) {
         const int64_t s = b + k;
         rk = __ldg(raw + s);
         la = -interval * softplus_f(rk + shift);
-        const float al = -expm1f(la);
+        al = -expm1f(la);
         if (rgb) gk = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
         if (g_w) gk += __ldg(g_w + s);
         Tk = __ldg(T + s);
-        A = 1.0f - al;
-        B = gk * al;
       }
-      // inclusive suffix composition Suf_lane = F_k o F_{k+1} o ... o F_{c0+31}
+      const float Tk1 = Tk * expf(la);
+      if (c0 == last_chunk) suf.add(gT * __shfl_sync(0xffffffffu, Tk1, (n - 1) & 31));   // T_end
+      const float wk = Tk * al;
+      const float v = valid ? gk * wk : 0.0f;
+      float sv = v;   // inclusive suffix sum within the chunk (lane .. 31)
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const float A2 = __shfl_down_sync(0xffffffffu, A, o);
-        const float B2 = __shfl_down_sync(0xffffffffu, B, o);
-        if (lane + o < 32) {
-          B = A * B2 + B;
-          A = A * A2;
-        }
+        const float a = __shfl_down_sync(0xffffffffu, sv, o);
+        if (lane + o < 32) sv += a;
       }
-      float An = __shfl_down_sync(0xffffffffu, A, 1);
-      float Bn = __shfl_down_sync(0xffffffffu, B, 1);
-      if (lane == 31) {
-        An = 1.0f;
-        Bn = 0.0f;
-      }
-      const float Rk = An * carry + Bn;
+      float ex = __shfl_down_sync(0xffffffffu, sv, 1);
+      if (lane == 31) ex = 0.0f;
+      const float Sk = __fadd_rn(suf.s, __fsub_rn(ex, suf.c));
       if (valid) {
-        const float Tk1 = Tk * expf(la);
-        g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
+        g_raw[b + k] = interval * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
         if (g_rgb) {
-          const float wk = Tk * -expm1f(la);
           g_rgb[3 * (b + k)] = wk * gc0;
           g_rgb[3 * (b + k) + 1] = wk * gc1;
           g_rgb[3 * (b + k) + 2] = wk * gc2;
         }
       }
-      const float A0 = __shfl_sync(0xffffffffu, A, 0);
-      const float B0 = __shfl_sync(0xffffffffu, B, 0);
-      carry = A0 * carry + B0;
+      suf.add(__shfl_sync(0xffffffffu, sv, 0));
     }
     for (int k = n + lane; k < N; k += 32) {
       g_raw[b + k] = 0.0f;
@@ -257,8 +254,9 @@ __global__ void __launch_bounds__(256) distortion_bwd_kernel(
 // r (samples b .. b + N, the first n live) given its totals W and WM of w and
 // w m (Kahan): chunks from the last to the first, Kahan-compensated suffix
 // sums W_{>i}, WM_{>i} give g_w_i (W_{<i} = W - W_{>i} - w_i), which enters
-// the reverse affine scan of the colour adjoint directly (g_w is never
-// stored).  One warp; every lane calls it.
+// the colour adjoint's suffix sum S_k = sum_{j>k} g_j w_j + g_T T_end (see
+// composite_bwd_kernel) directly (g_w is never stored).  One warp; every
+// lane calls it.
 __device__ __forceinline__ void composite_distortion_bwd_ray(
     int lane, int64_t b, int n, int N, float gc0, float gc1, float gc2, float Wt, float WMt, float g_L,
     const float* __restrict__ w, const float* __restrict__ raw, const float* __restrict__ T,
@@ -266,7 +264,8 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
     float shift, float interval, float bg0, float bg1, float bg2, float* __restrict__ g_raw) {
   const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
   Kahan sW, sWM;                                     // sums over the chunks after the current one
-  float carry = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;   // R_{n-1} = g_T
+  Kahan suf;                                         // sum_{j in later chunks} g_j w_j + g_T T_end
+  const float gT = bg0 * gc0 + bg1 * gc1 + bg2 * gc2;
   const int last_chunk = n > 0 ? ((n - 1) & ~31) : -32;
   for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
     const int k = c0 + lane;
@@ -281,7 +280,10 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
       rk = __ldg(raw + s);
       Tk = __ldg(T + s);
       c_rgb = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
+      la = -interval * softplus_f(rk + shift);
     }
+    const float Tk1 = Tk * expf(la);
+    if (c0 == last_chunk) suf.add(gT * __shfl_sync(0xffffffffu, Tk1, (n - 1) & 31));   // T_end
     // inclusive suffix sums within the chunk (lane .. 31)
     float sw = wi, swm = wi * mi;
 #pragma unroll
@@ -298,37 +300,19 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
     const float Wlt = Wt - Wgt - wi;
     const float WMlt = WMt - WMgt - wi * mi;
     const float gw = g_L * (2.0f * (mi * (Wlt - Wgt) - WMlt + WMgt) + (2.0f / 3.0f) * wi * di);
-    float A = 1.0f, B = 0.0f, gk = 0.0f;
-    if (valid) {
-      la = -interval * softplus_f(rk + shift);
-      const float al = -expm1f(la);
-      gk = c_rgb + gw;
-      A = 1.0f - al;
-      B = gk * al;
-    }
+    const float gk = valid ? c_rgb + gw : 0.0f;
+    const float v = gk * wi;
+    float sv = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const float A2 = __shfl_down_sync(0xffffffffu, A, o);
-      const float B2 = __shfl_down_sync(0xffffffffu, B, o);
-      if (lane + o < 32) {
-        B = A * B2 + B;
-        A = A * A2;
-      }
+      const float a = __shfl_down_sync(0xffffffffu, sv, o);
+      if (lane + o < 32) sv += a;
     }
-    float An = __shfl_down_sync(0xffffffffu, A, 1);
-    float Bn = __shfl_down_sync(0xffffffffu, B, 1);
-    if (lane == 31) {
-      An = 1.0f;
-      Bn = 0.0f;
-    }
-    const float Rk = An * carry + Bn;
-    if (valid) {
-      const float Tk1 = Tk * expf(la);
-      g_raw[b + k] = interval * sigmoid_f(rk + shift) * Tk1 * (gk - Rk);
-    }
-    const float A0 = __shfl_sync(0xffffffffu, A, 0);
-    const float B0 = __shfl_sync(0xffffffffu, B, 0);
-    carry = A0 * carry + B0;
+    float ex = __shfl_down_sync(0xffffffffu, sv, 1);
+    if (lane == 31) ex = 0.0f;
+    const float Sk = __fadd_rn(suf.s, __fsub_rn(ex, suf.c));
+    if (valid) g_raw[b + k] = interval * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
+    suf.add(__shfl_sync(0xffffffffu, sv, 0));
     sW.add(__shfl_sync(0xffffffffu, sw, 0));
     sWM.add(__shfl_sync(0xffffffffu, swm, 0));
   }
