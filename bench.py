@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BF16 / learned-proposal comparison")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the second workload (unbounded_320) of the default run")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step's kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--profile-only", action="store_true",
@@ -231,90 +233,105 @@ def reduce_over_ranks(total_ms, e2e_ms, samples, device):
     return float(t[0]), float(t[1]), float(s[0])
 
 
-def run_ours(args, rank, world):
+def prepare(workload, mlp, rank, n_batches):
+    """Trainer of a workload and its ray batches resident in HBM (seed =
+    1000 * rank + batch), with the sample and live-sample count of each batch
+    (deterministic: the occupancy mask is fixed).  The trainer is re-created
+    after the counting passes, so the optimizer starts clean."""
     import torch
-    from paper_2206_05085_gb300 import build as B
     from paper_2206_05085_gb300 import synth, train
-    B.build()
-    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
-    cfg = synth.CONFIGS[args.workload]
+    cfg = synth.CONFIGS[workload]
     rp = synth.render_params(cfg)
-    prec = precision_of(args.workload, args.mlp)
+    prec = precision_of(workload, mlp)
     D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
     tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
-    nb = args.warmup + args.steps
-    # distinct ray batches per step, resident in HBM (seed = 1000*rank + step)
     batches, host_batches = [], []
-    for i in range(min(nb, 8)):
+    for i in range(min(n_batches, 8)):
         seed = 1000 * rank + i
         o, d = synth.rays(cfg, seed=seed)
         t = synth.target_rgb(cfg, seed=seed)
         host_batches.append((o, d, t))
         batches.append(tuple(torch.from_numpy(a).cuda() for a in (o, d, t)))
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    # samples per batch (deterministic: the mask is fixed)
-    S_of = []
+    S_of, SL_of = [], []
     for o, d, t in batches:
         tr.forward(o, d, t)
         torch.cuda.synchronize()
         S_of.append(int(tr.ray_off[-1].item()))
-    # restore a clean optimizer state after the sample-count passes
+        SL_of.append(int(tr.live_count.item()))
+    del tr
     tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
+    return dict(tr=tr, batches=batches, host_batches=host_batches, S_of=S_of, SL_of=SL_of, cfg=cfg,
+                rp=rp, prec=prec)
 
-    for i in range(args.warmup):
-        o, d, t = batches[i % len(batches)]
-        tr.step(o, d, t, tv_dense=args.tv_dense)
+
+def timed_steps(w, steps, warmup, flush, tv_dense, graph=True, clocks=None, world=1):
+    """warmup untimed steps, then `steps` steps each bracketed by CUDA events
+    on the launching stream (L2 flushed before each, outside the events).
+    With graph, the step is one CUDA graph replay; each replay first copies
+    its batch into the graph's input buffers (inside the events)."""
+    import torch
+    tr, batches, S_of, SL_of = w["tr"], w["batches"], w["S_of"], w["SL_of"]
+    stream = torch.cuda.current_stream()
+    for i in range(warmup):
+        tr.step(*batches[i % len(batches)], tv_dense=tv_dense)
     torch.cuda.synchronize()
-    if args.profile_only:
-        for i in range(args.steps):
-            o, d, t = batches[i % len(batches)]
-            tr.step(o, d, t, tv_dense=args.tv_dense)
-        torch.cuda.synchronize()
-        return None
-
-    # The step as one CUDA graph over fixed input buffers (each timed step
-    # copies its batch into them, device to device, inside the timed region);
-    # --no-graph launches the kernels one by one.
-    graph, g_in = None, None
-    if not args.no_graph:
-        graph, g_in = tr.capture(*batches[0], tv_dense=args.tv_dense)
+    g, g_in = None, None
+    if graph:
+        g, g_in = tr.capture(*batches[0], tv_dense=tv_dense)
         torch.cuda.synchronize()
 
     def one_step(o, d, t):
-        if graph is None:
-            return tr.step(o, d, t, tv_dense=args.tv_dense)
+        if g is None:
+            return tr.step(o, d, t, tv_dense=tv_dense)
         for dst, src in zip(g_in, (o, d, t)):
             dst.copy_(src, non_blocking=True)
-        graph.replay()
+        g.replay()
         return tr.loss
 
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
         time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ev = []
-    samples = 0
-    for i in range(args.steps):
+    ev, samples, live = [], 0, 0
+    for i in range(steps):
         flush.zero_()
-        b = (args.warmup + i) % len(batches)
-        o, d, t = batches[b]
+        b = (warmup + i) % len(batches)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one_step(o, d, t)
+        one_step(*batches[b])
         e1.record(stream)
         ev.append((e0, e1))
         samples += S_of[b]
+        live += SL_of[b]
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return dict(total_ms=total_ms, samples=samples, live=live, graph=g, g_in=g_in)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2206_05085_gb300 import _lib as L
+    from paper_2206_05085_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    w = prepare(args.workload, args.mlp, rank, args.warmup + args.steps)
+    tr, batches, host_batches = w["tr"], w["batches"], w["host_batches"]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    if args.profile_only:
+        for i in range(args.warmup + args.steps):
+            tr.step(*batches[i % len(batches)], tv_dense=args.tv_dense)
+        torch.cuda.synchronize()
+        return None
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    tm = timed_steps(w, args.steps, args.warmup, flush, args.tv_dense, graph=not args.no_graph,
+                     clocks=clocks, world=world)
+    graph, g_in = tm["graph"], tm["g_in"]
 
     # end-to-end through the public API with host buffers: pinned H2D of the
     # step's rays and targets, D2H of the loss, inside the timed region
@@ -342,35 +359,68 @@ def run_ours(args, rank, world):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     clock_info = clocks.stop() if clocks else None
+    # device status word of the kernels with range checks and bounded waits,
+    # read once after all timed steps (this call synchronises)
+    status = L.device_status()
 
     calls = per_kernel_times(tr, batches[:1], flush, reps=5)
     l2_gbs = l2_read_gbs()
     kt = by_entry_point(calls)
     counts = kernel_flops_bytes(tr)
     S, S_live = counts["S"], counts["S_live"]
-    total_ms, e2e_total, samples = reduce_over_ranks(total_ms, sum(e2e_ms), samples, "cuda")
-    return dict(total_ms=total_ms, steps=args.steps, l2_gbs=l2_gbs, samples=samples, e2e_total_ms=e2e_total,
-                e2e_samples=samples, kt=kt, calls=calls, counts=counts, clocks=clock_info, S=S,
-                S_live=S_live, h2d=h2d_bytes, cfg=cfg, rp=rp, prec=prec, tr=tr)
+    total_ms, e2e_total, samples = reduce_over_ranks(tm["total_ms"], sum(e2e_ms), tm["samples"], "cuda")
+    _, _, live = reduce_over_ranks(tm["total_ms"], 0.0, tm["live"], "cuda")
+    return dict(total_ms=total_ms, steps=args.steps, l2_gbs=l2_gbs, samples=samples, live=live,
+                e2e_total_ms=e2e_total, e2e_samples=samples, kt=kt, calls=calls, counts=counts,
+                clocks=clock_info, S=S, S_live=S_live, h2d=h2d_bytes, cfg=w["cfg"], rp=w["rp"],
+                prec=w["prec"], tr=tr, status=status)
+
+
+def run_secondary(workload, mlp, steps=20, warmup=3):
+    """A second workload in the same run (one GPU, rank 0): the same timed
+    loop (CUDA graph replays, L2 flushed before each step), its per-call
+    times and the memory-kernel record of its counts."""
+    import torch
+    from paper_2206_05085_gb300 import _lib as L
+    w = prepare(workload, mlp, 0, warmup + steps)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    tm = timed_steps(w, steps, warmup, flush, False)
+    status = L.device_status()
+    tr = w["tr"]
+    calls = per_kernel_times(tr, w["batches"][:1], flush, reps=3)
+    counts = kernel_flops_bytes(tr)
+    res = dict(total_ms=tm["total_ms"], steps=steps, samples=tm["samples"], live=tm["live"],
+               kt=by_entry_point(calls), calls=calls, counts=counts, S=counts["S"],
+               S_live=counts["S_live"], prec=w["prec"], cfg=w["cfg"], status=status)
+    del w, tr
+    torch.cuda.empty_cache()
+    return res
 
 
 # Algorithmic work per unit of each kernel (the roofline numerators).
 # Colour MLP, per live sample: forward 2*(39*128 + 128*128 + 128*3) FLOP; backward
-# (activations stored by the forward, nothing recomputed) g_z2 + dW3 (2*3*128 each),
-# dW2 and g_h1 (128*128 each), dW1 (128*40), g_k0 (128*12), all x2.
+# twice the forward (the two products of every layer: the input gradient and the
+# weight gradient), 87,040 FLOP.  What a kernel recomputes (the tensor-core
+# backward takes layer 2 again from the stored layer inputs) is not counted.
 MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)
-MLP_BWD_FLOP = 2 * (2 * 3 * 128 + 2 * 128 * 128 + 128 * 40 + 128 * 12)
-# The BF16 backward recomputes the forward on the tensor cores; the split-FP16
-# (FP32-accurate) backward recomputes the second layer only.
-MLP_BWD_FLOP_RECOMPUTE = MLP_BWD_FLOP + 2 * (39 * 128 + 128 * 128)
-MLP_BWD_FLOP_TC = MLP_BWD_FLOP + 2 * 128 * 128
-# kernels launched per C-ABI call (others launch one); the FP32 tensor-core MLP
+MLP_BWD_FLOP = 2 * MLP_FWD_FLOP
+# Tensor-core MMAs issued per algorithmic product: the FP32 form splits every
+# operand into two FP16 terms (hi*hi + hi*lo + lo*hi: 3); the BF16 form keeps
+# weights as one term (products with a weight matrix: 2) and splits both
+# operands of a weight gradient (3).  The inverse is the fraction of the tensor
+# peak a kernel can reach in algorithmic FLOP/s.
+MMA_CEILING = {("f32tc", "fwd"): 1 / 3, ("f32tc", "bwd"): 1 / 3, ("bf16", "fwd"): 1 / 2,
+               # backward: dW2 (3) and g_h1 (2) of 128x128, dW1 (3) of 128x40, g_k0 (2) of 128x12
+               ("bf16", "bwd"): (2 * 16384 + 5120 + 1536) / (5 * 16384 + 3 * 5120 + 2 * 1536)}
+# kernels launched per C-ABI call (others launch one); the tensor-core MLP
 # backward runs the backward and the partial-gradient reduction
 KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1}
 
 
 def roofline(res, peaks):
-    """Roofline record of the dominant kernel (largest share of the step)."""
+    """Roofline record of the dominant kernel (largest share of the step).
+    The kernel is timed per call, alone on the stream: the burst tensor peak
+    is its denominator."""
     kt = res["kt"]
     name, rec = max(kt.items(), key=lambda kv: kv[1]["ms_per_step"])
     S_live, prec = res["S_live"], res["prec"]
@@ -378,19 +428,18 @@ def roofline(res, peaks):
     fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12   # FP32 FMA TFLOP/s at the maximum SM clock
     out = {"kernel": name}
     if name in ("dvgo_rgbnet_bwd", "dvgo_rgbnet_fwd"):
-        if name.endswith("fwd"):
-            per = MLP_FWD_FLOP
-        else:
-            per = {"bf16": MLP_BWD_FLOP_RECOMPUTE, "f32tc": MLP_BWD_FLOP_TC}.get(prec, MLP_BWD_FLOP)
+        way = "fwd" if name.endswith("fwd") else "bwd"
+        per = MLP_FWD_FLOP if way == "fwd" else MLP_BWD_FLOP
         flop = per * S_live
         achieved = flop / (ms * 1e-3) / 1e12
-        if prec == "bf16":
-            bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
-            peak_src = "bf16_tflops_sustained of measured"
-        elif prec == "f32tc":
-            bound, peak, unit = "tensor", peaks.get("bf16_tflops_sustained", 1781.4), "TFLOP/s"
-            peak_src = ("bf16_tflops_sustained of measured (FP16 runs at the BF16 rate); each "
-                        "algorithmic product takes three FP16 MMAs, so 1/3 of it is the ceiling")
+        if prec in ("bf16", "f32tc"):
+            bound, unit = "tensor", "TFLOP/s"
+            peak = peaks.get("bf16_tflops", 1963.5)
+            peak_src = ("bf16_tflops of measured (burst; FP16 runs at the BF16 rate)" if "bf16_tflops" in peaks
+                        else "1.9 PFLOP/s bf16 burst (fallback)")
+            ceil = MMA_CEILING[(prec, way)]
+            out["mma_ceiling_frac"] = round(ceil, 4)
+            out["frac_of_mma_ceiling"] = round(achieved / (peak * ceil), 4)
         else:
             bound, peak, unit = "alu", round(fp32_peak, 2), "TFLOP/s"
             peak_src = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"
@@ -525,20 +574,30 @@ def traffic_for(name, prec, units):
         return None
 
 
+def fine_params(rp, factor=4):
+    """Render parameters of a converged reference render: the same sampler
+    with a step `factor` times finer (and the alpha interval scaled with it,
+    so the density integral is unchanged)."""
+    import dataclasses
+    return dataclasses.replace(rp, step=float(np.float32(rp.step / factor)),
+                               max_steps=rp.max_steps * factor,
+                               interval=float(np.float32(rp.interval / factor)))
+
+
 def forms_report(args):
     """The BF16 and learned-proposal forms against the plain FP32 form on the
-    same rays: PSNR of each render against the target and against the plain
-    render, and the iteration time of each (CUDA events, mean of 10 steps)."""
+    same rays.  The ground truth of the synthetic scene is its converged
+    render: the plain FP32 renderer with a 4x finer step.  Reported: PSNR of
+    each render against that ground truth and against the plain render, the
+    gap between a form's PSNR and the plain form's (the <= 0.1 dB criterion),
+    and the iteration time of each (CUDA events, mean of 10 steps)."""
     import torch
     from paper_2206_05085_gb300 import proposal, synth, train
+    psnr = proposal.psnr
     out = {}
-    # BF16 vs FP32 on the dvgo_160 scene
     cfg = synth.CFG2
     rp = synth.render_params(cfg)
     D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
-    o, d = synth.rays(cfg, seed=11)
-    t = synth.target_rgb(cfg, seed=11)
-    to, td, tt = (torch.from_numpy(a).cuda() for a in (o, d, t))
     st = torch.cuda.current_stream()
 
     def timed(fn, n=10):
@@ -555,20 +614,42 @@ def forms_report(args):
         torch.cuda.synchronize()
         return sum(x.elapsed_time(y) for x, y in ev) / n
 
-    colors, ms = {}, {}
+    def render(cfg_, rp_, prec, o, d, t, R):
+        tr = train.Trainer(cfg_, rp_, D, Fg, P, n_rays=R, precision=prec)
+        tr.forward(o, d, t)
+        c = tr.color.clone()
+        del tr
+        torch.cuda.empty_cache()
+        return c
+
+    # BF16 vs FP32 on the dvgo_160 scene: timing at the workload's 8192 rays
+    o, d = synth.rays(cfg, seed=11)
+    t = synth.target_rgb(cfg, seed=11)
+    to, td, tt = (torch.from_numpy(a).cuda() for a in (o, d, t))
+    ms = {}
     for prec in ("f32", "f32tc", "bf16"):
         tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision=prec)
-        tr.forward(to, td, tt)
-        colors[prec] = tr.color.clone()
         ms[prec] = timed(lambda: tr.step(to, td, tt))
         del tr
+    torch.cuda.empty_cache()
+    # quality on 4096 of those rays
+    Rq = 4096
+    qo, qd, qt = to[:Rq].contiguous(), td[:Rq].contiguous(), tt[:Rq].contiguous()
+    colors = {prec: render(cfg, rp, prec, qo, qd, qt, Rq) for prec in ("f32", "f32tc", "bf16")}
+    gt = render(cfg, fine_params(rp), "f32tc", qo, qd, qt, Rq)
+    out["ground_truth"] = ("the plain FP32 render with a 4x finer step (converged render of the "
+                           "synthetic scene), 4096 rays")
     out["fp32_mlp_on_cuda_cores"] = {
-        "psnr_vs_tensor_core_fp32_render_db": round(proposal.psnr(colors["f32"], colors["f32tc"]), 2),
+        "psnr_vs_tensor_core_fp32_render_db": round(psnr(colors["f32"], colors["f32tc"]), 2),
         "ms_per_step_cuda_cores": round(ms["f32"], 3), "ms_per_step_tensor_cores": round(ms["f32tc"], 3)}
-    out["bf16"] = {"psnr_vs_fp32_render_db": round(proposal.psnr(colors["bf16"], colors["f32"]), 2),
-                   "psnr_gap_vs_target_db": round(abs(proposal.psnr(colors["bf16"], tt) -
-                                                      proposal.psnr(colors["f32"], tt)), 4),
-                   "ms_per_step_8192_rays": round(ms["bf16"], 3)}
+    p_plain = psnr(colors["f32tc"], gt)
+    p_bf = psnr(colors["bf16"], gt)
+    out["bf16"] = {"psnr_vs_fp32_render_db": round(psnr(colors["bf16"], colors["f32tc"]), 2),
+                   "psnr_vs_ground_truth_db": round(p_bf, 3),
+                   "fp32_psnr_vs_ground_truth_db": round(p_plain, 3),
+                   "psnr_gap_db": round(abs(p_bf - p_plain), 4),
+                   "ms_per_step_8192_rays": round(ms["bf16"], 3),
+                   "fp32_ms_per_step_8192_rays": round(ms["f32tc"], 3)}
     # learned proposal vs dense candidates (<= 512 / ray), 16384 rays
     cfg5 = synth.CFG5
     R = cfg5.n_rays
@@ -598,12 +679,78 @@ def forms_report(args):
         prop.select_into(prop_tr, to5, td5)
         prop_tr.step(to5, td5, tt5, sample=False)
     ms_prop = timed(prop_step)
+    rp_c = proposal.candidate_params(cfg5, rp)
+    del dense, prop_tr
+    torch.cuda.empty_cache()
+    # ground truth: the dense candidates 4x finer, on 4096 of the rays
+    gt5 = render(cfg5, fine_params(rp_c), args.mlp, to5[:Rq].contiguous(), td5[:Rq].contiguous(),
+                 tt5[:Rq].contiguous(), Rq)
+    pd, pp = psnr(c_dense[:Rq], gt5), psnr(c_prop[:Rq], gt5)
     out["proposal"] = {
         "rays": R, "samples_dense": s_dense, "samples_proposal": s_prop,
-        "psnr_vs_dense_render_db": round(proposal.psnr(c_prop, c_dense), 2),
-        "psnr_gap_vs_target_db": round(abs(proposal.psnr(c_prop, tt5) - proposal.psnr(c_dense, tt5)), 4),
+        "psnr_vs_dense_render_db": round(psnr(c_prop, c_dense), 2),
+        "psnr_vs_ground_truth_db": round(pp, 3), "dense_psnr_vs_ground_truth_db": round(pd, 3),
+        "psnr_gap_db": round(abs(pp - pd), 4),
         "ms_per_step_dense": round(ms_dense, 3), "ms_per_step_proposal": round(ms_prop, 3),
         "proposal_training": f"400 steps x {R} rays on the plain renderer's weights, {train_s:.1f} s"}
+    return out
+
+
+def oracle_errors(mlp):
+    """Second product of the oracle leg: on the first rays of each form's
+    workload, the relative error (max|x - ref| / max|ref| per tensor) of every
+    output and gradient of one GPU training step, and of the parameters after
+    its TV + Adam update, against the same step composed from the FP64 oracle;
+    for the learned proposal, its network's output and parameter gradients."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from conftest import rel_err
+    from paper_2206_05085_gb300 import _lib as L
+    from paper_2206_05085_gb300 import synth
+    from step_parity import error_table, gpu_step, mlp_grad_errors, oracle_step
+    oracle.build()
+    out = {"definition": "max|gpu - oracle| / max|oracle| per tensor; FP64 oracle on the same rays"}
+    n = 64
+    for form, workload, prec, tau, tol in (("fp32", "dvgo_160", mlp, 1e-6, 1e-5),
+                                           ("bf16", "dvgo_160_bf16", "bf16", 1e-5, 2e-3)):
+        cfg = synth.CONFIGS[workload]
+        rp = synth.render_params(cfg)
+        D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+        o, d = synth.rays(cfg, seed=0)
+        t = synth.target_rgb(cfg, seed=0)
+        o, d, t = o[:n], d[:n], t[:n]
+        gpu = gpu_step(cfg, rp, D, Fg, P, o, d, t, prec, False)
+        fb, opt, Pr = oracle_step(cfg, rp, D, Fg, P, o, d, t, prec, False)
+        e = error_table(gpu, fb, opt, cfg, rp, Pr, tau)
+        rec = {k: (float(f"{v:.3g}") if isinstance(v, float) else v) for k, v in e.items()}
+        rec.update(workload=workload, rays=n, tolerance=tol, relu_tau=tau,
+                   max_error=float(f"{max(v for k, v in e.items() if isinstance(v, float) and not k.endswith(('max_step', '_raw'))):.3g}"))
+        out[form] = rec
+        del gpu, fb, opt
+        torch.cuda.empty_cache()
+    # learned proposal network (BF16 form) on 8192 points of the bbox
+    rng = np.random.default_rng(31)
+    m = 8192
+    xyz = rng.uniform(-1, 1, (m, 3)).astype(np.float32)
+    pp = synth.proposal_params()
+    pr = synth.bf16_round(pp)
+    g = rng.normal(size=m).astype(np.float32)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    lg = torch.empty(m, device="cuda")
+    L.proposal_fwd(dv(xyz), None, m, None, dv(pp), lg)
+    gpp = torch.zeros(pp.size, device="cuda")
+    L.proposal_bwd(dv(g), dv(xyz), None, m, None, dv(pp), gpp)
+    x = oracle.freq_encode(xyz, 6)
+    ref = oracle.mlp_fwd(synth.PROPOSAL_DIMS, pr, x, False)[:, 0]
+    got, ggot = lg.cpu().numpy(), gpp.cpu().numpy()
+    prop = {"points": m, "tolerance": 2e-3, "relu_tau": 2e-5, "logits": float(f"{rel_err(got, ref):.3g}")}
+    raw, adj, n_amb = mlp_grad_errors(synth.PROPOSAL_DIMS, pr, x, g[:, None], ggot, 2e-5, out_sigmoid=False)
+    for nm in raw:
+        prop["g_" + nm] = float(f"{adj[nm]:.3g}")
+        prop["g_" + nm + "_raw"] = float(f"{raw[nm]:.3g}")
+    prop["relu_ambiguous_points"] = n_amb
+    out["proposal_network"] = prop
     return out
 
 
@@ -729,23 +876,48 @@ def main():
                    "mlp": "39-128-128-3",
                    "mlp_precision": {"f32tc": "FP32 accuracy on tcgen05 (split-FP16 operands)",
                                      "f32": "FP32 on the CUDA cores",
-                                     "bf16": "BF16 on tcgen05"}[res["prec"]],
+                                     "bf16": "BF16 on tcgen05 (stored BF16 weights, two-term "
+                                             "BF16 activations and gradients)"}[res["prec"]],
                    "tv_dense": bool(args.tv_dense), "l2": "flushed (256 MB memset) before each timed step",
                    "launch": "one CUDA graph per step" if not args.no_graph else "eager kernel launches",
                    "parallelism": "replicas" if args.gpus > 1 else "single"},
         "e2e": {"value": round(e2e, 1), "unit": "ray-samples/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": 12},
+        # samples in front of each ray's halt: the ones the feature query, the
+        # colour MLP and the grid adjoints process
+        "live_samples_per_s": round(res["live"] / (res["total_ms"] * 1e-3), 1),
+        "device_status": res["status"],
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline(res, peaks),
         "memory_kernels": memory_kernels(res, peaks),
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in res["kt"].items()},
         "clocks": res["clocks"],
     }
+    if not args.no_secondary and world == 1 and args.workload != "unbounded_320":
+        # the 320^3 contracted workload: grids far larger than L2 (1.57 GB per
+        # FP32 feature array), the HBM-bound case of the memory kernels
+        sec = run_secondary("unbounded_320", args.mlp)
+        sec["l2_gbs"] = res["l2_gbs"]
+        line["unbounded_320"] = {
+            "value": round(sec["samples"] / (sec["total_ms"] * 1e-3), 1), "unit": "ray-samples/s",
+            "live_samples_per_s": round(sec["live"] / (sec["total_ms"] * 1e-3), 1),
+            "ms_per_step": round(sec["total_ms"] / sec["steps"], 4), "steps": sec["steps"], "warmup": 3,
+            "samples_per_step": sec["S"], "live_samples_per_step": sec["S_live"],
+            "device_status": sec["status"],
+            "roofline": roofline(sec, peaks), "memory_kernels": memory_kernels(sec, peaks),
+            "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in sec["kt"].items()}}
     if not args.no_forms and world == 1:
         line["forms"] = forms_report(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
+        line["errors_vs_oracle"] = oracle_errors(args.mlp)
+    bad = [v for v in (line["device_status"], line.get("unbounded_320", {}).get("device_status", 0)) if v]
+    if bad:
+        # a kernel reported a range or wait failure: the numbers above are not valid
+        line["error"] = f"device status {bad[0]} after the timed steps"
+        print(json.dumps(line))
+        sys.exit(1)
     print(json.dumps(line))
 
 
