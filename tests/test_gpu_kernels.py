@@ -214,6 +214,43 @@ def test_trilinear_adjoint_pair_along_rays(L):
         assert np.all(host(touched).reshape(nbv[2], nbv[1], nbv[0]).astype(bool)[tb])
 
 
+@pytest.mark.parametrize("bf16", [False, True])
+def test_trilinear_fwd_along_rays(L, bf16):
+    """The feature query on ray-ordered samples: neighbouring list positions
+    often share a cell (runs of up to ten at 0.1-voxel steps) and then share
+    one set of corner loads; against the oracle, with a list count that
+    leaves a partial last warp."""
+    rng = np.random.default_rng(46)
+    G = (40, 33, 37)
+    lo, hi = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0])
+    vs = 2.0 / 32
+    pts = []
+    for r in range(700):
+        o = rng.uniform(-0.9, 0.9, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        k = int(rng.choice([1, 2, 3, 33, 90]))
+        step = vs * rng.choice([0.1, 0.25, 0.5, 1.0])
+        pts.append(np.clip(o + d * step * np.arange(k)[:, None], -1.05, 1.05))
+    xyz = np.concatenate(pts).astype(np.float32)
+    n = len(xyz)
+    live = np.sort(rng.choice(n, int(0.9 * n), replace=False)).astype(np.int32)
+    m = len(live) - 13
+    dense = rng.normal(size=(G[2], G[1], G[0], 12)).astype(np.float32)
+    if bf16:
+        dense = synth.bf16_round(dense)
+    gd = L.GridDesc.make(lo, hi, G)
+    grid = _bricked(L, dense, G, 12, torch.bfloat16 if bf16 else torch.float32)
+    out = torch.full((n, 12), -7.0, device="cuda")
+    n_dev = torch.tensor([m], dtype=torch.int64, device="cuda")
+    L.sample_grid_fwd(grid, L.BF16 if bf16 else L.F32, gd, 12, dev(xyz), dev(live), n, n_dev, out)
+    got = host(out)
+    ref = oracle.trilinear(dense, lo, hi, xyz[live[:m]])
+    assert rel_err(got[live[:m]], ref) < TOL32
+    rest = np.setdiff1d(np.arange(n), live[:m])
+    assert np.all(got[rest] == -7.0)
+
+
 def test_trilinear_adjoint_pair(L):
     """The paired density / feature adjoint equals the two single ones."""
     rng = np.random.default_rng(44)
