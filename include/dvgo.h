@@ -110,11 +110,33 @@ int dvgo_grid_pack(const void* dense, void* bricked, const int32_t G[3], int32_t
 int dvgo_grid_unpack(const void* bricked, void* dense, const int32_t G[3], int32_t C, int dtype,
                      void* stream);
 
+/* Progressive grid scaling (Sec. 5.4, the grid-scaling schedule): the
+ * bricked FP32 grid src (G_src points per axis, C channels) trilinearly
+ * resampled to G_dst points per axis over the same box (corner-aligned
+ * grids: destination point x of axis a sits at source index x (G_src - 1) /
+ * (G_dst - 1)).  dst is bricked, dtype F32 or BF16 (rounded to nearest; the
+ * renderer's copy of a BF16-stored grid).  Any G >= 2 on both sides
+ * (down-sampling too).  Applied by the caller to each grid and to its Adam
+ * moments when the schedule raises the resolution. */
+int dvgo_grid_resample(const float* src, const int32_t G_src[3], void* dst, int dst_dtype,
+                       const int32_t G_dst[3], int32_t C, void* stream);
+
 /* Occupancy mask (Sec. 1): mask[v] = alpha(density[v]) >= alpha_thres with
  * alpha = 1 - exp(-interval softplus(raw + shift)).  density is bricked
  * (dtype F32 or BF16); mask is dense uint8 [Gz][Gy][Gx]. */
 int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_desc* grid, float shift,
                     float interval, float alpha_thres, uint8_t* mask, void* stream);
+
+/* Progressive occupancy-mask update (Sec. 1: the mask is updated as training
+ * goes, deactivating space whose density has become low): mask[v] =
+ * alpha(density[v]) >= alpha_thres, as dvgo_build_mask decides it, re-evaluated
+ * for the grid points of the listed bricks only (brick_list int32 [*brick_count],
+ * both device; both NULL = every brick).  Given the bricks an optimizer step
+ * changed (the compacted touched list of dvgo_touched_compact), it keeps the
+ * mask equal to dvgo_build_mask of the current density. */
+int dvgo_update_mask(const void* density, int dtype, const dvgo_grid_desc* grid, float shift, float interval,
+                     float alpha_thres, const int32_t* brick_list, const int32_t* brick_count, uint8_t* mask,
+                     void* stream);
 
 /* Trilinear query (Sec. 1, "constant time" grid query) of a bricked grid
  * with C channels at points xyz[n][3] (f32).  u_a = (x_a - lo_a) (G_a - 1) /
@@ -188,6 +210,19 @@ int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d, int64_t R
  * *live_count their number.  live_idx: int32 [capacity ray_off total].
  * ws: dvgo_live_samples_workspace_size(R) bytes. */
 size_t dvgo_live_samples_workspace_size(int64_t R);
+
+/* The colour-query list with low-weight samples skipped (a variant; DVGO's
+ * implementations skip colour queries of points with negligible compositing
+ * weight): the first seg_len[r] samples of every ray whose weight w[s] >=
+ * w_min, in ray order, and *live_count their number.  The rows of the skipped
+ * samples (before the halt, w < w_min) are set to zero in rgb [S][3] and g_k0
+ * [S][12] (each may be NULL; g_k0 16-byte aligned): their colour contributes
+ * nothing to the render and their features receive no gradient, so the
+ * compositing, its adjoint and the grid adjoints can keep using the full
+ * live list.  ws: dvgo_live_samples_workspace_size(R) bytes. */
+int dvgo_live_samples_cull(const int64_t* ray_off, const int32_t* seg_len, const float* w, float w_min,
+                           int64_t R, int32_t* live_idx, int64_t* live_count, float* rgb, float* g_k0,
+                           void* ws, size_t ws_bytes, void* stream);
 int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len, int64_t R,
                       int32_t* live_idx, int64_t* live_count, void* ws, size_t ws_bytes,
                       void* stream);

@@ -95,6 +95,7 @@ def _declare(L):
         getattr(L, nm).argtypes = [P, P, P, P, P, I64, P]
     for nm in ("or_distortion_grad", "or_distortion_grad_naive"):
         getattr(L, nm).argtypes = [P, P, P, P, P, P, I64, P]
+    L.or_grid_resample.argtypes = [P, P, INT, P, P]
     L.or_mlp_fwd.argtypes = [P, INT, P, P, I64, INT, P]
     L.or_mlp_bwd.argtypes = [P, INT, P, P, I64, INT, P, P, P]
     L.or_mlp_min_abs_preact.argtypes = [P, INT, P, P, I64, P]
@@ -224,6 +225,21 @@ def trilinear(grid, lo, hi, xyz):
     lib().or_trilinear(_p(grid), _p(G), C, _p(_vec3f(lo)), _p(_vec3f(hi)), _p(xyz),
                        xyz.shape[0], _p(out))
     return out
+
+
+def grid_resample(grid, G_dst):
+    """grid: dense [Gz, Gy, Gx] or [Gz, Gy, Gx, C] f32; G_dst (x, y, z).
+    Returns the trilinear resampling to G_dst points per axis (FP64)."""
+    g = _f32(grid)
+    squeeze = g.ndim == 3
+    if squeeze:
+        g = g[..., None]
+    Gs = _vec3i((g.shape[2], g.shape[1], g.shape[0]))
+    Gd = _vec3i(G_dst)
+    C = g.shape[3]
+    out = np.zeros((int(Gd[2]), int(Gd[1]), int(Gd[0]), C))
+    lib().or_grid_resample(_p(g), _p(Gs), C, _p(Gd), _p(out))
+    return out[..., 0] if squeeze else out
 
 
 def trilinear_adjoint(g_out, grid_shape, lo, hi, xyz):

@@ -318,6 +318,38 @@ OR_API void or_trilinear(const float* grid, const int32_t G[3], int C, const flo
   }
 }
 
+/* Progressive grid scaling (Sec. 5.4, grid-scaling schedule): the dense    */
+/* grid src (Gs points per axis, C channels) resampled to Gd points per axis */
+/* over the same box by trilinear interpolation of corner-aligned grids:     */
+/* destination point x of axis a sits at source index u = x (Gs-1)/(Gd-1).   */
+OR_API void or_grid_resample(const float* src, const int32_t Gs[3], int C, const int32_t Gd[3],
+                             double* dst) {
+  for (int64_t z = 0; z < Gd[2]; ++z)
+    for (int64_t y = 0; y < Gd[1]; ++y)
+      for (int64_t x = 0; x < Gd[0]; ++x) {
+        const int64_t p[3] = {x, y, z};
+        int64_t i0[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+          double u = (double)p[a] * (double)(Gs[a] - 1) / (double)(Gd[a] - 1);
+          int64_t i = (int64_t)floor(u);
+          if (i > Gs[a] - 2) i = Gs[a] - 2;
+          if (i < 0) i = 0;
+          i0[a] = i;
+          f[a] = u - (double)i;
+        }
+        double* o = dst + ((z * Gd[1] + y) * Gd[0] + x) * C;
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        for (int dz = 0; dz < 2; ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              double wgt = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+              int64_t v = ((i0[2] + dz) * Gs[1] + (i0[1] + dy)) * Gs[0] + (i0[0] + dx);
+              for (int c = 0; c < C; ++c) o[c] += wgt * (double)src[v * C + c];
+            }
+      }
+}
+
 /* Adjoint of or_trilinear: g_grid += sum_s weights(s) * g_out[s]. */
 OR_API void or_trilinear_adjoint(const double* g_out, const int32_t G[3], int C, const float lo[3],
                                  const float hi[3], const float* xyz, int64_t n, double* g_grid) {

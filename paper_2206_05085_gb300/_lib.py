@@ -125,6 +125,9 @@ def _declare(L):
         "dvgo_compact_samples": ([P, P, I32, P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P], INT),
         "dvgo_sample_rays_noalloc_max_rays": ([], I64),
         "dvgo_sample_rays_noalloc": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P], INT),
+        "dvgo_grid_resample": ([P, P, P, INT, P, I32, P], INT),
+        "dvgo_update_mask": ([P, INT, P, F, F, F, P, P, P, P], INT),
+        "dvgo_live_samples_cull": ([P, P, P, F, I64, P, P, P, P, P, SZ, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -197,6 +200,16 @@ def grid_unpack(bricked, dense, G, C, dtype, stream=None):
     _call("dvgo_grid_unpack", ptr(bricked), ptr(dense), _vec3(G, I32), C, dtype, _stream(stream))
 
 
+def grid_resample(src, G_src, dst, dst_dtype, G_dst, C, stream=None):
+    _call("dvgo_grid_resample", ptr(src), _vec3(G_src, I32), ptr(dst), dst_dtype, _vec3(G_dst, I32), C,
+          _stream(stream))
+
+
+def update_mask(density, dtype, gd, shift, interval, thres, brick_list, brick_count, mask, stream=None):
+    _call("dvgo_update_mask", ptr(density), dtype, ctypes.byref(gd), shift, interval, thres, ptr(brick_list),
+          ptr(brick_count), ptr(mask), _stream(stream))
+
+
 def build_mask(density, dtype, gd, shift, interval, thres, mask, stream=None):
     _call("dvgo_build_mask", ptr(density), dtype, ctypes.byref(gd), shift, interval, thres,
           ptr(mask), _stream(stream))
@@ -245,6 +258,11 @@ def sample_rays_noalloc(rays_o, rays_d, R, gd, sd, mask, S_cap, ray_off, xyz, ra
 
 def live_samples_workspace_size(R):
     return int(lib().dvgo_live_samples_workspace_size(R))
+
+
+def live_samples_cull(ray_off, seg_len, w, w_min, R, live_idx, live_count, rgb, g_k0, ws, stream=None):
+    _call("dvgo_live_samples_cull", ptr(ray_off), ptr(seg_len), ptr(w), w_min, R, ptr(live_idx),
+          ptr(live_count), ptr(rgb), ptr(g_k0), ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
 
 
 def live_samples(ray_off, seg_len, R, live_idx, live_count, ws, stream=None):

@@ -381,6 +381,67 @@ __global__ void pack_kernel(const Tv* __restrict__ dense, Tv* __restrict__ brick
   }
 }
 
+// -------------------------------------------------------------- resample
+// Progressive grid scaling (the grid-scaling schedule of the unbounded
+// experiments, Sec. 5.4): a bricked FP32 grid of Gs points per axis resampled
+// to Gd points per axis over the same box, by trilinear interpolation with
+// corner-aligned grids.  Destination point x of axis a sits at source index
+// u = x (Gs - 1) / (Gd - 1): the integer part and the remainder are exact
+// integer arithmetic, the fraction r / (Gd - 1) one FP32 rounding.  One
+// thread per destination voxel, all channels; dst is FP32 or (a renderer's
+// BF16 copy) BF16, rounded to nearest.
+__device__ __forceinline__ void resample_axis(int x, int gs, int gd, int& i, float& f) {
+  if (gd == 1 || gs == 1) {
+    i = 0;
+    f = 0.0f;
+    return;
+  }
+  const int64_t num = (int64_t)x * (gs - 1);
+  i = (int)(num / (gd - 1));
+  const int64_t r = num % (gd - 1);
+  f = __fdiv_rn((float)r, (float)(gd - 1));
+  if (i >= gs - 1) {   // the last point: the cell below it, fraction 1
+    i = gs - 2;
+    f = 1.0f;
+  }
+}
+
+template <bool kBF16Out>
+__global__ void __launch_bounds__(256) resample_kernel(const float* __restrict__ src, BrickGeom gs,
+                                                       void* __restrict__ dst, BrickGeom gd, int C) {
+  const int64_t nvox = (int64_t)gd.G[0] * gd.G[1] * gd.G[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(v % gd.G[0]), y = (int)((v / gd.G[0]) % gd.G[1]),
+              z = (int)(v / ((int64_t)gd.G[0] * gd.G[1]));
+    int i[3];
+    float f[3];
+    resample_axis(x, gs.G[0], gd.G[0], i[0], f[0]);
+    resample_axis(y, gs.G[1], gd.G[1], i[1], f[1]);
+    resample_axis(z, gs.G[2], gd.G[2], i[2], f[2]);
+    int64_t sl[8];
+    float w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      const int cx = min(i[0] + dx, gs.G[0] - 1), cy = min(i[1] + dy, gs.G[1] - 1),
+                cz = min(i[2] + dz, gs.G[2] - 1);
+      sl[k] = voxel_slot(gs, cx, cy, cz);
+      w[k] = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
+    }
+    const int64_t o = voxel_slot(gd, x, y, z) * C;
+    for (int c = 0; c < C; ++c) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc = fmaf(w[k], __ldg(src + sl[k] * C + c), acc);
+      if (kBF16Out)
+        reinterpret_cast<uint16_t*>(dst)[o + c] = f32_to_bf16_bits(acc);
+      else
+        reinterpret_cast<float*>(dst)[o + c] = acc;
+    }
+  }
+}
+
 // ----------------------------------------------------------------- mask
 __global__ void mask_kernel(const void* __restrict__ density, bool bf16, BrickGeom g, float thr,
                             uint8_t* __restrict__ mask) {
@@ -394,6 +455,30 @@ __global__ void mask_kernel(const void* __restrict__ density, bool bf16, BrickGe
     float raw = bf16 ? bf16_bits_to_f32(reinterpret_cast<const uint16_t*>(density)[slot])
                      : reinterpret_cast<const float*>(density)[slot];
     mask[v] = raw >= thr ? 1 : 0;
+  }
+}
+
+// Progressive mask update: one block of 512 threads per listed brick, thread
+// t on the brick's Morton slot t; padding voxels past the grid are skipped.
+__global__ void __launch_bounds__(512) mask_update_kernel(const void* __restrict__ density, bool bf16,
+                                                          BrickGeom g, float thr,
+                                                          const int32_t* __restrict__ brick_list,
+                                                          const int32_t* __restrict__ brick_count,
+                                                          uint8_t* __restrict__ mask) {
+  const int64_t nb = brick_list ? (int64_t)*brick_count : g.num_bricks();
+  const uint32_t t = threadIdx.x;
+  const int lx = (int)((t & 1u) | ((t >> 2) & 2u) | ((t >> 4) & 4u));
+  const int ly = (int)(((t >> 1) & 1u) | ((t >> 3) & 2u) | ((t >> 5) & 4u));
+  const int lz = (int)(((t >> 2) & 1u) | ((t >> 4) & 2u) | ((t >> 6) & 4u));
+  for (int64_t i = blockIdx.x; i < nb; i += gridDim.x) {
+    const int64_t b = brick_list ? (int64_t)__ldg(brick_list + i) : i;
+    const int x = (int)(b % g.nb[0]) * 8 + lx, y = (int)((b / g.nb[0]) % g.nb[1]) * 8 + ly,
+              z = (int)(b / ((int64_t)g.nb[0] * g.nb[1])) * 8 + lz;
+    if (x >= g.G[0] || y >= g.G[1] || z >= g.G[2]) continue;
+    const int64_t slot = b * kBrickVox + t;
+    const float raw = bf16 ? bf16_bits_to_f32(reinterpret_cast<const uint16_t*>(density)[slot])
+                           : reinterpret_cast<const float*>(density)[slot];
+    mask[((int64_t)z * g.G[1] + y) * g.G[0] + x] = raw >= thr ? 1 : 0;
   }
 }
 
@@ -762,9 +847,50 @@ extern "C" int dvgo_grid_pack(const void* dense, void* bricked, const int32_t G[
   return pack_impl(dense, bricked, G, C, dtype, stream, true);
 }
 
+extern "C" int dvgo_grid_resample(const float* src, const int32_t G_src[3], void* dst, int dst_dtype,
+                                  const int32_t G_dst[3], int32_t C, void* stream) {
+  DVGO_CHECK_ARG(src && dst && G_src && G_dst && C >= 1 && (dst_dtype == DVGO_F32 || dst_dtype == DVGO_BF16));
+  for (int a = 0; a < 3; ++a) DVGO_CHECK_ARG(G_src[a] >= 2 && G_dst[a] >= 2);
+  const BrickGeom gs = make_geom(G_src), gd = make_geom(G_dst);
+  const int64_t nvox = (int64_t)G_dst[0] * G_dst[1] * G_dst[2];
+  const int g = grid_for(nvox, 256, 16);
+  cudaStream_t st = as_stream(stream);
+  if (dst_dtype == DVGO_F32)
+    resample_kernel<false><<<g, 256, 0, st>>>(src, gs, dst, gd, C);
+  else
+    resample_kernel<true><<<g, 256, 0, st>>>(src, gs, dst, gd, C);
+  return launch_status();
+}
+
 extern "C" int dvgo_grid_unpack(const void* bricked, void* dense, const int32_t G[3], int32_t C,
                                 int dtype, void* stream) {
   return pack_impl(bricked, dense, G, C, dtype, stream, false);
+}
+
+// alpha(raw) >= thr  <=>  raw >= log(expm1(-log1p(-thr)/interval)) - shift.
+// The FP32 threshold is the smallest float not below the exact one, so the
+// FP32 comparison decides exactly like the FP64 one.
+static float mask_raw_threshold(float shift, float interval, float alpha_thres) {
+  const double q = -log1p(-(double)alpha_thres) / (double)interval;
+  const double thr64 = log(expm1(q)) - (double)shift;
+  float thr = (float)thr64;
+  if ((double)thr < thr64) thr = nextafterf(thr, INFINITY);
+  return thr;
+}
+
+extern "C" int dvgo_update_mask(const void* density, int dtype, const dvgo_grid_desc* grid, float shift,
+                                float interval, float alpha_thres, const int32_t* brick_list,
+                                const int32_t* brick_count, uint8_t* mask, void* stream) {
+  DVGO_CHECK_ARG(density && grid && mask && (dtype == DVGO_F32 || dtype == DVGO_BF16));
+  DVGO_CHECK_ARG(interval > 0.0f && alpha_thres > 0.0f && alpha_thres < 1.0f);
+  DVGO_CHECK_ARG(grid->G[0] >= 1 && grid->G[1] >= 1 && grid->G[2] >= 1);
+  DVGO_CHECK_ARG((brick_list == nullptr) == (brick_count == nullptr));
+  const float thr = mask_raw_threshold(shift, interval, alpha_thres);
+  const BrickGeom g = make_geom(grid->G);
+  const int blocks = (int)std::min<int64_t>(g.num_bricks(), (int64_t)kNumSMs * 4);
+  mask_update_kernel<<<blocks, 512, 0, as_stream(stream)>>>(density, dtype == DVGO_BF16, g, thr, brick_list,
+                                                             brick_count, mask);
+  return launch_status();
 }
 
 extern "C" int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_desc* grid,
@@ -773,13 +899,7 @@ extern "C" int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_d
   DVGO_CHECK_ARG(density && grid && mask && (dtype == DVGO_F32 || dtype == DVGO_BF16));
   DVGO_CHECK_ARG(interval > 0.0f && alpha_thres > 0.0f && alpha_thres < 1.0f);
   DVGO_CHECK_ARG(grid->G[0] >= 1 && grid->G[1] >= 1 && grid->G[2] >= 1);
-  // alpha(raw) >= thr  <=>  raw >= log(expm1(-log1p(-thr)/interval)) - shift.
-  // The FP32 threshold is the smallest float not below the exact one, so the
-  // FP32 comparison decides exactly like the FP64 one.
-  double q = -log1p(-(double)alpha_thres) / (double)interval;
-  double thr64 = log(expm1(q)) - (double)shift;
-  float thr = (float)thr64;
-  if ((double)thr < thr64) thr = nextafterf(thr, INFINITY);
+  const float thr = mask_raw_threshold(shift, interval, alpha_thres);
   BrickGeom g = make_geom(grid->G);
   int64_t nvox = (int64_t)grid->G[0] * grid->G[1] * grid->G[2];
   cudaStream_t st = as_stream(stream);

@@ -364,6 +364,51 @@ __global__ void live_fill_kernel(const int64_t* __restrict__ ray_off,
   }
 }
 
+// Low-weight cull of the colour-query list: warp per ray, the first
+// seg_len[r] samples, kept iff w >= w_min (one ballot per 32 samples).  With
+// fill, kept samples are listed in ray order and the rgb and g_k0 rows of the
+// culled ones are zeroed; without, only the count per ray is written.
+template <bool kFill>
+__global__ void cull_kernel(const int64_t* __restrict__ ray_off, const int32_t* __restrict__ seg_len,
+                            const float* __restrict__ w, float w_min, int64_t R, int32_t* __restrict__ counts,
+                            const int64_t* __restrict__ off, int32_t* __restrict__ live_idx,
+                            float* __restrict__ rgb, float* __restrict__ g_k0) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R; r += nw) {
+    const int64_t b = ray_off[r];
+    const int n = seg_len[r];
+    int64_t dst = kFill ? off[r] : 0;
+    int cnt = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < n;
+      const bool keep = valid && __ldg(w + b + i) >= w_min;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (kFill) {
+        if (keep) live_idx[dst + __popc(bal & lt)] = (int32_t)(b + i);
+        if (valid && !keep) {
+          const int64_t s = b + i;
+          if (rgb) {
+            rgb[3 * s] = 0.0f;
+            rgb[3 * s + 1] = 0.0f;
+            rgb[3 * s + 2] = 0.0f;
+          }
+          if (g_k0) {
+            float4* q = reinterpret_cast<float4*>(g_k0 + s * 12);
+            q[0] = q[1] = q[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
+        }
+        dst += __popc(bal);
+      } else {
+        cnt += __popc(bal);
+      }
+    }
+    if (!kFill && lane == 0) counts[r] = cnt;
+  }
+}
+
 static bool fill_args(SamplerArgs& A, const dvgo_grid_desc* g, const dvgo_sampler_desc* s) {
   for (int a = 0; a < 3; ++a) {
     A.lo[a] = g->lo[a];
@@ -439,7 +484,29 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
 }
 
 extern "C" size_t dvgo_live_samples_workspace_size(int64_t R) {
-  return (size_t)((R + 1) * sizeof(int64_t) + 255) / 256 * 256;
+  // offsets [R + 1] int64, then (the cull) counts [R] int32
+  return (size_t)((R + 1) * sizeof(int64_t) + 255) / 256 * 256 + (size_t)(R * sizeof(int32_t) + 255) / 256 * 256;
+}
+
+extern "C" int dvgo_live_samples_cull(const int64_t* ray_off, const int32_t* seg_len, const float* w,
+                                      float w_min, int64_t R, int32_t* live_idx, int64_t* live_count,
+                                      float* rgb, float* g_k0, void* ws, size_t ws_bytes, void* stream) {
+  DVGO_CHECK_ARG(ray_off && seg_len && w && live_idx && live_count && ws && R >= 0 && w_min >= 0.0f);
+  DVGO_CHECK_ARG(((uintptr_t)g_k0 % 16) == 0);
+  if (ws_bytes < dvgo_live_samples_workspace_size(R)) return DVGO_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  if (R == 0) {
+    cudaMemsetAsync(live_count, 0, sizeof(int64_t), st);
+    return launch_status();
+  }
+  int64_t* off = reinterpret_cast<int64_t*>(ws);
+  int32_t* counts = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(ws) +
+                                               (size_t)((R + 1) * sizeof(int64_t) + 255) / 256 * 256);
+  const int g = grid_for(R * 32, 256, 16);
+  cull_kernel<false><<<g, 256, 0, st>>>(ray_off, seg_len, w, w_min, R, counts, nullptr, nullptr, nullptr, nullptr);
+  scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, off, live_count);
+  cull_kernel<true><<<g, 256, 0, st>>>(ray_off, seg_len, w, w_min, R, nullptr, off, live_idx, rgb, g_k0);
+  return launch_status();
 }
 
 extern "C" int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len, int64_t R,

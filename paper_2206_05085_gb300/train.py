@@ -54,8 +54,15 @@ class GridParam:
 class Trainer:
     def __init__(self, cfg: SceneConfig, rp: RenderParams, density: np.ndarray,
                  feature: np.ndarray, mlp_params: np.ndarray, n_rays: int,
-                 precision: str = "f32", device: str = "cuda"):
+                 precision: str = "f32", device: str = "cuda", mask_update: bool = False,
+                 w_min: float | None = None):
         self.cfg, self.rp, self.R = cfg, rp, int(n_rays)
+        # mask_update: the occupancy mask follows the density (re-evaluated in the
+        # bricks each optimizer step changed); w_min: samples in front of the halt
+        # whose compositing weight is below w_min skip the colour query (feature
+        # gather and colour MLP)
+        self.mask_update = bool(mask_update)
+        self.w_min = w_min
         self.dev = torch.device(device)
         # "f32": colour MLP in FP32 on the CUDA cores; "f32tc": FP32-accurate on
         # the tensor cores (split-FP16 operands); "bf16": BF16 grids and MLP
@@ -122,14 +129,19 @@ class Trainer:
         self.T_end = torch.empty(R, **f32)
         self.live_idx = torch.empty(S, **i32)
         self.live_count = torch.zeros(1, dtype=torch.int64, device=dev)
+        if self.w_min is not None:   # the colour-query list after the low-weight cull
+            self.query_idx = torch.empty(S, **i32)
+            self.query_count = torch.zeros(1, dtype=torch.int64, device=dev)
+        else:
+            self.query_idx, self.query_count = self.live_idx, self.live_count
         self.k0 = torch.empty(S, FEAT, **f32)
-        self.rgb = torch.empty(S, 3, **f32)
+        self.rgb = torch.zeros(S, 3, **f32)
         self.color = torch.empty(R, 3, **f32)
         self.L_r = torch.empty(R, **f32)
         self.loss = torch.zeros(3, **f32)
         self.g_color = torch.empty(R, 3, **f32)
         self.g_raw = torch.empty(S, **f32)
-        self.g_k0 = torch.empty(S, FEAT, **f32)
+        self.g_k0 = torch.zeros(S, FEAT, **f32)
         # FP32 forms: what the colour-MLP forward saves for its backward (hidden
         # activations, or the split layer inputs of each 128-sample tile)
         # (BF16 form: the backward's per-CTA partial gradients)
@@ -165,10 +177,13 @@ class Trainer:
         L.density_alpha_fwd(dgrid, ddt, self.gd, self.xyz, self.ray_off, R, self.shift, rp.interval,
                             rp.T_stop, self.raw, self.w, self.T, self.n_live, self.T_end)
         L.live_samples(self.ray_off, self.n_live, R, self.live_idx, self.live_count, self.ws_live)
+        if self.w_min is not None:
+            L.live_samples_cull(self.ray_off, self.n_live, self.w, self.w_min, R, self.query_idx,
+                                self.query_count, self.rgb, self.g_k0, self.ws_live)
         fgrid, fdt = self.feature.render_view
-        L.sample_grid_fwd(fgrid, fdt, self.gd, FEAT, self.xyz, self.live_idx, S, self.live_count,
+        L.sample_grid_fwd(fgrid, fdt, self.gd, FEAT, self.xyz, self.query_idx, S, self.query_count,
                           self.k0)
-        L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.live_idx, S, self.live_count, self.mlp,
+        L.rgbnet_fwd(self.k0, rays_d, self.ray_id, self.query_idx, S, self.query_count, self.mlp,
                      self.precision, self.rgb, self.act)
         # colour accumulation, distortion loss and the photometric loss in one pass
         # over each ray (with tail_adjoint, followed in the same warp by the ray's
@@ -192,8 +207,8 @@ class Trainer:
             L.composite_distortion_bwd(self.g_color, rp.lambda_dist / R, self.w, self.raw, self.T,
                                        self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live,
                                        R, self.shift, rp.interval, rp.bg, self.g_raw)
-        L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.live_idx, S,
-                     self.live_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
+        L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.query_idx, S,
+                     self.query_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
                      self.act, self.rgb)
         # both grid adjoints in one pass over the live samples
         L.sample_grid_bwd2(self.g_raw, 1, self.density.g, self.density.touched, self.g_k0, FEAT,
@@ -224,6 +239,11 @@ class Trainer:
                        rp.lr_mlp))
         # the step count t lives on the device (so that a captured step can be replayed)
         L.adam_step_multi_dev(params, rp.beta1, rp.beta2, rp.eps, self.step_dev, True)
+        if self.mask_update and self.mask is not None:
+            # the density changed only in the listed bricks
+            dgrid, ddt = self.density.render_view
+            L.update_mask(dgrid, ddt, self.gd, self.shift, rp.interval, rp.mask_thres, self.brick_list,
+                          self.brick_count, self.mask)
 
     def step(self, rays_o, rays_d, target, tv_dense: bool = False, sample: bool = True):
         """One full training iteration; returns the device loss tensor [3]."""
@@ -251,6 +271,54 @@ class Trainer:
         with torch.cuda.graph(graph):
             self.step(*self.g_in, tv_dense=tv_dense)
         return graph, self.g_in
+
+    # ------------------------------------------------- progressive scaling
+    def upscale(self, grid: int, moments: str = "resample"):
+        """Progressive grid scaling (Sec. 5.4, grid-scaling schedule): both grids
+        resampled to `grid` points per axis over the same box (trilinear,
+        corner aligned), with the Adam moments m and v resampled the same way
+        (moments="reset": zeroed instead).  Gradients and touched flags start
+        empty, the renderer's BF16 copies are rebuilt, the sampler step is
+        re-derived for the new voxel size (half a voxel) and the occupancy mask
+        rebuilt from the new density.  The Adam step count carries on."""
+        import dataclasses
+        from . import synth
+        G_old, G_new = self.G, [int(grid)] * 3
+        for gp in (self.density, self.feature):
+            n = L.grid_bricked_elems(G_new, gp.C)
+            fresh = {}
+            for name in ("p", "m", "v"):
+                t = torch.empty(n, dtype=torch.float32, device=self.dev)
+                if name == "p" or moments == "resample":
+                    L.grid_resample(getattr(gp, name), G_old, t, L.F32, G_new, gp.C)
+                else:
+                    t.zero_()
+                fresh[name] = t
+            if gp.shadow is not None:
+                gp.shadow = torch.empty(n, dtype=torch.bfloat16, device=self.dev)
+                L.grid_resample(gp.p, G_old, gp.shadow, L.BF16, G_new, gp.C)
+            gp.p, gp.m, gp.v = fresh["p"], fresh["m"], fresh["v"]
+            gp.g = torch.zeros_like(gp.p)
+            gp.touched = torch.zeros(L.grid_num_bricks(G_new), dtype=torch.uint8, device=self.dev)
+        self.cfg = dataclasses.replace(self.cfg, grid=int(grid))
+        fine = synth.render_params(self.cfg)
+        self.rp = dataclasses.replace(self.rp, step=fine.step, max_steps=fine.max_steps, step_c=fine.step_c,
+                                      interval=fine.interval)
+        self.G = G_new
+        self.gd = L.GridDesc.make(self.cfg.bbox_min, self.cfg.bbox_max, G_new)
+        if self.rp.mask_thres is not None:
+            self.mask = torch.empty(G_new[2], G_new[1], G_new[0], dtype=torch.uint8, device=self.dev)
+            dgrid, dt = self.density.render_view
+            L.build_mask(dgrid, dt, self.gd, self.shift, self.rp.interval, self.rp.mask_thres, self.mask)
+        sd = self.sd
+        if self.rp.contracted:
+            sd.max_steps, sd.step_c = self.rp.max_steps, self.rp.step_c
+        else:
+            sd.step, sd.max_steps = self.rp.step, self.rp.max_steps
+        self.S_cap = self.R * self.rp.max_steps
+        step_dev = self.step_dev
+        self._alloc_step_buffers()
+        self.step_dev = step_dev
 
     # ------------------------------------------------------------- helpers
     def dense(self, gp: GridParam, which: str = "p") -> torch.Tensor:

@@ -34,9 +34,12 @@ def live_of(ray_off, n_live):
     return live
 
 
-def forward_backward(cfg, rp, density, feature, params, o, d, target, grads=True):
+def forward_backward(cfg, rp, density, feature, params, o, d, target, grads=True, w_min=None):
     """density [G,G,G] f32, feature [G,G,G,12] f32, params flat f32 (the values
-    the renderer reads: BF16-rounded already for the BF16 form)."""
+    the renderer reads: BF16-rounded already for the BF16 form).  w_min: the
+    low-weight cull -- samples in front of the halt whose compositing weight
+    is below w_min get no colour query (their colour is 0, their features no
+    gradient); out["query"] marks the queried samples."""
     lo, hi = cfg.bbox_min, cfg.bbox_max
     sh = shift32(rp.alpha_init)
     mask = None
@@ -47,18 +50,19 @@ def forward_backward(cfg, rp, density, feature, params, o, d, target, grads=True
     raw = oracle.trilinear(density, lo, hi, smp.xyz)[:, 0]
     c0 = oracle.composite(raw, None, smp.ray_off, sh, rp.interval, rp.T_stop, rp.bg)
     live = live_of(smp.ray_off, c0["n_live"])
-    k0 = oracle.trilinear(feature, lo, hi, smp.xyz[live])
-    x = oracle.rgbnet_input(k0, d[smp.ray_id[live]])
+    query = live & (c0["w"] >= w_min) if w_min is not None else live
+    k0 = oracle.trilinear(feature, lo, hi, smp.xyz[query])
+    x = oracle.rgbnet_input(k0, d[smp.ray_id[query]])
     p64 = params.astype(np.float64)
-    rgb_live = oracle.mlp_fwd(synth.RGBNET_DIMS, p64, x, True)
+    rgb_q = oracle.mlp_fwd(synth.RGBNET_DIMS, p64, x, True)
     rgb = np.zeros((smp.S, 3))
-    rgb[live] = rgb_live
+    rgb[query] = rgb_q
     comp = oracle.composite(raw, rgb, smp.ray_off, sh, rp.interval, rp.T_stop, rp.bg)
     L_r = oracle.distortion(comp["w"], smp.s_mid, smp.s_len, smp.ray_off, comp["n_live"])
     tgt = target.astype(np.float64)
     loss_rgb = np.mean((comp["color"] - tgt) ** 2)
     loss_dist = np.mean(L_r)
-    out = dict(mask=mask, smp=smp, raw=raw, live=live, k0=k0, rgb=rgb, L_r=L_r, x=x,
+    out = dict(mask=mask, smp=smp, raw=raw, live=live, query=query, k0=k0, rgb=rgb, L_r=L_r, x=x,
                loss=np.array([loss_rgb, loss_dist, loss_rgb + rp.lambda_dist * loss_dist]), **comp)
     if not grads:
         return out
@@ -67,9 +71,9 @@ def forward_backward(cfg, rp, density, feature, params, o, d, target, grads=True
                                  comp["n_live"])
     g_raw, g_rgb = oracle.composite_bwd(raw, rgb, smp.ray_off, sh, rp.interval, rp.T_stop, rp.bg,
                                         g_color, g_w)
-    g_params, g_x = oracle.mlp_bwd(synth.RGBNET_DIMS, p64, x, g_rgb[live], True)
+    g_params, g_x = oracle.mlp_bwd(synth.RGBNET_DIMS, p64, x, g_rgb[query], True)
     g_density = oracle.trilinear_adjoint(g_raw[live], density.shape, lo, hi, smp.xyz[live])
-    g_feature = oracle.trilinear_adjoint(g_x[:, :12], feature.shape, lo, hi, smp.xyz[live])
+    g_feature = oracle.trilinear_adjoint(g_x[:, :12], feature.shape, lo, hi, smp.xyz[query])
     out.update(g_color=g_color, g_w=g_w, g_raw=g_raw, g_rgb=g_rgb, g_params=g_params,
                g_k0=g_x[:, :12], g_density=g_density, g_feature=g_feature)
     return out

@@ -28,11 +28,11 @@ def _host(t):
     return t.detach().float().cpu().numpy()
 
 
-def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense):
+def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):
     """Forward, backward, TV and Adam of one batch through the library; the
     outputs and gradients before the optimizer and the parameters after it."""
     from paper_2206_05085_gb300 import train
-    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=len(o), precision=precision)
+    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=len(o), precision=precision, w_min=w_min)
     to, td, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (o, d, tgt))
     tr.forward(to, td, tt)
     tr.backward(td)
@@ -50,7 +50,7 @@ def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense):
     return gpu
 
 
-def oracle_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense):
+def oracle_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):
     """The same iteration from the oracle.  The BF16 form's stored values
     (grids and MLP parameters) are the BF16-rounded ones; the Adam masters
     stay FP32.  Returns (fb, opt, params the renderer read)."""
@@ -58,7 +58,7 @@ def oracle_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense):
     Dr = synth.bf16_round(D) if bf else D
     Fr = synth.bf16_round(Fg) if bf else Fg
     Pr = synth.bf16_round(P) if bf else P
-    fb = forward_backward(cfg, rp, Dr, Fr, Pr, o, d, tgt)
+    fb = forward_backward(cfg, rp, Dr, Fr, Pr, o, d, tgt, w_min=w_min)
     fb["density0"], fb["feature0"], fb["params0"] = D, Fg, P
     opt = optimizer(rp, 1, D, Fg, P, fb, tv_dense, Dr, Fr)
     return fb, opt, Pr
@@ -111,11 +111,12 @@ def error_table(gpu, fb, opt, cfg, rp, params, tau):
     e["color"] = rel_err(gpu["color"], fb["color"])
     e["loss"] = rel_err(gpu["loss"], fb["loss"])
     e["L_r"] = rel_err(gpu["L_r"], fb["L_r"])
-    live = fb["live"]
+    live = fb["query"]       # the samples that reached the colour MLP
     zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, params.astype(np.float64), fb["x"])
     amb = zmin < tau
     e["relu_ambiguous_samples"] = int(amb.sum())
-    e["live_samples"] = int(live.sum())
+    e["live_samples"] = int(fb["live"].sum())
+    e["colour_query_samples"] = int(live.sum())
     if same_list:
         e["w"] = rel_err(gpu["w"], fb["w"])
         e["rgb"] = rel_err(gpu["rgb"][live], fb["rgb"][live])

@@ -963,3 +963,149 @@ def test_invalid_arguments_raise(L):
     with pytest.raises(L.DvgoError):
         L.rgbnet_fwd(None, None, None, None, 10, None, None, 7, None)
     assert L.device_status() == 0
+
+
+# ------------------------------------------------------- grid scaling
+@pytest.mark.parametrize("Gs,Gd", [((13, 10, 17), (25, 19, 33)), ((13, 10, 17), (7, 6, 9)),
+                                   ((16, 16, 16), (16, 16, 16))])
+def test_grid_resample(L, Gs, Gd):
+    rng = np.random.default_rng(80)
+    C = 5
+    dense = rng.normal(size=(Gs[2], Gs[1], Gs[0], C)).astype(np.float32)
+    src = _bricked(L, dense, Gs, C)
+    out = torch.empty(L.grid_bricked_elems(Gd, C), device="cuda")
+    L.grid_resample(src, Gs, out, L.F32, Gd, C)
+    got = torch.empty(Gd[2], Gd[1], Gd[0], C, device="cuda")
+    L.grid_unpack(out, got, Gd, C, L.F32)
+    ref = oracle.grid_resample(dense, Gd)
+    assert rel_err(host(got), ref) < TOL32
+    if Gs == Gd:
+        assert np.array_equal(host(got), dense)
+    # the BF16 copy is the FP32 result rounded to nearest
+    outb = torch.empty(L.grid_bricked_elems(Gd, C), dtype=torch.bfloat16, device="cuda")
+    L.grid_resample(src, Gs, outb, L.BF16, Gd, C)
+    gotb = torch.empty(Gd[2], Gd[1], Gd[0], C, dtype=torch.bfloat16, device="cuda")
+    L.grid_unpack(outb, gotb, Gd, C, L.BF16)     # (brick padding is not written)
+    assert np.array_equal(host(gotb.float()), synth.bf16_round(host(got)))
+
+
+@pytest.mark.parametrize("precision", ["f32tc", "bf16"])
+def test_trainer_upscale_then_step(L, precision):
+    """A trainer whose grids are raised from 48^3 to 80^3 (moments resampled
+    with them) takes a step that matches the oracle's step on the resampled
+    grids."""
+    import dataclasses
+    from paper_2206_05085_gb300 import train
+    cfg = dataclasses.replace(synth.CFG2, grid=48)
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg, n_rays=256)
+    tgt = synth.target_rgb(cfg, n_rays=256)
+    to, td, tt = (dev(a) for a in (o, d, tgt))
+    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=256, precision=precision)
+    tr.step(to, td, tt)                       # moments and t are no longer zero
+    m_before = host(tr.dense(tr.feature, "m"))
+    tr.upscale(80)
+    assert tr.G == [80, 80, 80] and int(tr.step_dev[0].item()) == 1
+    Dn = host(tr.dense(tr.density, "p"))[..., 0]
+    Fn = host(tr.dense(tr.feature, "p"))
+    # the moments were resampled with the grids
+    assert rel_err(host(tr.dense(tr.feature, "m")), oracle.grid_resample(m_before, (80, 80, 80))) < TOL32
+    Pn = host(tr.mlp)
+    cfg2, rp2 = tr.cfg, tr.rp
+    assert rp2.max_steps > rp.max_steps
+    # one forward/backward on the new grids against the oracle's on the same stored values
+    tr.forward(to, td, tt)
+    tr.backward(td)
+    S = int(host(tr.ray_off)[-1])
+    gpu = dict(loss=host(tr.loss), color=host(tr.color), L_r=host(tr.L_r), n_live=host(tr.n_live), S=S)
+    from oracle_step import forward_backward
+    bf = precision == "bf16"
+    fb = forward_backward(cfg2, rp2, synth.bf16_round(Dn) if bf else Dn, synth.bf16_round(Fn) if bf else Fn,
+                          synth.bf16_round(Pn) if bf else Pn, o, d, tgt, grads=False)
+    assert S == fb["smp"].S
+    assert np.array_equal(gpu["n_live"], fb["n_live"])
+    tol = 2e-3 if bf else TOL32
+    assert rel_err(gpu["color"], fb["color"]) < tol
+    assert rel_err(gpu["loss"], fb["loss"]) < tol
+
+
+# ---------------------------------------------- progressive occupancy mask
+def test_update_mask_follows_density(L):
+    """After the density changes in some bricks, re-evaluating the mask in
+    those bricks gives the mask built from scratch (bit-exact against the
+    oracle's mask of the new density)."""
+    cfg = synth.CFG2
+    G = [cfg.grid] * 3
+    gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, G)
+    D0 = synth.density_grid(cfg)
+    rng = np.random.default_rng(90)
+    nbx = (cfg.grid + 7) // 8
+    bricks = np.sort(rng.choice(nbx ** 3, 400, replace=False)).astype(np.int32)
+    D1 = D0.copy()
+    for b in bricks:
+        bx, by, bz = b % nbx, (b // nbx) % nbx, b // (nbx * nbx)
+        sl = np.s_[bz * 8:bz * 8 + 8, by * 8:by * 8 + 8, bx * 8:bx * 8 + 8]
+        D1[sl] += rng.normal(0, 6.0, D1[sl].shape).astype(np.float32)
+    m = torch.empty(G[2], G[1], G[0], dtype=torch.uint8, device="cuda")
+    L.build_mask(_bricked(L, D0, G, 1), L.F32, gd, shift32(), 0.5, 1e-4, m)
+    L.update_mask(_bricked(L, D1, G, 1), L.F32, gd, shift32(), 0.5, 1e-4, dev(bricks),
+                  torch.tensor([len(bricks)], dtype=torch.int32, device="cuda"), m)
+    ref = oracle.build_mask(D1, shift32(), 0.5, 1e-4)
+    assert not np.array_equal(ref, oracle.build_mask(D0, shift32(), 0.5, 1e-4))
+    assert np.array_equal(host(m), ref)
+    # every brick (no list), on a grid whose side is not a multiple of 8
+    Gs = [37, 29, 45]
+    gds = L.GridDesc.make(-1.0, 1.0, Gs)
+    Ds = rng.normal(-3, 4, (Gs[2], Gs[1], Gs[0])).astype(np.float32)
+    ms = torch.zeros(Gs[2], Gs[1], Gs[0], dtype=torch.uint8, device="cuda")
+    L.update_mask(_bricked(L, Ds, Gs, 1), L.F32, gds, shift32(), 0.5, 1e-4, None, None, ms)
+    assert np.array_equal(host(ms), oracle.build_mask(Ds, shift32(), 0.5, 1e-4))
+
+
+def test_trainer_mask_follows_training(L):
+    """With the progressive update on, after every step the mask equals the
+    mask built from the current density."""
+    from paper_2206_05085_gb300 import train
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    tr = train.Trainer(cfg, rp, D, Fg, P, n_rays=2048, precision="f32tc", mask_update=True)
+    changed = False
+    m0 = host(tr.mask).copy()
+    for it in range(3):
+        o, d = synth.rays(cfg, seed=40 + it, n_rays=2048)
+        t = synth.target_rgb(cfg, seed=40 + it, n_rays=2048)
+        tr.step(dev(o), dev(d), dev(t))
+        dens = host(tr.dense(tr.density, "p"))[..., 0]
+        ref = oracle.build_mask(dens, shift32(), rp.interval, rp.mask_thres)
+        assert np.array_equal(host(tr.mask), ref)
+        changed |= not np.array_equal(ref, m0)
+    assert changed     # the lr-0.1 Adam steps move grid points across the threshold
+
+
+def test_live_samples_cull(L):
+    rng = np.random.default_rng(91)
+    counts = np.array([0, 1, 5, 31, 32, 33, 100, 300] + list(rng.integers(0, 260, 300)))
+    R = len(counts)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(off[-1])
+    n_live = np.array([rng.integers(0, c + 1) for c in counts], np.int32)
+    w = np.where(rng.uniform(size=S) < 0.4, 10.0 ** rng.uniform(-7, -1, S), 0.0).astype(np.float32)
+    w_min = 1e-4
+    live_idx = torch.full((S,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rgb = torch.full((S, 3), 5.0, device="cuda")
+    gk = torch.full((S, 12), 5.0, device="cuda")
+    ws = torch.empty(L.live_samples_workspace_size(R), dtype=torch.uint8, device="cuda")
+    L.live_samples_cull(dev(off), dev(n_live), dev(w), w_min, R, live_idx, cnt, rgb, gk, ws)
+    live = np.zeros(S, bool)
+    for r in range(R):
+        live[off[r]:off[r] + n_live[r]] = True
+    keep = live & (w >= w_min)
+    ref = np.nonzero(keep)[0]
+    assert int(host(cnt)[0]) == len(ref)
+    assert np.array_equal(host(live_idx)[:len(ref)], ref)
+    culled = live & ~keep
+    assert np.all(host(rgb)[culled] == 0) and np.all(host(gk)[culled] == 0)
+    assert np.all(host(rgb)[~culled] == 5.0) and np.all(host(gk)[~culled] == 5.0)

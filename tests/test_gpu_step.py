@@ -54,7 +54,7 @@ def _compare(gpu, fb, opt, tol, cfg, rp, params, bf16=False):
         assert e[k] < tol, (k, e[k])
     from conftest import check_mlp_grads
     check_mlp_grads(oracle, synth.RGBNET_DIMS, params.astype(np.float64), fb["x"],
-                    fb["g_rgb"][fb["live"]], gpu["g_mlp"], None, tol, tau=tau)
+                    fb["g_rgb"][fb["query"]], gpu["g_mlp"], None, tol, tau=tau)
     # voxels of samples with an ambiguous ReLU unit are few
     assert e["g_feature_voxels_set_aside"] <= 0.05 * e["g_feature_voxels_touched"] + 8
     # elsewhere the first Adam step is bounded by the learning rate
@@ -90,6 +90,33 @@ def test_step_dvgo160_fp32_dense_tv(T):
 def test_step_dvgo160_bf16(T):
     gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG4, 1024, "bf16", tv_dense=False, ray_stride=16)
     _compare(gpu, fb, opt, 2e-3, cfg, rp, P, bf16=True)
+
+
+def test_step_low_weight_cull(T):
+    """The colour query skips samples whose compositing weight is below 1e-4:
+    the step equals the oracle's step with the same cull (colour 0 and no
+    feature gradient for the skipped samples, density gradient for all), and
+    the render stays close to the uncull render."""
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg)
+    tgt = synth.target_rgb(cfg)
+    o, d, tgt = o[::8][:1024], d[::8][:1024], tgt[::8][:1024]
+    gpu = gpu_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False, w_min=1e-4)
+    fb, opt, Pr = oracle_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False, w_min=1e-4)
+    skipped = fb["live"] & ~fb["query"]
+    assert skipped.sum() > 0.05 * fb["live"].sum()     # the cull does something here
+    # no weight sits so close to the threshold that FP32 and FP64 could disagree
+    w = fb["w"][fb["live"]]
+    assert np.min(np.abs(w - 1e-4)) > 1e-5 * 1e-4
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, Pr)
+    full = oracle_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False)[0]
+    mse = np.mean((gpu["color"].astype(np.float64) - full["color"]) ** 2)
+    psnr = -10 * np.log10(mse)
+    print(f"low-weight cull: {int(skipped.sum())} of {int(fb['live'].sum())} live samples skipped, "
+          f"render vs full render {psnr:.1f} dB")
+    assert psnr > 50
 
 
 def test_step_unbounded_contracted(T):
