@@ -123,19 +123,23 @@ def kernel_flops_bytes(tr):
     torch.cuda.synchronize()
     S = int(tr.ray_off[-1].item())
     S_live = int(tr.live_count.item())
-    G = tr.G[0]
+    Gx, Gy, Gz = tr.G
     cfg = tr.cfg
-    scale = (G - 1) / (cfg.bbox_max - cfg.bbox_min)
-    offs = torch.tensor([(k >> 2) * G * G + ((k >> 1) & 1) * G + (k & 1) for k in range(8)],
-                        dtype=torch.int64, device=tr.xyz.device)
+    dev = tr.xyz.device
+    Gt = torch.tensor([Gx, Gy, Gz], dtype=torch.float32, device=dev)
+    scale = (Gt - 1) / (cfg.bbox_max - cfg.bbox_min)
+    offs = torch.tensor([(k >> 2) * Gx * Gy + ((k >> 1) & 1) * Gx + (k & 1) for k in range(8)],
+                        dtype=torch.int64, device=dev)
 
     def distinct(xyz):
-        u = ((xyz - cfg.bbox_min) * scale).clamp(0, G - 1).floor().to(torch.int64).clamp(max=G - 2)
-        base = (u[:, 2] * G + u[:, 1]) * G + u[:, 0]
+        u = ((xyz - cfg.bbox_min) * scale).clamp(min=0)
+        u = torch.minimum(u, Gt - 1).floor().to(torch.int64)
+        u = torch.minimum(u, (Gt - 2).to(torch.int64))
+        base = (u[:, 2] * Gy + u[:, 1]) * Gx + u[:, 0]
         vox = torch.unique((base[:, None] + offs).reshape(-1))
-        x, y, z = vox % G, (vox // G) % G, vox // (G * G)
-        nbx = (G + 7) // 8
-        bricks = torch.unique(((z // 8) * nbx + y // 8) * nbx + x // 8)
+        x, y, z = vox % Gx, (vox // Gx) % Gy, vox // (Gx * Gy)
+        nbx, nby = (Gx + 7) // 8, (Gy + 7) // 8
+        bricks = torch.unique(((z // 8) * nby + y // 8) * nbx + x // 8)
         return int(vox.numel()), int(bricks.numel())
 
     V_all, _ = distinct(tr.xyz[:S])

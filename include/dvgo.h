@@ -66,7 +66,7 @@ typedef struct {
   int32_t G[3];
 } dvgo_grid_desc;
 
-/* Ray sampler (Sec. 3 "Re-implement rendering utils", Sec. 5.3).
+/* Ray sampler (Sec. 3 "Re-implement rendering utils", Sec. 5.2, Sec. 5.3).
  * mode 0 (bbox): t_k = t_lo + (k + step_offset) step, k < n, where
  *   [t_lo, t_hi] = [near, far], clipped to the ray/bbox slab when use_slab,
  *   n = min(max_steps, ceil((t_hi - t_lo)/step - step_offset)); a sample
@@ -80,7 +80,20 @@ typedef struct {
  *   contraction with parameter b, p = inf when p_inf else 2); emits the
  *   contracted points for k < max_steps while their contracted p-norm
  *   radius stays below (1 + b) - step_c; s_mid = (k + 0.5)/max_steps,
- *   s_len = 1/max_steps. */
+ *   s_len = 1/max_steps.
+ * mode 2 (forward-facing, Sec. 5.2 "Points parameterization and sampling"):
+ *   each world ray (d_z < 0, the camera looking down -z) is moved to the
+ *   plane z = -ndc_near and warped to normalized device coordinates, o' =
+ *   (-fx o_x/o_z, -fy o_y/o_z, 1 + 2 ndc_near/o_z), d' = (-fx (d_x/d_z -
+ *   o_x/o_z), -fy (d_y/d_z - o_y/o_z), -2 ndc_near/o_z) with fx = ndc_fx, fy =
+ *   ndc_fy (focal / half the image width / height); the grid is a stack of
+ *   G_z depth layers over the box's z extent (multiplane images), and the
+ *   samples are the ray's crossings of the layer planes z_k = lo_z + k step
+ *   (hi_z - lo_z)/(G_z - 1), k < K = min(max_steps, floor((G_z - 1)/step) + 1)
+ *   (step in layers); a crossing exists iff it lies in the box and, with a
+ *   mask, the mask is on at its nearest grid point.  All in IEEE FP32 with
+ *   the operation order of the sampler source.  s_mid = (k + 0.5)/K, s_len =
+ *   1/K. */
 typedef struct {
   int32_t mode;
   float near;
@@ -92,6 +105,9 @@ typedef struct {
   float contract_b;
   int32_t p_inf;
   float step_c;
+  float ndc_fx;
+  float ndc_fy;
+  float ndc_near;
 } dvgo_sampler_desc;
 
 int dvgo_version(void);

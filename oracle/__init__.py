@@ -83,6 +83,8 @@ def _declare(L):
     L.or_sample_rays_bbox.restype = I64
     L.or_sample_rays_bbox.argtypes = [P, P, I64, P, P, P, F, F, F, F, INT, I32, P,
                                       P, P, P, P, P, P, I64]
+    L.or_sample_rays_ndc.restype = I64
+    L.or_sample_rays_ndc.argtypes = [P, P, I64, P, P, P, F, F, F, F, I32, P, P, P, P, P, P, P, I64]
     L.or_contract.argtypes = [P, I64, D, INT, P]
     L.or_sample_rays_contracted.restype = I64
     L.or_sample_rays_contracted.argtypes = [P, P, I64, F, INT, F, F, I32, P, P, P, P,
@@ -187,6 +189,25 @@ def sample_rays_bbox(o, d, lo, hi, G, near, far, step, off, use_slab, max_steps,
                                   _p(_vec3i(G)), near, far, step, off, int(use_slab),
                                   max_steps, _p(mask), _p(ray_off), _p(xyz), _p(rid),
                                   _p(sk), _p(sm), _p(sl), cap)
+    return Samples(ray_off, xyz[:S], rid[:S], sk[:S], sm[:S], sl[:S])
+
+
+def sample_rays_ndc(o, d, lo, hi, G, fx, fy, near, step, max_steps, mask=None):
+    """Forward-facing sampling: NDC warp of each ray, crossings of the depth
+    layers (see or_sample_rays_ndc)."""
+    o, d = _f32(o), _f32(d)
+    R = o.shape[0]
+    cap = R * max_steps
+    ray_off = np.zeros(R + 1, np.int64)
+    xyz = np.zeros((cap, 3), np.float32)
+    rid = np.zeros(cap, np.int32)
+    sk = np.zeros(cap, np.int32)
+    sm = np.zeros(cap, np.float64)
+    sl = np.zeros(cap, np.float64)
+    mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    S = lib().or_sample_rays_ndc(_p(o), _p(d), R, _p(_vec3f(lo)), _p(_vec3f(hi)), _p(_vec3i(G)), fx, fy,
+                                 near, step, max_steps, _p(mask), _p(ray_off), _p(xyz), _p(rid), _p(sk),
+                                 _p(sm), _p(sl), cap)
     return Samples(ray_off, xyz[:S], rid[:S], sk[:S], sm[:S], sl[:S])
 
 

@@ -163,6 +163,77 @@ OR_API int64_t or_sample_rays_bbox(const float* o, const float* d, int64_t R,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Forward-facing scenes (Sec. 5.2 "Points parameterization and sampling"):  */
+/* NeRF's normalized device coordinates warp the frustum in front of a       */
+/* camera looking down -z to a box; the grid is D depth layers over the      */
+/* box's z extent (multiplane images) and the samples are the ray's          */
+/* crossings of the layer planes, one every `step` layers.                   */
+/* Per ray (d_z < 0, else no samples), in FP32 with this operation order:    */
+/*   t  = -(near + o_z)/d_z ; p_a = o_a + t*d_a  (the ray moved to z = -near) */
+/*   rx = p_x/p_z ; ry = p_y/p_z  (no samples unless p_z < 0)                 */
+/*   o' = (-(fx*rx), -(fy*ry), 1 + (2*near)/p_z)                             */
+/*   d' = (-(fx*(d_x/d_z - rx)), -(fy*(d_y/d_z - ry)), -((2*near)/p_z))       */
+/*   K  = min(max_steps, floor((G_z - 1)/step) + 1)                          */
+/*   layer k < K: dz = (hi_z - lo_z)/(G_z - 1) ; z = lo_z + (k*step)*dz ;     */
+/*                t = (z - o'_z)/d'_z ; x = (o'_x + t*d'_x, o'_y + t*d'_y, z) */
+/* A crossing exists iff it lies in the box and the mask is on at its        */
+/* nearest grid point.  Distortion coordinates: s_mid = (k + 0.5)/K,         */
+/* s_len = 1/K (uniform in layer index, i.e. in inverse depth).              */
+/* ------------------------------------------------------------------------ */
+OR_API int64_t or_sample_rays_ndc(const float* o, const float* d, int64_t R, const float lo[3],
+                                  const float hi[3], const int32_t G[3], float fx, float fy,
+                                  float near, float step, int32_t max_steps, const uint8_t* mask,
+                                  int64_t* ray_off, float* xyz, int32_t* ray_id, int32_t* step_k,
+                                  double* s_mid, double* s_len, int64_t cap) {
+  int64_t S = 0;
+  ray_off[0] = 0;
+  for (int64_t r = 0; r < R; ++r) {
+    const float* ro = o + 3 * r;
+    const float* rd = d + 3 * r;
+    int32_t K = 0;
+    float qo[3] = {0, 0, 0}, qd[3] = {0, 0, 0};
+    if (rd[2] < 0.0f) {
+      float t = -(near + ro[2]) / rd[2];
+      float px = ro[0] + t * rd[0], py = ro[1] + t * rd[1], pz = ro[2] + t * rd[2];
+      if (pz < 0.0f) {
+        float rx = px / pz, ry = py / pz, two_n = 2.0f * near;
+        qo[0] = -(fx * rx);
+        qo[1] = -(fy * ry);
+        qo[2] = 1.0f + two_n / pz;
+        qd[0] = -(fx * (rd[0] / rd[2] - rx));
+        qd[1] = -(fy * (rd[1] / rd[2] - ry));
+        qd[2] = -(two_n / pz);
+        float nf = floorf((float)(G[2] - 1) / step);
+        K = (int32_t)nf + 1;
+        if (K > max_steps) K = max_steps;
+      }
+    }
+    float dz = (hi[2] - lo[2]) / (float)(G[2] - 1);
+    for (int32_t k = 0; k < K; ++k) {
+      float z = lo[2] + ((float)k * step) * dz;
+      float t = (z - qo[2]) / qd[2];
+      float x[3] = {qo[0] + t * qd[0], qo[1] + t * qd[1], z};
+      int inside = 1;
+      for (int a = 0; a < 3; ++a)
+        if (!(x[a] >= lo[a] && x[a] <= hi[a])) inside = 0;
+      if (!inside || !mask_on(mask, G, lo, hi, x)) continue;
+      if (S < cap) {
+        xyz[3 * S + 0] = x[0];
+        xyz[3 * S + 1] = x[1];
+        xyz[3 * S + 2] = x[2];
+        ray_id[S] = (int32_t)r;
+        step_k[S] = k;
+        s_mid[S] = ((double)k + 0.5) / (double)K;
+        s_len[S] = 1.0 / (double)K;
+      }
+      ++S;
+    }
+    ray_off[r + 1] = S;
+  }
+  return S;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Unbounded scenes, Eq. (ub) of Sec. 5.3:                                   */
 /*   x' = x                                      if ||x||_p <= 1             */
 /*   x' = (1 + b - b/||x||_p) (x / ||x||_p)      otherwise,  p in {2, inf}.  */

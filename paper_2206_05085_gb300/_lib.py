@@ -44,7 +44,7 @@ class GridDesc(ctypes.Structure):
 class SamplerDesc(ctypes.Structure):
     _fields_ = [("mode", I32), ("near", F), ("far", F), ("step", F), ("step_offset", F),
                 ("use_slab", I32), ("max_steps", I32), ("contract_b", F), ("p_inf", I32),
-                ("step_c", F)]
+                ("step_c", F), ("ndc_fx", F), ("ndc_fy", F), ("ndc_near", F)]
 
 
 class TvGrid(ctypes.Structure):

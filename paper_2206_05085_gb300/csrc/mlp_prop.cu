@@ -34,7 +34,6 @@ namespace prop {
 
 constexpr int kH = 64;                        // hidden width
 constexpr int kPropFreq = 6;
-constexpr int kNP = kH * kIn + kH + kH * kH + kH + kH + 1;   // 6785 parameters
 constexpr int oW1 = 0, oB1 = kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kH;
 constexpr int kK1 = 48;                       // padded input width
 constexpr int kH1W = kH + 16;                 // [H1 | 1 | 0..] in the backward

@@ -92,6 +92,49 @@ __device__ __forceinline__ void load_ray(const float* __restrict__ ro, const flo
   }
 }
 
+// Mode 2: the ray in normalized device coordinates (forward-facing scenes);
+// ok is false for a ray that does not look down -z.
+struct NdcRay {
+  float o[3], d[3];
+  int n;   // layer crossings
+};
+
+__device__ __forceinline__ NdcRay ndc_ray(const SamplerArgs& A, const float o[3], const float d[3]) {
+  NdcRay q;
+  q.n = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) q.o[a] = q.d[a] = 0.0f;
+  if (!(d[2] < 0.0f)) return q;
+  const float nr = A.s.ndc_near;
+  const float t = __fdiv_rn(-__fadd_rn(nr, o[2]), d[2]);
+  const float ox = __fadd_rn(o[0], __fmul_rn(t, d[0]));
+  const float oy = __fadd_rn(o[1], __fmul_rn(t, d[1]));
+  const float oz = __fadd_rn(o[2], __fmul_rn(t, d[2]));
+  if (!(oz < 0.0f)) return q;
+  const float rx = __fdiv_rn(ox, oz), ry = __fdiv_rn(oy, oz);
+  const float two_n = __fmul_rn(2.0f, nr);
+  q.o[0] = -__fmul_rn(A.s.ndc_fx, rx);
+  q.o[1] = -__fmul_rn(A.s.ndc_fy, ry);
+  q.o[2] = __fadd_rn(1.0f, __fdiv_rn(two_n, oz));
+  q.d[0] = -__fmul_rn(A.s.ndc_fx, __fsub_rn(__fdiv_rn(d[0], d[2]), rx));
+  q.d[1] = -__fmul_rn(A.s.ndc_fy, __fsub_rn(__fdiv_rn(d[1], d[2]), ry));
+  q.d[2] = -__fdiv_rn(two_n, oz);
+  const float nf = floorf(__fdiv_rn((float)(A.G[2] - 1), A.s.step));
+  const int K = (int)nf + 1;
+  q.n = K < A.s.max_steps ? K : A.s.max_steps;
+  return q;
+}
+
+// Crossing of layer plane k: z_k = lo_z + (k step) dz, dz = (hi_z - lo_z)/(G_z - 1).
+__device__ __forceinline__ void ndc_point(const SamplerArgs& A, const NdcRay& q, int k, float x[3]) {
+  const float dz = __fdiv_rn(__fsub_rn(A.hi[2], A.lo[2]), (float)(A.G[2] - 1));
+  const float z = __fadd_rn(A.lo[2], __fmul_rn(__fmul_rn((float)k, A.s.step), dz));
+  const float t = __fdiv_rn(__fsub_rn(z, q.o[2]), q.d[2]);
+  x[0] = __fadd_rn(q.o[0], __fmul_rn(t, q.d[0]));
+  x[1] = __fadd_rn(q.o[1], __fmul_rn(t, q.d[1]));
+  x[2] = z;
+}
+
 // Steps per ray whose keep bits pass 1 records for pass 2: one word of 32
 // steps per lane of the ray's warp (1024 steps).  Longer marches recompute
 // the keep test in pass 2.
@@ -101,6 +144,8 @@ constexpr int kBitWords = 32;
 // the warp also stores each 32-step chunk's keep ballot (lane j holds chunk
 // j's word; one coalesced store per ray), so that pass 2 need not repeat the
 // occupancy lookups.
+// kNdc: mode 2 (layer crossings of the warped ray) instead of mode 0.
+template <bool kNdc>
 __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
                                   const float* __restrict__ rd, int64_t R,
                                   const uint8_t* __restrict__ mask, int32_t* __restrict__ counts,
@@ -111,7 +156,14 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
   for (int64_t r = warp; r < R; r += nwarps) {
     float o[3], d[3];
     load_ray(ro, rd, r, o, d);
-    RaySpan sp = ray_span(A, o, d);
+    RaySpan sp{0.0f, 0.0f, 0};
+    NdcRay q;
+    if (kNdc) {
+      q = ndc_ray(A, o, d);
+      sp.n = q.n;
+    } else {
+      sp = ray_span(A, o, d);
+    }
     int cnt = 0;
     uint32_t mine = 0;
     for (int k0 = 0; k0 < sp.n; k0 += 32) {
@@ -119,7 +171,8 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
       bool keep = false;
       if (k < sp.n) {
         float x[3];
-        point_at(A, o, d, sp.tlo, k, x);
+        if (kNdc) ndc_point(A, q, k, x);
+        else point_at(A, o, d, sp.tlo, k, x);
         keep = keep_point(A, mask, x);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -135,6 +188,7 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
 // With bits (only when max_steps <= 32 kBitWords = 1024) the keep decisions are
 // pass 1's ballots; without, the keep test is evaluated again (same FP32
 // operations, same result).
+template <bool kNdc>
 __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
                                  const float* __restrict__ rd, int64_t R,
                                  const uint8_t* __restrict__ mask,
@@ -149,9 +203,19 @@ __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
   for (int64_t r = warp; r < R; r += nwarps) {
     float o[3], d[3];
     load_ray(ro, rd, r, o, d);
-    RaySpan sp = ray_span(A, o, d);
-    float span = __fsub_rn(sp.thi, sp.tlo);
-    float slen = __fdiv_rn(A.s.step, span);
+    RaySpan sp{0.0f, 0.0f, 0};
+    NdcRay q;
+    float span, slen;
+    if (kNdc) {
+      q = ndc_ray(A, o, d);
+      sp.n = q.n;
+      span = (float)q.n;                 // s = (k + 0.5)/K, length 1/K
+      slen = __fdiv_rn(1.0f, span);
+    } else {
+      sp = ray_span(A, o, d);
+      span = __fsub_rn(sp.thi, sp.tlo);
+      slen = __fdiv_rn(A.s.step, span);
+    }
     int64_t pos = ray_off[r];
     uint32_t mine = 0;
     if (bits && 32 * lane < sp.n) mine = bits[r * kBitWords + lane];
@@ -163,10 +227,14 @@ __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
       if (bits) {
         bal = __shfl_sync(0xffffffffu, mine, k0 >> 5);
         keep = (bal >> lane) & 1u;
-        if (keep) point_at(A, o, d, sp.tlo, k, x);
+        if (keep) {
+          if (kNdc) ndc_point(A, q, k, x);
+          else point_at(A, o, d, sp.tlo, k, x);
+        }
       } else {
         if (k < sp.n) {
-          point_at(A, o, d, sp.tlo, k, x);
+          if (kNdc) ndc_point(A, q, k, x);
+          else point_at(A, o, d, sp.tlo, k, x);
           keep = keep_point(A, mask, x);
         }
         bal = __ballot_sync(0xffffffffu, keep);
@@ -178,7 +246,8 @@ __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
         xyz[3 * s + 2] = x[2];
         ray_id[s] = (int32_t)r;
         step_k[s] = k;
-        s_mid[s] = __fdiv_rn(__fmul_rn(__fadd_rn((float)k, A.s.step_offset), A.s.step), span);
+        s_mid[s] = kNdc ? __fdiv_rn(__fadd_rn((float)k, 0.5f), span)
+                        : __fdiv_rn(__fmul_rn(__fadd_rn((float)k, A.s.step_offset), A.s.step), span);
         s_len[s] = slen;
       }
       pos += __popc(bal);
@@ -445,10 +514,11 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
                                 void* ws, size_t ws_bytes, void* stream) {
   DVGO_CHECK_ARG(grid && smp && ray_off && R >= 0);
   DVGO_CHECK_ARG(R == 0 || (rays_o && rays_d && xyz && ray_id && step_k && s_mid && s_len && ws));
-  DVGO_CHECK_ARG(smp->mode == 0 || smp->mode == 1);
+  DVGO_CHECK_ARG(smp->mode >= 0 && smp->mode <= 2);
   DVGO_CHECK_ARG(smp->max_steps >= 0);
-  if (smp->mode == 0) DVGO_CHECK_ARG(smp->step > 0.0f);
+  if (smp->mode == 0 || smp->mode == 2) DVGO_CHECK_ARG(smp->step > 0.0f);
   if (smp->mode == 1) DVGO_CHECK_ARG(smp->step_c > 0.0f && smp->contract_b > 0.0f);
+  if (smp->mode == 2) DVGO_CHECK_ARG(smp->ndc_near > 0.0f && smp->ndc_fx > 0.0f && smp->ndc_fy > 0.0f);
   if (S_cap < R * (int64_t)smp->max_steps || S_cap > INT32_MAX) return DVGO_ERR_SHAPE;
   if (ws_bytes < dvgo_sample_rays_workspace_size(R)) return DVGO_ERR_WORKSPACE;
   SamplerArgs A;
@@ -459,16 +529,23 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
     return launch_status();
   }
   int32_t* counts = reinterpret_cast<int32_t*>(ws);
-  if (smp->mode == 0) {
+  if (smp->mode == 0 || smp->mode == 2) {
     const int block = 256;
     int g = grid_for(R * 32, block, 16);
     uint32_t* bits = smp->max_steps <= 32 * kBitWords
                          ? reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + counts_bytes(R))
                          : nullptr;
-    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, bits);
-    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, bits, ray_off, xyz, ray_id,
-                                          step_k, s_mid, s_len);
+    if (smp->mode == 0) {
+      bbox_count_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, bits);
+      scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+      bbox_fill_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, bits, ray_off, xyz, ray_id,
+                                                   step_k, s_mid, s_len);
+    } else {
+      bbox_count_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, bits);
+      scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+      bbox_fill_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, bits, ray_off, xyz, ray_id,
+                                                  step_k, s_mid, s_len);
+    }
   } else {
     // one warp of rays per block, so that the sequential marches spread over
     // every SM (8192 rays: 256 blocks)
@@ -613,10 +690,11 @@ extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d
                                         float* s_mid, float* s_len, void* stream) {
   DVGO_CHECK_ARG(grid && smp && ray_off && R >= 0);
   DVGO_CHECK_ARG(R == 0 || (rays_o && rays_d && xyz && ray_id && step_k && s_mid && s_len));
-  DVGO_CHECK_ARG(smp->mode == 0 || smp->mode == 1);
+  DVGO_CHECK_ARG(smp->mode >= 0 && smp->mode <= 2);
   DVGO_CHECK_ARG(smp->max_steps >= 0);
-  if (smp->mode == 0) DVGO_CHECK_ARG(smp->step > 0.0f);
+  if (smp->mode == 0 || smp->mode == 2) DVGO_CHECK_ARG(smp->step > 0.0f);
   if (smp->mode == 1) DVGO_CHECK_ARG(smp->step_c > 0.0f && smp->contract_b > 0.0f);
+  if (smp->mode == 2) DVGO_CHECK_ARG(smp->ndc_near > 0.0f && smp->ndc_fx > 0.0f && smp->ndc_fy > 0.0f);
   if (R > kNoAllocMaxRays) return DVGO_ERR_SHAPE;
   if (S_cap < R * (int64_t)smp->max_steps || S_cap > INT32_MAX) return DVGO_ERR_SHAPE;
   SamplerArgs A;
@@ -634,10 +712,17 @@ extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d
   if (smp->mode == 0) {
     const int block = 256;
     int g = grid_for(R * 32, block, 16);
-    bbox_count_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr);
+    bbox_count_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr);
     scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    bbox_fill_kernel<<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
-                                          ray_id, step_k, s_mid, s_len);
+    bbox_fill_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+                                                 ray_id, step_k, s_mid, s_len);
+  } else if (smp->mode == 2) {
+    const int block = 256;
+    int g = grid_for(R * 32, block, 16);
+    bbox_count_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
+    bbox_fill_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+                                                ray_id, step_k, s_mid, s_len);
   } else {
     // one warp of rays per block, so that the sequential marches spread over
     // every SM (8192 rays: 256 blocks)

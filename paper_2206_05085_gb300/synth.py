@@ -56,10 +56,15 @@ class SceneConfig:
     feat_dim: int = 12
     feat_std: float = 0.1
     blob_center_range: float = 1.0
-    camera: str = "sphere"          # "sphere" (radius cam_radius) or "circle" (z=0, radius cam_radius)
+    camera: str = "sphere"          # "sphere" (radius cam_radius), "circle" (z=0, radius cam_radius)
+                                    # or "forward" (pinhole cameras near z=0 looking down -z)
     cam_radius: float = 4.0
     jitter: float = 0.3
     shell: tuple | None = None      # (r_lo, r_hi, raw) background shell in contracted L-inf radius
+    dims: tuple | None = None       # (Gx, Gy, Gz) when the grid is not cubic
+    focal: float = 400.0            # "forward": pinhole focal length and image size (pixels)
+    img_w: int = 400
+    img_h: int = 400
 
 
 CFG1 = SceneConfig("small_64", grid=64, bbox_min=-2.0, bbox_max=2.0, n_rays=2048,
@@ -72,12 +77,22 @@ CFG3 = SceneConfig("unbounded_320", grid=320, bbox_min=-2.0, bbox_max=2.0, n_ray
                    camera="circle", cam_radius=1.0, shell=(1.6, 1.9, 6.0))
 CFG4 = dataclasses.replace(CFG2, name="dvgo_160_bf16", n_rays=16384)
 CFG5 = dataclasses.replace(CFG2, name="dvgo_160_proposal", n_rays=16384)
+# Forward-facing capture (Sec. 5.2): the grid lives in normalized device
+# coordinates, D = 256 depth layers of 384 x 384 (multiplane-image layout).
+CFG6 = SceneConfig("forward_facing_384", grid=384, dims=(384, 384, 256), bbox_min=-1.0, bbox_max=1.0,
+                   n_rays=8192, n_blobs=24, sigma_lo=0.12, sigma_hi=0.3, blob_center_range=0.7,
+                   camera="forward", cam_radius=0.1, jitter=0.0)
 
-CONFIGS = {c.name: c for c in (CFG1, CFG2, CFG3, CFG4, CFG5)}
+CONFIGS = {c.name: c for c in (CFG1, CFG2, CFG3, CFG4, CFG5, CFG6)}
 
 
-def grid_axis(cfg: SceneConfig) -> np.ndarray:
-    return np.linspace(cfg.bbox_min, cfg.bbox_max, cfg.grid, dtype=np.float64)
+def grid_dims(cfg: SceneConfig) -> tuple:
+    """Grid points per axis (x, y, z)."""
+    return tuple(cfg.dims) if cfg.dims is not None else (cfg.grid,) * 3
+
+
+def grid_axis(cfg: SceneConfig, axis: int = 0) -> np.ndarray:
+    return np.linspace(cfg.bbox_min, cfg.bbox_max, grid_dims(cfg)[axis], dtype=np.float64)
 
 
 def density_grid(cfg: SceneConfig, seed: int = 0) -> np.ndarray:
@@ -86,8 +101,7 @@ def density_grid(cfg: SceneConfig, seed: int = 0) -> np.ndarray:
     rb = st[_S_BLOB]
     c = rb.uniform(-cfg.blob_center_range, cfg.blob_center_range, (cfg.n_blobs, 3))
     s = rb.uniform(cfg.sigma_lo, cfg.sigma_hi, cfg.n_blobs)
-    ax = grid_axis(cfg)
-    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    Z, Y, X = np.meshgrid(grid_axis(cfg, 2), grid_axis(cfg, 1), grid_axis(cfg, 0), indexing="ij")
     D = np.full(X.shape, cfg.blob_bias, dtype=np.float64)
     amp = cfg.blob_peak - cfg.blob_bias      # an isolated blob peaks at blob_peak
     for b in range(cfg.n_blobs):
@@ -104,9 +118,9 @@ def density_grid(cfg: SceneConfig, seed: int = 0) -> np.ndarray:
 def feature_grid(cfg: SceneConfig, seed: int = 0) -> np.ndarray:
     """Feature grid, float32, dense [Z][Y][X][C] (channel innermost)."""
     st = _streams(seed)
-    g = cfg.grid
+    gx, gy, gz = grid_dims(cfg)
     return np.ascontiguousarray(
-        st[_S_FEAT].normal(0.0, cfg.feat_std, (g, g, g, cfg.feat_dim)).astype(np.float32))
+        st[_S_FEAT].normal(0.0, cfg.feat_std, (gz, gy, gx, cfg.feat_dim)).astype(np.float32))
 
 
 def _orthonormal_pair(d: np.ndarray):
@@ -129,11 +143,25 @@ def rays(cfg: SceneConfig, seed: int = 0, n_rays: int | None = None):
     "sphere": origins uniform on a sphere of radius cam_radius, aimed at the
     origin; "circle": origins on the circle of radius cam_radius in z=0.
     Each direction is then rotated by two angles U[-jitter, jitter] about two
-    axes orthogonal to it.
+    axes orthogonal to it.  "forward": pinhole cameras with centres uniform in
+    the disc of radius cam_radius in z = 0, all looking down -z; each ray goes
+    through a pixel (u, v) uniform over the img_w x img_h image, direction
+    ((u - w/2)/f, -(v - h/2)/f, -1) normalised.
     """
     R = cfg.n_rays if n_rays is None else n_rays
     st = _streams(seed)
     ro = st[_S_RAY_O]
+    if cfg.camera == "forward":
+        rr = cfg.cam_radius * np.sqrt(ro.uniform(0, 1, R))
+        phi = ro.uniform(0, 2 * math.pi, R)
+        o = np.stack([rr * np.cos(phi), rr * np.sin(phi), np.zeros(R)], 1)
+        rj = st[_S_RAY_J]
+        u = rj.uniform(0, cfg.img_w, R)
+        v = rj.uniform(0, cfg.img_h, R)
+        d = np.stack([(u - 0.5 * cfg.img_w) / cfg.focal, -(v - 0.5 * cfg.img_h) / cfg.focal, -np.ones(R)], 1)
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        return (np.ascontiguousarray(o.astype(np.float32)),
+                np.ascontiguousarray(d.astype(np.float32)))
     if cfg.camera == "sphere":
         o = ro.normal(size=(R, 3))
         o /= np.linalg.norm(o, axis=1, keepdims=True)
@@ -235,6 +263,10 @@ class RenderParams:
     tv_delta: float = 1.0
     mask_thres: float | None = None     # occupancy mask alpha threshold (None: no mask)
     contracted: bool = False
+    ndc: bool = False               # forward-facing: NDC warp, samples on the depth layers
+    ndc_fx: float = 0.0             # focal / (img_w / 2)
+    ndc_fy: float = 0.0             # focal / (img_h / 2)
+    ndc_near: float = 1.0
     contract_b: float = 1.0
     contract_p_inf: bool = True
     step_c: float = 0.0
@@ -250,6 +282,15 @@ def voxel_size(cfg: SceneConfig) -> np.float32:
 
 
 def render_params(cfg: SceneConfig) -> RenderParams:
+    if cfg.camera == "forward":
+        # Sec. 5.2 implementation details: step of one layer, TV weights 1e-5
+        # (density) and 1e-6 (features), distortion weight 1e-2; the alpha
+        # interval is the step in voxel (layer) units
+        D = grid_dims(cfg)[2]
+        return RenderParams(near=0.0, far=0.0, step=1.0, step_offset=0.0, use_slab=False, max_steps=D,
+                            interval=1.0, tv_w_density=1e-5, tv_w_feature=1e-6, mask_thres=1e-4,
+                            ndc=True, ndc_fx=float(np.float32(cfg.focal / (0.5 * cfg.img_w))),
+                            ndc_fy=float(np.float32(cfg.focal / (0.5 * cfg.img_h))), ndc_near=1.0)
     vs = voxel_size(cfg)
     if cfg.grid == 64:
         step = np.float32(4.0 / 128)

@@ -67,7 +67,8 @@ class Trainer:
         # "f32": colour MLP in FP32 on the CUDA cores; "f32tc": FP32-accurate on
         # the tensor cores (split-FP16 operands); "bf16": BF16 grids and MLP
         self.precision = {"f32": L.F32, "f32tc": L.F32_TC, "bf16": L.BF16}[precision]
-        G = [cfg.grid] * 3
+        from .synth import grid_dims
+        G = list(grid_dims(cfg))
         self.G = G
         self.gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, G)
         self.shift = alpha_shift(rp.alpha_init)
@@ -86,7 +87,10 @@ class Trainer:
             L.build_mask(grid, dt, self.gd, self.shift, rp.interval, rp.mask_thres, self.mask)
         # sampler
         sd = L.SamplerDesc()
-        if rp.contracted:
+        if rp.ndc:
+            sd.mode, sd.step, sd.max_steps = 2, rp.step, rp.max_steps
+            sd.ndc_fx, sd.ndc_fy, sd.ndc_near = rp.ndc_fx, rp.ndc_fy, rp.ndc_near
+        elif rp.contracted:
             sd.mode, sd.near, sd.max_steps = 1, rp.near, rp.max_steps
             sd.contract_b, sd.p_inf, sd.step_c = rp.contract_b, int(rp.contract_p_inf), rp.step_c
         else:

@@ -17,6 +17,9 @@ def shift32(alpha_init):
 
 
 def sample(cfg, rp, o, d, mask):
+    if rp.ndc:
+        return oracle.sample_rays_ndc(o, d, cfg.bbox_min, cfg.bbox_max, synth.grid_dims(cfg), rp.ndc_fx,
+                                      rp.ndc_fy, rp.ndc_near, rp.step, rp.max_steps, mask)
     if rp.contracted:
         return oracle.sample_rays_contracted(o, d, rp.contract_b, rp.contract_p_inf, rp.near,
                                              rp.step_c, rp.max_steps, cfg.bbox_min, cfg.bbox_max,

@@ -91,8 +91,9 @@ def mlp_grad_errors(dims, params, x, g_out, gpu_gp, tau, out_sigmoid=True, names
 
 def cell_voxels(cfg, xyz):
     """Dense indices (z, y, x) of the 8 corners of each point's trilinear cell."""
-    u = (xyz.astype(np.float64) - cfg.bbox_min) / (cfg.bbox_max - cfg.bbox_min) * (cfg.grid - 1)
-    i0 = np.clip(np.floor(np.clip(u, 0, cfg.grid - 1)).astype(int), 0, cfg.grid - 2)
+    G = np.array(synth.grid_dims(cfg))
+    u = (xyz.astype(np.float64) - cfg.bbox_min) / (cfg.bbox_max - cfg.bbox_min) * (G - 1)
+    i0 = np.clip(np.floor(np.clip(u, 0, G - 1)).astype(int), 0, G - 2)
     out = []
     for dz in (0, 1):
         for dy in (0, 1):

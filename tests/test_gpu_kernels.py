@@ -296,9 +296,12 @@ def test_build_mask_bit_exact(L):
 def _gpu_sample(L, cfg, rp, o, d, mask=None):
     R = o.shape[0]
     S_cap = R * rp.max_steps
-    gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, [cfg.grid] * 3)
+    gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, list(synth.grid_dims(cfg)))
     sd = L.SamplerDesc()
-    if rp.contracted:
+    if rp.ndc:
+        sd.mode, sd.step, sd.max_steps = 2, rp.step, rp.max_steps
+        sd.ndc_fx, sd.ndc_fy, sd.ndc_near = rp.ndc_fx, rp.ndc_fy, rp.ndc_near
+    elif rp.contracted:
         sd.mode, sd.near, sd.max_steps = 1, rp.near, rp.max_steps
         sd.contract_b, sd.p_inf, sd.step_c = rp.contract_b, int(rp.contract_p_inf), rp.step_c
     else:
@@ -328,9 +331,16 @@ def _check_samples(got, ref):
     assert rel_err(got["s_len"], ref.s_len) < TOL32
 
 
-@pytest.mark.parametrize("name", ["small_64", "dvgo_160", "unbounded_320"])
+def _forward_facing_small():
+    """The forward-facing workload on a 96 x 96 x 64 layer stack (the oracle's
+    passes over the full 384^2 x 256 stack would take minutes)."""
+    import dataclasses
+    return dataclasses.replace(synth.CFG6, name="forward_facing_96", grid=96, dims=(96, 96, 64))
+
+
+@pytest.mark.parametrize("name", ["small_64", "dvgo_160", "unbounded_320", "forward_facing_96"])
 def test_sampler_bit_exact(L, name):
-    cfg = synth.CONFIGS[name]
+    cfg = _forward_facing_small() if name == "forward_facing_96" else synth.CONFIGS[name]
     rp = synth.render_params(cfg)
     o, d = synth.rays(cfg)            # full ray count of the workload
     mask_np = mask_t = None

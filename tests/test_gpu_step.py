@@ -119,6 +119,15 @@ def test_step_low_weight_cull(T):
     assert psnr > 50
 
 
+def test_step_forward_facing_ndc(T):
+    """Forward-facing capture: NDC warp and depth-layer sampling (96 x 96 x 64
+    layers standing in for 384^2 x 256), the full step against the oracle."""
+    cfg = dataclasses.replace(synth.CFG6, grid=96, dims=(96, 96, 64))
+    gpu, fb, opt, cfg, rp, P = _run(T, cfg, 512, "f32tc", tv_dense=False, ray_stride=8)
+    assert fb["live"].sum() > 5000
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
+
+
 def test_step_unbounded_contracted(T):
     # the 320^3 grids of the workload are exercised by the benchmark; a 96^3
     # grid keeps the FP64 oracle's TV/Adam pass small here

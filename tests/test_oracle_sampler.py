@@ -131,3 +131,99 @@ def test_contracted_step_is_constant_in_contracted_space(orc, p_inf):
         # the march follows the contraction of a straight world ray
         if p_inf:
             assert np.all(cn <= 2.0)
+
+
+# ------------------------------------------------ forward-facing (NDC) sampling
+def _ndc_cfg():
+    import dataclasses
+    cfg = dataclasses.replace(synth.CFG6, dims=(48, 40, 32), grid=48)
+    return cfg, synth.render_params(cfg)
+
+
+def _ndc_sample(orc, cfg, rp, o, d, mask=None):
+    return orc.sample_rays_ndc(o, d, cfg.bbox_min, cfg.bbox_max, synth.grid_dims(cfg), rp.ndc_fx,
+                               rp.ndc_fy, rp.ndc_near, rp.step, rp.max_steps, mask)
+
+
+def test_ndc_samples_lie_on_the_world_ray(orc):
+    """Mapping every sample back to world space (the inverse of the NDC warp,
+    written from the pinhole projection: world depth z = 2 near/(z' - 1),
+    x = -x' z / fx, y = -y' z / fy) gives points on the original ray, at
+    increasing depth."""
+    cfg, rp = _ndc_cfg()
+    o, d = synth.rays(cfg, n_rays=300)
+    s = _ndc_sample(orc, cfg, rp, o, d)
+    assert s.S > 1000
+    for r in range(300):
+        a, b = s.ray_off[r], s.ray_off[r + 1]
+        if b == a:
+            continue
+        p = s.xyz[a:b].astype(np.float64)
+        inf = p[:, 2] == 1.0          # the last layer is the plane at infinity: the vanishing point
+        if inf.any():
+            van = [-rp.ndc_fx * d[r, 0] / d[r, 2], -rp.ndc_fy * d[r, 1] / d[r, 2]]
+            assert np.allclose(p[inf, :2], van, atol=1e-5)
+            p = p[~inf]
+        zw = 2.0 * rp.ndc_near / (p[:, 2] - 1.0)
+        xw = -p[:, 0] * zw / rp.ndc_fx
+        yw = -p[:, 1] * zw / rp.ndc_fy
+        w = np.stack([xw, yw, zw], 1)
+        ro, rd = o[r].astype(np.float64), d[r].astype(np.float64)
+        v = w - ro
+        off_line = np.linalg.norm(v - (v @ rd)[:, None] * rd, axis=1)
+        assert np.all(off_line <= 1e-4 * np.abs(zw)), (r, off_line.max())
+        assert np.all(np.diff(zw) < 0)            # further down -z, layer after layer
+        assert np.all(np.diff(s.step_k[a:b]) > 0)
+    assert s.S > 0
+
+
+def test_ndc_central_ray_crosses_every_layer(orc):
+    cfg, rp = _ndc_cfg()
+    Gz = synth.grid_dims(cfg)[2]
+    o = np.zeros((2, 3), np.float32)
+    d = np.array([[0, 0, -1], [0, 0, 1]], np.float32)      # the second looks away: no samples
+    s = _ndc_sample(orc, cfg, rp, o, d)
+    assert np.diff(s.ray_off).tolist() == [Gz, 0]
+    assert np.array_equal(s.step_k, np.arange(Gz))
+    assert np.all(s.xyz[:, :2] == 0)
+    dz = np.float32(np.float32(2.0) / np.float32(Gz - 1))
+    z = (np.float32(-1.0) + (np.arange(Gz).astype(np.float32) * np.float32(rp.step)) * dz).astype(np.float32)
+    assert np.array_equal(s.xyz[:, 2], z)
+    assert s.xyz[0, 2] == -1.0                      # the near plane maps to z' = -1
+    assert np.allclose(s.s_mid, (np.arange(Gz) + 0.5) / Gz) and np.allclose(s.s_len, 1.0 / Gz)
+
+
+def test_ndc_box_and_mask_culling(orc):
+    """Crossings outside the box are dropped; with a mask, exactly those whose
+    nearest grid point (FP64, ties excluded) has the mask on are kept."""
+    cfg, rp = _ndc_cfg()
+    G = synth.grid_dims(cfg)
+    o, d = synth.rays(cfg, n_rays=200)
+    # widen the field of view beyond the image so that some crossings leave the box
+    d = d.copy()
+    d[:, :2] *= 1.6
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d.astype(np.float32)
+    full = _ndc_sample(orc, cfg, rp, o, d)
+    assert np.all(np.abs(full.xyz) <= 1.0)
+    assert np.sum(np.diff(full.ray_off) < G[2]) > 20
+    rng = np.random.default_rng(5)
+    mask = (rng.uniform(size=(G[2], G[1], G[0])) < 0.5).astype(np.uint8)
+    cut = _ndc_sample(orc, cfg, rp, o, d, mask)
+    u = (full.xyz.astype(np.float64) + 1.0) / 2.0 * (np.array(G) - 1)
+    near = np.floor(u + 0.5).astype(int)
+    tie = np.any(np.abs(u - np.round(u) - 0.5 * np.sign(u - np.round(u))) < 1e-4, axis=1) & \
+        np.any(np.abs(np.abs(u - np.floor(u)) - 0.5) < 1e-4, axis=1)
+    on = mask[near[:, 2], near[:, 1], near[:, 0]] == 1
+    keep_full = set()
+    for r in range(200):
+        for i in range(full.ray_off[r], full.ray_off[r + 1]):
+            if on[i] and not tie[i]:
+                keep_full.add((r, int(full.step_k[i])))
+    got = set()
+    for r in range(200):
+        for i in range(cut.ray_off[r], cut.ray_off[r + 1]):
+            got.add((r, int(cut.step_k[i])))
+    amb = {(r, int(full.step_k[i])) for r in range(200) for i in range(full.ray_off[r], full.ray_off[r + 1])
+           if tie[i]}
+    assert keep_full <= got and got - keep_full <= amb
