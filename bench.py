@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dvgo_160")
+    ap.add_argument("--rays", type=int, default=0,
+                    help="rays per step (0: the workload's own count; smaller for profiler captures)")
     ap.add_argument("--tv-dense", action="store_true")
     ap.add_argument("--mlp", default="f32tc", choices=["f32tc", "f32"],
                     help="colour MLP of the FP32 workloads: tensor cores with split-FP16 "
@@ -237,7 +239,7 @@ def reduce_over_ranks(total_ms, e2e_ms, samples, device):
     return float(t[0]), float(t[1]), float(s[0])
 
 
-def prepare(workload, mlp, rank, n_batches):
+def prepare(workload, mlp, rank, n_batches, rays=0):
     """Trainer of a workload and its ray batches resident in HBM (seed =
     1000 * rank + batch), with the sample and live-sample count of each batch
     (deterministic: the occupancy mask is fixed).  The trainer is re-created
@@ -245,6 +247,9 @@ def prepare(workload, mlp, rank, n_batches):
     import torch
     from paper_2206_05085_gb300 import synth, train
     cfg = synth.CONFIGS[workload]
+    if rays:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, n_rays=int(rays))
     rp = synth.render_params(cfg)
     prec = precision_of(workload, mlp)
     D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
@@ -323,7 +328,7 @@ def run_ours(args, rank, world):
     from paper_2206_05085_gb300 import build as B
     B.build()
     torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
-    w = prepare(args.workload, args.mlp, rank, args.warmup + args.steps)
+    w = prepare(args.workload, args.mlp, rank, args.warmup + args.steps, args.rays)
     tr, batches, host_batches = w["tr"], w["batches"], w["host_batches"]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -421,7 +426,7 @@ MMA_CEILING = {("f32tc", "fwd"): 1 / 3, ("f32tc", "bwd"): 1 / 3, ("bf16", "fwd")
 KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1}
 
 
-def roofline(res, peaks):
+def roofline(res, peaks, mk=None):
     """Roofline record of the dominant kernel (largest share of the step).
     The kernel is timed per call, alone on the stream: the burst tensor peak
     is its denominator."""
@@ -451,8 +456,13 @@ def roofline(res, peaks):
                    frac=round(achieved / peak, 4), flop_per_unit=per, units=S_live,
                    peak_source=peak_src)
     else:
-        out.update(bound="hbm", achieved=None, peak=peaks.get("hbm_gbs", 6701.5), unit="GB/s",
-                   frac=None)
+        # a memory kernel: its algorithmic bytes (memory_kernels) over its time
+        peak = peaks.get("hbm_gbs", 6701.5)
+        b = (mk or {}).get("kernels", {}).get(name + "#0", {}).get("bytes")
+        ach = b / (ms * 1e-3) / 1e9 if b else None
+        out.update(bound="hbm", achieved=round(ach, 1) if ach else None, peak=peak, unit="GB/s",
+                   frac=round(ach / peak, 4) if ach else None, bytes_per_launch=b,
+                   peak_source="hbm_gbs of measured" if "hbm_gbs" in peaks else "6701.5 GB/s (fallback)")
     out["traffic"] = traffic_for(name, prec, S_live)
     out["ms_per_call"] = round(ms, 4)
     out["share"] = round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)
@@ -648,6 +658,27 @@ def forms_report(args):
         "ms_per_step_cuda_cores": round(ms["f32"], 3), "ms_per_step_tensor_cores": round(ms["f32tc"], 3)}
     p_plain = psnr(colors["f32tc"], gt)
     p_bf = psnr(colors["bf16"], gt)
+    # the low-weight cull of the colour query (w < 1e-4), and the progressive mask update
+    trc = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision="f32tc", w_min=1e-4)
+    ms_cull = timed(lambda: trc.step(to, td, tt))
+    del trc
+    trm = train.Trainer(cfg, rp, D, Fg, P, n_rays=cfg.n_rays, precision="f32tc", mask_update=True)
+    ms_mask = timed(lambda: trm.step(to, td, tt))
+    del trm
+    trc = train.Trainer(cfg, rp, D, Fg, P, n_rays=Rq, precision="f32tc", w_min=1e-4)
+    trc.forward(qo, qd, qt)
+    c_cull = trc.color.clone()
+    n_q, n_l = int(trc.query_count.item()), int(trc.live_count.item())
+    del trc
+    torch.cuda.empty_cache()
+    out["low_weight_cull"] = {
+        "w_min": 1e-4, "colour_queries": n_q, "live_samples": n_l,
+        "psnr_vs_full_render_db": round(psnr(c_cull, colors["f32tc"]), 2),
+        "psnr_vs_ground_truth_db": round(psnr(c_cull, gt), 3),
+        "psnr_gap_db": round(abs(psnr(c_cull, gt) - psnr(colors["f32tc"], gt)), 4),
+        "ms_per_step_8192_rays": round(ms_cull, 3)}
+    out["mask_update"] = {"ms_per_step_8192_rays": round(ms_mask, 3),
+                          "without_ms_per_step_8192_rays": round(ms["f32tc"], 3)}
     out["bf16"] = {"psnr_vs_fp32_render_db": round(psnr(colors["bf16"], colors["f32tc"]), 2),
                    "psnr_vs_ground_truth_db": round(p_bf, 3),
                    "fp32_psnr_vs_ground_truth_db": round(p_plain, 3),
@@ -892,23 +923,27 @@ def main():
         "live_samples_per_s": round(res["live"] / (res["total_ms"] * 1e-3), 1),
         "device_status": res["status"],
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": roofline(res, peaks),
+        "roofline": roofline(res, peaks, memory_kernels(res, peaks)),
         "memory_kernels": memory_kernels(res, peaks),
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in res["kt"].items()},
         "clocks": res["clocks"],
     }
-    if not args.no_secondary and world == 1 and args.workload != "unbounded_320":
-        # the 320^3 contracted workload: grids far larger than L2 (1.57 GB per
-        # FP32 feature array), the HBM-bound case of the memory kernels
-        sec = run_secondary("unbounded_320", args.mlp)
+    # second workloads, timed the same way: the 320^3 contracted scene (grids far
+    # larger than L2, 1.57 GB per FP32 feature array: the HBM-bound case of the
+    # memory kernels) and the forward-facing 384^2 x 256 layer stack (NDC sampling)
+    for name in (() if args.no_secondary or world > 1 else ("unbounded_320", "forward_facing_384")):
+        if name == args.workload:
+            continue
+        sec = run_secondary(name, args.mlp)
         sec["l2_gbs"] = res["l2_gbs"]
-        line["unbounded_320"] = {
+        line[name] = {
             "value": round(sec["samples"] / (sec["total_ms"] * 1e-3), 1), "unit": "ray-samples/s",
             "live_samples_per_s": round(sec["live"] / (sec["total_ms"] * 1e-3), 1),
             "ms_per_step": round(sec["total_ms"] / sec["steps"], 4), "steps": sec["steps"], "warmup": 3,
             "samples_per_step": sec["S"], "live_samples_per_step": sec["S_live"],
             "device_status": sec["status"],
-            "roofline": roofline(sec, peaks), "memory_kernels": memory_kernels(sec, peaks),
+            "roofline": roofline(sec, peaks, memory_kernels(sec, peaks)),
+            "memory_kernels": memory_kernels(sec, peaks),
             "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in sec["kt"].items()}}
     if not args.no_forms and world == 1:
         line["forms"] = forms_report(args)
@@ -916,7 +951,8 @@ def main():
         line["cpu_baseline"] = cpu_baseline(args.workload)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
         line["errors_vs_oracle"] = oracle_errors(args.mlp)
-    bad = [v for v in (line["device_status"], line.get("unbounded_320", {}).get("device_status", 0)) if v]
+    bad = [v for v in [line["device_status"]] + [line.get(k, {}).get("device_status", 0)
+                                                  for k in ("unbounded_320", "forward_facing_384")] if v]
     if bad:
         # a kernel reported a range or wait failure: the numbers above are not valid
         line["error"] = f"device status {bad[0]} after the timed steps"

@@ -13,10 +13,11 @@
  *  - Return value: DVGO_OK (0) or a negative dvgo_status.  Arguments are
  *    validated on the host before any launch; invalid arguments launch
  *    nothing.  DVGO_ERR_CUDA reports a launch error (cudaGetLastError).
- *  - No call allocates or frees memory and no call synchronises.  Every
- *    buffer is caller-owned device memory unless marked "host".  Scratch is
- *    passed as (ws, ws_bytes); the required size comes from the matching
- *    *_workspace_size call.
+ *  - No call allocates or frees memory, and no call synchronises except
+ *    dvgo_device_status (a host read of the device status word, which must
+ *    wait for the stream).  Every buffer is caller-owned device memory unless
+ *    marked "host".  Scratch is passed as (ws, ws_bytes); the required size
+ *    comes from the matching *_workspace_size call.
  *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
  *  - Ragged sample lists are CSR: ray_off[R+1] int64, non-decreasing,
  *    ray_off[0] = 0; the samples of ray r are [ray_off[r], ray_off[r+1]).
@@ -32,6 +33,24 @@
  *    order of the 512 voxels inside a brick, channels innermost.
  *    dvgo_grid_pack/unpack convert from/to the dense layout
  *    g[((z*Gy + y)*Gx + x)*C + c].
+ *
+ * Which calls are the operations of the method, and which are fusions:
+ *  - The operations (one call each, each the plain form of one step):
+ *    dvgo_sample_rays, dvgo_sample_grid_fwd / _bwd, dvgo_alpha_weights_fwd,
+ *    dvgo_composite_fwd / _bwd, dvgo_composite_rgb_fwd,
+ *    dvgo_distortion_fwd / _bwd, dvgo_rgb_loss, dvgo_rgbnet_fwd / _bwd,
+ *    dvgo_tv_add_grad, dvgo_adam_step, dvgo_grid_adam_step, dvgo_build_mask,
+ *    dvgo_update_mask, dvgo_grid_resample, dvgo_live_samples, and the
+ *    learned proposal (dvgo_proposal_*, dvgo_compact_samples).
+ *  - Fusions the training step uses, each equal to a sequence of the calls
+ *    above (stated at each): dvgo_density_alpha_fwd, dvgo_sample_grid_bwd2,
+ *    dvgo_composite_distortion_fwd / _bwd,
+ *    dvgo_composite_distortion_loss_fwd / _fwd_bwd, dvgo_tv_add_grad_multi,
+ *    dvgo_adam_step_multi / _multi_dev, dvgo_touched_compact.
+ *  - Variants: dvgo_live_samples_cull (low-weight colour-query cull),
+ *    dvgo_sample_rays_noalloc (no workspace).
+ *  - Helpers: grid geometry, workspace sizes, dvgo_device_status, and one
+ *    measurement aid that is no step of the method (dvgo_read_probe, last).
  */
 #ifndef DVGO_H_
 #define DVGO_H_
@@ -66,7 +85,7 @@ typedef struct {
   int32_t G[3];
 } dvgo_grid_desc;
 
-/* Ray sampler (Sec. 3 "Re-implement rendering utils", Sec. 5.2, Sec. 5.3).
+/* Ray sampler (Sec. 3 "Re-implement rendering utils", Sec. 5.3, Sec. 5.4).
  * mode 0 (bbox): t_k = t_lo + (k + step_offset) step, k < n, where
  *   [t_lo, t_hi] = [near, far], clipped to the ray/bbox slab when use_slab,
  *   n = min(max_steps, ceil((t_hi - t_lo)/step - step_offset)); a sample
@@ -81,7 +100,7 @@ typedef struct {
  *   contracted points for k < max_steps while their contracted p-norm
  *   radius stays below (1 + b) - step_c; s_mid = (k + 0.5)/max_steps,
  *   s_len = 1/max_steps.
- * mode 2 (forward-facing, Sec. 5.2 "Points parameterization and sampling"):
+ * mode 2 (forward-facing, Sec. 5.3 "Points parameterization and sampling"):
  *   each world ray (d_z < 0, the camera looking down -z) is moved to the
  *   plane z = -ndc_near and warped to normalized device coordinates, o' =
  *   (-fx o_x/o_z, -fy o_y/o_z, 1 + 2 ndc_near/o_z), d' = (-fx (d_x/d_z -
@@ -541,8 +560,10 @@ int dvgo_adam_step_multi_dev(const dvgo_adam_param* params, int32_t count, float
  * set (DVGO_ERR_TIMEOUT) instead of hanging.  Synchronises the stream. */
 int dvgo_device_status(void* stream);
 
-/* Measurement aid (not a step of the method): sink_len blocks of 512 threads
- * each read the first bytes/16 float4 of buf (16-byte aligned) reps times and
+/* ------------------------------------------------------ measurement aid */
+/* Not a step of the method (the benchmark's L2 read-rate probe): sink_len
+ * blocks of 512 threads each read the first bytes/16 float4 of buf (16-byte
+ * aligned) reps times and
  * add a checksum into sink[block] (f32 [sink_len], caller-zeroed).  A buffer
  * well inside L2 gives the L2 read rate the gathers' corner reads see. */
 int dvgo_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink, int32_t sink_len,

@@ -142,7 +142,7 @@ def _vec3i(v):
 
 # --------------------------------------------------------------------------
 def alpha_shift(alpha_init: float) -> float:
-    """shift = log(1/(1 - alpha_init) - 1) (alpha_init of Sec. 5.3)."""
+    """shift = log(1/(1 - alpha_init) - 1) (alpha_init of Sec. 5.4)."""
     return lib().or_alpha_shift(alpha_init)
 
 

@@ -163,7 +163,7 @@ OR_API int64_t or_sample_rays_bbox(const float* o, const float* d, int64_t R,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Forward-facing scenes (Sec. 5.2 "Points parameterization and sampling"):  */
+/* Forward-facing scenes (Sec. 5.3 "Points parameterization and sampling"):  */
 /* NeRF's normalized device coordinates warp the frustum in front of a       */
 /* camera looking down -z to a box; the grid is D depth layers over the      */
 /* box's z extent (multiplane images) and the samples are the ray's          */
@@ -234,7 +234,7 @@ OR_API int64_t or_sample_rays_ndc(const float* o, const float* d, int64_t R, con
 }
 
 /* ------------------------------------------------------------------------ */
-/* Unbounded scenes, Eq. (ub) of Sec. 5.3:                                   */
+/* Unbounded scenes, Eq. (ub) of Sec. 5.4:                                   */
 /*   x' = x                                      if ||x||_p <= 1             */
 /*   x' = (1 + b - b/||x||_p) (x / ||x||_p)      otherwise,  p in {2, inf}.  */
 /* FP64 form, used by the pins.                                              */
@@ -255,7 +255,7 @@ OR_API void or_contract(const double* x, int64_t n, double b, int p_inf, double*
   }
 }
 
-/* Sampling with the step measured in the contracted space (Sec. 5.3).       */
+/* Sampling with the step measured in the contracted space (Sec. 5.4).       */
 /* Reading: march in world space, x_{k+1} = x_k + h_k d, where h_k is the    */
 /* world length that advances the contracted point by step_c to first order: */
 /* h_k = step_c / ||J(x_k) d||_2, J the Jacobian of Eq. (ub).  With          */

@@ -1,5 +1,5 @@
 // Ray sampling (Sec. 3 "Re-implement rendering utils": sample only inside
-// the scene bbox; Sec. 1 occupancy mask; Sec. 5.3 contracted step for
+// the scene bbox; Sec. 1 occupancy mask; Sec. 5.4 contracted step for
 // unbounded scenes) and the live-sample list used after early stop.
 //
 // Every decision that creates or drops a sample is IEEE FP32 with explicit

@@ -77,7 +77,7 @@ CFG3 = SceneConfig("unbounded_320", grid=320, bbox_min=-2.0, bbox_max=2.0, n_ray
                    camera="circle", cam_radius=1.0, shell=(1.6, 1.9, 6.0))
 CFG4 = dataclasses.replace(CFG2, name="dvgo_160_bf16", n_rays=16384)
 CFG5 = dataclasses.replace(CFG2, name="dvgo_160_proposal", n_rays=16384)
-# Forward-facing capture (Sec. 5.2): the grid lives in normalized device
+# Forward-facing capture (Sec. 5.3): the grid lives in normalized device
 # coordinates, D = 256 depth layers of 384 x 384 (multiplane-image layout).
 CFG6 = SceneConfig("forward_facing_384", grid=384, dims=(384, 384, 256), bbox_min=-1.0, bbox_max=1.0,
                    n_rays=8192, n_blobs=24, sigma_lo=0.12, sigma_hi=0.3, blob_center_range=0.7,
@@ -283,7 +283,7 @@ def voxel_size(cfg: SceneConfig) -> np.float32:
 
 def render_params(cfg: SceneConfig) -> RenderParams:
     if cfg.camera == "forward":
-        # Sec. 5.2 implementation details: step of one layer, TV weights 1e-5
+        # Sec. 5.3 implementation details: step of one layer, TV weights 1e-5
         # (density) and 1e-6 (features), distortion weight 1e-2; the alpha
         # interval is the step in voxel (layer) units
         D = grid_dims(cfg)[2]

@@ -31,7 +31,7 @@ FEAT = 12
 
 
 def alpha_shift(alpha_init: float) -> float:
-    """shift = log(1/(1 - alpha_init) - 1), rounded to FP32 (Sec. 5.3 alpha_init)."""
+    """shift = log(1/(1 - alpha_init) - 1), rounded to FP32 (Sec. 5.4 alpha_init)."""
     return float(np.float32(math.log(1.0 / (1.0 - alpha_init) - 1.0)))
 
 

@@ -1,6 +1,7 @@
 """Pins of the oracle's ray samplers: bbox-limited sampling (Sec. 3
 "Re-implement rendering utils") with occupancy culling (Sec. 1), and the
-contracted-space sampling of unbounded scenes (Sec. 5.3, Eq. ub)."""
+contracted-space sampling of unbounded scenes (Sec. 5.4, Eq. ub), and
+the depth-layer sampling of forward-facing scenes (Sec. 5.3)."""
 import numpy as np
 import pytest
 
