@@ -232,3 +232,94 @@ def test_full_size_step_sampled_outputs(T):
     zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
     keep = zmin >= 1e-6
     assert rel_err(g_k0[rows][live][keep], fb["g_k0"][keep] * scale) < 1e-5
+
+
+def _exclusive_voxels(cfg, xyz_all, live_all, ray_all, sel):
+    """Dense voxel indices reached by the trilinear corners of the live samples
+    of the rays in sel and by no other ray's live samples (on those voxels the
+    batch's grid gradient is the selected rays' gradient alone)."""
+    from step_parity import cell_voxels
+    G = np.array(synth.grid_dims(cfg))
+    pts = xyz_all[live_all]
+    rays = ray_all[live_all]
+    v = cell_voxels(cfg, pts)                          # [8 n, 3] (corner-major)
+    lin = (v[:, 0] * G[1] + v[:, 1]) * G[0] + v[:, 2]
+    mine = np.isin(np.tile(rays, 8), sel)
+    return np.setdiff1d(np.unique(lin[mine]), np.unique(lin[~mine]))
+
+
+@pytest.mark.parametrize("name", ["dvgo_160", "unbounded_320"])
+def test_full_size_grid_gradients_and_adam(T, name):
+    """At the benchmark's full size (the workload's grids and ray count): the
+    per-ray and per-sample outputs of 48 sampled rays, and the grid gradients
+    and the parameters after TV + Adam on the voxels that only those rays
+    reach, against the oracle run on those rays (its gradients rescaled from
+    1/48 to the batch's 1/R)."""
+    import oracle
+    from oracle_step import forward_backward, optimizer
+    cfg = synth.CONFIGS[name]
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg, seed=0)
+    tgt = synth.target_rgb(cfg, seed=0)
+    R = cfg.n_rays
+    tr = T.Trainer(cfg, rp, D, Fg, P, n_rays=R, precision="f32tc")
+    to, td, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (o, d, tgt))
+    tr.forward(to, td, tt, tail_adjoint=True)
+    tr.backward(td, tail_done=True)
+    torch.cuda.synchronize()
+    ray_off = tr.ray_off.cpu().numpy()
+    S = int(ray_off[-1])
+    n_live = tr.n_live.cpu().numpy()
+    xyz, ray_id = host(tr.xyz[:S]), tr.ray_id[:S].cpu().numpy()
+    live_all = np.zeros(S, bool)
+    for r in range(R):
+        live_all[ray_off[r]:ray_off[r] + n_live[r]] = True
+    color, L_r = host(tr.color), host(tr.L_r)
+    w, rgb, g_raw, g_k0 = (host(x[:S]) for x in (tr.w, tr.rgb, tr.g_raw, tr.g_k0))
+    g_d = host(tr.dense(tr.density, "g"))[..., 0]
+    g_f = host(tr.dense(tr.feature, "g"))
+    tr.regularize_and_step(False)
+    p_d = host(tr.dense(tr.density, "p"))[..., 0]
+    p_f = host(tr.dense(tr.feature, "p"))
+    rng = np.random.default_rng(8)
+    sel = np.sort(rng.choice(np.nonzero(n_live > 0)[0], 48, replace=False))
+    fb = forward_backward(cfg, rp, D, Fg, P, o[sel], d[sel], tgt[sel])
+    assert np.array_equal(n_live[sel], fb["n_live"])
+    # per-ray and per-sample outputs of the selected rays
+    rows = np.concatenate([np.arange(ray_off[r], ray_off[r + 1]) for r in sel]).astype(np.int64)
+    live = fb["live"]
+    scale = len(sel) / R
+    assert np.array_equal(xyz[rows], fb["smp"].xyz)
+    assert rel_err(color[sel], fb["color"]) < 1e-5
+    assert rel_err(L_r[sel], fb["L_r"]) < 1e-5
+    assert rel_err(w[rows], fb["w"]) < 1e-5
+    assert rel_err(rgb[rows][live], fb["rgb"][live]) < 1e-5
+    assert rel_err(g_raw[rows][live], fb["g_raw"][live] * scale) < 1e-5
+    excl = _exclusive_voxels(cfg, xyz, live_all, ray_id, sel)
+    assert len(excl) > 500
+    fb_g = dict(fb, g_density=fb["g_density"] * scale, g_feature=fb["g_feature"] * scale,
+                g_params=np.zeros_like(fb["g_params"]))
+    ref_d = fb_g["g_density"].reshape(-1)[excl]
+    ref_f = fb_g["g_feature"].reshape(-1, 12)[excl]
+    assert rel_err(g_d.reshape(-1)[excl], ref_d) < 1e-5
+    # feature voxels of samples with a ReLU input within rounding of 0 are set aside
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
+    amb = zmin < 1e-6
+    keep = np.ones(len(excl), bool)
+    if amb.any():
+        from step_parity import cell_voxels
+        G = np.array(synth.grid_dims(cfg))
+        v = cell_voxels(cfg, fb["smp"].xyz[fb["live"]][amb])
+        bad = (v[:, 0] * G[1] + v[:, 1]) * G[0] + v[:, 2]
+        keep = ~np.isin(excl, bad)
+    assert rel_err(g_f.reshape(-1, 12)[excl][keep], ref_f[keep]) < 1e-5
+    # TV + Adam (first step from zero moments) on those voxels, where the
+    # gradient is clear of rounding noise
+    opt = optimizer(rp, 1, D, Fg, P, fb_g, False, D, Fg)
+    for got, ref, g in ((p_d.reshape(-1)[excl], opt["density"].reshape(-1)[excl],
+                         opt["g_density_tv"].reshape(-1)[excl]),
+                        (p_f.reshape(-1, 12)[excl][keep], opt["feature"].reshape(-1, 12)[excl][keep],
+                         opt["g_feature_tv"].reshape(-1, 12)[excl][keep])):
+        clear = np.abs(g) > 1e-3 * np.max(np.abs(g))
+        assert np.max(np.abs(got - ref)[clear]) / np.max(np.abs(ref)) < 1e-5
