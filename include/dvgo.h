@@ -263,22 +263,28 @@ int dvgo_live_samples(const int64_t* ray_off, const int32_t* seg_len, int64_t R,
                       void* stream);
 
 /* -------------------------------------------------------------- rendering */
-/* raw -> alpha and transmittance (Sec. 3 "Re-implement rendering utils",
+/* Per-sample intervals: the calls that turn raw into alpha take the common
+ * alpha interval (voxel units) and an optional per-sample array delta [S]
+ * (f32, may be NULL); sample s uses delta[s] when it is given (a sample that
+ * stands for the stretch up to the next one, as the learned proposal's picks
+ * do), else interval.  "interval" below means that per-sample value.
+ *
+ * raw -> alpha and transmittance (Sec. 3 "Re-implement rendering utils",
  * fused): per ray, alpha_i = 1 - exp(-interval softplus(raw_i + shift)),
  * T_i = prod_{j<i}(1 - alpha_j) carried as an FP32 log-sum with compensated
  * carries, w_i = T_i alpha_i; the ray halts at the first i with T_i < T_stop
  * (that sample is not composited).  Writes w[S], T[S] (T_end beyond the
  * stop), n_live[R] (halting index) and T_end[R]. */
 int dvgo_alpha_weights_fwd(const float* raw, const int64_t* ray_off, int64_t R, float shift,
-                           float interval, float T_stop, float* w, float* T, int32_t* n_live,
-                           float* T_end, void* stream);
+                           float interval, const float* delta, float T_stop, float* w, float* T,
+                           int32_t* n_live, float* T_end, void* stream);
 
 /* The whole compositing forward of a ray batch in one call:
  * dvgo_alpha_weights_fwd (raw -> w, T, n_live, T_end) followed by
  * dvgo_composite_rgb_fwd (color).  Its adjoint is dvgo_composite_bwd. */
 int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_off, int64_t R,
-                       float shift, float interval, float T_stop, const float bg[3], float* color,
-                       float* w, float* T, int32_t* n_live, float* T_end, void* stream);
+                       float shift, float interval, const float* delta, float T_stop, const float bg[3],
+                       float* color, float* w, float* T, int32_t* n_live, float* T_end, void* stream);
 
 /* dvgo_sample_grid_fwd of a one-channel density grid fused with
  * dvgo_alpha_weights_fwd: raw[S], w[S], T[S], n_live[R], T_end[R] as those
@@ -287,8 +293,8 @@ int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_of
  * it).  xyz [S][3] f32 in ray order (the sampler's output). */
 int dvgo_density_alpha_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd, const float* xyz,
                            const int64_t* ray_off, int64_t R, float shift, float interval,
-                           float T_stop, float* raw, float* w, float* T, int32_t* n_live,
-                           float* T_end, void* stream);
+                           const float* delta, float T_stop, float* raw, float* w, float* T,
+                           int32_t* n_live, float* T_end, void* stream);
 
 /* Colour accumulation: color[r] = sum_{i < n_live[r]} w_i rgb_i + T_end[r] bg. */
 int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_off,
@@ -306,8 +312,8 @@ int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const int64_t* ray_
  * Samples past the halting index get zero gradients. */
 int dvgo_composite_bwd(const float* g_color, const float* g_w, const float* raw, const float* T,
                        const float* rgb, const int64_t* ray_off, const int32_t* n_live, int64_t R,
-                       float shift, float interval, const float bg[3], float* g_raw, float* g_rgb,
-                       void* stream);
+                       float shift, float interval, const float* delta, const float bg[3], float* g_raw,
+                       float* g_rgb, void* stream);
 
 /* Distortion loss (Sec. 2, Eq. dist_loss, O(N) prefix-sum form) per ray:
  * L_r = 2 sum_i w_i (m_i W_{<i} - WM_{<i}) + 1/3 sum_i w_i^2 ds_i over the
@@ -337,8 +343,8 @@ int dvgo_composite_distortion_fwd(const float* w, const float* rgb, const float*
 int dvgo_composite_distortion_bwd(const float* g_color, float g_L, const float* w, const float* raw,
                                   const float* T, const float* rgb, const float* m, const float* ds,
                                   const int64_t* ray_off, const int32_t* n_live, int64_t R,
-                                  float shift, float interval, const float bg[3], float* g_raw,
-                                  void* stream);
+                                  float shift, float interval, const float* delta, const float bg[3],
+                                  float* g_raw, void* stream);
 
 /* dvgo_composite_distortion_fwd and dvgo_rgb_loss (with L_r) in one launch:
  * color, L_r, g_color and loss_out exactly as those two calls define them
@@ -364,8 +370,9 @@ int dvgo_composite_distortion_loss_fwd_bwd(const float* w, const float* rgb, con
                                            const float bg[3], const float* target,
                                            float lambda_dist, float g_L, const float* raw,
                                            const float* T, float shift, float interval,
-                                           float* color, float* L_r, float* g_color,
-                                           float* loss_out, float* g_raw, void* ws, void* stream);
+                                           const float* delta, float* color, float* L_r,
+                                           float* g_color, float* loss_out, float* g_raw, void* ws,
+                                           void* stream);
 
 /* Photometric loss and its gradient: loss_out[0] = mean over R x 3 of
  * (color - target)^2, loss_out[1] = mean_r L_r (0 if L_r is NULL),
@@ -461,13 +468,25 @@ int dvgo_proposal_select(const float* q, const int64_t* ray_off, int64_t R, int3
                          int32_t* sel, int32_t* n_sel, void* stream);
 /* Gathers the selected samples into a new ragged list (out_ray_off [R+1]
  * from a scan of n_sel; per-sample arrays copied; out_src, may be NULL,
- * receives each kept sample's index in the input list). */
+ * receives each kept sample's index in the input list).
+ * out_delta (f32 [n], may be NULL): each pick then stands for the candidates
+ * from itself up to the next pick of its ray (the last pick: up to the ray's
+ * last candidate), so that the picks cover the same depth range as the
+ * candidates.  For pick j with next pick j' (j' = the ray's candidate count
+ * after the last pick) the kernel writes, in FP32 round-to-nearest,
+ *   out_delta = interval * (j' - j)   (the per-sample alpha interval of
+ *                                      dvgo_alpha_weights_fwd, voxel units)
+ *   start = s_mid[j] - 0.5 s_len[j]; end = s_mid[j'] - 0.5 s_len[j'], or
+ *   s_mid[last] + 0.5 s_len[last] after the last pick;
+ *   out_s_mid = 0.5 (start + end); out_s_len = end - start.
+ * (The candidates are contiguous spans.)  interval > 0 when out_delta is
+ * given, else ignored. */
 int dvgo_compact_samples(const int32_t* sel, const int32_t* n_sel, int32_t n_draw,
                          const int64_t* ray_off, int64_t R, const float* xyz, const int32_t* ray_id,
                          const int32_t* step_k, const float* s_mid, const float* s_len,
                          int64_t* out_ray_off, float* out_xyz, int32_t* out_ray_id,
                          int32_t* out_step_k, float* out_s_mid, float* out_s_len, int32_t* out_src,
-                         void* stream);
+                         float interval, float* out_delta, void* stream);
 
 /* ------------------------------------------------------------ regularisers */
 /* TV gradient (Sec. 2, "Efficient total variation (TV) loss"), added into

@@ -91,8 +91,8 @@ def _declare(L):
                                             P, P, P, P, P, P, I64]
     L.or_trilinear.argtypes = [P, P, INT, P, P, P, I64, P]
     L.or_trilinear_adjoint.argtypes = [P, P, INT, P, P, P, I64, P]
-    L.or_composite.argtypes = [P, P, P, I64, D, D, D, P, P, P, P, P, P]
-    L.or_composite_bwd.argtypes = [P, P, P, I64, D, D, D, P, P, P, P, P]
+    L.or_composite.argtypes = [P, P, P, I64, D, D, P, D, P, P, P, P, P, P]
+    L.or_composite_bwd.argtypes = [P, P, P, I64, D, D, P, D, P, P, P, P, P]
     for nm in ("or_distortion_naive", "or_distortion"):
         getattr(L, nm).argtypes = [P, P, P, P, P, I64, P]
     for nm in ("or_distortion_grad", "or_distortion_grad_naive"):
@@ -276,8 +276,9 @@ def trilinear_adjoint(g_out, grid_shape, lo, hi, xyz):
     return gg.reshape(grid_shape)
 
 
-def composite(raw, rgb, ray_off, shift, interval, T_stop, bg):
-    """Returns dict(w, T, n_live, T_end, color)."""
+def composite(raw, rgb, ray_off, shift, interval, T_stop, bg, delta=None):
+    """Returns dict(w, T, n_live, T_end, color).  delta: optional per-sample
+    intervals (voxel units) in place of the scalar interval."""
     raw = _f64(raw)
     S = raw.size
     rgb = None if rgb is None else _f64(rgb).reshape(S, 3)
@@ -288,13 +289,15 @@ def composite(raw, rgb, ray_off, shift, interval, T_stop, bg):
     n_live = np.zeros(R, np.int32)
     T_end = np.zeros(R)
     color = np.zeros((R, 3))
-    lib().or_composite(_p(raw), _p(rgb), _p(ray_off), R, shift, interval, T_stop,
+    dl = None if delta is None else _f64(delta)
+    lib().or_composite(_p(raw), _p(rgb), _p(ray_off), R, shift, interval, _p(dl), T_stop,
                        _p(_f64(np.broadcast_to(bg, (3,)))), _p(w), _p(T), _p(n_live),
                        _p(T_end), _p(color))
     return dict(w=w, T=T, n_live=n_live, T_end=T_end, color=color)
 
 
-def composite_bwd(raw, rgb, ray_off, shift, interval, T_stop, bg, g_color, g_w_extra=None):
+def composite_bwd(raw, rgb, ray_off, shift, interval, T_stop, bg, g_color, g_w_extra=None,
+                  delta=None):
     raw = _f64(raw)
     S = raw.size
     rgb = None if rgb is None else _f64(rgb).reshape(S, 3)
@@ -304,7 +307,8 @@ def composite_bwd(raw, rgb, ray_off, shift, interval, T_stop, bg, g_color, g_w_e
     gwe = None if g_w_extra is None else _f64(g_w_extra)
     g_raw = np.zeros(S)
     g_rgb = np.zeros((S, 3))
-    lib().or_composite_bwd(_p(raw), _p(rgb), _p(ray_off), R, shift, interval, T_stop,
+    dl = None if delta is None else _f64(delta)
+    lib().or_composite_bwd(_p(raw), _p(rgb), _p(ray_off), R, shift, interval, _p(dl), T_stop,
                            _p(_f64(np.broadcast_to(bg, (3,)))), _p(g_color), _p(gwe),
                            _p(g_raw), _p(g_rgb))
     return g_raw, g_rgb

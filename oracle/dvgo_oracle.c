@@ -446,6 +446,9 @@ OR_API void or_trilinear_adjoint(const double* g_out, const int32_t G[3], int C,
 /*   w_i = T_i alpha_i ; T_{i+1} = T_i (1 - alpha_i).                        */
 /*   C = sum_{i<n} w_i c_i + T_n bg ; samples i >= n get w_i = 0.            */
 /* The halting sample itself is not composited (T is tested before use).     */
+/* alpha_i = 1 - exp(-delta_i softplus(raw_i + shift)) (Eq. 1 with the      */
+/* softplus density), delta_i = interval for every sample, or the caller's   */
+/* per-sample interval delta[i] when delta is given.                         */
 /* ------------------------------------------------------------------------ */
 static int64_t seg_end(const int64_t* ray_off, const int32_t* seg_len, int64_t r) {
   int64_t e = ray_off[r + 1];
@@ -454,7 +457,8 @@ static int64_t seg_end(const int64_t* ray_off, const int32_t* seg_len, int64_t r
 }
 
 OR_API void or_composite(const double* raw, const double* rgb, const int64_t* ray_off, int64_t R,
-                         double shift, double interval, double T_stop, const double bg[3],
+                         double shift, double interval, const double* delta, double T_stop,
+                         const double bg[3],
                          double* w, double* T, int32_t* n_live, double* T_end, double* color) {
   for (int64_t r = 0; r < R; ++r) {
     int64_t b = ray_off[r], e = ray_off[r + 1];
@@ -463,7 +467,7 @@ OR_API void or_composite(const double* raw, const double* rgb, const int64_t* ra
     double acc[3] = {0, 0, 0};
     for (int64_t i = b; i < e; ++i) {
       if (t < T_stop) { stop = i; break; }
-      double a = -expm1(-interval * softplus(raw[i] + shift));
+      double a = -expm1(-(delta ? delta[i] : interval) * softplus(raw[i] + shift));
       T[i] = t;
       w[i] = t * a;
       if (rgb)
@@ -488,7 +492,8 @@ OR_API void or_composite(const double* raw, const double* rgb, const int64_t* ra
 /*   dL/dc_k = w_k dL/dC ;  samples k >= n get zero gradient.                */
 /* ------------------------------------------------------------------------ */
 OR_API void or_composite_bwd(const double* raw, const double* rgb, const int64_t* ray_off, int64_t R,
-                             double shift, double interval, double T_stop, const double bg[3],
+                             double shift, double interval, const double* delta, double T_stop,
+                             const double bg[3],
                              const double* g_color, const double* g_w_extra, double* g_raw,
                              double* g_rgb) {
   for (int64_t r = 0; r < R; ++r) {
@@ -500,7 +505,7 @@ OR_API void or_composite_bwd(const double* raw, const double* rgb, const int64_t
     int64_t n = N;
     for (int64_t i = 0; i < N; ++i) {
       if (t < T_stop) { n = i; break; }
-      a[i] = -expm1(-interval * softplus(raw[b + i] + shift));
+      a[i] = -expm1(-(delta ? delta[b + i] : interval) * softplus(raw[b + i] + shift));
       T[i] = t;
       t = t * (1.0 - a[i]);
     }
@@ -524,7 +529,7 @@ OR_API void or_composite_bwd(const double* raw, const double* rgb, const int64_t
       double gk = (rgb ? rgb[3 * s] * gC[0] + rgb[3 * s + 1] * gC[1] + rgb[3 * s + 2] * gC[2] : 0.0) +
                   (g_w_extra ? g_w_extra[s] : 0.0);
       double Tk1 = T[k] * (1.0 - a[k]);
-      g_raw[s] = interval * sigmoid(raw[s] + shift) * (gk * Tk1 - tail);
+      g_raw[s] = (delta ? delta[s] : interval) * sigmoid(raw[s] + shift) * (gk * Tk1 - tail);
       if (g_rgb) for (int c = 0; c < 3; ++c) g_rgb[3 * s + c] = T[k] * a[k] * gC[c];
     }
     free(a);

@@ -92,22 +92,22 @@ def _declare(L):
         "dvgo_sample_rays": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P, SZ, P], INT),
         "dvgo_live_samples_workspace_size": ([I64], SZ),
         "dvgo_live_samples": ([P, P, I64, P, P, P, SZ, P], INT),
-        "dvgo_alpha_weights_fwd": ([P, P, I64, F, F, F, P, P, P, P, P], INT),
+        "dvgo_alpha_weights_fwd": ([P, P, I64, F, F, P, F, P, P, P, P, P], INT),
         "dvgo_composite_rgb_fwd": ([P, P, P, P, P, I64, P, P, P], INT),
-        "dvgo_composite_fwd": ([P, P, P, I64, F, F, F, P, P, P, P, P, P, P], INT),
+        "dvgo_composite_fwd": ([P, P, P, I64, F, F, P, F, P, P, P, P, P, P, P], INT),
         "dvgo_grid_adam_step": ([P, P, P, P, P, P, I32, P, F, F, F, F, I64, INT, P], INT),
-        "dvgo_composite_bwd": ([P, P, P, P, P, P, P, I64, F, F, P, P, P, P], INT),
+        "dvgo_composite_bwd": ([P, P, P, P, P, P, P, I64, F, F, P, P, P, P, P], INT),
         "dvgo_distortion_fwd": ([P, P, P, P, P, I64, P, P], INT),
         "dvgo_distortion_bwd": ([P, F, P, P, P, P, P, I64, P, P], INT),
         "dvgo_rgb_loss": ([P, P, P, I64, F, P, P, P], INT),
         "dvgo_composite_distortion_fwd": ([P, P, P, P, P, P, P, I64, P, P, P, P], INT),
         "dvgo_composite_loss_workspace_size": ([I64], SZ),
         "dvgo_read_probe": ([P, I64, I32, P, I32, P], INT),
-        "dvgo_density_alpha_fwd": ([P, INT, P, P, P, I64, F, F, F, P, P, P, P, P, P], INT),
+        "dvgo_density_alpha_fwd": ([P, INT, P, P, P, I64, F, F, P, F, P, P, P, P, P, P], INT),
         "dvgo_composite_distortion_loss_fwd": ([P, P, P, P, P, P, P, I64, P, P, F, P, P, P, P, P, P], INT),
-        "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P], INT),
+        "dvgo_composite_distortion_bwd": ([P, F, P, P, P, P, P, P, P, P, I64, F, F, P, P, P, P], INT),
         "dvgo_composite_distortion_loss_fwd_bwd": ([P, P, P, P, P, P, P, I64, P, P, F, F, P, P, F, F,
-                                                    P, P, P, P, P, P, P], INT),
+                                                    P, P, P, P, P, P, P, P], INT),
         "dvgo_rgbnet_fwd": ([P, P, P, P, I64, P, P, INT, P, P, P], INT),
         "dvgo_rgbnet_bwd": ([P, P, P, P, P, P, P, I64, P, P, INT, P, P, P, P, P], INT),
         "dvgo_rgbnet_act_bytes": ([I64, INT], I64),
@@ -122,7 +122,7 @@ def _declare(L):
         "dvgo_proposal_bwd": ([P, P, P, I64, P, P, P, P], INT),
         "dvgo_proposal_xent": ([P, P, P, I64, F, F, P, P, P, P], INT),
         "dvgo_proposal_select": ([P, P, I64, I32, P, P, P], INT),
-        "dvgo_compact_samples": ([P, P, I32, P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P], INT),
+        "dvgo_compact_samples": ([P, P, I32, P, I64, P, P, P, P, P, P, P, P, P, P, P, P, F, P, P], INT),
         "dvgo_sample_rays_noalloc_max_rays": ([], I64),
         "dvgo_sample_rays_noalloc": ([P, P, I64, P, P, P, I64, P, P, P, P, P, P, P], INT),
         "dvgo_grid_resample": ([P, P, P, INT, P, I32, P], INT),
@@ -272,14 +272,16 @@ def live_samples(ray_off, seg_len, R, live_idx, live_count, ws, stream=None):
 
 # ------------------------------------------------------------ rendering
 def density_alpha_fwd(grid, dtype, gd, xyz, ray_off, R, shift, interval, T_stop, raw, w, T, n_live,
-                      T_end, stream=None):
+                      T_end, stream=None, delta=None):
     _call("dvgo_density_alpha_fwd", ptr(grid), dtype, ctypes.byref(gd), ptr(xyz), ptr(ray_off), R,
-          shift, interval, T_stop, ptr(raw), ptr(w), ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
+          shift, interval, ptr(delta), T_stop, ptr(raw), ptr(w), ptr(T), ptr(n_live), ptr(T_end),
+          _stream(stream))
 
 
-def alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end, stream=None):
-    _call("dvgo_alpha_weights_fwd", ptr(raw), ptr(ray_off), R, shift, interval, T_stop, ptr(w),
-          ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
+def alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end, stream=None,
+                      delta=None):
+    _call("dvgo_alpha_weights_fwd", ptr(raw), ptr(ray_off), R, shift, interval, ptr(delta), T_stop,
+          ptr(w), ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
 
 
 def composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream=None):
@@ -288,8 +290,8 @@ def composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream=None)
 
 
 def composite_fwd(raw, rgb, ray_off, R, shift, interval, T_stop, bg, color, w, T, n_live, T_end,
-                  stream=None):
-    _call("dvgo_composite_fwd", ptr(raw), ptr(rgb), ptr(ray_off), R, shift, interval, T_stop,
+                  stream=None, delta=None):
+    _call("dvgo_composite_fwd", ptr(raw), ptr(rgb), ptr(ray_off), R, shift, interval, ptr(delta), T_stop,
           _vec3(bg, F), ptr(color), ptr(w), ptr(T), ptr(n_live), ptr(T_end), _stream(stream))
 
 
@@ -300,9 +302,10 @@ def grid_adam_step(p, p_shadow, g, m, v, G, C, touched, lr, beta1, beta2, eps, s
 
 
 def composite_bwd(g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, bg, g_raw,
-                  g_rgb=None, stream=None):
+                  g_rgb=None, stream=None, delta=None):
     _call("dvgo_composite_bwd", ptr(g_color), ptr(g_w), ptr(raw), ptr(T), ptr(rgb), ptr(ray_off),
-          ptr(n_live), R, shift, interval, _vec3(bg, F), ptr(g_raw), ptr(g_rgb), _stream(stream))
+          ptr(n_live), R, shift, interval, ptr(delta), _vec3(bg, F), ptr(g_raw), ptr(g_rgb),
+          _stream(stream))
 
 
 def composite_distortion_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, color, L_r, stream=None):
@@ -323,18 +326,18 @@ def composite_distortion_loss_fwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, 
 
 def composite_distortion_loss_fwd_bwd(w, rgb, m, ds, ray_off, n_live, T_end, R, bg, target,
                                       lambda_dist, g_L, raw, T, shift, interval, color, L_r,
-                                      g_color, loss_out, g_raw, ws, stream=None):
+                                      g_color, loss_out, g_raw, ws, stream=None, delta=None):
     _call("dvgo_composite_distortion_loss_fwd_bwd", ptr(w), ptr(rgb), ptr(m), ptr(ds), ptr(ray_off),
           ptr(n_live), ptr(T_end), R, _vec3(bg, F), ptr(target), lambda_dist, g_L, ptr(raw), ptr(T),
-          shift, interval, ptr(color), ptr(L_r), ptr(g_color), ptr(loss_out), ptr(g_raw), ptr(ws),
-          _stream(stream))
+          shift, interval, ptr(delta), ptr(color), ptr(L_r), ptr(g_color), ptr(loss_out), ptr(g_raw),
+          ptr(ws), _stream(stream))
 
 
 def composite_distortion_bwd(g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift,
-                             interval, bg, g_raw, stream=None):
+                             interval, bg, g_raw, stream=None, delta=None):
     _call("dvgo_composite_distortion_bwd", ptr(g_color), g_L, ptr(w), ptr(raw), ptr(T), ptr(rgb),
-          ptr(m), ptr(ds), ptr(ray_off), ptr(n_live), R, shift, interval, _vec3(bg, F), ptr(g_raw),
-          _stream(stream))
+          ptr(m), ptr(ds), ptr(ray_off), ptr(n_live), R, shift, interval, ptr(delta), _vec3(bg, F),
+          ptr(g_raw), _stream(stream))
 
 
 def distortion_fwd(w, m, ds, ray_off, seg_len, R, L_r, stream=None):
@@ -448,8 +451,9 @@ def proposal_select(q, ray_off, R, n_draw, sel, n_sel, stream=None):
 
 
 def compact_samples(sel, n_sel, n_draw, ray_off, R, xyz, ray_id, step_k, s_mid, s_len, out_ray_off,
-                    out_xyz, out_ray_id, out_step_k, out_s_mid, out_s_len, out_src=None, stream=None):
+                    out_xyz, out_ray_id, out_step_k, out_s_mid, out_s_len, out_src=None, stream=None,
+                    interval=0.0, out_delta=None):
     _call("dvgo_compact_samples", ptr(sel), ptr(n_sel), n_draw, ptr(ray_off), R, ptr(xyz),
           ptr(ray_id), ptr(step_k), ptr(s_mid), ptr(s_len), ptr(out_ray_off), ptr(out_xyz),
           ptr(out_ray_id), ptr(out_step_k), ptr(out_s_mid), ptr(out_s_len), ptr(out_src),
-          _stream(stream))
+          interval, ptr(out_delta), _stream(stream))

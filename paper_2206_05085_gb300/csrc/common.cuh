@@ -96,6 +96,14 @@ __device__ __forceinline__ float warp_incl_sum(float v) {
   return v;
 }
 
+// The exclusive prefix of lane k from an inclusive scan: lane k-1's inclusive
+// sum (0 in lane 0), taken by a shuffle rather than incl - v, so that a large
+// own term does not cancel against its prefix.
+__device__ __forceinline__ float warp_excl_from_incl(float incl) {
+  const float e = __shfl_up_sync(0xffffffffu, incl, 1);
+  return (threadIdx.x & 31) ? e : 0.0f;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -916,7 +916,8 @@ extern "C" int dvgo_build_mask(const void* density, int dtype, const dvgo_grid_d
 template <bool kBF16>
 __global__ void __launch_bounds__(256) density_alpha_kernel(
     const void* __restrict__ grid, TriArgs Tr, const float* __restrict__ xyz,
-    const int64_t* __restrict__ ray_off, int64_t R, float shift, float interval, float T_stop,
+    const int64_t* __restrict__ ray_off, int64_t R, float shift, float interval,
+    const float* __restrict__ delta, float T_stop,
     float* __restrict__ raw, float* __restrict__ w, float* __restrict__ T,
     int32_t* __restrict__ n_live, float* __restrict__ T_end) {
   const int lane = threadIdx.x & 31;
@@ -945,9 +946,9 @@ __global__ void __launch_bounds__(256) density_alpha_kernel(
         }
         raw[b + i] = rv;
       }
-      const float la = valid ? -interval * softplus_f(rv + shift) : 0.0f;
+      const float la = valid ? -(delta ? __ldg(delta + b + i) : interval) * softplus_f(rv + shift) : 0.0f;
       const float incl = warp_incl_sum(la);
-      const float logT = __fadd_rn(carry.s, __fsub_rn(incl - la, carry.c));
+      const float logT = __fadd_rn(carry.s, __fsub_rn(warp_excl_from_incl(incl), carry.c));
       const float Ti = expf(logT);
       const unsigned below = __ballot_sync(0xffffffffu, valid && Ti < T_stop);
       const int first = below ? __ffs(below) - 1 : 32;
@@ -985,8 +986,9 @@ __global__ void __launch_bounds__(256) density_alpha_kernel(
 
 extern "C" int dvgo_density_alpha_fwd(const void* grid, int dtype, const dvgo_grid_desc* gd,
                                       const float* xyz, const int64_t* ray_off, int64_t R,
-                                      float shift, float interval, float T_stop, float* raw, float* w,
-                                      float* T, int32_t* n_live, float* T_end, void* stream) {
+                                      float shift, float interval, const float* delta, float T_stop,
+                                      float* raw, float* w, float* T, int32_t* n_live, float* T_end,
+                                      void* stream) {
   DVGO_CHECK_ARG(gd && R >= 0 && interval > 0.0f && T_stop >= 0.0f);
   DVGO_CHECK_ARG(dtype == DVGO_F32 || dtype == DVGO_BF16);
   if (R == 0) return DVGO_OK;
@@ -996,10 +998,10 @@ extern "C" int dvgo_density_alpha_fwd(const void* grid, int dtype, const dvgo_gr
   const int g = grid_for(R * 32, 256, 16);
   if (dtype == DVGO_F32)
     density_alpha_kernel<false><<<g, 256, 0, as_stream(stream)>>>(grid, Tr, xyz, ray_off, R, shift, interval,
-                                                                   T_stop, raw, w, T, n_live, T_end);
+                                                                   delta, T_stop, raw, w, T, n_live, T_end);
   else
     density_alpha_kernel<true><<<g, 256, 0, as_stream(stream)>>>(grid, Tr, xyz, ray_off, R, shift, interval,
-                                                                  T_stop, raw, w, T, n_live, T_end);
+                                                                  delta, T_stop, raw, w, T, n_live, T_end);
   return launch_status();
 }
 

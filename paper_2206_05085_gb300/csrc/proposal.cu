@@ -126,23 +126,39 @@ __global__ void compact_kernel(const int32_t* __restrict__ sel, const int32_t* _
                                const float* __restrict__ s_len, const int64_t* __restrict__ out_off,
                                float* __restrict__ o_xyz, int32_t* __restrict__ o_ray_id,
                                int32_t* __restrict__ o_step_k, float* __restrict__ o_s_mid,
-                               float* __restrict__ o_s_len, int32_t* __restrict__ o_src) {
+                               float* __restrict__ o_s_len, int32_t* __restrict__ o_src,
+                               float interval, float* __restrict__ o_delta) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp0; r < R; r += nwarps) {
     const int n = n_sel[r];
     const int64_t dst0 = out_off[r], src0 = ray_off[r];
+    const int n_cand = (int)(ray_off[r + 1] - src0);
     for (int i = lane; i < n; i += 32) {
-      const int64_t src = src0 + sel[r * n_draw + i];
+      const int j = sel[r * n_draw + i];
+      const int64_t src = src0 + j;
       const int64_t dst = dst0 + i;
       o_xyz[3 * dst] = xyz[3 * src];
       o_xyz[3 * dst + 1] = xyz[3 * src + 1];
       o_xyz[3 * dst + 2] = xyz[3 * src + 2];
       o_ray_id[dst] = ray_id[src];
       o_step_k[dst] = step_k[src];
-      o_s_mid[dst] = s_mid[src];
-      o_s_len[dst] = s_len[src];
+      if (o_delta) {
+        // the pick stands for every candidate up to the next pick (the last
+        // one up to the end of the ray's candidates)
+        const int j_next = i + 1 < n ? sel[r * n_draw + i + 1] : n_cand;
+        const float start = __fsub_rn(s_mid[src], __fmul_rn(0.5f, s_len[src]));
+        const int64_t e = src0 + (j_next < n_cand ? j_next : n_cand - 1);
+        const float end = j_next < n_cand ? __fsub_rn(s_mid[e], __fmul_rn(0.5f, s_len[e]))
+                                          : __fadd_rn(s_mid[e], __fmul_rn(0.5f, s_len[e]));
+        o_s_mid[dst] = __fmul_rn(0.5f, __fadd_rn(start, end));
+        o_s_len[dst] = __fsub_rn(end, start);
+        o_delta[dst] = __fmul_rn(interval, (float)(j_next - j));
+      } else {
+        o_s_mid[dst] = s_mid[src];
+        o_s_len[dst] = s_len[src];
+      }
       if (o_src) o_src[dst] = (int32_t)src;
     }
   }
@@ -196,8 +212,10 @@ extern "C" int dvgo_compact_samples(const int32_t* sel, const int32_t* n_sel, in
                                     const int32_t* ray_id, const int32_t* step_k, const float* s_mid,
                                     const float* s_len, int64_t* out_ray_off, float* out_xyz,
                                     int32_t* out_ray_id, int32_t* out_step_k, float* out_s_mid,
-                                    float* out_s_len, int32_t* out_src, void* stream) {
+                                    float* out_s_len, int32_t* out_src, float interval,
+                                    float* out_delta, void* stream) {
   DVGO_CHECK_ARG(R >= 0 && n_draw >= 1);
+  DVGO_CHECK_ARG(!out_delta || interval > 0.0f);
   DVGO_CHECK_ARG(out_ray_off);
   cudaStream_t st = as_stream(stream);
   if (R == 0) {
@@ -209,6 +227,6 @@ extern "C" int dvgo_compact_samples(const int32_t* sel, const int32_t* n_sel, in
   scan_i32_kernel<<<1, 1024, 0, st>>>(n_sel, R, out_ray_off);
   compact_kernel<<<grid_for(R * 32, 256, 16), 256, 0, st>>>(
       sel, n_sel, n_draw, ray_off, R, xyz, ray_id, step_k, s_mid, s_len, out_ray_off, out_xyz,
-      out_ray_id, out_step_k, out_s_mid, out_s_len, out_src);
+      out_ray_id, out_step_k, out_s_mid, out_s_len, out_src, interval, out_delta);
   return launch_status();
 }

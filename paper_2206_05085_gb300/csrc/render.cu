@@ -23,10 +23,17 @@ __device__ __forceinline__ void ray_range(const int64_t* __restrict__ ray_off,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;            \
   for (int64_t r = warp0; r < (R); r += nwarps)
 
+// The alpha interval of sample s: delta[s] when a per-sample interval is
+// given (a proposal pick standing for the gap to the next pick), else the
+// common interval.
+__device__ __forceinline__ float interval_of(const float* __restrict__ delta, float interval, int64_t s) {
+  return delta ? __ldg(delta + s) : interval;
+}
+
 // ------------------------------------------------------------- weights fwd
 __global__ void __launch_bounds__(256) alpha_weights_kernel(
     const float* __restrict__ raw, const int64_t* __restrict__ ray_off, int64_t R, float shift,
-    float interval, float T_stop, float* __restrict__ w, float* __restrict__ T,
+    float interval, const float* __restrict__ delta, float T_stop, float* __restrict__ w, float* __restrict__ T,
     int32_t* __restrict__ n_live, float* __restrict__ T_end) {
   DVGO_WARP_LOOP(R) {
     int64_t b;
@@ -39,9 +46,10 @@ __global__ void __launch_bounds__(256) alpha_weights_kernel(
     for (; c0 < N; c0 += 32) {
       const int i = c0 + lane;
       const bool valid = i < N;
-      const float la = valid ? -interval * softplus_f(__ldg(raw + b + i) + shift) : 0.0f;
+      const float la =
+          valid ? -interval_of(delta, interval, b + i) * softplus_f(__ldg(raw + b + i) + shift) : 0.0f;
       const float incl = warp_incl_sum(la);
-      const float logT = __fadd_rn(carry.s, __fsub_rn(incl - la, carry.c));
+      const float logT = __fadd_rn(carry.s, __fsub_rn(warp_excl_from_incl(incl), carry.c));
       const float Ti = expf(logT);
       const unsigned below = __ballot_sync(0xffffffffu, valid && Ti < T_stop);
       const int first = below ? __ffs(below) - 1 : 32;
@@ -116,8 +124,9 @@ __global__ void __launch_bounds__(256) composite_rgb_kernel(
 __global__ void __launch_bounds__(256) composite_bwd_kernel(
     const float* __restrict__ g_color, const float* __restrict__ g_w, const float* __restrict__ raw,
     const float* __restrict__ T, const float* __restrict__ rgb, const int64_t* __restrict__ ray_off,
-    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval, float bg0,
-    float bg1, float bg2, float* __restrict__ g_raw, float* __restrict__ g_rgb) {
+    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval,
+    const float* __restrict__ delta, float bg0, float bg1, float bg2, float* __restrict__ g_raw,
+    float* __restrict__ g_rgb) {
   DVGO_WARP_LOOP(R) {
     int64_t b;
     int n, N;
@@ -130,11 +139,12 @@ __global__ void __launch_bounds__(256) composite_bwd_kernel(
     for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
       const int k = c0 + lane;
       const bool valid = k < n;
-      float gk = 0.0f, la = 0.0f, rk = 0.0f, Tk = 0.0f, al = 0.0f;
+      float gk = 0.0f, la = 0.0f, rk = 0.0f, Tk = 0.0f, al = 0.0f, dk = 0.0f;
       if (valid) {
         const int64_t s = b + k;
         rk = __ldg(raw + s);
-        la = -interval * softplus_f(rk + shift);
+        dk = interval_of(delta, interval, s);
+        la = -dk * softplus_f(rk + shift);
         al = -expm1f(la);
         if (rgb) gk = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
         if (g_w) gk += __ldg(g_w + s);
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(256) composite_bwd_kernel(
       if (lane == 31) ex = 0.0f;
       const float Sk = __fadd_rn(suf.s, __fsub_rn(ex, suf.c));
       if (valid) {
-        g_raw[b + k] = interval * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
+        g_raw[b + k] = dk * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
         if (g_rgb) {
           g_rgb[3 * (b + k)] = wk * gc0;
           g_rgb[3 * (b + k) + 1] = wk * gc1;
@@ -261,7 +271,8 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
     int lane, int64_t b, int n, int N, float gc0, float gc1, float gc2, float Wt, float WMt, float g_L,
     const float* __restrict__ w, const float* __restrict__ raw, const float* __restrict__ T,
     const float* __restrict__ rgb, const float* __restrict__ m, const float* __restrict__ ds,
-    float shift, float interval, float bg0, float bg1, float bg2, float* __restrict__ g_raw) {
+    float shift, float interval, const float* __restrict__ delta, float bg0, float bg1, float bg2,
+    float* __restrict__ g_raw) {
   const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
   Kahan sW, sWM;                                     // sums over the chunks after the current one
   Kahan suf;                                         // sum_{j in later chunks} g_j w_j + g_T T_end
@@ -270,7 +281,7 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
   for (int c0 = last_chunk; c0 >= 0; c0 -= 32) {
     const int k = c0 + lane;
     const bool valid = k < n;
-    float wi = 0.0f, mi = 0.0f, di = 0.0f, rk = 0.0f, Tk = 0.0f, la = 0.0f;
+    float wi = 0.0f, mi = 0.0f, di = 0.0f, rk = 0.0f, Tk = 0.0f, la = 0.0f, dk = 0.0f;
     float c_rgb = 0.0f;
     if (valid) {
       const int64_t s = b + k;
@@ -280,7 +291,8 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
       rk = __ldg(raw + s);
       Tk = __ldg(T + s);
       c_rgb = __ldg(rgb + 3 * s) * gc0 + __ldg(rgb + 3 * s + 1) * gc1 + __ldg(rgb + 3 * s + 2) * gc2;
-      la = -interval * softplus_f(rk + shift);
+      dk = interval_of(delta, interval, s);
+      la = -dk * softplus_f(rk + shift);
     }
     const float Tk1 = Tk * expf(la);
     if (c0 == last_chunk) suf.add(gT * __shfl_sync(0xffffffffu, Tk1, (n - 1) & 31));   // T_end
@@ -311,7 +323,7 @@ __device__ __forceinline__ void composite_distortion_bwd_ray(
     float ex = __shfl_down_sync(0xffffffffu, sv, 1);
     if (lane == 31) ex = 0.0f;
     const float Sk = __fadd_rn(suf.s, __fsub_rn(ex, suf.c));
-    if (valid) g_raw[b + k] = interval * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
+    if (valid) g_raw[b + k] = dk * sigmoid_f(rk + shift) * (Tk1 * gk - Sk);
     suf.add(__shfl_sync(0xffffffffu, sv, 0));
     sW.add(__shfl_sync(0xffffffffu, sw, 0));
     sWM.add(__shfl_sync(0xffffffffu, swm, 0));
@@ -334,6 +346,7 @@ struct BwdTail {
   const float* raw;
   const float* T;
   float shift, interval;
+  const float* delta;   // per-sample intervals (may be NULL)
   float* g_raw;
 };
 
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
       gc2 = __shfl_sync(0xffffffffu, gc2, 0);
       composite_distortion_bwd_ray(lane, b, n, N, gc0, gc1, gc2, __fsub_rn(tW.s, tW.c),
                                    __fsub_rn(tWM.s, tWM.c), bt.g_L, w, bt.raw, bt.T, rgb, m, ds,
-                                   bt.shift, bt.interval, bg0, bg1, bg2, bt.g_raw);
+                                   bt.shift, bt.interval, bt.delta, bg0, bg1, bg2, bt.g_raw);
     }
   }
   if constexpr (kLoss) {
@@ -483,8 +496,8 @@ __global__ void __launch_bounds__(256) composite_distortion_bwd_kernel(
     const float* __restrict__ g_color, float g_L, const float* __restrict__ w,
     const float* __restrict__ raw, const float* __restrict__ T, const float* __restrict__ rgb,
     const float* __restrict__ m, const float* __restrict__ ds, const int64_t* __restrict__ ray_off,
-    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval, float bg0, float bg1,
-    float bg2, float* __restrict__ g_raw) {
+    const int32_t* __restrict__ n_live, int64_t R, float shift, float interval,
+    const float* __restrict__ delta, float bg0, float bg1, float bg2, float* __restrict__ g_raw) {
   DVGO_WARP_LOOP(R) {
     int64_t b;
     int n, N;
@@ -502,7 +515,7 @@ __global__ void __launch_bounds__(256) composite_distortion_bwd_kernel(
     }
     composite_distortion_bwd_ray(lane, b, n, N, gc0, gc1, gc2, __fsub_rn(tW.s, tW.c),
                                  __fsub_rn(tWM.s, tWM.c), g_L, w, raw, T, rgb, m, ds, shift, interval,
-                                 bg0, bg1, bg2, g_raw);
+                                 delta, bg0, bg1, bg2, g_raw);
   }
 }
 
@@ -576,13 +589,13 @@ using namespace dvgo;
 static int warp_grid(int64_t R) { return grid_for(R * 32, 256, 16); }
 
 extern "C" int dvgo_alpha_weights_fwd(const float* raw, const int64_t* ray_off, int64_t R,
-                                      float shift, float interval, float T_stop, float* w, float* T,
-                                      int32_t* n_live, float* T_end, void* stream) {
+                                      float shift, float interval, const float* delta, float T_stop,
+                                      float* w, float* T, int32_t* n_live, float* T_end, void* stream) {
   DVGO_CHECK_ARG(R >= 0 && interval > 0.0f && T_stop >= 0.0f);
   if (R == 0) return DVGO_OK;
   DVGO_CHECK_ARG(raw && ray_off && w && T && n_live && T_end);
   alpha_weights_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(raw, ray_off, R, shift,
-                                                                    interval, T_stop, w, T, n_live,
+                                                                    interval, delta, T_stop, w, T, n_live,
                                                                     T_end);
   return launch_status();
 }
@@ -601,12 +614,13 @@ extern "C" int dvgo_composite_rgb_fwd(const float* w, const float* rgb, const in
 extern "C" int dvgo_composite_bwd(const float* g_color, const float* g_w, const float* raw,
                                   const float* T, const float* rgb, const int64_t* ray_off,
                                   const int32_t* n_live, int64_t R, float shift, float interval,
-                                  const float bg[3], float* g_raw, float* g_rgb, void* stream) {
+                                  const float* delta, const float bg[3], float* g_raw, float* g_rgb,
+                                  void* stream) {
   DVGO_CHECK_ARG(R >= 0 && interval > 0.0f);
   if (R == 0) return DVGO_OK;
   DVGO_CHECK_ARG(g_color && raw && T && ray_off && n_live && bg && g_raw);
   composite_bwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
-      g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, bg[0], bg[1], bg[2], g_raw,
+      g_color, g_w, raw, T, rgb, ray_off, n_live, R, shift, interval, delta, bg[0], bg[1], bg[2], g_raw,
       g_rgb);
   return launch_status();
 }
@@ -681,14 +695,15 @@ extern "C" int dvgo_composite_distortion_loss_fwd_bwd(
     const float* w, const float* rgb, const float* m, const float* ds, const int64_t* ray_off,
     const int32_t* n_live, const float* T_end, int64_t R, const float bg[3], const float* target,
     float lambda_dist, float g_L, const float* raw, const float* T, float shift, float interval,
-    float* color, float* L_r, float* g_color, float* loss_out, float* g_raw, void* ws, void* stream) {
+    const float* delta, float* color, float* L_r, float* g_color, float* loss_out, float* g_raw, void* ws,
+    void* stream) {
   DVGO_CHECK_ARG(R > 0);
   DVGO_CHECK_ARG(w && rgb && m && ds && ray_off && T_end && bg && color && L_r && target && g_color &&
                  loss_out && ws && raw && T && g_raw);
   DVGO_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 15u) == 0);
   LossTail lt{target, lambda_dist, g_color, loss_out, reinterpret_cast<unsigned int*>(ws),
               reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 16)};
-  BwdTail bt{g_L, raw, T, shift, interval, g_raw};
+  BwdTail bt{g_L, raw, T, shift, interval, delta, g_raw};
   composite_distortion_fwd_kernel<true, true><<<warp_grid(R), 256, 0, as_stream(stream)>>>(
       w, rgb, m, ds, ray_off, n_live, T_end, R, bg[0], bg[1], bg[2], color, L_r, lt, bt);
   return launch_status();
@@ -699,21 +714,22 @@ extern "C" int dvgo_composite_distortion_bwd(const float* g_color, float g_L, co
                                              const float* m, const float* ds,
                                              const int64_t* ray_off, const int32_t* n_live,
                                              int64_t R, float shift, float interval,
-                                             const float bg[3], float* g_raw, void* stream) {
+                                             const float* delta, const float bg[3], float* g_raw,
+                                             void* stream) {
   DVGO_CHECK_ARG(R >= 0 && interval > 0.0f);
   if (R == 0) return DVGO_OK;
   DVGO_CHECK_ARG(g_color && w && raw && T && rgb && m && ds && ray_off && n_live && bg && g_raw);
   composite_distortion_bwd_kernel<<<warp_grid(R), 256, 0, as_stream(stream)>>>(
-      g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift, interval, bg[0], bg[1], bg[2],
+      g_color, g_L, w, raw, T, rgb, m, ds, ray_off, n_live, R, shift, interval, delta, bg[0], bg[1], bg[2],
       g_raw);
   return launch_status();
 }
 
 extern "C" int dvgo_composite_fwd(const float* raw, const float* rgb, const int64_t* ray_off, int64_t R,
-                                  float shift, float interval, float T_stop, const float bg[3],
-                                  float* color, float* w, float* T, int32_t* n_live, float* T_end,
-                                  void* stream) {
-  const int r = dvgo_alpha_weights_fwd(raw, ray_off, R, shift, interval, T_stop, w, T, n_live, T_end,
+                                  float shift, float interval, const float* delta, float T_stop,
+                                  const float bg[3], float* color, float* w, float* T, int32_t* n_live,
+                                  float* T_end, void* stream) {
+  const int r = dvgo_alpha_weights_fwd(raw, ray_off, R, shift, interval, delta, T_stop, w, T, n_live, T_end,
                                        stream);
   if (r != DVGO_OK) return r;
   return dvgo_composite_rgb_fwd(w, rgb, ray_off, n_live, T_end, R, bg, color, stream);

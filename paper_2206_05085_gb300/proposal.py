@@ -5,10 +5,12 @@ ray inside the scene bbox (no occupancy mask).  The plain renderer's own
 compositing weights over the candidates (raw->alpha, transmittance, early
 stop) are the training target of a BF16 tensor-core MLP on the candidates'
 position encoding; at render time the network's per-ray softmax is inverted
-at 64 evenly spaced quantiles, the picked candidates (duplicates collapsed)
-keep their interval, and the plain training step runs on them.  The plain
-dense render over all candidates stays the fallback.  Every step runs in the
-library's kernels (dvgo_proposal_*, dvgo_compact_samples, the renderer).
+at 64 evenly spaced quantiles (duplicates collapsed), each pick stands for
+the candidates from itself up to the next pick (its alpha interval and
+distortion span cover that gap), and the plain training step runs on them.
+The plain dense render over all candidates stays the fallback.  Every step
+runs in the library's kernels (dvgo_proposal_*, dvgo_compact_samples, the
+renderer).
 """
 from __future__ import annotations
 
@@ -107,10 +109,11 @@ class Proposal:
                     0.9, 0.99, 1e-15, self.it, True)
         return self.loss_r
 
-    def select_into(self, tr: Trainer, rays_o, rays_d, uniform: bool = False):
+    def select_into(self, tr: Trainer, rays_o, rays_d, uniform: bool = False, spans: bool = True):
         """Candidates -> proposal softmax -> inverse-CDF picks -> the picked
         samples written into the trainer's sample buffers.  uniform=True picks
-        with a flat distribution instead (the baseline without the network)."""
+        with a flat distribution instead (the baseline without the network).
+        spans=False keeps each pick's own one-candidate interval."""
         self.candidates(rays_o, rays_d)
         S_dev = self.ray_off[self.R:]
         if uniform:
@@ -119,9 +122,14 @@ class Proposal:
             L.proposal_fwd(self.xyz, None, self.S_cap, S_dev, self.params, self.logits)
         L.proposal_xent(self.logits, None, self.ray_off, self.R, 0.0, 0.0, None, None, self.q)
         L.proposal_select(self.q, self.ray_off, self.R, N_DRAW, self.sel, self.n_sel)
+        if spans and tr.delta is None:
+            tr.delta = torch.empty(tr.S_cap, dtype=torch.float32, device=self.dev)
+        elif not spans:
+            tr.delta = None
         L.compact_samples(self.sel, self.n_sel, N_DRAW, self.ray_off, self.R, self.xyz,
                           self.ray_id, self.step_k, self.s_mid, self.s_len, tr.ray_off, tr.xyz,
-                          tr.ray_id, tr.step_k, tr.s_mid, tr.s_len)
+                          tr.ray_id, tr.step_k, tr.s_mid, tr.s_len,
+                          interval=self.rp.interval, out_delta=tr.delta)
 
 
 def psnr(a: torch.Tensor, b: torch.Tensor) -> float:

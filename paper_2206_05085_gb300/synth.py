@@ -22,7 +22,7 @@ import math
 import numpy as np
 
 # Child-stream slots (fixed order; never renumber).
-_S_BLOB, _S_NOISE, _S_FEAT, _S_RAY_O, _S_RAY_J, _S_TARGET, _S_MLP, _S_PROP, _S_SHELL = range(9)
+_S_BLOB, _S_NOISE, _S_FEAT, _S_RAY_O, _S_RAY_J, _S_TARGET, _S_MLP, _S_PROP, _S_SHELL, _S_DETAIL = range(10)
 
 
 def _streams(seed: int, n: int = 16):
@@ -220,6 +220,15 @@ def uniform(shape, lo=0.0, hi=1.0, seed: int = 0, stream: int = 15, dtype=np.flo
 
 def normal(shape, std=1.0, seed: int = 0, stream: int = 14, dtype=np.float32):
     return np.ascontiguousarray(_streams(seed)[stream].normal(0.0, std, shape).astype(dtype))
+
+
+def truth_detail(shape, std: float, seed: int = 0) -> np.ndarray:
+    """Fine-scale detail of the held-out truth scene: i.i.d. N(0, std^2),
+    float32, drawn in float32 (the arrays are large)."""
+    rng = _streams(seed)[_S_DETAIL]
+    out = rng.standard_normal(shape, dtype=np.float32)
+    out *= np.float32(std)
+    return out
 
 
 def bf16_round(x: np.ndarray) -> np.ndarray:

@@ -161,6 +161,10 @@ class Trainer:
         self.brick_list = torch.empty(nb, **i32)
         self.brick_count = torch.zeros(1, **i32)
         self.step_dev = torch.zeros(2, dtype=torch.int64, device=dev)   # Adam's t (+ scratch)
+        # per-sample alpha intervals of a given sample list (a proposal's picks,
+        # each covering the span up to the next pick); None = the scalar interval
+        self.delta = None
+        self._delta = None
 
     # --------------------------------------------------------------- forward
     def sample(self, rays_o, rays_d):
@@ -169,17 +173,19 @@ class Trainer:
 
     def forward(self, rays_o, rays_d, target, sample: bool = True, tail_adjoint: bool = False):
         """Forward pass.  sample=False renders the sample list already in the
-        buffers (ray_off, xyz, ray_id, step_k, s_mid, s_len), e.g. the samples
-        a proposal network selected.  tail_adjoint: the compositing adjoint of
+        buffers (ray_off, xyz, ray_id, step_k, s_mid, s_len, and delta when it
+        is set), e.g. the samples a proposal network selected.  tail_adjoint: the compositing adjoint of
         each ray (g_raw) runs in the same pass as its loss (then backward takes
         tail_done=True)."""
         rp, R, S = self.rp, self.R, self.S_cap
         if sample:
             self.sample(rays_o, rays_d)
+        self._delta = None if sample else self.delta
         # density query and weights in one pass over each ray, up to its halt
         dgrid, ddt = self.density.render_view
         L.density_alpha_fwd(dgrid, ddt, self.gd, self.xyz, self.ray_off, R, self.shift, rp.interval,
-                            rp.T_stop, self.raw, self.w, self.T, self.n_live, self.T_end)
+                            rp.T_stop, self.raw, self.w, self.T, self.n_live, self.T_end,
+                            delta=self._delta)
         L.live_samples(self.ray_off, self.n_live, R, self.live_idx, self.live_count, self.ws_live)
         if self.w_min is not None:
             L.live_samples_cull(self.ray_off, self.n_live, self.w, self.w_min, R, self.query_idx,
@@ -196,7 +202,8 @@ class Trainer:
             L.composite_distortion_loss_fwd_bwd(
                 self.w, self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live, self.T_end, R,
                 rp.bg, target, rp.lambda_dist, rp.lambda_dist / R, self.raw, self.T, self.shift,
-                rp.interval, self.color, self.L_r, self.g_color, self.loss, self.g_raw, self.ws_loss)
+                rp.interval, self.color, self.L_r, self.g_color, self.loss, self.g_raw, self.ws_loss,
+                delta=self._delta)
         else:
             L.composite_distortion_loss_fwd(self.w, self.rgb, self.s_mid, self.s_len, self.ray_off,
                                             self.n_live, self.T_end, R, rp.bg, target,
@@ -210,7 +217,8 @@ class Trainer:
         if not tail_done:
             L.composite_distortion_bwd(self.g_color, rp.lambda_dist / R, self.w, self.raw, self.T,
                                        self.rgb, self.s_mid, self.s_len, self.ray_off, self.n_live,
-                                       R, self.shift, rp.interval, rp.bg, self.g_raw)
+                                       R, self.shift, rp.interval, rp.bg, self.g_raw,
+                                       delta=self._delta)
         L.rgbnet_bwd(None, self.g_color, self.w, self.k0, rays_d, self.ray_id, self.query_idx, S,
                      self.query_count, self.mlp, self.precision, self.mlp_g, self.g_k0,
                      self.act, self.rgb)
@@ -330,3 +338,52 @@ class Trainer:
         out = torch.empty(self.G[2], self.G[1], self.G[0], gp.C, dtype=src.dtype, device=self.dev)
         L.grid_unpack(src, out, self.G, gp.C, L.BF16 if src.dtype == torch.bfloat16 else L.F32)
         return out
+
+
+# ------------------------------------------------------ quality reference
+TRUTH_DETAIL_STD = 1.6
+
+
+def heldout_truth_render(cfg: SceneConfig, rp: RenderParams, density: np.ndarray,
+                         feature: np.ndarray, mlp_params: np.ndarray, rays_o, rays_d, target,
+                         detail_std: float = TRUTH_DETAIL_STD, seed: int = 0,
+                         step_factor: int = 4) -> torch.Tensor:
+    """Colours of a held-out truth scene on the given rays, the reference of
+    the PSNR comparisons between forms of the step.  The truth holds what the
+    model's grids cannot: both grids refined to the 2x lattice (2G-1 points
+    per axis over the same box, corner aligned, so that the refined trilinear
+    field is the model's own) plus i.i.d. Gaussian detail of std detail_std
+    in raw density and in every feature channel.  It is rendered with a
+    `step_factor` times finer step (the converged integral), its densities
+    kept in the model's voxel units (the alpha interval scales with the
+    step only), no occupancy mask, the same colour MLP."""
+    from . import synth
+    assert not rp.contracted and not rp.ndc, "bounded scenes only"
+    G = synth.grid_dims(cfg)
+    G2 = [2 * g - 1 for g in G]
+    dev = rays_o.device
+    grids = []
+    for slot, (arr, C) in enumerate(((density, 1), (feature, feature.shape[-1]))):
+        src = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32)).to(dev)
+        packed = torch.empty(L.grid_bricked_elems(G, C), dtype=torch.float32, device=dev)
+        L.grid_pack(src, packed, G, C, L.F32)
+        fine = torch.empty(L.grid_bricked_elems(G2, C), dtype=torch.float32, device=dev)
+        L.grid_resample(packed, G, fine, L.F32, G2, C)
+        out = torch.empty(G2[2], G2[1], G2[0], C, dtype=torch.float32, device=dev)
+        L.grid_unpack(fine, out, G2, C, L.F32)
+        arr2 = out.cpu().numpy()
+        arr2 += synth.truth_detail(arr2.shape, detail_std, seed=seed + slot)
+        grids.append(arr2 if C > 1 else arr2[..., 0])
+        del src, packed, fine, out
+    cfg2 = dataclasses.replace(cfg, grid=G2[0], dims=tuple(G2) if cfg.dims is not None else None)
+    rp2 = dataclasses.replace(rp, step=float(np.float32(rp.step / step_factor)),
+                              max_steps=rp.max_steps * step_factor,
+                              interval=float(np.float32(rp.interval / step_factor)),
+                              mask_thres=None)
+    R = int(rays_o.shape[0])
+    tr = Trainer(cfg2, rp2, grids[0], grids[1], mlp_params, n_rays=R, precision="f32tc")
+    tr.forward(rays_o, rays_d, target)
+    color = tr.color.clone()
+    del tr
+    torch.cuda.empty_cache()
+    return color

@@ -17,7 +17,7 @@ import torch
 
 import oracle
 from conftest import rel_err
-from oracle_step import forward_backward, optimizer
+from oracle_step import forward_backward, optimizer, proposal_picks
 from paper_2206_05085_gb300 import synth
 
 MLP_TENSORS = ("W1", "b1", "W2", "b2", "W3", "b3")
@@ -36,6 +36,10 @@ def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):
     to, td, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (o, d, tgt))
     tr.forward(to, td, tt)
     tr.backward(td)
+    return _gpu_outputs(tr, tv_dense)
+
+
+def _gpu_outputs(tr, tv_dense):
     S = int(_host(tr.ray_off)[-1])
     gpu = dict(loss=_host(tr.loss), color=_host(tr.color), L_r=_host(tr.L_r), n_live=_host(tr.n_live),
                S=S, w=_host(tr.w[:S]), rgb=_host(tr.rgb[:S]), g_raw=_host(tr.g_raw[:S]),
@@ -48,6 +52,52 @@ def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):
     from paper_2206_05085_gb300 import _lib as L
     gpu["device_status"] = L.device_status()
     return gpu
+
+
+def gpu_proposal_step(cfg, rp, D, Fg, P, PP, o, d, tgt, precision, tv_dense):
+    """The learned-proposal form of one iteration through the library: the
+    proposal (parameters PP) picks <= 64 of the <= 512 candidates per ray, the
+    plain step runs on the picks with their spans.  Also returns the picks
+    (sel [R][64], n_sel)."""
+    import dataclasses
+    from paper_2206_05085_gb300 import proposal, train
+    R = len(o)
+    rp_c = proposal.candidate_params(cfg, rp)
+    tr = train.Trainer(cfg, dataclasses.replace(rp_c, max_steps=proposal.N_DRAW), D, Fg, P,
+                       n_rays=R, precision=precision)
+    grid, dt = tr.density.render_view
+    prop = proposal.Proposal(cfg, rp, grid, dt, PP, R)
+    to, td, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (o, d, tgt))
+    prop.select_into(tr, to, td)
+    tr.forward(to, td, tt, sample=False)
+    tr.backward(td)
+    sel = _host(prop.sel).astype(np.int64).reshape(R, proposal.N_DRAW)
+    n_sel = _host(prop.n_sel).astype(np.int64)
+    S = int(_host(tr.ray_off)[-1])
+    delta = _host(tr.delta)[:S]
+    gpu = _gpu_outputs(tr, tv_dense)
+    gpu.update(sel=sel, n_sel=n_sel, delta=delta)
+    return gpu
+
+
+def oracle_proposal_step(cfg, rp, D, Fg, P, PP, o, d, tgt, precision, tv_dense):
+    """The same from the oracle: its own picks (proposal network in FP64 on
+    the BF16-stored proposal parameters), the spans, then the step.  Returns
+    (fb, opt, params the renderer read, sel, n_sel)."""
+    import dataclasses
+    from paper_2206_05085_gb300 import proposal
+    bf = precision == "bf16"
+    Dr = synth.bf16_round(D) if bf else D
+    Fr = synth.bf16_round(Fg) if bf else Fg
+    Pr = synth.bf16_round(P) if bf else P
+    rp_c = proposal.candidate_params(cfg, rp)
+    picks, delta, sel, n_sel = proposal_picks(cfg, rp_c, synth.bf16_round(PP), o, d, proposal.N_DRAW)
+    rp_p = dataclasses.replace(rp_c, max_steps=proposal.N_DRAW)
+    fb = forward_backward(cfg, rp_p, Dr, Fr, Pr, o, d, tgt, smp=picks, delta=delta)
+    fb["density0"], fb["feature0"], fb["params0"] = D, Fg, P
+    fb["delta"] = delta
+    opt = optimizer(rp_p, 1, D, Fg, P, fb, tv_dense, Dr, Fr)
+    return fb, opt, Pr, sel, n_sel
 
 
 def oracle_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):

@@ -496,11 +496,12 @@ def test_composite_distortion_fused(L):
         assert rel_err(host(g_raw), gr) < TOL32
 
 
-@pytest.mark.parametrize("bf16", [False, True])
-def test_density_alpha_fused(L, bf16):
+@pytest.mark.parametrize("bf16,per_sample", [(False, False), (True, False), (False, True)])
+def test_density_alpha_fused(L, bf16, per_sample):
     """Density query + weights in one pass = dvgo_sample_grid_fwd then
     dvgo_alpha_weights_fwd (bit-equal w, T, n_live, T_end; raw equal before
-    each ray's halt), on rays sampled through a blob scene so that many halt."""
+    each ray's halt), on rays sampled through a blob scene so that many halt;
+    per_sample: with per-sample intervals."""
     rng = np.random.default_rng(50 + bf16)
     G = (40, 40, 40)
     lo, hi = np.array([-1.0] * 3), np.array([1.0] * 3)
@@ -524,16 +525,18 @@ def test_density_alpha_fused(L, bf16):
     grid = _bricked(L, dense, G, 1, torch.bfloat16 if bf16 else torch.float32)
     dt = L.BF16 if bf16 else L.F32
     sh = shift32()
+    dl = dev(0.5 * rng.integers(1, 6, S).astype(np.float32)) if per_sample else None
     outs = []
     for fused in (False, True):
         raw, w, T = (torch.full((S,), -9.0, device="cuda") for _ in range(3))
         n_live = torch.empty(R, dtype=torch.int32, device="cuda")
         T_end = torch.empty(R, device="cuda")
         if fused:
-            L.density_alpha_fwd(grid, dt, gd, dev(xyz), dev(off), R, sh, 0.5, 1e-3, raw, w, T, n_live, T_end)
+            L.density_alpha_fwd(grid, dt, gd, dev(xyz), dev(off), R, sh, 0.5, 1e-3, raw, w, T, n_live,
+                                T_end, delta=dl)
         else:
             L.sample_grid_fwd(grid, dt, gd, 1, dev(xyz), None, S, None, raw)
-            L.alpha_weights_fwd(raw, dev(off), R, sh, 0.5, 1e-3, w, T, n_live, T_end)
+            L.alpha_weights_fwd(raw, dev(off), R, sh, 0.5, 1e-3, w, T, n_live, T_end, delta=dl)
         outs.append([host(x) for x in (raw, w, T, n_live, T_end)])
     (r0, w0, T0, n0, e0), (r1, w1, T1, n1, e1) = outs
     assert np.array_equal(n0, n1) and np.array_equal(e0, e1)
@@ -543,6 +546,80 @@ def test_density_alpha_fused(L, bf16):
     for r in range(R):
         k = slice(off[r], off[r] + n0[r])
         assert np.array_equal(r0[k], r1[k])
+
+
+def test_per_sample_intervals(L):
+    """Every compositing entry with a per-sample interval array (the spans of
+    a proposal's picks) against the oracle given the same intervals: weights,
+    halting, colour, the compositing adjoint, and the fused tails (forward,
+    distortion adjoint, loss + adjoint) bit-equal to the unfused calls."""
+    off, raw, rgb = _ragged_case(12, COUNTS, scale=2.0, bias=4.0)
+    R, S = len(off) - 1, int(off[-1])
+    rng = np.random.default_rng(13)
+    delta = (0.5 * rng.integers(1, 24, S)).astype(np.float32)
+    bg = np.array([0.2, 0.9, 0.4], np.float32)
+    sh = shift32()
+    m = np.zeros(S, np.float32)
+    for r in range(R):
+        m[off[r]:off[r + 1]] = np.sort(rng.uniform(0, 1, off[r + 1] - off[r]))
+    ds = rng.uniform(0.001, 0.01, S).astype(np.float32)
+    g_color = rng.normal(size=(R, 3)).astype(np.float32)
+    target = rng.uniform(0, 1, (R, 3)).astype(np.float32)
+    gL, lam = 0.37, 0.01
+    dl = dev(delta)
+    for T_stop in (1e-3, 0.0):
+        w, T = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+        n_live = torch.empty(R, dtype=torch.int32, device="cuda")
+        T_end = torch.empty(R, device="cuda")
+        L.alpha_weights_fwd(dev(raw), dev(off), R, sh, 0.5, T_stop, w, T, n_live, T_end, delta=dl)
+        ref = oracle.composite(raw, rgb, off, sh, 0.5, T_stop, bg, delta=delta)
+        nl = host(n_live)
+        diff = np.nonzero(nl != ref["n_live"])[0]
+        for r in diff:
+            k = min(nl[r], ref["n_live"][r])
+            assert abs(ref["T"][off[r] + k] / T_stop - 1) < 1e-5, (r, nl[r], ref["n_live"][r])
+        ok = np.setdiff1d(np.arange(R), diff)
+        okS = np.concatenate([np.arange(off[r], off[r + 1]) for r in ok])
+        assert rel_err(host(w)[okS], ref["w"][okS]) < TOL32
+        assert rel_err(host(T_end)[ok], ref["T_end"][ok]) < TOL32
+        assert (nl < np.diff(off)).sum() > 100 or T_stop == 0.0
+        # colour through the one-pass compositing forward
+        c_one = torch.empty(R, 3, device="cuda")
+        w2, T2 = torch.empty(S, device="cuda"), torch.empty(S, device="cuda")
+        n2, e2 = torch.empty(R, dtype=torch.int32, device="cuda"), torch.empty(R, device="cuda")
+        L.composite_fwd(dev(raw), dev(rgb), dev(off), R, sh, 0.5, T_stop, bg, c_one, w2, T2, n2, e2,
+                        delta=dl)
+        assert torch.equal(w, w2) and torch.equal(n_live, n2)
+        assert rel_err(host(c_one)[ok], ref["color"][ok]) < TOL32
+        # compositing adjoint (with the live counts of the oracle where they agree)
+        g_w = rng.normal(size=S).astype(np.float32)
+        g_raw = torch.empty(S, device="cuda")
+        L.composite_bwd(dev(g_color), dev(g_w), dev(raw), T, dev(rgb), dev(off), n_live, R, sh, 0.5,
+                        bg, g_raw, None, delta=dl)
+        gr, _ = oracle.composite_bwd(raw, rgb, off, sh, 0.5, T_stop, bg, g_color, g_w, delta=delta)
+        assert rel_err(host(g_raw)[okS], gr[okS]) < TOL32
+        # distortion adjoint inside the reverse scan
+        gd_raw = torch.empty(S, device="cuda")
+        L.composite_distortion_bwd(dev(g_color), gL, w, dev(raw), T, dev(rgb), dev(m), dev(ds),
+                                   dev(off), n_live, R, sh, 0.5, bg, gd_raw, delta=dl)
+        g_wd = oracle.distortion_grad(gL, ref["w"], m, ds, off, ref["n_live"])
+        grd, _ = oracle.composite_bwd(raw, rgb, off, sh, 0.5, T_stop, bg, g_color, g_wd, delta=delta)
+        assert rel_err(host(gd_raw)[okS], grd[okS]) < TOL32
+        # loss + adjoint in one pass: bit-equal to the loss pass then the adjoint
+        args = (w, dev(rgb), dev(m), dev(ds), dev(off), n_live, T_end, R, bg)
+        ws = torch.zeros(L.composite_loss_workspace_size(R), dtype=torch.uint8, device="cuda")
+        c1, l1 = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+        loss1, g1 = torch.empty(3, device="cuda"), torch.empty(R, 3, device="cuda")
+        L.composite_distortion_loss_fwd(*args, dev(target), lam, c1, l1, g1, loss1, ws)
+        gr1 = torch.empty(S, device="cuda")
+        L.composite_distortion_bwd(g1, lam / R, w, dev(raw), T, dev(rgb), dev(m), dev(ds), dev(off),
+                                   n_live, R, sh, 0.5, bg, gr1, delta=dl)
+        c3, l3 = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+        loss3, g3, gr3 = (torch.empty(3, device="cuda"), torch.empty(R, 3, device="cuda"),
+                          torch.empty(S, device="cuda"))
+        L.composite_distortion_loss_fwd_bwd(*args, dev(target), lam, lam / R, dev(raw), T, sh, 0.5,
+                                            c3, l3, g3, loss3, gr3, ws, delta=dl)
+        assert torch.equal(c1, c3) and torch.equal(g1, g3) and torch.equal(gr1, gr3)
 
 
 @pytest.mark.parametrize("R_rays", [37, 5000])

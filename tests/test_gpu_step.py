@@ -9,7 +9,8 @@ import torch
 
 from conftest import rel_err
 from paper_2206_05085_gb300 import synth
-from step_parity import error_table, gpu_step, oracle_step
+from step_parity import (error_table, gpu_proposal_step, gpu_step, oracle_proposal_step,
+                         oracle_step)
 
 pytestmark = pytest.mark.gpu
 
@@ -117,6 +118,44 @@ def test_step_low_weight_cull(T):
     print(f"low-weight cull: {int(skipped.sum())} of {int(fb['live'].sum())} live samples skipped, "
           f"render vs full render {psnr:.1f} dB")
     assert psnr > 50
+
+
+@pytest.mark.parametrize("precision,tol", [("f32tc", 1e-5), ("bf16", 2e-3)])
+def test_step_learned_proposal(T, precision, tol):
+    """The learned-proposal form: the proposal network picks <= 64 of the
+    <= 512 candidates of each ray and the step runs on the picks, each with
+    the span up to the next pick.  The picks equal the oracle's (its FP64
+    network on the same stored parameters) except on rays where a CDF value
+    sits within the network's rounding of a quantile; on the rays whose
+    picks agree, the spans and the whole step match the oracle's."""
+    import dataclasses as dc
+    from paper_2206_05085_gb300 import proposal
+    cfg = synth.CFG5 if precision == "f32tc" else synth.CFG4
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    PP = (synth.proposal_params() * 3.0).astype(np.float32)
+    o, d = synth.rays(cfg)
+    tgt = synth.target_rgb(cfg)
+    o, d, tgt = o[::16][:384], d[::16][:384], tgt[::16][:384]
+    args = (cfg, rp, D, Fg, P, PP)
+    gpu = gpu_proposal_step(*args, o, d, tgt, precision, False)
+    fb, opt, Pr, sel, n_sel = oracle_proposal_step(*args, o, d, tgt, precision, False)
+    R = len(o)
+    agree = np.array([n_sel[r] == gpu["n_sel"][r] and
+                      np.array_equal(sel[r, :n_sel[r]], gpu["sel"][r, :n_sel[r]]) for r in range(R)])
+    print(f"picks equal on {int(agree.sum())} of {R} rays; {int(n_sel.sum())} picks")
+    assert agree.mean() > 0.9
+    if not agree.all():
+        o, d, tgt = o[agree], d[agree], tgt[agree]
+        gpu = gpu_proposal_step(*args, o, d, tgt, precision, False)
+        fb, opt, Pr, sel, n_sel = oracle_proposal_step(*args, o, d, tgt, precision, False)
+        assert np.array_equal(gpu["n_sel"], n_sel)
+    assert np.array_equal(gpu["sel"], np.where(sel >= 0, sel, gpu["sel"]))
+    assert n_sel.mean() > 20 and (n_sel < 64).any()        # spans longer than one candidate
+    assert rel_err(gpu["delta"], fb["delta"]) < 1e-6
+    assert np.max(fb["delta"]) > 4 * np.min(fb["delta"])
+    rp_p = dc.replace(proposal.candidate_params(cfg, rp), max_steps=proposal.N_DRAW)
+    _compare(gpu, fb, opt, tol, cfg, rp_p, Pr, bf16=precision == "bf16")
 
 
 def test_step_forward_facing_ndc(T):

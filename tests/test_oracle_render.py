@@ -207,3 +207,54 @@ def test_trilinear_against_grid_sample(orc):
     ref = torch.nn.functional.grid_sample(inp, grid, mode="bilinear", align_corners=True)
     ref = ref.view(C, -1).T.numpy()
     assert rel_err(out, ref) < 1e-12
+
+
+def test_per_sample_interval_equals_repeated_samples(orc):
+    """A sample whose interval is k voxel steps absorbs exactly as k equal
+    samples of one step each (1 - (1 - a)^k = 1 - exp(-k delta sigma)), so a
+    ray of merged spans renders the colour of the ray of repeated samples."""
+    shift = orc.alpha_shift(SHIFT_INIT)
+    rng = np.random.default_rng(11)
+    ks = np.array([1, 3, 1, 7, 2, 5])
+    raw = rng.normal(8.0, 2.0, ks.size)
+    rgb = rng.uniform(0, 1, (ks.size, 3))
+    bg = np.array([0.2, 0.7, 0.4])
+    merged = orc.composite(raw, rgb, np.array([0, ks.size]), shift, 0.5, 0.0, bg, delta=0.5 * ks)
+    rep = orc.composite(np.repeat(raw, ks), np.repeat(rgb, ks, axis=0), np.array([0, ks.sum()]),
+                        shift, 0.5, 0.0, bg)
+    assert np.allclose(merged["color"], rep["color"], rtol=1e-13, atol=1e-15)
+    assert merged["T_end"][0] == pytest.approx(rep["T_end"][0], rel=1e-12)
+    # the weight of a merged span is the summed weight of its copies
+    ends = np.cumsum(ks)
+    assert np.allclose(merged["w"], np.add.reduceat(rep["w"], ends - ks), rtol=1e-12)
+    # a uniform per-sample interval is the scalar interval
+    same = orc.composite(raw, rgb, np.array([0, ks.size]), shift, 0.5, 0.0, bg,
+                         delta=np.full(ks.size, 0.5))
+    plain = orc.composite(raw, rgb, np.array([0, ks.size]), shift, 0.5, 0.0, bg)
+    assert np.array_equal(same["color"], plain["color"])
+
+
+def test_composite_backward_per_sample_interval_fd(orc):
+    shift = orc.alpha_shift(SHIFT_INIT)
+    rng = np.random.default_rng(12)
+    off, raw, rgb = _rays_samples(rng, [1, 6, 20])
+    raw = raw + 8.0
+    R = len(off) - 1
+    delta = rng.uniform(0.2, 4.0, raw.size)
+    bg = np.array([0.3, 0.2, 0.9])
+    u = rng.normal(size=(R, 3))
+    v = rng.normal(size=raw.size)
+
+    def L(raw_):
+        c = orc.composite(raw_, rgb, off, shift, 0.5, 0.0, bg, delta=delta)
+        return np.sum(c["color"] * u) + np.dot(c["w"], v)
+
+    g_raw, _ = orc.composite_bwd(raw, rgb, off, shift, 0.5, 0.0, bg, u, v, delta=delta)
+    h = 1e-6
+    fd = np.zeros_like(raw)
+    for k in range(raw.size):
+        rp, rm = raw.copy(), raw.copy()
+        rp[k] += h
+        rm[k] -= h
+        fd[k] = (L(rp) - L(rm)) / (2 * h)
+    assert rel_err(g_raw, fd) < 1e-7
