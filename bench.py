@@ -443,7 +443,7 @@ def roofline(res, peaks, mk=None):
         achieved = flop / (ms * 1e-3) / 1e12
         if prec in ("bf16", "f32tc"):
             bound, unit = "tensor", "TFLOP/s"
-            peak = peaks.get("bf16_tflops", 1963.5)
+            peak = peaks.get("bf16_tflops", 1900.0)
             peak_src = ("bf16_tflops of measured (burst; FP16 runs at the BF16 rate)" if "bf16_tflops" in peaks
                         else "1.9 PFLOP/s bf16 burst (fallback)")
             ceil = MMA_CEILING[(prec, way)]
@@ -457,12 +457,12 @@ def roofline(res, peaks, mk=None):
                    peak_source=peak_src)
     else:
         # a memory kernel: its algorithmic bytes (memory_kernels) over its time
-        peak = peaks.get("hbm_gbs", 6701.5)
+        peak = peaks.get("hbm_gbs", 6800.0)
         b = (mk or {}).get("kernels", {}).get(name + "#0", {}).get("bytes")
         ach = b / (ms * 1e-3) / 1e9 if b else None
         out.update(bound="hbm", achieved=round(ach, 1) if ach else None, peak=peak, unit="GB/s",
                    frac=round(ach / peak, 4) if ach else None, bytes_per_launch=b,
-                   peak_source="hbm_gbs of measured" if "hbm_gbs" in peaks else "6701.5 GB/s (fallback)")
+                   peak_source="hbm_gbs of measured" if "hbm_gbs" in peaks else "6800 GB/s (fallback)")
     out["traffic"] = traffic_for(name, prec, S_live)
     out["ms_per_call"] = round(ms, 4)
     out["share"] = round(rec["ms_per_step"] / sum(v["ms_per_step"] for v in kt.values()), 3)
@@ -527,7 +527,7 @@ def memory_kernels(res, peaks):
     }
     if dens_key:
         algo[dens_key] = S * (12 + 4) + Va * e
-    peak = peaks.get("hbm_gbs", 6701.5)
+    peak = peaks.get("hbm_gbs", 6800.0)
     out = {}
     for key, b in algo.items():
         if key not in calls:
@@ -558,7 +558,7 @@ def memory_kernels(res, peaks):
     step_ms = res["total_ms"] / max(res.get("steps", 1), 1)
     it_gbs = it_b / (step_ms * 1e-3) / 1e9
     return {"peak_gbs": peak, "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks
-            else "6701.5 GB/s (earlier measurement on this pool)",
+            else "6800 GB/s (fallback)",
             "counts": c, "kernels": out,
             "all": {"bytes": tot_b, "ms": round(tot_ms, 4),
                     "achieved_gbs": round(tot_b / (tot_ms * 1e-3) / 1e9, 1),

@@ -137,11 +137,18 @@ constexpr uint32_t cTmp = 0, cDW2 = 128, cDW1 = 256, cGX = 352, cGH = 384;
 
 struct Side {
   float4 smp[kTile];  // per tile row: (g_z3[0..2], the row's gradient scale sG2)
-  float red[16];
+  float red[32];      // block_max scratch: one entry per warp (17 warps)
   uint64_t bar_h;     // H1 terms of a tile image landed
   uint64_t bar_x;     // X terms landed
-  uint64_t bar_mma;
+  uint64_t bar_d2;    // D2^T of a tile done
+  uint64_t bar_gh;    // g_h1 done
+  uint64_t bar_dw2;   // dW2 done (the tile's H1 terms are free)
+  uint64_t bar_gx;    // g_X and dW1 done (G's shared memory and X are free)
+  uint64_t bar_fin;   // every product done (before the accumulators are read)
+  uint64_t g2_full;   // G2 of a tile in tensor and shared memory (16 warp arrivals)
+  uint64_t g1_full;   // G1 of a tile in tensor and shared memory (16 warp arrivals)
   uint32_t tmem_slot;
+  int abort;          // a wait gave up: later waits return at once
 };
 static_assert(bEnd + sizeof(Side) <= 227 * 1024, "backward shared memory");
 
@@ -234,6 +241,54 @@ __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t a_tmem, uint32_t bh
     tc::mma_ts(d, al, dbh, idesc, 1u);
     dbh += ib;
     dbl += ib;
+  }
+}
+
+// D (+)= A B^T over K = 16 * ksteps with A (128 rows) in tensor memory as
+// split terms in 16-column chunks: K step j at a_tmem + 16 j, its hi terms
+// packed two per column in the first 8 columns and its lo terms in the next 8.
+template <bool kBLo = true>
+__device__ __forceinline__ void mma3_ts16(uint32_t d, uint32_t a_tmem, uint32_t bh, uint32_t bl, uint32_t b_step,
+                                          uint32_t b_lbo, uint32_t b_sbo, int ksteps, uint32_t idesc,
+                                          bool accumulate) {
+  uint64_t dbh = tc::smem_desc(bh, b_lbo, b_sbo), dbl = tc::smem_desc(bl, b_lbo, b_sbo);
+  const uint64_t ib = b_step >> 4;
+#pragma unroll 1
+  for (int j = 0; j < ksteps; ++j) {
+    const uint32_t ah = a_tmem + 16u * (uint32_t)j, al = ah + 8u;
+    tc::mma_ts(d, ah, dbh, idesc, (accumulate || j > 0) ? 1u : 0u);
+    if (kBLo) tc::mma_ts(d, ah, dbl, idesc, 1u);
+    tc::mma_ts(d, al, dbh, idesc, 1u);
+    dbh += ib;
+    dbl += ib;
+  }
+}
+
+// 16 values times s split into the 16-column chunk layout of mma3_ts16: hi
+// terms of value pairs in words 0-7, lo terms in words 8-15.
+template <class Op>
+__device__ __forceinline__ void split16(const float (&v)[16], float s, uint32_t (&hl)[16], float& vmax) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float a = s * v[2 * c], b = s * v[2 * c + 1];
+    vmax = fmaxf(vmax, fmaxf(fabsf(a), fabsf(b)));
+    hl[c] = Op::split2(a, b, hl[8 + c]);
+  }
+}
+
+// The split terms of split16 times r (a power of two <= 1) as the hi / lo
+// core-matrix rows of columns k0 .. k0 + 15 of row `row` in shared memory.
+template <class Op, bool kScale = true>
+__device__ __forceinline__ void st_terms16(uint8_t* hi, uint8_t* lo, int row, int k0, const uint32_t (&hl)[16],
+                                           float r) {
+  auto m = [&](uint32_t x) { return kScale ? Op::mul2(x, r) : x; };
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint32_t off = tc::cm_off(row, k0 + 8 * q, kSboH);
+    *reinterpret_cast<uint4*>(hi + off) =
+        make_uint4(m(hl[4 * q]), m(hl[4 * q + 1]), m(hl[4 * q + 2]), m(hl[4 * q + 3]));
+    *reinterpret_cast<uint4*>(lo + off) =
+        make_uint4(m(hl[8 + 4 * q]), m(hl[9 + 4 * q]), m(hl[10 + 4 * q]), m(hl[11 + 4 * q]));
   }
 }
 
@@ -775,14 +830,32 @@ __global__ void __launch_bounds__(544, 1) rgbnet_fwd_tc_kernel(
 }
 
 // ----------------------------------------------------------------- backward
-// 512 threads: warp w covers TMEM lane quarter w & 3 and column quarter
-// q = w / 4.  In the products with the tile rows on the TMEM lanes (g_h1,
-// g_X) a thread holds row 32 (w & 3) + lane and hidden columns 32 q .. + 31;
-// in the transposed layer 2 (D2^T) it holds hidden unit 32 (w & 3) + lane
-// and tile rows 32 q .. + 31.  The upstream colour gradient of the next
-// tile is loaded in three dependent steps over the current tile, and the
-// next tile's image is copied in as soon as the MMAs that read each part
-// have completed (H1 after dW2, X before the next dW1).
+// 544 threads.  Warps 0-15 compute: warp w covers TMEM lane quarter w & 3
+// and column quarter q = w / 4.  In the products with the tile rows on the
+// TMEM lanes (g_h1, g_X) a thread holds row 32 (w & 3) + lane and hidden
+// columns 32 q .. + 31; in the transposed layer 2 (D2^T) it holds hidden unit
+// 32 (w & 3) + lane and tile rows 32 q .. + 31.  Warp 16 issues the MMAs and
+// the X copies, so that the tensor core runs while the compute warps work:
+// dW2 first (its completion frees H1's buffer for the next tile's copy),
+// then g_h1, then the next tile's D2^T as soon as its H1 has landed, then
+// this tile's g_X and dW1 once G1 is in.
+//
+// Order per tile t of this CTA (tn = the next one):
+//   compute: wait h_full(t) -> row scales, relu mask (reads H1(t)); wait
+//            d2(t) -> G2 epilogue; wait gx(t - 1) -> G2 into shared memory,
+//            g_X(t - 1) -> g_k0; arrive g2_full(t).  Thread 0: wait dw2(t)
+//            -> copy H1(tn) in.  Wait gh(t) -> G1 epilogue; arrive
+//            g1_full(t).
+//   MMA:     wait gx(t - 1) -> copy X(t) in; wait g2_full(t) -> dW2(t),
+//            commit dw2; g_h1(t), commit gh; wait h_full(tn) -> D2^T(tn),
+//            commit d2; wait g1_full(t) and X(t) -> g_X(t) and dW1(t),
+//            commit gx.
+// A tensor-memory column range or shared buffer is rewritten only after the
+// barrier that follows its last reader.  The G2 and G1 split terms in tensor
+// memory use 16-column chunks (mma3_ts16), so that each epilogue runs in two
+// halves of 16 columns and rewrites only columns it has already read.  The
+// upstream colour gradient of the next tile is loaded in three dependent
+// steps over the current tile.
 struct UpIn {
   int64_t s;       // sample index (-1 past the list end)
   int32_t r;
@@ -819,8 +892,18 @@ __device__ __forceinline__ void up_l3(UpIn& u, const float* __restrict__ g_rgb,
   for (int c = 0; c < kOut; ++c) u.g[c] = u.g[c] * y[c] * (1.0f - y[c]);
 }
 
+// Bounded wait of the backward; after the first timeout every later wait
+// returns false at once, so that both roles still reach the kernel's end.
+__device__ __forceinline__ bool bwd_wait(Side* fs, uint64_t* bar, uint32_t parity) {
+  if (*reinterpret_cast<volatile int*>(&fs->abort)) return false;
+  if (tc::mbar_wait(bar, parity, kSpin)) return true;
+  *reinterpret_cast<volatile int*>(&fs->abort) = 1;
+  set_status(DVGO_ERR_TIMEOUT);
+  return false;
+}
+
 template <class Op>
-__global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
+__global__ void __launch_bounds__(544, 1) rgbnet_bwd_tc_kernel(
     const float* __restrict__ g_rgb, const float* __restrict__ g_color, const float* __restrict__ w,
     const float* __restrict__ rgb, const int32_t* __restrict__ ray_id, const int32_t* __restrict__ idx,
     int64_t n_cap, const int64_t* __restrict__ n_dev, const float* __restrict__ params,
@@ -828,35 +911,36 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   extern __shared__ __align__(1024) uint8_t sm[];
   Side* fs = reinterpret_cast<Side*>(sm + bEnd);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int qw = warp >> 2, row = (warp & 3) * 32 + lane;
+  const int qw = (warp >> 2) & 3, row = (warp & 3) * 32 + lane;
+  const bool compute = warp < 16;
   const int64_t n = mlp_count(n_cap, n_dev);
   const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t nt = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto tile_of = [&](int64_t k) { return (int64_t)blockIdx.x + k * (int64_t)gridDim.x; };
   const uint8_t* img_g = act + kActHeader;
   uint8_t* img = sm + bImg;
-  bool inflight_h = false, inflight_x = false;   // thread 0: copies not yet waited for
-  auto load_h = [&](int64_t tile) {
-    tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
-    tc::bulk_g2s(img + iHh, img_g + (size_t)tile * kImage + iHh, 2 * kHBytes, &fs->bar_h);
-    inflight_h = true;
-  };
-  auto load_x = [&](int64_t tile) {
-    tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
-    tc::bulk_g2s(img + iX, img_g + (size_t)tile * kImage + iX, 2 * kXBytes, &fs->bar_x);
-    inflight_x = true;
-  };
   if (warp == 0) tc::tmem_alloc(&fs->tmem_slot, 512);
   if (tid == 0) {
     tc::mbar_init(&fs->bar_h, 1);
     tc::mbar_init(&fs->bar_x, 1);
-    tc::mbar_init(&fs->bar_mma, 1);
-    // the first image and upstream rows are fetched while the weights are prepared
-    if ((int64_t)blockIdx.x < ntiles) {
-      load_h(blockIdx.x);
-      load_x(blockIdx.x);
+    tc::mbar_init(&fs->bar_d2, 1);
+    tc::mbar_init(&fs->bar_gh, 1);
+    tc::mbar_init(&fs->bar_dw2, 1);
+    tc::mbar_init(&fs->bar_gx, 1);
+    tc::mbar_init(&fs->bar_fin, 1);
+    tc::mbar_init(&fs->g2_full, 16);
+    tc::mbar_init(&fs->g1_full, 16);
+    fs->abort = 0;
+    // the first image is fetched while the weights are prepared
+    if (nt > 0) {
+      tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
+      tc::bulk_g2s(img + iHh, img_g + (size_t)tile_of(0) * kImage + iHh, 2 * kHBytes, &fs->bar_h);
+      tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
+      tc::bulk_g2s(img + iX, img_g + (size_t)tile_of(0) * kImage + iX, 2 * kXBytes, &fs->bar_x);
     }
   }
   UpIn cur, nxt;
-  up_l1(cur, idx, (int64_t)blockIdx.x * kTile + row, n);
+  if (compute) up_l1(cur, idx, tile_of(0) * kTile + row, n);
   // scales: W2 and W1[:, 0:16] per matrix; G2 from the upstream bound, G1 from G2's
   float m1 = 0.0f, m3 = 0.0f;
 #pragma unroll 4
@@ -878,14 +962,13 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   // its own scale.
   float gm = 0.0f;
   {
-    const int64_t nt = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t cnt = nt * kTile;
     for (int64_t e0 = tid; e0 < cnt; e0 += 4 * (int64_t)blockDim.x) {
       int64_t sv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t e = e0 + u * (int64_t)blockDim.x;
-        const int64_t j = ((int64_t)blockIdx.x + (e / kTile) * gridDim.x) * kTile + e % kTile;
+        const int64_t j = tile_of(e / kTile) * kTile + e % kTile;
         sv[u] = (e < cnt && j < n) ? (idx ? (int64_t)__ldg(idx + j) : j) : -1;
       }
 #pragma unroll
@@ -903,221 +986,306 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   const float w21 = mw2 * (float)kHid;
   const float S2 = pow2_scale(0.25f * gmax * mw3);
   const float S1 = pow2_scale(0.25f * gmax * mw3 * w21);
-  up_l2(cur, g_rgb, w, ray_id);
-  // W1[:, 0:16] as split [o][k] rows for g_X = G1 W1[:, 0:16]
+  if (compute) up_l2(cur, g_rgb, w, ray_id);
   // W1[:, 0:16] split, hi and lo core matrices side by side in each 8-row
-  // group, so that [hi | lo] is one 32-wide B operand of g_X
+  // group, so that [hi | lo] is one 32-wide B operand of g_X = G1 W1[:, 0:16]
   load_w1<Op, 16>(params, sm + bW1h, sm + bW1h + 256, kSboW1s, sW1);
   load_w2<Op>(params, sm + bW2h, sm + bW2l, sW2);
-  up_l3(cur, g_rgb, g_color, rgb);
-  const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
-  // this thread's hidden unit in the transposed layer-2 products (TMEM lane)
-  const int oh = (warp & 3) * 32 + lane;
-  const float b2o = Op::param(__ldg(params + kOffB2 + oh)), w3o0 = Op::param(__ldg(params + kOffW3 + oh)),
-              w3o1 = Op::param(__ldg(params + kOffW3 + kHid + oh)),
-              w3o2 = Op::param(__ldg(params + kOffW3 + 2 * kHid + oh));
+  if (compute) up_l3(cur, g_rgb, g_color, rgb);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = fs->tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sW1h = tc::smem_u32(sm + bW1h);
   const uint32_t sW2h = tc::smem_u32(sm + bW2h), sW2l = tc::smem_u32(sm + bW2l);
   const uint32_t sX = tc::smem_u32(img + iX);
   const uint32_t sHh = tc::smem_u32(img + iHh), sHl = tc::smem_u32(img + iHl);
   const uint32_t sGh = tc::smem_u32(sm + bGh), sGl = tc::smem_u32(sm + bGl);
-  float dW3acc[kOut], db2acc = 0.0f, db3acc[kOut];
-#pragma unroll
-  for (int i = 0; i < kOut; ++i) dW3acc[i] = 0.0f;
-#pragma unroll
-  for (int c = 0; c < kOut; ++c) db3acc[c] = 0.0f;
-  uint32_t ph_h = 0, ph_x = 0, ph_mma = 0;
-  bool ok = true, dw_started = false;
   float vmax = 0.0f;   // largest magnitude split (range check)
-  auto mma_wait = [&]() -> bool {
-    const bool r = __syncthreads_and(tc::mbar_wait(&fs->bar_mma, ph_mma, kSpin));
-    ph_mma ^= 1;
-    tc::fence_after_sync();
-    return r;
-  };
-  // The MMAs are issued by one thread of warp 4; while the tensor core runs
-  // a product, the other warps do the work that does not feed it (this
-  // row's gradient scales, the layer-1 relu mask), warp 4 after its issue.
-  constexpr int kIssuer = 128;
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int64_t tn = t + gridDim.x;   // this CTA's next tile
-    const bool valid = cur.s >= 0;
-    const int64_t s = cur.s;
-    float fG1 = 0.0f, invX = 0.0f, r1 = 0.0f;
-    // g_z3 of this row's sample and its gradient scales (for g_h1 and g_X);
-    // the weight-gradient products take the CTA-wide S2, S1 instead
-    auto prologue = [&]() {
-      float gz3[kOut] = {0.0f, 0.0f, 0.0f};
-      if (valid) {
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) gz3[c] = cur.g[c];
+  // per-thread partial sums of dW3, db2 (hidden unit oh) and db3 (tile row)
+  float dW3acc[kOut] = {0.0f, 0.0f, 0.0f}, db2acc = 0.0f, db3acc[kOut] = {0.0f, 0.0f, 0.0f};
+  if (warp == 16) {
+    // ------------------------------------------------------------ MMA warp
+    // lane 0 polls and issues; the outcome of a wait is the warp's
+    auto wait0 = [&](uint64_t* bar, uint32_t parity) -> bool {
+      int r = 0;
+      if (lane == 0) r = bwd_wait(fs, bar, parity) ? 1 : 0;
+      return __shfl_sync(0xffffffffu, r, 0) != 0;
+    };
+    bool inflight_x = nt > 0;   // lane 0: an X copy not yet seen landed
+    uint32_t ph_h = 0, ph_x = 0, ph_gx = 0, ph_g2 = 0, ph_g1 = 0;
+    auto load_x = [&](int64_t k) {
+      tc::mbar_arrive_expect_tx(&fs->bar_x, 2 * kXBytes);
+      tc::bulk_g2s(img + iX, img_g + (size_t)tile_of(k) * kImage + iX, 2 * kXBytes, &fs->bar_x);
+      inflight_x = true;
+    };
+    // D2^T = W2 H1^T of the tile whose H1 terms have landed (TMEM lane =
+    // hidden unit, column = tile row); after a failed wait only the commit
+    auto d2 = [&](bool h_ok) {
+      if (h_ok) {
+        mma3<Op::kWeightLo, true>(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH,
+                                  kHid / 16, Op::idesc(128, kTile, 0, 0), false);
       }
-      const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
-      const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
-      const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
-      fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
-      invX = 1.0f / (sG1 * sW1);           // g_X
-      r1 = S1 / sG1;                       // G1 terms -> the dW1 copy
-      if (qw == 0) {
-        fs->smp[row] = make_float4(gz3[0], gz3[1], gz3[2], sG2);
+      tc::mma_commit(&fs->bar_d2);
+    };
+    if (nt > 0) {
+      const bool h_ok = wait0(&fs->bar_h, ph_h);
+      ph_h ^= 1;
+      tc::fence_after_sync();
+      if (lane == 0) d2(h_ok);
+      __syncwarp();
+    }
+    for (int64_t k = 0; k < nt; ++k) {
+      const bool has_next = k + 1 < nt;
+      // X(k): the buffer is free once g_X and dW1 of tile k - 1 are done
+      if (k > 0) {
+        if (wait0(&fs->bar_gx, ph_gx) && lane == 0) load_x(k);
+        ph_gx ^= 1;
+      }
+      // dW2 += G2^T H1 (A from tensor memory), then g_h1 = G2 W2 (A MN-major)
+      const bool g2 = wait0(&fs->g2_full, ph_g2);
+      ph_g2 ^= 1;
+      tc::fence_after_sync();
+      if (lane == 0) {
+        if (g2)
+          mma3_ts16(tmem + cDW2, tmem + cTmp, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
+                    Op::idesc(128, kHid, 0, 1), k > 0);
+        tc::mma_commit(&fs->bar_dw2);
+        if (g2)
+          mma3<true, Op::kWeightLo>(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH,
+                                    kSboH, 128, kHid / 16, Op::idesc(128, kHid, 1, 1), false);
+        tc::mma_commit(&fs->bar_gh);
+      }
+      __syncwarp();
+      // the next tile's D2^T once its H1 has landed (compute thread 0 copies
+      // it in when dW2 has read this one's); it needs no G1 of this tile
+      if (has_next) {
+        const bool h_ok = wait0(&fs->bar_h, ph_h);
+        ph_h ^= 1;
+        tc::fence_after_sync();
+        if (lane == 0) d2(h_ok);
+        __syncwarp();
+      }
+      // once G1 and X are in: g_X = G1 W1[:, 0:16] (A from tensor memory) and
+      // dW1|db1 += G1^T X
+      const bool g1 = wait0(&fs->g1_full, ph_g1);
+      ph_g1 ^= 1;
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const bool x_ok = g1 && bwd_wait(fs, &fs->bar_x, ph_x);
+        ph_x ^= 1;
+        if (x_ok) {
+          inflight_x = false;
+          {   // per K step: G1h [W1h | W1l] (N = 32: hi*hi in columns 0-15, hi*lo in 16-31), G1l W1h
+            const uint32_t id32 = Op::idesc(128, 32, 0, 1), id16 = Op::idesc(128, 16, 0, 1);
+            uint64_t db = tc::smem_desc(sW1h, kSboW1s, 128);
+#pragma unroll 1
+            for (uint32_t j = 0; j < kHid / 16; ++j) {
+              const uint32_t ah = tmem + cGH + 16u * j, al = ah + 8u;
+              tc::mma_ts(tmem + cGX, ah, db, id32, j > 0 ? 1u : 0u);
+              tc::mma_ts(tmem + cGX, al, db, id16, 1u);
+              db += (2 * kSboW1s) >> 4;
+            }
+          }
+          {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
+            const uint32_t id96 = Op::idesc(128, 2 * kK1, 1, 1), id48 = Op::idesc(128, kK1, 1, 1);
+            uint64_t dah = tc::smem_desc(sGh, kSboH, 128), dal = tc::smem_desc(sGl, kSboH, 128);
+            uint64_t dbx = tc::smem_desc(sX, kSboXs, 128);
+#pragma unroll 1
+            for (int kk = 0; kk < kTile / 16; ++kk) {
+              tc::mma_bf16(tmem + cDW1, dah, dbx, id96, (k > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_bf16(tmem + cDW1, dal, dbx, id48, 1u);
+              dah += (2 * kSboH) >> 4;
+              dal += (2 * kSboH) >> 4;
+              dbx += (2 * kSboXs) >> 4;
+            }
+          }
+        }
+        tc::mma_commit(&fs->bar_gx);
+      }
+      __syncwarp();
+    }
+    // every product has finished before the accumulators are read and the
+    // tensor memory is released; a copy issued but never seen landed (only
+    // after a failed wait) lands before exit
+    if (lane == 0) {
+      tc::mma_commit(&fs->bar_fin);
+      if (!tc::mbar_wait(&fs->bar_fin, 0, kSpin)) {
+        *reinterpret_cast<volatile int*>(&fs->abort) = 1;
+        set_status(DVGO_ERR_TIMEOUT);
+      }
+      if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_x, kSpin);
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------- compute warps
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const float inv2 = 1.0f / (kSH * sW2);           // D2 -> z2 - b2
+    // this thread's hidden unit in the transposed layer-2 products (TMEM lane)
+    const int oh = (warp & 3) * 32 + lane;
+    const float b2o = Op::param(__ldg(params + kOffB2 + oh)), w3o0 = Op::param(__ldg(params + kOffW3 + oh)),
+                w3o1 = Op::param(__ldg(params + kOffW3 + kHid + oh)),
+                w3o2 = Op::param(__ldg(params + kOffW3 + 2 * kHid + oh));
+    uint32_t ph_h = 0, ph_d2 = 0, ph_gh = 0, ph_gx = 0, ph_dw2 = 0;
+    bool inflight_h = tid == 0 && nt > 0;   // thread 0: an H1 copy not yet seen landed
+    int64_t prev_s = -1;       // the previous tile's row: its g_X is stored one tile later
+    float prev_invX = 0.0f;
+    // g_X = G1 W1[:, 0:16] of the previous tile (lane quarter qw == 0) -> g_k0
+    auto store_gx = [&]() {
+      float ga[16], gb[16];
+      tc::tmem_ld16(lane_base + cGX, ga);
+      tc::tmem_ld16(lane_base + cGX + 16, gb);
+      if (prev_s >= 0) {
+        float4* dst = reinterpret_cast<float4*>(g_k0 + prev_s * kFeat);
 #pragma unroll
-        for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
+        for (int q = 0; q < 3; ++q)
+          dst[q] = make_float4((ga[4 * q] + gb[4 * q]) * prev_invX, (ga[4 * q + 1] + gb[4 * q + 1]) * prev_invX,
+                               (ga[4 * q + 2] + gb[4 * q + 2]) * prev_invX,
+                               (ga[4 * q + 3] + gb[4 * q + 3]) * prev_invX);
       }
     };
-    up_l1(nxt, idx, tn * kTile + row, n);
-    ok = __syncthreads_and(tc::mbar_wait(&fs->bar_h, ph_h, kSpin));
-    if (!ok) break;
-    ph_h ^= 1;
-    inflight_h = false;
-    if (tid == kIssuer) {   // D2^T = W2 H1^T (TMEM lane = hidden unit, column = tile row)
-      tc::fence_after_sync();
-      mma3<Op::kWeightLo, true>(tmem + cTmp, sW2h, sW2l, 256, 128, kSboH, sHh, sHl, 256, 128, kSboH,
-                                kHid / 16, Op::idesc(128, kTile, 0, 0), false);
-      tc::mma_commit(&fs->bar_mma);
-    }
-    if (warp != kIssuer / 32) prologue();
-    // relu mask of layer 1 on this quarter's columns (H1 > 0 <=> hi > 0)
-    uint32_t m1b = 0u;
-#pragma unroll
-    for (int k8 = 0; k8 < 32; k8 += 8) {
-      const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(row, 32 * qw + k8, kSboH));
-      const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = k8 + 2 * i;
-        if ((int16_t)(wd[i] & 0xffffu) > 0) m1b |= 1u << k;
-        if ((int16_t)(wd[i] >> 16) > 0) m1b |= 1u << (k + 1);
-      }
-    }
-    up_l2(nxt, g_rgb, w, ray_id);
-    if (!(ok = mma_wait())) break;
-    // Hidden unit oh over the tile rows 32 qw .. 32 qw + 31: G2 = (W3^T g_z3)
-    // * (z2 > 0), and the sums over rows dW3 += g_z3 h2^T, db2 += G2 in
-    // registers.  G2 goes out twice: at the CTA-wide scale S2 into tensor
-    // memory over this thread's D2 columns (lane = unit, K = row: the A
-    // operand of dW2), and at each row's own scale sG2 into shared memory as
-    // [unit][row] core matrices (the MN-major A operand of g_h1).
-    {
-      float v[32];
-      tc::tmem_ld32(lane_base + cTmp + 32 * qw, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float4 q = fs->smp[32 * qw + i];
-        const float z2 = fmaf(v[i], inv2, b2o);
-        const float gs = fmaf(w3o2, q.z, fmaf(w3o1, q.y, w3o0 * q.x));
-        const float g = z2 > 0.0f ? gs : 0.0f;
-        const float h = fmaxf(z2, 0.0f);
-        db2acc += g;
-        dW3acc[0] = fmaf(q.x, h, dW3acc[0]);
-        dW3acc[1] = fmaf(q.y, h, dW3acc[1]);
-        dW3acc[2] = fmaf(q.z, h, dW3acc[2]);
-        v[i] = g;
-      }
-      uint32_t hl[32];
-      split32<Op>(v, S2, hl, vmax);
-      tc::tmem_st32(lane_base + cTmp + 32 * qw, hl);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] *= fs->smp[32 * qw + i].w;
-      split32<Op>(v, 1.0f, hl, vmax);
-      st_terms32<Op, false>(sm + bGh, sm + bGl, oh, 32 * qw, hl, 1.0f);
-    }
-    tc::tmem_wait_st();
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == kIssuer) {   // dW2 += G2^T H1 (A from tensor memory);  g_h1 = G2 W2 (A MN-major)
-      tc::fence_after_sync();
-      mma3_ts(tmem + cDW2, tmem + cTmp, sHh, sHl, 2 * kSboH, kSboH, 128, kTile / 16,
-              Op::idesc(128, kHid, 0, 1), dw_started);
-      mma3<true, Op::kWeightLo>(tmem + cGH, sGh, sGl, 2 * kSboH, kSboH, 128, sW2h, sW2l, 2 * kSboH, kSboH, 128,
-                                kHid / 16, Op::idesc(128, kHid, 1, 1), false);
-      tc::mma_commit(&fs->bar_mma);
-    }
-    if (warp == kIssuer / 32) prologue();
-    up_l3(nxt, g_rgb, g_color, rgb);
-    if (!(ok = mma_wait())) break;
-    if (tid == 0 && tn < ntiles) load_h(tn);   // this tile's H1 is no longer read
-    // G1 = g_h1 * (H1 > 0): at S1 in shared memory (dW1), at sG1 in tensor memory (g_X)
-    {
-      float v[32];
-      tc::tmem_ld32(lane_base + cGH + 32 * qw, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = ((m1b >> i) & 1u) ? v[i] : 0.0f;
-      uint32_t hl[32];
-      split32<Op>(v, fG1, hl, vmax);
-      tc::tmem_st32(lane_base + cGH + 32 * qw, hl);
-      st_terms32<Op>(sm + bGh, sm + bGl, row, 32 * qw, hl, r1);
-    }
-    tc::tmem_wait_st();
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    // the tile's X (the B operand of dW1, loaded since the previous tile's dW1) has landed
-    ok = __syncthreads_and(tid != kIssuer || tc::mbar_wait(&fs->bar_x, ph_x, kSpin));
-    if (!ok) break;
-    ph_x ^= 1;
-    inflight_x = false;
-    if (tid == kIssuer) {   // dW1|db1 += G1^T X;  g_X = G1 W1[:, 0:16] (A from tensor memory)
-      tc::fence_after_sync();
-      {   // per K step: G1h [Xh | Xl] (N = 96: hi*hi in columns 0-47, hi*lo in 48-95), G1l Xh
-        const uint32_t id96 = Op::idesc(128, 2 * kK1, 1, 1), id48 = Op::idesc(128, kK1, 1, 1);
-        uint64_t dah = tc::smem_desc(sGh, kSboH, 128), dal = tc::smem_desc(sGl, kSboH, 128);
-        uint64_t dbx = tc::smem_desc(sX, kSboXs, 128);
-#pragma unroll 1
-        for (int k = 0; k < kTile / 16; ++k) {
-          tc::mma_bf16(tmem + cDW1, dah, dbx, id96, (dw_started || k > 0) ? 1u : 0u);
-          tc::mma_bf16(tmem + cDW1, dal, dbx, id48, 1u);
-          dah += (2 * kSboH) >> 4;
-          dal += (2 * kSboH) >> 4;
-          dbx += (2 * kSboXs) >> 4;
-        }
-      }
-      {   // per K step: G1h [W1h | W1l] (N = 32: hi*hi in columns 0-15, hi*lo in 16-31), G1l W1h
-        const uint32_t id32 = Op::idesc(128, 32, 0, 1), id16 = Op::idesc(128, 16, 0, 1);
-        uint64_t db = tc::smem_desc(sW1h, kSboW1s, 128);
-#pragma unroll 1
-        for (uint32_t j = 0; j < kHid / 16; ++j) {
-          const uint32_t ah = tmem + cGH + 32u * (j >> 1) + 8u * (j & 1u), al = ah + 16u;
-          tc::mma_ts(tmem + cGX, ah, db, id32, j > 0 ? 1u : 0u);
-          tc::mma_ts(tmem + cGX, al, db, id16, 1u);
-          db += (2 * kSboW1s) >> 4;
-        }
-      }
-      tc::mma_commit(&fs->bar_mma);
-      dw_started = true;
-    }
-    if (!(ok = mma_wait())) break;
-    if (tid == 0 && tn < ntiles) load_x(tn);   // nor its X
-    if (qw == 0) {
-      float gx[16];
+    for (int64_t k = 0; k < nt; ++k) {
+      const bool valid = cur.s >= 0;
+      const int64_t s = cur.s;
+      up_l1(nxt, idx, tile_of(k + 1) * kTile + row, n);
+      // this tile's H1 terms (for the relu mask)
+      if (bwd_wait(fs, &fs->bar_h, ph_h)) inflight_h = false;
+      ph_h ^= 1;
+      // g_z3 of this row's sample and its gradient scales (for g_h1 and g_X);
+      // the weight-gradient products take the CTA-wide S2, S1 instead
+      float fG1, invX, r1;
       {
-        float gd[32];
-        tc::tmem_ld32(lane_base + cGX, gd);
+        float gz3[kOut] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) gx[i] = gd[i] + gd[16 + i];
+          for (int c = 0; c < kOut; ++c) gz3[c] = cur.g[c];
+        }
+        const float b2s = mw3 * fmaxf(fabsf(gz3[0]), fmaxf(fabsf(gz3[1]), fabsf(gz3[2])));
+        const float sG2 = b2s > 0.0f ? fmaxf(pow2_scale(b2s), S2) : S2;
+        const float sG1 = b2s > 0.0f ? fmaxf(pow2_scale(b2s * w21), S1) : S1;
+        fG1 = sG1 / (sG2 * sW2);             // (sG2 G2)(sW2 W2) -> sG1 g_h1
+        invX = 1.0f / (sG1 * sW1);           // g_X
+        r1 = S1 / sG1;                       // G1 terms -> the dW1 copy
+        if (qw == 0) {
+          fs->smp[row] = make_float4(gz3[0], gz3[1], gz3[2], sG2);
+#pragma unroll
+          for (int c = 0; c < kOut; ++c) db3acc[c] += gz3[c];
+        }
       }
-      if (valid) {
-        float4* dst = reinterpret_cast<float4*>(g_k0 + s * kFeat);
-        dst[0] = make_float4(gx[0] * invX, gx[1] * invX, gx[2] * invX, gx[3] * invX);
-        dst[1] = make_float4(gx[4] * invX, gx[5] * invX, gx[6] * invX, gx[7] * invX);
-        dst[2] = make_float4(gx[8] * invX, gx[9] * invX, gx[10] * invX, gx[11] * invX);
+      // relu mask of layer 1 on this quarter's columns (H1 > 0 <=> hi > 0)
+      uint32_t m1b = 0u;
+#pragma unroll
+      for (int k8 = 0; k8 < 32; k8 += 8) {
+        const uint4 q = *reinterpret_cast<const uint4*>(img + iHh + tc::cm_off(row, 32 * qw + k8, kSboH));
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int kq = k8 + 2 * i;
+          if ((int16_t)(wd[i] & 0xffffu) > 0) m1b |= 1u << kq;
+          if ((int16_t)(wd[i] >> 16) > 0) m1b |= 1u << (kq + 1);
+        }
       }
+      up_l2(nxt, g_rgb, w, ray_id);
+      tc::named_sync(1, 512);   // every row's g_z3 and scale are in fs->smp
+      bwd_wait(fs, &fs->bar_d2, ph_d2);
+      ph_d2 ^= 1;
+      tc::fence_after_sync();
+      // Hidden unit oh over the tile rows 32 qw .. 32 qw + 31 (two halves of
+      // 16): G2 = (W3^T g_z3) * (z2 > 0), and the sums over rows dW3 +=
+      // g_z3 h2^T, db2 += G2 in registers.  G2 goes out twice: at the
+      // CTA-wide scale S2 into tensor memory over the half's own D2 columns
+      // (lane = unit, K = row: the A operand of dW2), and at each row's own
+      // scale sG2 into shared memory as [unit][row] core matrices (the
+      // MN-major A operand of g_h1).
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int r0 = 32 * qw + 16 * h;
+        float v[16];
+        tc::tmem_ld16(lane_base + cTmp + r0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float4 q = fs->smp[r0 + i];
+          const float z2 = fmaf(v[i], inv2, b2o);
+          const float gs = fmaf(w3o2, q.z, fmaf(w3o1, q.y, w3o0 * q.x));
+          const float g = z2 > 0.0f ? gs : 0.0f;
+          const float hh = fmaxf(z2, 0.0f);
+          db2acc += g;
+          dW3acc[0] = fmaf(q.x, hh, dW3acc[0]);
+          dW3acc[1] = fmaf(q.y, hh, dW3acc[1]);
+          dW3acc[2] = fmaf(q.z, hh, dW3acc[2]);
+          v[i] = g;
+        }
+        uint32_t hl[16];
+        split16<Op>(v, S2, hl, vmax);
+        tc::tmem_st16(lane_base + cTmp + r0, hl);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] *= fs->smp[r0 + i].w;
+        split16<Op>(v, 1.0f, hl, vmax);
+        // the previous tile's g_X and dW1 (readers of G's shared memory, X and
+        // the g_X columns) are done
+        if (h == 0 && k > 0) {
+          bwd_wait(fs, &fs->bar_gx, ph_gx);
+          ph_gx ^= 1;
+          tc::fence_after_sync();
+        }
+        st_terms16<Op, false>(sm + bGh, sm + bGl, oh, r0, hl, 1.0f);
+      }
+      if (k > 0 && qw == 0) store_gx();
+      tc::tmem_wait_st();
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fs->g2_full);
+      up_l3(nxt, g_rgb, g_color, rgb);
+      // the next tile's H1 terms, once dW2 has read this tile's
+      if (tid == 0 && k + 1 < nt) {
+        if (bwd_wait(fs, &fs->bar_dw2, ph_dw2)) {
+          tc::mbar_arrive_expect_tx(&fs->bar_h, 2 * kHBytes);
+          tc::bulk_g2s(img + iHh, img_g + (size_t)tile_of(k + 1) * kImage + iHh, 2 * kHBytes, &fs->bar_h);
+          inflight_h = true;
+        }
+        ph_dw2 ^= 1;
+      }
+      bwd_wait(fs, &fs->bar_gh, ph_gh);
+      ph_gh ^= 1;
+      tc::fence_after_sync();
+      // G1 = g_h1 * (H1 > 0): at S1 in shared memory (dW1), at sG1 in tensor
+      // memory (g_X), in two halves of 16 hidden units
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = 32 * qw + 16 * h;
+        float v[16];
+        tc::tmem_ld16(lane_base + cGH + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = ((m1b >> (16 * h + i)) & 1u) ? v[i] : 0.0f;
+        uint32_t hl[16];
+        split16<Op>(v, fG1, hl, vmax);
+        tc::tmem_st16(lane_base + cGH + c0, hl);
+        st_terms16<Op>(sm + bGh, sm + bGl, row, c0, hl, r1);
+      }
+      tc::tmem_wait_st();
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fs->g1_full);
+      prev_s = valid ? s : -1;
+      prev_invX = invX;
+      cur = nxt;
     }
-    cur = nxt;
-    tc::fence_before_sync();
-    __syncthreads();
-  }
-  // a load still in flight (only after a failed wait) must land before exit
-  if (!ok && tid == 0) {
+    // the last tile's g_X
+    if (nt > 0) {
+      bwd_wait(fs, &fs->bar_gx, ph_gx);
+      tc::fence_after_sync();
+      if (qw == 0) store_gx();
+    }
+    // a copy issued but never seen landed (only after a failed wait) lands before exit
     if (inflight_h) tc::mbar_wait(&fs->bar_h, ph_h, kSpin);
-    if (inflight_x) tc::mbar_wait(&fs->bar_x, ph_x, kSpin);
-    set_status(DVGO_ERR_TIMEOUT);
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const bool ok = !*reinterpret_cast<volatile int*>(&fs->abort);
   if (vmax >= Op::kMaxScaled) set_status(DVGO_ERR_RANGE);
   // This CTA's gradient goes to its own row of the partials array (every
   // parameter written, no atomics); a second kernel sums the rows in a fixed
@@ -1125,10 +1293,12 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   // memory first (the G and image buffers are free now).
   float* pr = reinterpret_cast<float*>(sm + bGh);            // [16 warps][4][32]
   float* pr3 = pr + 16 * 4 * 32;                             // [4 lane quarters][3]
+  if (compute) {
 #pragma unroll
-  for (int c = 0; c < kOut; ++c) pr[(warp * 4 + c) * 32 + lane] = dW3acc[c];
-  pr[(warp * 4 + 3) * 32 + lane] = db2acc;
-  if (qw == 0) {
+    for (int c = 0; c < kOut; ++c) pr[(warp * 4 + c) * 32 + lane] = dW3acc[c];
+    pr[(warp * 4 + 3) * 32 + lane] = db2acc;
+  }
+  if (compute && qw == 0) {
 #pragma unroll
     for (int c = 0; c < kOut; ++c) {
       float v = db3acc[c];
@@ -1142,7 +1312,7 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
   tc::fence_after_sync();
   float* P = part + (size_t)blockIdx.x * kNumParams;
   const bool has_tiles = (int64_t)blockIdx.x < ntiles;
-  if (has_tiles && qw == 0) {   // warp l: W3[:, 32 l + lane] and b2[32 l + lane] over the 4 row quarters
+  if (has_tiles && compute && qw == 0) {   // warp l: W3[:, 32 l + lane] and b2[32 l + lane] over the 4 row quarters
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float v = ((pr[((warp + 0) * 4 + c) * 32 + lane] + pr[((warp + 4) * 4 + c) * 32 + lane]) +
@@ -1151,7 +1321,8 @@ __global__ void __launch_bounds__(512, 1) rgbnet_bwd_tc_kernel(
     }
   }
   if (has_tiles && tid < kOut) P[kOffB3 + tid] = ((pr3[tid] + pr3[kOut + tid]) + pr3[2 * kOut + tid]) + pr3[3 * kOut + tid];
-  if (has_tiles) {
+  if (has_tiles && compute) {
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     // dW2 / dW1 rows (TMEM lane = output neuron) through a per-warp 32 x 33
     // shared-memory transpose, so that each store covers 32 consecutive
     // parameters of one row
@@ -1266,7 +1437,7 @@ static int rgbnet_bwd_tc(const float* g_rgb, const float* g_color, const float* 
   }
   const int grid = (int)std::min<int64_t>((n_cap + kTile - 1) / kTile, kNumSMs);
   float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(act) + act_images_end(n_cap));
-  rgbnet_bwd_tc_kernel<Op><<<grid, 512, smem, st>>>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev,
+  rgbnet_bwd_tc_kernel<Op><<<grid, 544, smem, st>>>(g_rgb, g_color, w, rgb, ray_id, idx, n_cap, n_dev,
                                                     params, reinterpret_cast<const uint8_t*>(act), part,
                                                     g_k0);
   partials_reduce_kernel<<<(kNumParams + 31) / 32, 256, 0, st>>>(part, grid, n_cap, n_dev, g_params);
