@@ -1147,13 +1147,26 @@ extern "C" int dvgo_sample_grid_bwd2(const float* g_out_a, int32_t C_a, float* g
   return dvgo_sample_grid_bwd(g_out_b, gd, C_b, xyz, idx, n_cap, n_dev, g_grid_b, touched_b, stream);
 }
 
+// beta^t in FP64 by binary exponentiation (about 2 log2 t products; this
+// GPU's FP64 rate makes a general pow() cost several microseconds on one
+// thread).
+__device__ __forceinline__ double pow_int(double beta, int64_t t) {
+  double r = 1.0;
+  while (t > 0) {
+    if (t & 1) r *= beta;
+    beta *= beta;
+    t >>= 1;
+  }
+  return r;
+}
+
 // step[0] += 1; step[1] holds the two FP32 bias corrections of the new t.
 __global__ void step_increment_kernel(int64_t* step, float beta1, float beta2) {
   const int64_t t = step[0] + 1;
   step[0] = t;
   float* c = reinterpret_cast<float*>(step + 1);
-  c[0] = (float)(1.0 / (1.0 - pow((double)beta1, (double)t)));
-  c[1] = (float)(1.0 / (1.0 - pow((double)beta2, (double)t)));
+  c[0] = (float)(1.0 / (1.0 - pow_int((double)beta1, t)));
+  c[1] = (float)(1.0 / (1.0 - pow_int((double)beta2, t)));
 }
 
 static int adam_multi(const dvgo_adam_param* params, int32_t count, float beta1, float beta2, float eps,

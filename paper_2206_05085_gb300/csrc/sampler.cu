@@ -146,7 +146,7 @@ constexpr int kBitWords = 32;
 // occupancy lookups.
 // kNdc: mode 2 (layer crossings of the warped ray) instead of mode 0.
 template <bool kNdc>
-__global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
+__global__ void __launch_bounds__(256, 8) bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
                                   const float* __restrict__ rd, int64_t R,
                                   const uint8_t* __restrict__ mask, int32_t* __restrict__ counts,
                                   uint32_t* __restrict__ bits) {
@@ -166,18 +166,27 @@ __global__ void bbox_count_kernel(SamplerArgs A, const float* __restrict__ ro,
     }
     int cnt = 0;
     uint32_t mine = 0;
-    for (int k0 = 0; k0 < sp.n; k0 += 32) {
-      int k = k0 + lane;
-      bool keep = false;
-      if (k < sp.n) {
-        float x[3];
-        if (kNdc) ndc_point(A, q, k, x);
-        else point_at(A, o, d, sp.tlo, k, x);
-        keep = keep_point(A, mask, x);
+    // four 32-step chunks per round, so that their occupancy lookups are in
+    // flight together
+    for (int k0 = 0; k0 < sp.n; k0 += 128) {
+      bool keep[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + 32 * u + lane;
+        keep[u] = false;
+        if (k < sp.n) {
+          float x[3];
+          if (kNdc) ndc_point(A, q, k, x);
+          else point_at(A, o, d, sp.tlo, k, x);
+          keep[u] = keep_point(A, mask, x);
+        }
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (lane == (k0 >> 5)) mine = bal;
-      cnt += __popc(bal);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned bal = __ballot_sync(0xffffffffu, keep[u]);
+        if (lane == (k0 >> 5) + u) mine = bal;
+        cnt += __popc(bal);
+      }
     }
     if (lane == 0) counts[r] = cnt;
     if (bits && 32 * lane < sp.n) bits[r * kBitWords + lane] = mine;
