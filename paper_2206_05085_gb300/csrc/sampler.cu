@@ -264,21 +264,109 @@ __global__ void bbox_fill_kernel(SamplerArgs A, const float* __restrict__ ro,
   }
 }
 
-// Mode 1: contracted-space march (Eq. ub), one thread per ray.  The march is
-// sequential; pass 1 counts, pass 2 repeats it and writes.
+// Mode 1: contracted-space march (Eq. ub).  One step at world point x: the
+// contracted point xc and the Jacobian-mapped direction j (false when xc's
+// contracted radius has reached rmax: the march ends before xc), then the
+// advance of x by the contracted step (false when the step is not finite).
+struct CMarch {
+  float b, opb, rmax, two_b;
+  bool p_inf;
+};
+
+__device__ __forceinline__ CMarch cmarch_consts(const SamplerArgs& A) {
+  CMarch M;
+  M.b = A.s.contract_b;
+  M.opb = __fadd_rn(1.0f, M.b);
+  M.rmax = __fsub_rn(M.opb, A.s.step_c);
+  M.two_b = __fmul_rn(2.0f, M.b);
+  M.p_inf = A.s.p_inf != 0;
+  return M;
+}
+
+__device__ __forceinline__ bool cmarch_point(const CMarch& M, const float x[3], const float d[3], float xc[3],
+                                             float j[3]) {
+  float rad;
+  int m = 0;
+  if (M.p_inf) {
+    float a0 = fabsf(x[0]), a1 = fabsf(x[1]), a2 = fabsf(x[2]);
+    rad = a0;
+    if (a1 > rad) { rad = a1; m = 1; }
+    if (a2 > rad) { rad = a2; m = 2; }
+  } else {
+    rad = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])),
+                               __fmul_rn(x[2], x[2])));
+  }
+  if (rad <= 1.0f) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { xc[a] = x[a]; j[a] = d[a]; }
+  } else {
+    float r2 = __fmul_rn(rad, rad);
+    float gr = __fsub_rn(__fdiv_rn(M.opb, rad), __fdiv_rn(M.b, r2));
+    float gp = __fsub_rn(__fdiv_rn(M.two_b, __fmul_rn(r2, rad)), __fdiv_rn(M.opb, r2));
+    float rdot;
+    if (M.p_inf) {
+      float xm = m == 0 ? x[0] : (m == 1 ? x[1] : x[2]);
+      float dm = m == 0 ? d[0] : (m == 1 ? d[1] : d[2]);
+      rdot = xm < 0.0f ? -dm : dm;
+    } else {
+      rdot = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], d[0]), __fmul_rn(x[1], d[1])),
+                                 __fmul_rn(x[2], d[2])), rad);
+    }
+    float gq = __fmul_rn(gp, rdot);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xc[a] = __fmul_rn(gr, x[a]);
+      j[a] = __fadd_rn(__fmul_rn(gr, d[a]), __fmul_rn(gq, x[a]));
+    }
+  }
+  float cr;
+  if (M.p_inf) {
+    cr = fabsf(xc[0]);
+    if (fabsf(xc[1]) > cr) cr = fabsf(xc[1]);
+    if (fabsf(xc[2]) > cr) cr = fabsf(xc[2]);
+  } else {
+    cr = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(xc[0], xc[0]), __fmul_rn(xc[1], xc[1])),
+                              __fmul_rn(xc[2], xc[2])));
+  }
+  return cr < M.rmax;
+}
+
+__device__ __forceinline__ bool cmarch_advance(const SamplerArgs& A, float x[3], const float d[3],
+                                               const float j[3]) {
+  float nj = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(j[0], j[0]), __fmul_rn(j[1], j[1])),
+                                  __fmul_rn(j[2], j[2])));
+  float h = __fdiv_rn(A.s.step_c, nj);
+  if (!(h > 0.0f) || isinf(h)) return false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(x[a], __fmul_rn(h, d[a]));
+  return true;
+}
+
+// Checkpoints of the march for the parallel second pass: the march of a ray
+// is cut into kCkpt chunks of L = ceil(max_steps / kCkpt) steps; record c of
+// the ray holds x at step c L (3 floats) and the kept samples of chunk c
+// (int32, -1 for a chunk the march never reaches).  kCkpt x 4 words per ray
+// fit the per-ray keep-bit words of the workspace.
+constexpr int kCkpt = 8;
+
+__device__ __forceinline__ int ckpt_len(const SamplerArgs& A) {
+  return (A.s.max_steps + kCkpt - 1) / kCkpt;
+}
+
+// Mode 1, one thread per ray: the whole march.  Pass 1 (kWrite false)
+// counts, and with ckpt records the checkpoints; pass 2 without checkpoints
+// (kWrite) repeats the march and writes.
 template <bool kWrite>
 __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
                                   const float* __restrict__ rd, int64_t R,
                                   const uint8_t* __restrict__ mask, int32_t* __restrict__ counts,
+                                  uint32_t* __restrict__ ckpt,
                                   const int64_t* __restrict__ ray_off, float* __restrict__ xyz,
                                   int32_t* __restrict__ ray_id, int32_t* __restrict__ step_k,
                                   float* __restrict__ s_mid, float* __restrict__ s_len) {
-  const float b = A.s.contract_b;
-  const float opb = __fadd_rn(1.0f, b);
-  const float rmax = __fsub_rn(opb, A.s.step_c);
-  const float two_b = __fmul_rn(2.0f, b);
-  const bool p_inf = A.s.p_inf != 0;
+  const CMarch M = cmarch_consts(A);
   const float inv_steps = __fdiv_rn(1.0f, (float)A.s.max_steps);
+  const int L = ckpt_len(A);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
        r += (int64_t)gridDim.x * blockDim.x) {
     float o[3], d[3];
@@ -286,54 +374,20 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
     float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(A.s.near, d[a]));
-    int cnt = 0;
+    int cnt = 0, chunk_start = 0, c = -1;
     int64_t pos = kWrite ? ray_off[r] : 0;
+    uint32_t* rec = ckpt ? ckpt + r * (4 * kCkpt) : nullptr;
     for (int k = 0; k < A.s.max_steps; ++k) {
-      float rad;
-      int m = 0;
-      if (p_inf) {
-        float a0 = fabsf(x[0]), a1 = fabsf(x[1]), a2 = fabsf(x[2]);
-        rad = a0;
-        if (a1 > rad) { rad = a1; m = 1; }
-        if (a2 > rad) { rad = a2; m = 2; }
-      } else {
-        rad = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])),
-                                   __fmul_rn(x[2], x[2])));
+      if (!kWrite && rec && k % L == 0) {   // a new chunk: close the previous one, record x
+        if (c >= 0) rec[4 * c + 3] = (uint32_t)(cnt - chunk_start);
+        ++c;
+        chunk_start = cnt;
+        rec[4 * c] = __float_as_uint(x[0]);
+        rec[4 * c + 1] = __float_as_uint(x[1]);
+        rec[4 * c + 2] = __float_as_uint(x[2]);
       }
       float xc[3], j[3];
-      if (rad <= 1.0f) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) { xc[a] = x[a]; j[a] = d[a]; }
-      } else {
-        float r2 = __fmul_rn(rad, rad);
-        float gr = __fsub_rn(__fdiv_rn(opb, rad), __fdiv_rn(b, r2));
-        float gp = __fsub_rn(__fdiv_rn(two_b, __fmul_rn(r2, rad)), __fdiv_rn(opb, r2));
-        float rdot;
-        if (p_inf) {
-          float xm = m == 0 ? x[0] : (m == 1 ? x[1] : x[2]);
-          float dm = m == 0 ? d[0] : (m == 1 ? d[1] : d[2]);
-          rdot = xm < 0.0f ? -dm : dm;
-        } else {
-          rdot = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], d[0]), __fmul_rn(x[1], d[1])),
-                                     __fmul_rn(x[2], d[2])), rad);
-        }
-        float gq = __fmul_rn(gp, rdot);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          xc[a] = __fmul_rn(gr, x[a]);
-          j[a] = __fadd_rn(__fmul_rn(gr, d[a]), __fmul_rn(gq, x[a]));
-        }
-      }
-      float cr;
-      if (p_inf) {
-        cr = fabsf(xc[0]);
-        if (fabsf(xc[1]) > cr) cr = fabsf(xc[1]);
-        if (fabsf(xc[2]) > cr) cr = fabsf(xc[2]);
-      } else {
-        cr = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(xc[0], xc[0]), __fmul_rn(xc[1], xc[1])),
-                                  __fmul_rn(xc[2], xc[2])));
-      }
-      if (!(cr < rmax)) break;
+      if (!cmarch_point(M, x, d, xc, j)) break;
       if (keep_point(A, mask, xc)) {
         if (kWrite) {
           int64_t s = pos + cnt;
@@ -347,15 +401,107 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
         }
         ++cnt;
       }
-      float nj = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(j[0], j[0]), __fmul_rn(j[1], j[1])),
-                                      __fmul_rn(j[2], j[2])));
-      float h = __fdiv_rn(A.s.step_c, nj);
-      if (!(h > 0.0f) || isinf(h)) break;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(x[a], __fmul_rn(h, d[a]));
+      if (!cmarch_advance(A, x, d, j)) break;
     }
-    if (!kWrite) counts[r] = cnt;
+    if (!kWrite) {
+      counts[r] = cnt;
+      if (rec) {
+        if (c >= 0) rec[4 * c + 3] = (uint32_t)(cnt - chunk_start);
+        for (int cc = c + 1; cc < kCkpt; ++cc) rec[4 * cc + 3] = 0xffffffffu;
+      }
+    }
   }
+}
+
+// Mode 1, pass 2 from the checkpoints: a block of 256 threads takes 32 rays,
+// warp c of it chunk c of each of them (the lanes of a warp march the same
+// part of 32 rays, so they take the same branches); each thread repeats the
+// march of its chunk from the recorded x (the same FP32 operations as pass
+// 1, so the same points) and writes its kept samples after those of the
+// ray's earlier chunks.
+__global__ void __launch_bounds__(32 * kCkpt) contracted_fill_kernel(
+    SamplerArgs A, const float* __restrict__ rd, int64_t R, const uint8_t* __restrict__ mask,
+    const uint32_t* __restrict__ ckpt, const int64_t* __restrict__ ray_off, float* __restrict__ xyz,
+    int32_t* __restrict__ ray_id, int32_t* __restrict__ step_k, float* __restrict__ s_mid,
+    float* __restrict__ s_len) {
+  __shared__ int kept[kCkpt][32];
+  const CMarch M = cmarch_consts(A);
+  const float inv_steps = __fdiv_rn(1.0f, (float)A.s.max_steps);
+  const int L = ckpt_len(A);
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+  const bool ray_ok = r < R;
+  const uint32_t* rec = ckpt + (ray_ok ? r : 0) * (4 * kCkpt) + 4 * c;
+  const uint32_t n_c = ray_ok ? rec[3] : 0xffffffffu;
+  const int mine = n_c == 0xffffffffu ? 0 : (int)n_c;
+  kept[c][lane] = mine;
+  __syncthreads();
+  int before = 0;   // kept samples of the ray's earlier chunks
+  for (int q = 0; q < c; ++q) before += kept[q][lane];
+  if (mine == 0) return;
+  float d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = __ldg(rd + 3 * r + a);
+  float x[3] = {__uint_as_float(rec[0]), __uint_as_float(rec[1]), __uint_as_float(rec[2])};
+  int64_t s = ray_off[r] + before;
+  const bool vec = ((reinterpret_cast<uintptr_t>(xyz) | reinterpret_cast<uintptr_t>(ray_id) |
+                     reinterpret_cast<uintptr_t>(step_k) | reinterpret_cast<uintptr_t>(s_mid) |
+                     reinterpret_cast<uintptr_t>(s_len)) & 15u) == 0;
+  // samples are written in groups of four consecutive list positions (16-byte
+  // stores; xyz as three), one at a time before the first aligned position
+  float bx[4][3];
+  int bk[4];
+  int nb = 0;
+  auto put1 = [&](const float* p, int k) {
+    xyz[3 * s] = p[0];
+    xyz[3 * s + 1] = p[1];
+    xyz[3 * s + 2] = p[2];
+    ray_id[s] = (int32_t)r;
+    step_k[s] = k;
+    s_mid[s] = __fmul_rn(__fadd_rn((float)k, 0.5f), inv_steps);
+    s_len[s] = inv_steps;
+    ++s;
+  };
+  auto flush4 = [&]() {
+    float4* xq = reinterpret_cast<float4*>(xyz + 3 * s);
+    xq[0] = make_float4(bx[0][0], bx[0][1], bx[0][2], bx[1][0]);
+    xq[1] = make_float4(bx[1][1], bx[1][2], bx[2][0], bx[2][1]);
+    xq[2] = make_float4(bx[2][2], bx[3][0], bx[3][1], bx[3][2]);
+    *reinterpret_cast<int4*>(ray_id + s) = make_int4((int)r, (int)r, (int)r, (int)r);
+    *reinterpret_cast<int4*>(step_k + s) = make_int4(bk[0], bk[1], bk[2], bk[3]);
+    *reinterpret_cast<float4*>(s_mid + s) = make_float4(
+        __fmul_rn(__fadd_rn((float)bk[0], 0.5f), inv_steps), __fmul_rn(__fadd_rn((float)bk[1], 0.5f), inv_steps),
+        __fmul_rn(__fadd_rn((float)bk[2], 0.5f), inv_steps), __fmul_rn(__fadd_rn((float)bk[3], 0.5f), inv_steps));
+    *reinterpret_cast<float4*>(s_len + s) = make_float4(inv_steps, inv_steps, inv_steps, inv_steps);
+    s += 4;
+  };
+  const int k_end = min((c + 1) * L, A.s.max_steps);
+  for (int k = c * L; k < k_end; ++k) {
+    float xc[3], j[3];
+    if (!cmarch_point(M, x, d, xc, j)) break;
+    if (keep_point(A, mask, xc)) {
+      if (!vec || ((s & 3) != 0 && nb == 0)) {
+        put1(xc, k);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)   // static slots, so that the buffer stays in registers
+          if (q == nb) {
+            bx[q][0] = xc[0];
+            bx[q][1] = xc[1];
+            bx[q][2] = xc[2];
+            bk[q] = k;
+          }
+        if (++nb == 4) {
+          flush4();
+          nb = 0;
+        }
+      }
+    }
+    if (!cmarch_advance(A, x, d, j)) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < nb) put1(bx[q], bk[q]);
 }
 
 // Exclusive scan of int32 counts into int64 offsets off[0..n] (one block of
@@ -506,8 +652,9 @@ static bool fill_args(SamplerArgs& A, const dvgo_grid_desc* g, const dvgo_sample
 
 using namespace dvgo;
 
-// Workspace: per-ray counts ((R+1) int32, padded to 256 bytes), then the
-// per-ray keep bits of pass 1 (R x kBitWords uint32).
+// Workspace: per-ray counts ((R+1) int32, padded to 256 bytes), then R x
+// kBitWords uint32 per-ray words: the keep bits of pass 1 (modes 0 and 2) or
+// the march checkpoints of pass 1 (mode 1).
 static size_t counts_bytes(int64_t R) {
   return (size_t)((R + 1) * sizeof(int32_t) + 255) / 256 * 256;
 }
@@ -560,11 +707,14 @@ extern "C" int dvgo_sample_rays(const float* rays_o, const float* rays_d, int64_
     // every SM (8192 rays: 256 blocks)
     const int block = 32;
     int g = (int)ceil_div(R, block);
-    contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
-                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+    // pass 1 records the march's checkpoints in the keep-bit words, so that
+    // pass 2 runs kCkpt chunks of each march in parallel
+    uint32_t* ckpt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + counts_bytes(R));
+    contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, ckpt,
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    contracted_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
-                                                 ray_id, step_k, s_mid, s_len);
+    contracted_fill_kernel<<<(int)ceil_div(R, 32), 32 * kCkpt, 0, st>>>(A, rays_d, R, mask, ckpt, ray_off,
+                                                                        xyz, ray_id, step_k, s_mid, s_len);
   }
   return launch_status();
 }
@@ -738,9 +888,9 @@ extern "C" int dvgo_sample_rays_noalloc(const float* rays_o, const float* rays_d
     const int block = 32;
     int g = (int)ceil_div(R, block);
     contracted_kernel<false><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, counts, nullptr,
-                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     scan_counts_kernel<<<1, 1024, 0, st>>>(counts, R, ray_off, nullptr);
-    contracted_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, ray_off, xyz,
+    contracted_kernel<true><<<g, block, 0, st>>>(A, rays_o, rays_d, R, mask, nullptr, nullptr, ray_off, xyz,
                                                  ray_id, step_k, s_mid, s_len);
   }
   return launch_status();
