@@ -378,6 +378,35 @@ def test_sampler_long_march(L, step_scale):
     _check_samples(got, ref)
 
 
+@pytest.mark.parametrize("max_steps", [1, 7, 13, 100, 600])
+def test_contracted_march_chunks(L, max_steps):
+    """The contracted march's second pass runs eight chunks of each march in
+    parallel from checkpoints that the first pass records: step caps that
+    leave one-step chunks, a partial last chunk, and marches that end (at the
+    contracted boundary) before the cap, on rays from inside and outside the
+    unit ball, bit-exact against the oracle's sequential march."""
+    import dataclasses
+    cfg = synth.CFG3
+    rp = dataclasses.replace(synth.render_params(cfg), max_steps=max_steps)
+    o, d = synth.rays(cfg, n_rays=300)
+    o = o.copy()
+    o[::3] *= np.float32(1.6)      # a third of the rays start outside the unit ball
+    mask_np = mask_t = None
+    if max_steps >= 100:   # with occupancy culling (the first steps near the origin are empty)
+        D = synth.density_grid(cfg)
+        mask_np = oracle.build_mask(D, shift32(), rp.interval, 1e-4)
+        mask_t = dev(mask_np)
+    got = _gpu_sample(L, cfg, rp, o, d, mask_t)
+    from oracle_step import sample
+    ref = sample(cfg, rp, o, d, mask_np)
+    assert ref.S > 0
+    _check_samples(got, ref)
+    if max_steps == 600:   # some marches end at the contracted boundary before the cap
+        last = np.array([ref.step_k[b:e].max() if e > b else -1
+                         for b, e in zip(ref.ray_off[:-1], ref.ray_off[1:])])
+        assert (last < max_steps - 1).sum() > 10
+
+
 def test_sampler_edge_cases(L):
     cfg = synth.CFG2
     rp = synth.render_params(cfg)
