@@ -218,7 +218,8 @@ def test_full_size_step_sampled_outputs(T):
     checked where the oracle can follow it: the whole sample list (bit-exact
     against the oracle's sampler), the per-ray and per-sample outputs of 48
     sampled rays (oracle run on those rays, gradients rescaled to the batch's
-    1/R), and the loss as the mean of the per-ray terms."""
+    1/R), the grids after the step's TV + Adam on the voxels only those rays
+    reach, and the loss as the mean of the per-ray terms."""
     import oracle
     from oracle_step import forward_backward, sample, shift32
     from paper_2206_05085_gb300 import _lib as L
@@ -245,6 +246,9 @@ def test_full_size_step_sampled_outputs(T):
     n_live = host(tr.n_live)
     color, L_r, loss = host(tr.color), host(tr.L_r), host(tr.loss)
     w, rgb, g_raw, g_k0, xyz = (host(x[:S]) for x in (tr.w, tr.rgb, tr.g_raw, tr.g_k0, tr.xyz))
+    ray_id = tr.ray_id[:S].cpu().numpy()
+    p_d = host(tr.dense(tr.density, "p"))[..., 0]
+    p_f = host(tr.dense(tr.feature, "p"))
     # the whole sample list
     mask = oracle.build_mask(D, shift32(rp.alpha_init), rp.interval, rp.mask_thres)
     smp = sample(cfg, rp, o, d, mask)
@@ -271,6 +275,12 @@ def test_full_size_step_sampled_outputs(T):
     zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
     keep = zmin >= 1e-6
     assert rel_err(g_k0[rows][live][keep], fb["g_k0"][keep] * scale) < 1e-5
+    # the grids after the step's TV + Adam on the voxels only those rays reach
+    live_all = np.zeros(S, bool)
+    for r in range(R):
+        a = int(ray_off[r])
+        live_all[a:a + int(n_live[r])] = True
+    _check_exclusive_voxels(cfg, rp, D, Fg, P, fb, scale, xyz, live_all, ray_id, sel, p_d, p_f)
 
 
 def _exclusive_voxels(cfg, xyz_all, live_all, ray_all, sel):
@@ -287,15 +297,52 @@ def _exclusive_voxels(cfg, xyz_all, live_all, ray_all, sel):
     return np.setdiff1d(np.unique(lin[mine]), np.unique(lin[~mine]))
 
 
-@pytest.mark.parametrize("name", ["dvgo_160", "unbounded_320"])
+def _check_exclusive_voxels(cfg, rp, D, Fg, P, fb, scale, xyz, live_all, ray_id, sel, p_d, p_f,
+                            g_d=None, g_f=None):
+    """On the voxels that only the selected rays reach: the grid gradients
+    (when given) and the grids after TV + Adam (first step from zero moments)
+    against the oracle run on those rays, its gradients rescaled by scale."""
+    import oracle
+    from oracle_step import optimizer
+    excl = _exclusive_voxels(cfg, xyz, live_all, ray_id, sel)
+    assert len(excl) > 500
+    fb_g = dict(fb, g_density=fb["g_density"] * scale, g_feature=fb["g_feature"] * scale,
+                g_params=np.zeros_like(fb["g_params"]))
+    ref_d = fb_g["g_density"].reshape(-1)[excl]
+    ref_f = fb_g["g_feature"].reshape(-1, 12)[excl]
+    if g_d is not None:
+        assert rel_err(g_d.reshape(-1)[excl], ref_d) < 1e-5
+    # feature voxels of samples with a ReLU input within rounding of 0 are set aside
+    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
+    amb = zmin < 1e-6
+    keep = np.ones(len(excl), bool)
+    if amb.any():
+        from step_parity import cell_voxels
+        G = np.array(synth.grid_dims(cfg))
+        v = cell_voxels(cfg, fb["smp"].xyz[fb["live"]][amb])
+        bad = (v[:, 0] * G[1] + v[:, 1]) * G[0] + v[:, 2]
+        keep = ~np.isin(excl, bad)
+    if g_f is not None:
+        assert rel_err(g_f.reshape(-1, 12)[excl][keep], ref_f[keep]) < 1e-5
+    # TV + Adam (first step from zero moments) on those voxels, where the
+    # gradient is clear of rounding noise
+    opt = optimizer(rp, 1, D, Fg, P, fb_g, False, D, Fg)
+    for got, ref, g in ((p_d.reshape(-1)[excl], opt["density"].reshape(-1)[excl],
+                         opt["g_density_tv"].reshape(-1)[excl]),
+                        (p_f.reshape(-1, 12)[excl][keep], opt["feature"].reshape(-1, 12)[excl][keep],
+                         opt["g_feature_tv"].reshape(-1, 12)[excl][keep])):
+        clear = np.abs(g) > 1e-3 * np.max(np.abs(g))
+        assert np.max(np.abs(got - ref)[clear]) / np.max(np.abs(ref)) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["dvgo_160", "unbounded_320", "forward_facing_384"])
 def test_full_size_grid_gradients_and_adam(T, name):
     """At the benchmark's full size (the workload's grids and ray count): the
     per-ray and per-sample outputs of 48 sampled rays, and the grid gradients
     and the parameters after TV + Adam on the voxels that only those rays
     reach, against the oracle run on those rays (its gradients rescaled from
     1/48 to the batch's 1/R)."""
-    import oracle
-    from oracle_step import forward_backward, optimizer
+    from oracle_step import forward_backward
     cfg = synth.CONFIGS[name]
     rp = synth.render_params(cfg)
     D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
@@ -315,7 +362,7 @@ def test_full_size_grid_gradients_and_adam(T, name):
     for r in range(R):
         live_all[ray_off[r]:ray_off[r] + n_live[r]] = True
     color, L_r = host(tr.color), host(tr.L_r)
-    w, rgb, g_raw, g_k0 = (host(x[:S]) for x in (tr.w, tr.rgb, tr.g_raw, tr.g_k0))
+    w, rgb, g_raw = (host(x[:S]) for x in (tr.w, tr.rgb, tr.g_raw))
     g_d = host(tr.dense(tr.density, "g"))[..., 0]
     g_f = host(tr.dense(tr.feature, "g"))
     tr.regularize_and_step(False)
@@ -335,30 +382,5 @@ def test_full_size_grid_gradients_and_adam(T, name):
     assert rel_err(w[rows], fb["w"]) < 1e-5
     assert rel_err(rgb[rows][live], fb["rgb"][live]) < 1e-5
     assert rel_err(g_raw[rows][live], fb["g_raw"][live] * scale) < 1e-5
-    excl = _exclusive_voxels(cfg, xyz, live_all, ray_id, sel)
-    assert len(excl) > 500
-    fb_g = dict(fb, g_density=fb["g_density"] * scale, g_feature=fb["g_feature"] * scale,
-                g_params=np.zeros_like(fb["g_params"]))
-    ref_d = fb_g["g_density"].reshape(-1)[excl]
-    ref_f = fb_g["g_feature"].reshape(-1, 12)[excl]
-    assert rel_err(g_d.reshape(-1)[excl], ref_d) < 1e-5
-    # feature voxels of samples with a ReLU input within rounding of 0 are set aside
-    zmin = oracle.mlp_min_abs_preact(synth.RGBNET_DIMS, P.astype(np.float64), fb["x"])
-    amb = zmin < 1e-6
-    keep = np.ones(len(excl), bool)
-    if amb.any():
-        from step_parity import cell_voxels
-        G = np.array(synth.grid_dims(cfg))
-        v = cell_voxels(cfg, fb["smp"].xyz[fb["live"]][amb])
-        bad = (v[:, 0] * G[1] + v[:, 1]) * G[0] + v[:, 2]
-        keep = ~np.isin(excl, bad)
-    assert rel_err(g_f.reshape(-1, 12)[excl][keep], ref_f[keep]) < 1e-5
-    # TV + Adam (first step from zero moments) on those voxels, where the
-    # gradient is clear of rounding noise
-    opt = optimizer(rp, 1, D, Fg, P, fb_g, False, D, Fg)
-    for got, ref, g in ((p_d.reshape(-1)[excl], opt["density"].reshape(-1)[excl],
-                         opt["g_density_tv"].reshape(-1)[excl]),
-                        (p_f.reshape(-1, 12)[excl][keep], opt["feature"].reshape(-1, 12)[excl][keep],
-                         opt["g_feature_tv"].reshape(-1, 12)[excl][keep])):
-        clear = np.abs(g) > 1e-3 * np.max(np.abs(g))
-        assert np.max(np.abs(got - ref)[clear]) / np.max(np.abs(ref)) < 1e-5
+    _check_exclusive_voxels(cfg, rp, D, Fg, P, fb, scale, xyz, live_all, ray_id, sel, p_d, p_f,
+                            g_d, g_f)
