@@ -515,27 +515,45 @@ __device__ __forceinline__ float load_val(const void* grid, int64_t e) {
                : __ldg(reinterpret_cast<const float*>(grid) + e);
 }
 
+// The six neighbour slots of voxel (x, y, z) = local Morton index t of brick
+// b, in the order -x, +x, -y, +y, -z, +z, as offsets from the voxel's own
+// slot (0 where the grid ends; has[d] says which exist; a brick layer of
+// nb[0] nb[1] 512 voxels fits an int32 for every grid the library accepts).  Inside the brick a step along axis a changes only a's
+// interleaved bits (mask M): +1 is ((t | ~M) + 1) & M, -1 is ((t & M) - 1) & M,
+// with t's other bits kept; at the brick face the neighbour is voxel 0 / 7 of
+// the next / previous brick along a.
+struct TvNbr {
+  int32_t off[6];
+  bool has[6];
+};
+
+__device__ __forceinline__ void tv_neighbours(const BrickGeom& g, int64_t b, int t, int x, int y, int z,
+                                              TvNbr& q) {
+  const int c[3] = {x, y, z};
+  const int32_t bstride[3] = {kBrickVox, g.nb[0] * kBrickVox, g.nb[0] * g.nb[1] * kBrickVox};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int32_t M = 0x49 << a, u = t;
+    q.has[2 * a] = c[a] > 0;
+    q.has[2 * a + 1] = c[a] + 1 < g.G[a];
+    // new local index minus the old, plus the brick step where the face is crossed
+    const int32_t lo = (c[a] & 7) == 0 ? (u | M) - u - bstride[a] : ((((u & M) - 1) & M) | (u & ~M)) - u;
+    const int32_t hi = (c[a] & 7) == 7 ? (u & ~M) - u + bstride[a] : ((((u | ~M) + 1) & M) | (u & ~M)) - u;
+    q.off[2 * a] = q.has[2 * a] ? lo : 0;
+    q.off[2 * a + 1] = q.has[2 * a + 1] ? hi : 0;
+  }
+}
+
 // TV gradient of one voxel (thread t of brick b) of one grid.
 template <bool kBF16>
-__device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, const BrickGeom& g, int C,
-                                         float scale, float delta, int dense_mode,
-                                         float* __restrict__ g_grid, int64_t b, int t, int x, int y,
-                                         int z) {
+__device__ __forceinline__ void tv_voxel(const void* __restrict__ grid, int C, float scale, float delta,
+                                         int dense_mode, float* __restrict__ g_grid, int64_t b, int t,
+                                         const TvNbr& q) {
   const int64_t self = b * kBrickVox + t;
   int64_t nbr[6];
-  bool has[6];
-  has[0] = x > 0;
-  has[1] = x + 1 < g.G[0];
-  has[2] = y > 0;
-  has[3] = y + 1 < g.G[1];
-  has[4] = z > 0;
-  has[5] = z + 1 < g.G[2];
-  nbr[0] = has[0] ? voxel_slot(g, x - 1, y, z) : self;
-  nbr[1] = has[1] ? voxel_slot(g, x + 1, y, z) : self;
-  nbr[2] = has[2] ? voxel_slot(g, x, y - 1, z) : self;
-  nbr[3] = has[3] ? voxel_slot(g, x, y + 1, z) : self;
-  nbr[4] = has[4] ? voxel_slot(g, x, y, z - 1) : self;
-  nbr[5] = has[5] ? voxel_slot(g, x, y, z + 1) : self;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nbr[d] = self + q.off[d];
+  const bool* has = q.has;
   if (C % 4 == 0) {
     // sparse mode: a voxel whose data gradient is zero in every channel gets
     // no TV gradient, so its value and neighbours are not loaded at all
@@ -620,15 +638,17 @@ __global__ void __launch_bounds__(512, 2) tv_kernel(TvMulti M, BrickGeom g, floa
     const int bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
     const int x = bx * 8 + lx, y = by * 8 + ly, z = bz * 8 + lz;
     const bool inside = x < g.G[0] && y < g.G[1] && z < g.G[2];
+    TvNbr q;
+    if (inside) tv_neighbours(g, b, t, x, y, z, q);   // shared by the grids
     for (int i = 0; i < M.count; ++i) {
       const TvGridArgs& A = M.a[i];
       if (!dense_mode && A.touched && A.touched[b] == 0) continue;
       if (dense_mode && A.touched && t == 0) A.touched[b] = 1;
       if (!inside) continue;
       if (A.bf16)
-        tv_voxel<true>(A.grid, g, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, x, y, z);
+        tv_voxel<true>(A.grid, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, q);
       else
-        tv_voxel<false>(A.grid, g, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, x, y, z);
+        tv_voxel<false>(A.grid, A.C, A.scale, delta, dense_mode, A.g_grid, b, t, q);
     }
   }
 }

@@ -373,6 +373,16 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     int n, N;
     ray_range(ray_off, n_live, r, b, n, N);
     const float m0 = n > 0 ? __ldg(m + b) : 0.0f;
+    // lane 0's per-ray inputs, loaded before the chunk loop that they follow
+    float te = 0.0f, tg0 = 0.0f, tg1 = 0.0f, tg2 = 0.0f;
+    if (lane == 0) {
+      te = __ldg(T_end + r);
+      if constexpr (kLoss) {
+        tg0 = __ldg(lt.target + 3 * r);
+        tg1 = __ldg(lt.target + 3 * r + 1);
+        tg2 = __ldg(lt.target + 3 * r + 2);
+      }
+    }
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, acc = 0.0f;
     Kahan cW, cWM, tW, tWM;
     for (int c0 = 0; c0 < n; c0 += 32) {
@@ -406,15 +416,13 @@ __global__ void __launch_bounds__(256) composite_distortion_fwd_kernel(
     acc = warp_sum(acc);
     float gc0 = 0.0f, gc1 = 0.0f, gc2 = 0.0f;
     if (lane == 0) {
-      const float te = T_end[r];
       const float c0 = a0 + te * bg0, c1 = a1 + te * bg1, c2 = a2 + te * bg2;
       color[3 * r] = c0;
       color[3 * r + 1] = c1;
       color[3 * r + 2] = c2;
       L_r[r] = acc;
       if constexpr (kLoss) {
-        const float e0 = c0 - __ldg(lt.target + 3 * r), e1 = c1 - __ldg(lt.target + 3 * r + 1),
-                    e2 = c2 - __ldg(lt.target + 3 * r + 2);
+        const float e0 = c0 - tg0, e1 = c1 - tg1, e2 = c2 - tg2;
         gc0 = gscale * e0;
         gc1 = gscale * e1;
         gc2 = gscale * e2;
