@@ -284,7 +284,7 @@ __device__ __forceinline__ CMarch cmarch_consts(const SamplerArgs& A) {
 }
 
 __device__ __forceinline__ bool cmarch_point(const CMarch& M, const float x[3], const float d[3], float xc[3],
-                                             float j[3]) {
+                                             float j[3], bool& inside) {
   float rad;
   int m = 0;
   if (M.p_inf) {
@@ -296,9 +296,13 @@ __device__ __forceinline__ bool cmarch_point(const CMarch& M, const float x[3], 
     rad = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])),
                                __fmul_rn(x[2], x[2])));
   }
-  if (rad <= 1.0f) {
+  inside = rad <= 1.0f;
+  if (inside) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) { xc[a] = x[a]; j[a] = d[a]; }
+    // xc = x: its contracted radius is rad itself (the same operations on
+    // the same values)
+    return rad < M.rmax;
   } else {
     float r2 = __fmul_rn(rad, rad);
     float gr = __fsub_rn(__fdiv_rn(M.opb, rad), __fdiv_rn(M.b, r2));
@@ -331,11 +335,18 @@ __device__ __forceinline__ bool cmarch_point(const CMarch& M, const float x[3], 
   return cr < M.rmax;
 }
 
+// step_c / |j|, the contracted step along j
+__device__ __forceinline__ float cmarch_step_len(const SamplerArgs& A, const float j[3]) {
+  const float nj = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(j[0], j[0]), __fmul_rn(j[1], j[1])),
+                                        __fmul_rn(j[2], j[2])));
+  return __fdiv_rn(A.s.step_c, nj);
+}
+
+// Inside the unit ball j = d, so the step is the ray's constant h_in =
+// cmarch_step_len(A, d), formed once per ray (the same value bit for bit).
 __device__ __forceinline__ bool cmarch_advance(const SamplerArgs& A, float x[3], const float d[3],
-                                               const float j[3]) {
-  float nj = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(j[0], j[0]), __fmul_rn(j[1], j[1])),
-                                  __fmul_rn(j[2], j[2])));
-  float h = __fdiv_rn(A.s.step_c, nj);
+                                               const float j[3], bool inside, float h_in) {
+  const float h = inside ? h_in : cmarch_step_len(A, j);
   if (!(h > 0.0f) || isinf(h)) return false;
 #pragma unroll
   for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(x[a], __fmul_rn(h, d[a]));
@@ -371,6 +382,7 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
        r += (int64_t)gridDim.x * blockDim.x) {
     float o[3], d[3];
     load_ray(ro, rd, r, o, d);
+    const float h_in = cmarch_step_len(A, d);
     float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(A.s.near, d[a]));
@@ -387,7 +399,8 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
         rec[4 * c + 2] = __float_as_uint(x[2]);
       }
       float xc[3], j[3];
-      if (!cmarch_point(M, x, d, xc, j)) break;
+      bool inside;
+      if (!cmarch_point(M, x, d, xc, j, inside)) break;
       if (keep_point(A, mask, xc)) {
         if (kWrite) {
           int64_t s = pos + cnt;
@@ -401,7 +414,7 @@ __global__ void contracted_kernel(SamplerArgs A, const float* __restrict__ ro,
         }
         ++cnt;
       }
-      if (!cmarch_advance(A, x, d, j)) break;
+      if (!cmarch_advance(A, x, d, j, inside, h_in)) break;
     }
     if (!kWrite) {
       counts[r] = cnt;
@@ -442,6 +455,7 @@ __global__ void __launch_bounds__(32 * kCkpt) contracted_fill_kernel(
   float d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) d[a] = __ldg(rd + 3 * r + a);
+  const float h_in = cmarch_step_len(A, d);
   float x[3] = {__uint_as_float(rec[0]), __uint_as_float(rec[1]), __uint_as_float(rec[2])};
   int64_t s = ray_off[r] + before;
   const bool vec = ((reinterpret_cast<uintptr_t>(xyz) | reinterpret_cast<uintptr_t>(ray_id) |
@@ -449,8 +463,8 @@ __global__ void __launch_bounds__(32 * kCkpt) contracted_fill_kernel(
                      reinterpret_cast<uintptr_t>(s_len)) & 15u) == 0;
   // samples are written in groups of four consecutive list positions (16-byte
   // stores; xyz as three), one at a time before the first aligned position
-  float bx[4][3];
-  int bk[4];
+  float bx[4][3] = {};
+  int bk[4] = {};
   int nb = 0;
   auto put1 = [&](const float* p, int k) {
     xyz[3 * s] = p[0];
@@ -478,7 +492,8 @@ __global__ void __launch_bounds__(32 * kCkpt) contracted_fill_kernel(
   const int k_end = min((c + 1) * L, A.s.max_steps);
   for (int k = c * L; k < k_end; ++k) {
     float xc[3], j[3];
-    if (!cmarch_point(M, x, d, xc, j)) break;
+    bool inside;
+    if (!cmarch_point(M, x, d, xc, j, inside)) break;
     if (keep_point(A, mask, xc)) {
       if (!vec || ((s & 3) != 0 && nb == 0)) {
         put1(xc, k);
@@ -497,7 +512,7 @@ __global__ void __launch_bounds__(32 * kCkpt) contracted_fill_kernel(
         }
       }
     }
-    if (!cmarch_advance(A, x, d, j)) break;
+    if (!cmarch_advance(A, x, d, j, inside, h_in)) break;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
