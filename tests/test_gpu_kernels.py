@@ -1225,3 +1225,69 @@ def test_live_samples_cull(L):
     culled = live & ~keep
     assert np.all(host(rgb)[culled] == 0) and np.all(host(gk)[culled] == 0)
     assert np.all(host(rgb)[~culled] == 5.0) and np.all(host(gk)[~culled] == 5.0)
+
+
+# --------------------------------------------------------- zero-size calls
+def test_zero_size_calls(L):
+    """Every entry point over samples or rays accepts an empty batch (n_cap =
+    0, R = 0, a device count of 0): it returns DVGO_OK, launches no work that
+    faults, and leaves its outputs as they were, except the CSR offsets and
+    counts that an empty batch defines (ray_off = [0], counts 0)."""
+    f = lambda *s: torch.full(s or (4,), 7.0, device="cuda")                       # noqa: E731
+    i32 = lambda *s: torch.full(s or (4,), 7, dtype=torch.int32, device="cuda")     # noqa: E731
+    i64 = lambda *s: torch.full(s or (4,), 7, dtype=torch.int64, device="cuda")     # noqa: E731
+    G = (16, 16, 16)
+    gd = L.GridDesc.make((-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), G)
+    grid = torch.zeros(L.grid_bricked_elems(G, 12), device="cuda")
+    touched = torch.zeros(L.grid_num_bricks(G), dtype=torch.uint8, device="cuda")
+    params = dev(synth.mlp_params())
+    zero_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # samples: n_cap = 0, and n_cap > 0 with a device count of 0
+    for n_cap, n_dev in ((0, None), (5, zero_dev)):
+        out = f(5, 12)
+        L.sample_grid_fwd(grid, L.F32, gd, 12, f(5, 3), None, n_cap, n_dev, out)
+        assert torch.all(out == 7.0)
+        gg = torch.zeros_like(grid)
+        L.sample_grid_bwd(f(5, 12), gd, 12, f(5, 3), None, n_cap, n_dev, gg, touched)
+        L.sample_grid_bwd2(f(5), 1, torch.zeros(L.grid_bricked_elems(G, 1), device="cuda"), touched,
+                           f(5, 12), 12, gg, touched, gd, f(5, 3), None, n_cap, n_dev)
+        assert not torch.any(gg) and not torch.any(touched)
+        for prec in (L.F32, L.F32_TC, L.BF16):
+            rgb = f(5, 3)
+            act = torch.empty(max(L.rgbnet_act_bytes(5, prec), 16), dtype=torch.uint8, device="cuda")
+            if prec == L.F32:
+                act = torch.empty(5, 256, device="cuda")
+            L.rgbnet_fwd(f(5, 12), f(2, 3), i32(5), None, n_cap, n_dev, params, prec, rgb, act)
+            assert torch.all(rgb == 7.0)
+            gp = torch.zeros_like(params)
+            gk = f(5, 12)
+            L.rgbnet_bwd(f(5, 3), None, None, f(5, 12), f(2, 3), i32(5), None, n_cap, n_dev, params,
+                         prec, gp, gk, act, rgb)
+            assert not torch.any(gp)
+        logits = f(5)
+        L.proposal_fwd(f(5, 3), None, n_cap, n_dev, dev(synth.proposal_params()), logits)
+        assert torch.all(logits == 7.0)
+    # rays: R = 0
+    ray_off = i64(1)
+    sd = L.SamplerDesc()
+    sd.mode, sd.near, sd.far, sd.step, sd.max_steps = 0, 0.0, 4.0, 0.1, 64
+    ws = torch.empty(max(L.sample_rays_workspace_size(0), 16), dtype=torch.uint8, device="cuda")
+    L.sample_rays(f(1, 3), f(1, 3), 0, gd, sd, None, 0, ray_off, f(1, 3), i32(1), i32(1), f(1), f(1), ws)
+    assert ray_off.tolist() == [0]
+    live_idx, live_count = i32(1), i64(1)
+    wsl = torch.empty(max(L.live_samples_workspace_size(0), 16), dtype=torch.uint8, device="cuda")
+    L.live_samples(torch.zeros(1, dtype=torch.int64, device="cuda"), i32(1), 0, live_idx, live_count, wsl)
+    assert int(live_count.item()) == 0
+    color, L_r, n_live, T_end = f(1, 3), f(1), i32(1), f(1)
+    off0 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L.alpha_weights_fwd(f(1), off0, 0, 0.0, 0.5, 1e-3, f(1), f(1), n_live, T_end)
+    L.density_alpha_fwd(torch.zeros(L.grid_bricked_elems(G, 1), device="cuda"), L.F32, gd, f(1, 3), off0,
+                        0, 0.0, 0.5, 1e-3, f(1), f(1), f(1), n_live, T_end)
+    L.composite_rgb_fwd(f(1), f(1, 3), off0, n_live, T_end, 0, (0.0, 0.0, 0.0), color)
+    L.composite_distortion_fwd(f(1), f(1, 3), f(1), f(1), off0, n_live, T_end, 0, (0.0, 0.0, 0.0),
+                               color, L_r)
+    L.distortion_fwd(f(1), f(1), f(1), off0, None, 0, L_r)
+    L.distortion_bwd(f(1), 1.0, f(1), f(1), f(1), off0, None, 0, f(1))
+    L.composite_bwd(f(1, 3), None, f(1), f(1), f(1, 3), off0, n_live, 0, 0.0, 0.5, (0.0, 0.0, 0.0), f(1))
+    assert torch.all(color == 7.0) and torch.all(L_r == 7.0)
+    assert L.device_status() == 0
