@@ -517,8 +517,8 @@ __device__ __forceinline__ float load_val(const void* grid, int64_t e) {
 
 // The six neighbour slots of voxel (x, y, z) = local Morton index t of brick
 // b, in the order -x, +x, -y, +y, -z, +z, as offsets from the voxel's own
-// slot (0 where the grid ends; has[d] says which exist; a brick layer of
-// nb[0] nb[1] 512 voxels fits an int32 for every grid the library accepts).  Inside the brick a step along axis a changes only a's
+// slot (0 where the grid ends; has[d] says which exist; the host checks
+// that a layer of nb[0] nb[1] bricks of 512 voxels fits an int32).  Inside the brick a step along axis a changes only a's
 // interleaved bits (mask M): +1 is ((t | ~M) + 1) & M, -1 is ((t & M) - 1) & M,
 // with t's other bits kept; at the brick face the neighbour is voxel 0 / 7 of
 // the next / previous brick along a.
@@ -1093,6 +1093,8 @@ extern "C" int dvgo_tv_add_grad_multi(const dvgo_tv_grid* grids, int32_t count, 
   DVGO_CHECK_ARG(grids && count >= 1 && count <= kMaxMulti && G && delta > 0.0f);
   DVGO_CHECK_ARG(G[0] >= 1 && G[1] >= 1 && G[2] >= 1);
   BrickGeom g = make_geom(G);
+  // neighbour offsets are int32: one layer of bricks must fit
+  DVGO_CHECK_ARG((int64_t)g.nb[0] * g.nb[1] * kBrickVox <= (int64_t)INT32_MAX / 2);
   const double N = (double)G[0] * G[1] * G[2];
   TvMulti M{};
   M.count = count;

@@ -78,3 +78,16 @@ def test_host_validation_without_gpu(lib):
     assert lib.dvgo_rgbnet_act_bytes(-1, 0) == -1
     assert lib.dvgo_rgbnet_act_bytes(5, 7) == -1
     assert lib.dvgo_status_string(-8) == b"value outside the range of a split-FP16 operand"
+
+
+def test_tv_rejects_a_grid_too_large_for_its_offsets(lib):
+    """The TV kernel forms neighbour slots as int32 offsets: a grid whose layer
+    of bricks does not fit is refused on the host, before any launch."""
+    from paper_2206_05085_gb300 import _lib
+    lib.dvgo_tv_add_grad_multi.restype = ctypes.c_int
+    lib.dvgo_tv_add_grad_multi.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]
+    one = _lib.TvGrid(16, 0, 1, 1.0, None, 16)
+    G = (ctypes.c_int32 * 3)(20000, 20000, 8)
+    assert lib.dvgo_tv_add_grad_multi(ctypes.byref(one), 1, G, 1.0, 1, None, None, None) == -1
