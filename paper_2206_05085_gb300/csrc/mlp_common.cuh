@@ -129,36 +129,8 @@ __device__ __forceinline__ void upstream_rgb_grad(const float* __restrict__ g_rg
   }
 }
 
-// Butterfly reduce-scatter: lane l returns sum over the warp of v[l].
-// reduce_scatter32 of v[0..31] (times a when kScale) that leaves v unchanged:
-// the first exchange reads v (and multiplies as it goes) into 16 partial sums.
-template <bool kScale>
-__device__ __forceinline__ float reduce_scatter32_keep(const float (&v)[32], float a, int lane) {
-  float w[16];
-  const bool up = (lane & 16) != 0;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    float send = up ? v[j] : v[j + 16];
-    float keep = up ? v[j + 16] : v[j];
-    if (kScale) {
-      send *= a;
-      keep *= a;
-    }
-    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int h = 8; h >= 1; h >>= 1) {
-    const bool u = (lane & h) != 0;
-#pragma unroll
-    for (int j = 0; j < h; ++j) {
-      const float send = u ? w[j] : w[j + h];
-      const float keep = u ? w[j + h] : w[j];
-      w[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-    }
-  }
-  return w[0];
-}
-
+// Butterfly reduce-scatter: lane l returns sum over the warp of v[l] (v is
+// overwritten).
 __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
 #pragma unroll
   for (int h = 16; h >= 1; h >>= 1) {
