@@ -423,7 +423,11 @@ MMA_CEILING = {("f32tc", "fwd"): 1 / 3, ("f32tc", "bwd"): 1 / 3, ("bf16", "fwd")
                ("bf16", "bwd"): (2 * 16384 + 5120 + 1536) / (5 * 16384 + 3 * 5120 + 2 * 1536)}
 # kernels launched per C-ABI call (others launch one); the tensor-core MLP
 # backward runs the backward and the partial-gradient reduction
-KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1}
+# kernels each C-ABI call launches (the rest launch one): sampling counts,
+# scans and fills; the live list scans and fills; the device-side Adam step
+# advances its step count, then updates
+KERNELS_PER_CALL = {"dvgo_sample_rays": 3, "dvgo_live_samples": 2, "dvgo_touched_compact": 1,
+                    "dvgo_adam_step_multi_dev": 2}
 
 
 def roofline(res, peaks, mk=None):
