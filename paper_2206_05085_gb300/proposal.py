@@ -21,7 +21,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .synth import PROPOSAL_DIMS, RenderParams, SceneConfig, mlp_num_params, voxel_size
+from .synth import PROPOSAL_DIMS, RenderParams, SceneConfig, grid_dims, mlp_num_params, voxel_size
 from .train import Trainer, alpha_shift
 
 N_CAND = 512
@@ -54,7 +54,7 @@ class Proposal:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.it = 0
-        self.gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, [cfg.grid] * 3)
+        self.gd = L.GridDesc.make(cfg.bbox_min, cfg.bbox_max, list(grid_dims(cfg)))
         sd = L.SamplerDesc()
         sd.mode, sd.near, sd.far, sd.step = 0, self.rp.near, self.rp.far, self.rp.step
         sd.step_offset, sd.use_slab, sd.max_steps = self.rp.step_offset, 1, N_CAND

@@ -23,8 +23,8 @@ def sample(cfg, rp, o, d, mask):
     if rp.contracted:
         return oracle.sample_rays_contracted(o, d, rp.contract_b, rp.contract_p_inf, rp.near,
                                              rp.step_c, rp.max_steps, cfg.bbox_min, cfg.bbox_max,
-                                             cfg.grid, mask)
-    return oracle.sample_rays_bbox(o, d, cfg.bbox_min, cfg.bbox_max, cfg.grid, rp.near, rp.far,
+                                             synth.grid_dims(cfg), mask)
+    return oracle.sample_rays_bbox(o, d, cfg.bbox_min, cfg.bbox_max, synth.grid_dims(cfg), rp.near, rp.far,
                                    rp.step, rp.step_offset, rp.use_slab, rp.max_steps, mask)
 
 

@@ -83,6 +83,17 @@ def test_step_fp32_tensor_core_mlp(T, cfg_name):
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
 
 
+@pytest.mark.parametrize("precision,tv_dense,tol", [("f32tc", False, 1e-5), ("f32", True, 1e-5)])
+def test_step_ragged_grid(T, precision, tv_dense, tol):
+    """A grid whose sides are no multiple of the 8-voxel brick (61 x 47 x 53
+    points): padded bricks in the queries, the adjoints, the touched list,
+    TV and Adam, and a non-cubic occupancy mask, against the oracle."""
+    cfg = dataclasses.replace(synth.CFG1, name="small_ragged", grid=61, dims=(61, 47, 53))
+    gpu, fb, opt, cfg, rp, P = _run(T, cfg, 1024, precision, tv_dense=tv_dense, ray_stride=2)
+    assert fb["live"].sum() > 5000
+    _compare(gpu, fb, opt, tol, cfg, rp, P)
+
+
 def test_step_dvgo160_fp32_dense_tv(T):
     gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
