@@ -265,8 +265,8 @@ def grid_resample(grid, G_dst):
 
 def trilinear_adjoint(g_out, grid_shape, lo, hi, xyz):
     """Returns the dense f64 gradient of the grid (shape grid_shape)."""
-    g_out = _f64(g_out).reshape(xyz.shape[0], -1)
-    C = g_out.shape[1]
+    C = 1 if len(grid_shape) == 3 else int(grid_shape[3])
+    g_out = _f64(g_out).reshape(xyz.shape[0], C)
     Gz, Gy, Gx = grid_shape[:3]
     G = _vec3i((Gx, Gy, Gz))
     xyz = _f32(xyz).reshape(-1, 3)

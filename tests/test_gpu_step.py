@@ -94,6 +94,31 @@ def test_step_ragged_grid(T, precision, tv_dense, tol):
     _compare(gpu, fb, opt, tol, cfg, rp, P)
 
 
+def test_step_empty_sample_list(T):
+    """Degenerate batch: a density so low that the occupancy mask is empty and
+    no ray has a sample.  The colour is the background and the loss the
+    oracle's, every gradient is zero and the optimizer leaves every parameter
+    as it was."""
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    assert rp.mask_thres is not None
+    D = np.full(synth.density_grid(cfg).shape, -100.0, np.float32)
+    Fg, P = synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg)
+    tgt = synth.target_rgb(cfg)
+    o, d, tgt = o[:256], d[:256], tgt[:256]
+    gpu = gpu_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False)
+    fb, opt, _ = oracle_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False)
+    assert gpu["S"] == 0 == fb["smp"].S
+    assert gpu["device_status"] == 0
+    assert np.all(gpu["n_live"] == 0)
+    assert rel_err(gpu["color"], fb["color"]) < 1e-6
+    assert rel_err(gpu["loss"], fb["loss"]) < 1e-6
+    assert not np.any(gpu["g_mlp"]) and not np.any(gpu["g_density"]) and not np.any(gpu["g_feature"])
+    assert np.array_equal(gpu["density"], D) and np.array_equal(gpu["feature"], Fg)
+    assert np.array_equal(gpu["params"], P)
+
+
 def test_step_dvgo160_fp32_dense_tv(T):
     gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
