@@ -119,6 +119,24 @@ def test_step_empty_sample_list(T):
     assert np.array_equal(gpu["params"], P)
 
 
+def test_step_opaque_scene(T):
+    """Degenerate batch: a density so high that every ray halts after its
+    first sample (alpha = 1 in FP32), so that the live list holds one sample
+    per non-empty ray: the whole step against the oracle."""
+    cfg = synth.CFG2
+    rp = synth.render_params(cfg)
+    D = np.full(synth.density_grid(cfg).shape, 50.0, np.float32)
+    Fg, P = synth.feature_grid(cfg), synth.mlp_params()
+    o, d = synth.rays(cfg)
+    tgt = synth.target_rgb(cfg)
+    o, d, tgt = o[::16][:512], d[::16][:512], tgt[::16][:512]
+    gpu = gpu_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False)
+    fb, opt, Pr = oracle_step(cfg, rp, D, Fg, P, o, d, tgt, "f32tc", False)
+    counts = np.diff(fb["smp"].ray_off)
+    assert np.array_equal(fb["n_live"], np.minimum(counts, 1)) and counts.max() > 10
+    _compare(gpu, fb, opt, 1e-5, cfg, rp, Pr)
+
+
 def test_step_dvgo160_fp32_dense_tv(T):
     gpu, fb, opt, cfg, rp, P = _run(T, synth.CFG2, 256, "f32", tv_dense=True, ray_stride=32)
     _compare(gpu, fb, opt, 1e-5, cfg, rp, P)
