@@ -407,6 +407,27 @@ def test_contracted_march_chunks(L, max_steps):
         assert (last < max_steps - 1).sum() > 10
 
 
+@pytest.mark.parametrize("b", [1.0, 0.5])
+def test_contracted_march_euclidean(L, b):
+    """The contraction with the Euclidean norm (p = 2; the workloads use the
+    max norm) and two contraction parameters b: the march's samples bit-exact
+    against the oracle's sequential march, with occupancy culling, on rays
+    from inside and outside the unit ball."""
+    import dataclasses
+    cfg = synth.CFG3
+    rp = dataclasses.replace(synth.render_params(cfg), contract_p_inf=False, contract_b=b, max_steps=300)
+    o, d = synth.rays(cfg, n_rays=300)
+    o = o.copy()
+    o[::3] *= np.float32(1.6)
+    D = synth.density_grid(cfg)
+    mask_np = oracle.build_mask(D, shift32(), rp.interval, 1e-4)
+    got = _gpu_sample(L, cfg, rp, o, d, dev(mask_np))
+    from oracle_step import sample
+    ref = sample(cfg, rp, o, d, mask_np)
+    assert ref.S > 1000
+    _check_samples(got, ref)
+
+
 def test_sampler_edge_cases(L):
     cfg = synth.CFG2
     rp = synth.render_params(cfg)
