@@ -338,10 +338,20 @@ def _forward_facing_small():
     return dataclasses.replace(synth.CFG6, name="forward_facing_96", grid=96, dims=(96, 96, 64))
 
 
-@pytest.mark.parametrize("name", ["small_64", "dvgo_160", "unbounded_320", "forward_facing_96"])
+@pytest.mark.parametrize("name", ["small_64", "dvgo_160", "unbounded_320", "forward_facing_96",
+                                  "forward_facing_96_wide"])
 def test_sampler_bit_exact(L, name):
-    cfg = _forward_facing_small() if name == "forward_facing_96" else synth.CONFIGS[name]
+    import dataclasses
+    if name.startswith("forward_facing_96"):
+        cfg = _forward_facing_small()
+        if name.endswith("wide"):   # a 400 x 240 image at focal 300: fx != fy
+            cfg = dataclasses.replace(cfg, name=name, img_w=400, img_h=240, focal=300.0)
+    else:
+        cfg = synth.CONFIGS[name]
     rp = synth.render_params(cfg)
+    if name.endswith("wide"):
+        rp = dataclasses.replace(rp, ndc_near=0.5)
+        assert rp.ndc_fx != rp.ndc_fy
     o, d = synth.rays(cfg)            # full ray count of the workload
     mask_np = mask_t = None
     if rp.mask_thres is not None:
