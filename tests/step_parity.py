@@ -42,7 +42,7 @@ def gpu_step(cfg, rp, D, Fg, P, o, d, tgt, precision, tv_dense, w_min=None):
 def _gpu_outputs(tr, tv_dense):
     S = int(_host(tr.ray_off)[-1])
     gpu = dict(loss=_host(tr.loss), color=_host(tr.color), L_r=_host(tr.L_r), n_live=_host(tr.n_live),
-               S=S, w=_host(tr.w[:S]), rgb=_host(tr.rgb[:S]), g_raw=_host(tr.g_raw[:S]),
+               S=S, ray_off=tr.ray_off.cpu().numpy(), w=_host(tr.w[:S]), rgb=_host(tr.rgb[:S]), g_raw=_host(tr.g_raw[:S]),
                g_k0=_host(tr.g_k0[:S]), g_mlp=_host(tr.mlp_g),
                g_density=_host(tr.dense(tr.density, "g"))[..., 0],
                g_feature=_host(tr.dense(tr.feature, "g")))

@@ -212,6 +212,49 @@ def test_step_learned_proposal(T, precision, tol):
     _compare(gpu, fb, opt, tol, cfg, rp_p, Pr, bf16=precision == "bf16")
 
 
+def test_full_size_learned_proposal(T):
+    """The learned-proposal form at the benchmark's size (16384 rays of the
+    dvgo_160 scene, <= 512 candidates per ray): for 48 sampled rays the picks
+    equal the oracle's (except where a CDF value sits within the network's
+    rounding of a quantile), and on the rays whose picks agree the spans,
+    the colour and loss terms, and the per-sample weights, colours and raw
+    gradients (rescaled from 1/48 to the batch's 1/R) match the oracle's."""
+    cfg = synth.CFG5
+    rp = synth.render_params(cfg)
+    D, Fg, P = synth.density_grid(cfg), synth.feature_grid(cfg), synth.mlp_params()
+    PP = (synth.proposal_params() * 3.0).astype(np.float32)
+    o, d = synth.rays(cfg)
+    tgt = synth.target_rgb(cfg)
+    R = len(o)
+    args = (cfg, rp, D, Fg, P, PP)
+    gpu = gpu_proposal_step(*args, o, d, tgt, "f32tc", False)
+    rays = np.sort(np.random.default_rng(9).choice(R, 48, replace=False))
+    fb, _, _, sel, n_sel = oracle_proposal_step(*args, o[rays], d[rays], tgt[rays], "f32tc", False)
+    agree = np.array([n_sel[i] == gpu["n_sel"][r] and
+                      np.array_equal(sel[i, :n_sel[i]], gpu["sel"][r, :n_sel[i]])
+                      for i, r in enumerate(rays)])
+    assert agree.mean() > 0.9 and n_sel.mean() > 20
+    scale = len(rays) / R
+    off_g, off_o = gpu["ray_off"], fb["smp"].ray_off
+    g_rows, o_rows = [], []
+    for i in np.nonzero(agree)[0]:
+        r = rays[i]
+        assert off_g[r + 1] - off_g[r] == off_o[i + 1] - off_o[i]
+        assert gpu["n_live"][r] == fb["n_live"][i]
+        g_rows.append(np.arange(off_g[r], off_g[r + 1]))
+        o_rows.append(np.arange(off_o[i], off_o[i + 1]))
+    g_rows, o_rows = np.concatenate(g_rows), np.concatenate(o_rows)
+    live = fb["live"][o_rows]
+    assert live.sum() > 500
+    assert rel_err(gpu["delta"][g_rows], fb["delta"][o_rows]) < 1e-6
+    assert rel_err(gpu["w"][g_rows], fb["w"][o_rows]) < 1e-5
+    assert rel_err(gpu["rgb"][g_rows][live], fb["rgb"][o_rows][live]) < 1e-5
+    assert rel_err(gpu["g_raw"][g_rows][live], fb["g_raw"][o_rows][live] * scale) < 1e-5
+    a = rays[agree]
+    assert rel_err(gpu["color"][a], fb["color"][agree]) < 1e-5
+    assert rel_err(gpu["L_r"][a], fb["L_r"][agree]) < 1e-5
+
+
 def test_step_forward_facing_ndc(T):
     """Forward-facing capture: NDC warp and depth-layer sampling (96 x 96 x 64
     layers standing in for 384^2 x 256), the full step against the oracle."""
